@@ -1,0 +1,266 @@
+"""ctypes wrapper of the CPU oracle (test infrastructure only).
+
+The oracle is a plain, serial FP64 restatement of the paper's GRMHD substep.
+Only the tests, the smoke check and the benchmark's CPU-baseline leg use it;
+the product (the CUDA library and its binding) never imports this package.
+Arrays are numpy float64, C-contiguous, field-major (nf, n2+6, n1+6, px).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NF, NST, NP = 32, 22, 10
+NID = 26
+
+_P_DOUBLES = ["kappa_z", "kappa_c", "kappa_2", "eta", "sigma_ko", "c_b", "kappa_b", "gamma_th", "K_atmo",
+              "rho_atmo", "rho_min", "rho_low", "rho_max", "alpha_bh", "W_max", "eps_max", "ye_min", "ye_max",
+              "ye_atmo", "T_atmo", "h0", "c2p_xtol"]
+_P_INTS = ["eos_kind", "bc", "max_iter", "pad_"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS]
+
+
+class EosTable(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("nt", ctypes.c_int), ("ny", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("lr0", ctypes.c_double), ("dlr", ctypes.c_double), ("lt0", ctypes.c_double),
+                ("dlt", ctypes.c_double), ("ye0", ctypes.c_double), ("dye", ctypes.c_double),
+                ("p", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("cs2", ctypes.c_void_p)]
+
+
+def make_params(d):
+    p = Params()
+    for n in _P_DOUBLES:
+        setattr(p, n, float(d.get(n, 0.0)))
+    for n in _P_INTS:
+        setattr(p, n, int(d.get(n, 0)))
+    return p
+
+
+class _Table:
+    """Keeps the numpy node arrays alive while the C struct points at them."""
+
+    def __init__(self, t):
+        self.arrays = [np.ascontiguousarray(t[k], dtype=np.float64) for k in ("p", "eps", "cs2")]
+        self.s = EosTable(t["nr"], t["nt"], t["ny"], 0, t["lr0"], t["dlr"], t["lt0"], t["dlt"], t["ye0"], t["dye"],
+                          *[a.ctypes.data for a in self.arrays])
+
+
+def make_table(t):
+    return None if t is None else _Table(t)
+
+
+_libs = {}
+
+
+def lib(flops=False):
+    name = "liboracle_flops.so" if flops else "liboracle.so"
+    if name not in _libs:
+        _build.build()
+        L = ctypes.CDLL(os.path.join(os.path.dirname(os.path.abspath(__file__)), name))
+        d, i, l, vp = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
+        sig = {
+            "oracle_flop_counter": (ctypes.c_longlong, [i]),
+            "oracle_ghost_fill": (i, [vp, vp, i, vp, i]),
+            "oracle_init_state": (i, [vp, vp, vp, i, d, vp, vp]),
+            "oracle_con2prim_patch": (i, [vp, vp, vp, i, vp, vp, vp, vp]),
+            "oracle_rhs_patch": (i, [vp, vp, i, d, vp, vp, vp]),
+            "oracle_rhs_points": (i, [vp, vp, i, d, vp, vp, i, vp, vp]),
+            "oracle_geom_point": (i, [vp, vp, i, d, vp, vp, i, i, i, vp, vp, vp, vp]),
+            "oracle_substep": (i, [vp, vp, vp, i, d, i, d, vp, vp, vp, vp, vp, vp]),
+            "oracle_rk4_step": (i, [vp, vp, vp, i, d, d, vp, vp, vp, vp, vp, vp]),
+            "oracle_c2p_point": (i, [vp, vp, vp, vp, d, d, vp, vp, vp]),
+            "oracle_c2p_flat": (i, [vp, vp, l, vp, vp, vp, vp]),
+            "oracle_prim2con_point": (i, [vp, vp, vp, vp]),
+            "oracle_eos_from_eps": (i, [vp, vp, d, d, d, vp]),
+            "oracle_eos_from_T": (i, [vp, vp, d, d, d, vp]),
+            "oracle_fd_d1": (d, [vp, d]),
+            "oracle_fd_d2": (d, [vp, d]),
+            "oracle_fd_d11": (d, [vp, l, d]),
+            "oracle_fd_up": (d, [vp, d, d]),
+            "oracle_fd_ko": (d, [vp, d, d]),
+            "oracle_mp5": (d, [vp]),
+            "oracle_minmod4": (d, [d, d, d, d]),
+            "oracle_fast_speeds": (i, [d, d, d, d, d, d, vp, vp]),
+            "oracle_flux_point": (i, [vp, vp, vp, i, vp, vp]),
+            "oracle_matter_point": (i, [vp, vp, vp, vp, vp]),
+        }
+        for fn, (res, args) in sig.items():
+            f = getattr(L, fn)
+            f.restype = res
+            f.argtypes = args
+        _libs[name] = L
+    return _libs[name]
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+def _ref(x):
+    return ctypes.byref(x) if x is not None else None
+
+
+def _chk(a, dtype=np.float64):
+    assert a.dtype == dtype and a.flags["C_CONTIGUOUS"]
+    return a
+
+
+def _n3(n):
+    return (ctypes.c_int * 3)(*[int(v) for v in n])
+
+
+class Oracle:
+    """Oracle bound to one parameter set (and optional EOS table)."""
+
+    def __init__(self, params, table=None, flops=False):
+        self.L = lib(flops)
+        self.P = make_params(params)
+        self.T = make_table(table)
+        self.Tp = _ref(self.T.s) if self.T is not None else None
+
+    # ---- patch operations --------------------------------------------------
+    def ghost_fill(self, U, n):
+        _chk(U)
+        self.L.oracle_ghost_fill(_ref(self.P), _n3(n), U.shape[-1], _p(U), U.shape[0])
+
+    def init_state(self, ID, n, dx):
+        _chk(ID)
+        U = np.zeros((NF,) + ID.shape[1:])
+        self.L.oracle_init_state(_ref(self.P), self.Tp, _n3(n), ID.shape[-1], dx, _p(ID), _p(U))
+        return U
+
+    def con2prim_patch(self, U, n):
+        _chk(U)
+        prim = np.zeros((NP,) + U.shape[1:])
+        status = np.zeros(U.shape[1:], dtype=np.int8)
+        its = ctypes.c_long(0)
+        worst = self.L.oracle_con2prim_patch(_ref(self.P), self.Tp, _n3(n), U.shape[-1], _p(U), _p(prim),
+                                             _p(status), ctypes.byref(its))
+        return prim, status, worst, its.value
+
+    def rhs_patch(self, U, prim, n, dx):
+        rhs = np.zeros_like(U)
+        self.L.oracle_rhs_patch(_ref(self.P), _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)), _p(rhs))
+        return rhs
+
+    def rhs_points(self, U, prim, n, dx, ijk):
+        ijk = np.ascontiguousarray(ijk, dtype=np.int32)
+        out = np.zeros((ijk.shape[0], NF))
+        self.L.oracle_rhs_points(_ref(self.P), _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)),
+                                 ijk.shape[0], _p(ijk), _p(out))
+        return out
+
+    def geom_point(self, U, prim, n, dx, i, j, k):
+        R = np.zeros(6)
+        Rtr = np.zeros(1)
+        Gt = np.zeros(3)
+        Z = np.zeros(3)
+        self.L.oracle_geom_point(_ref(self.P), _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)), i, j, k,
+                                 _p(R), _p(Rtr), _p(Gt), _p(Z))
+        return R, Rtr[0], Gt, Z
+
+    def substep(self, regs, prim, status, n, dx, stage, dt):
+        Un, Ua, Ub, acc = regs
+        return self.L.oracle_substep(_ref(self.P), self.Tp, _n3(n), Un.shape[-1], dx, stage, dt, _p(Un), _p(Ua),
+                                     _p(Ub), _p(acc), _p(prim), _p(status))
+
+    def rk4_step(self, regs, prim, status, n, dx, dt):
+        Un, Ua, Ub, acc = regs
+        return self.L.oracle_rk4_step(_ref(self.P), self.Tp, _n3(n), Un.shape[-1], dx, dt, _p(Un), _p(Ua),
+                                      _p(Ub), _p(acc), _p(prim), _p(status))
+
+    # ---- pointwise ---------------------------------------------------------
+    def c2p_point(self, cons_bar, gt, chi, alpha):
+        cb = np.ascontiguousarray(cons_bar, dtype=np.float64)
+        g = np.ascontiguousarray(gt, dtype=np.float64)
+        prim = np.zeros(NP)
+        co = np.zeros(10)
+        it = ctypes.c_int(0)
+        st = self.L.oracle_c2p_point(_ref(self.P), self.Tp, _p(cb), _p(g), chi, alpha, _p(prim), _p(co),
+                                     ctypes.byref(it))
+        return st, prim, co, it.value
+
+    def c2p_flat(self, cons):
+        cons = np.ascontiguousarray(cons, dtype=np.float64)
+        n = cons.shape[0]
+        prim = np.zeros((n, NP))
+        status = np.zeros(n, dtype=np.int8)
+        iters = np.zeros(n, dtype=np.int32)
+        self.L.oracle_c2p_flat(_ref(self.P), self.Tp, n, _p(cons), _p(prim), _p(status), _p(iters))
+        return prim, status, iters
+
+    def eos_from_eps(self, rho, eps, ye):
+        out = np.zeros(4)
+        self.L.oracle_eos_from_eps(_ref(self.P), self.Tp, rho, eps, ye, _p(out))
+        return out  # p, eps, T, cs2
+
+    def eos_from_T(self, rho, T, ye):
+        out = np.zeros(4)
+        self.L.oracle_eos_from_T(_ref(self.P), self.Tp, rho, T, ye, _p(out))
+        return out
+
+    def flux_point(self, U32, prim, d):
+        U32 = np.ascontiguousarray(U32, dtype=np.float64)
+        prim = np.ascontiguousarray(prim, dtype=np.float64)
+        F = np.zeros(10)
+        lam = np.zeros(1)
+        self.L.oracle_flux_point(_ref(self.P), _p(U32), _p(prim), d, _p(F), _p(lam))
+        return F, lam[0]
+
+    def flops(self, reset=True):
+        return self.L.oracle_flop_counter(1 if reset else 0)
+
+
+def prim2con_point(prim, B, gdd):
+    pr = np.ascontiguousarray(prim, dtype=np.float64)
+    b = np.ascontiguousarray(B, dtype=np.float64)
+    g = np.ascontiguousarray(gdd, dtype=np.float64)
+    out = np.zeros(9)
+    lib().oracle_prim2con_point(_p(pr), _p(b), _p(g), _p(out))
+    return out
+
+
+def matter_point(U32, prim):
+    U32 = np.ascontiguousarray(U32, dtype=np.float64)
+    prim = np.ascontiguousarray(prim, dtype=np.float64)
+    E = np.zeros(1)
+    S = np.zeros(3)
+    Sij = np.zeros(6)
+    lib().oracle_matter_point(_p(U32), _p(prim), _p(E), _p(S), _p(Sij))
+    return E[0], S, Sij
+
+
+def fast_speeds(alpha, betad, gudd, vd, v2, a2):
+    lp, lm = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_fast_speeds(alpha, betad, gudd, vd, v2, a2, ctypes.byref(lp), ctypes.byref(lm))
+    return lp.value, lm.value
+
+
+def fd(kind, u, *args):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    f = getattr(lib(), "oracle_fd_" + kind)
+    c = u.size // 2
+    ptr = u.ctypes.data + 8 * c
+    return f(ptr, *args)
+
+
+def fd_d11(u2d, dx):
+    """D_y(D_x u) at the centre of a 5x5 (or larger, odd) 2-D array u[y, x]."""
+    u = np.ascontiguousarray(u2d, dtype=np.float64)
+    cy, cx = u.shape[0] // 2, u.shape[1] // 2
+    ptr = u.ctypes.data + 8 * (cy * u.shape[1] + cx)
+    return lib().oracle_fd_d11(ptr, u.shape[1], dx)
+
+
+def mp5(f5):
+    f = np.ascontiguousarray(f5, dtype=np.float64)
+    return lib().oracle_mp5(_p(f))
+
+
+def minmod4(a, b, c, d):
+    return lib().oracle_minmod4(a, b, c, d)

@@ -1,0 +1,197 @@
+// C entry points of the oracle, loaded through ctypes by oracle/__init__.py.
+// Host pointers only.  Patch arrays are field-major [field][z][y][x] with
+// ghosted extents (n0 + 6 padded to px, n1 + 6, n2 + 6).
+#include <cstring>
+#include <vector>
+#include "oracle.hpp"
+
+grid make_grid(const int n[3], int px, double dx);
+void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf);
+void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* ID, double* U);
+int c2p_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, double* U, double* prim,
+              int8_t* status, long* iters_total);
+void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs);
+int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, int stage, double dt, double* Un,
+            double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs);
+
+#ifdef ORACLE_COUNT_FLOPS
+long long oracle_flops = 0;
+#endif
+
+extern "C" {
+
+long long oracle_flop_counter(int reset) {
+#ifdef ORACLE_COUNT_FLOPS
+  long long v = oracle_flops;
+  if (reset) oracle_flops = 0;
+  return v;
+#else
+  (void)reset;
+  return -1;
+#endif
+}
+
+int oracle_ghost_fill(const oracle_params* P, const int* n, int px, double* U, int nf) {
+  ghost_fill(P, make_grid(n, px, 1.0), U, nf);
+  return 0;
+}
+
+int oracle_init_state(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx,
+                      const double* ID, double* U) {
+  init_state(P, E, make_grid(n, px, dx), ID, U);
+  return 0;
+}
+
+int oracle_con2prim_patch(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double* U,
+                          double* prim, int8_t* status, long* iters) {
+  return c2p_patch(P, E, make_grid(n, px, 1.0), U, prim, status, iters);
+}
+
+int oracle_rhs_patch(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
+                     double* rhs) {
+  rhs_patch(P, make_grid(n, px, dx), U, prim, rhs);
+  return 0;
+}
+
+// Right-hand side at a list of interior points; out is [npts][32].
+int oracle_rhs_points(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
+                      int npts, const int* ijk, double* out) {
+  grid G = make_grid(n, px, dx);
+  for (int q = 0; q < npts; ++q) {
+    real r[NF];
+    rhs_point(P, G, U, prim, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r);
+    for (int f = 0; f < NF; ++f) out[(long)q * NF + f] = dbl(r[f]);
+  }
+  return 0;
+}
+
+// Diagnostic geometry at one interior point: Rsum_ij = Rhat_ij + R^chi_ij
+// (= R_ij + 2 D_(i Z_j)), its trace R + 2 D_i Z^i, and Gt^i.
+int oracle_geom_point(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
+                      int i, int j, int k, double* Rsum6, double* Rtr, double* Gt3, double* Z3) {
+  grid G = make_grid(n, px, dx);
+  real r[NST];
+  geom Gm;
+  ccz4_rhs_point(P, G, U, prim, i, j, k, r, &Gm);
+  for (int q = 0; q < 6; ++q) Rsum6[q] = dbl(Gm.Rsum[q]);
+  *Rtr = dbl(Gm.Rtr);
+  for (int a = 0; a < 3; ++a) {
+    Gt3[a] = dbl(Gm.Gt[a]);
+    Z3[a] = dbl(Gm.Z[a]);
+  }
+  return 0;
+}
+
+int oracle_substep(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx, int stage,
+                   double dt, double* Un, double* Ua, double* Ub, double* acc, double* prim, int8_t* status) {
+  grid G = make_grid(n, px, dx);
+  std::vector<double> k((size_t)NF * G.sf, 0.0);
+  return substep(P, E, G, stage, dt, Un, Ua, Ub, acc, prim, status, k.data());
+}
+
+int oracle_rk4_step(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx, double dt,
+                    double* Un, double* Ua, double* Ub, double* acc, double* prim, int8_t* status) {
+  grid G = make_grid(n, px, dx);
+  std::vector<double> k((size_t)NF * G.sf, 0.0);
+  int worst = 0;
+  for (int s = 0; s < 4; ++s) {
+    int w = substep(P, E, G, s, dt, Un, Ua, Ub, acc, prim, status, k.data());
+    if (w < worst) worst = w;
+  }
+  return worst;
+}
+
+// ---- pointwise entry points used by the pins ------------------------------
+int oracle_c2p_point(const oracle_params* P, const oracle_eos_table* E, const double* cons_bar, const double* gt,
+                     double chi, double alpha, double* prim, double* cons_out, int* iters) {
+  return c2p_point(P, E, cons_bar, gt, chi, alpha, prim, cons_out, iters);
+}
+
+// con2prim on n independent states with a flat metric: cons [n][10]
+// (D, DYe, tau, S_i, B^i, phi), prim [n][NP].
+int oracle_c2p_flat(const oracle_params* P, const oracle_eos_table* E, long n, const double* cons, double* prim,
+                    int8_t* status, int* iters) {
+  const double gt[6] = {1, 0, 0, 1, 0, 1};
+  int worst = 0;
+  for (long q = 0; q < n; ++q) {
+    double co[10];
+    int it = 0;
+    int st = c2p_point(P, E, cons + q * 10, gt, 1.0, 1.0, prim + q * NP, co, &it);
+    if (status) status[q] = (int8_t)st;
+    if (iters) iters[q] = it;
+    if (st < worst) worst = st;
+  }
+  return worst;
+}
+
+// Undensitized conserved variables (D, DYe, tau, S_i, B^i) from primitives
+// (rho, eps, p, v^i, ..., Ye) and the physical metric gamma_ij.
+int oracle_prim2con_point(const double* prim, const double* B, const double* gdd, double* cons) {
+  real pr[NP], b[3], g[6], c[9];
+  for (int q = 0; q < NP; ++q) pr[q] = prim[q];
+  for (int q = 0; q < 3; ++q) b[q] = B[q];
+  for (int q = 0; q < 6; ++q) g[q] = gdd[q];
+  prim2con_point(pr, b, g, c);
+  for (int q = 0; q < 9; ++q) cons[q] = dbl(c[q]);
+  return 0;
+}
+
+int oracle_eos_from_eps(const oracle_params* P, const oracle_eos_table* E, double rho, double eps, double ye,
+                        double* out4) {
+  eos_state s = eos_from_eps(P, E, rho, eps, ye);
+  out4[0] = dbl(s.p);
+  out4[1] = dbl(s.eps);
+  out4[2] = dbl(s.T);
+  out4[3] = dbl(s.cs2);
+  return 0;
+}
+
+int oracle_eos_from_T(const oracle_params* P, const oracle_eos_table* E, double rho, double T, double ye,
+                      double* out4) {
+  eos_state s = eos_from_T(P, E, rho, T, ye);
+  out4[0] = dbl(s.p);
+  out4[1] = dbl(s.eps);
+  out4[2] = dbl(s.T);
+  out4[3] = dbl(s.cs2);
+  return 0;
+}
+
+double oracle_fd_d1(const double* u, double dx) { return dbl(fd_d1(u, 1, 1.0 / (12.0 * dx))); }
+double oracle_fd_d2(const double* u, double dx) { return dbl(fd_d2(u, 1, 1.0 / (12.0 * dx * dx))); }
+// u points at the centre of a 2-D array with row stride ld (axis 2); returns D_2(D_1 u).
+double oracle_fd_d11(const double* u, long ld, double dx) { return dbl(fd_d11(u, 1, ld, 1.0 / (144.0 * dx * dx))); }
+double oracle_fd_up(const double* u, double beta, double dx) { return dbl(fd_up(u, 1, beta, 1.0 / (12.0 * dx))); }
+double oracle_fd_ko(const double* u, double sigma, double dx) { return dbl(fd_ko(u, 1, sigma / (64.0 * dx))); }
+double oracle_mp5(const double* f) { return dbl(mp5(f[0], f[1], f[2], f[3], f[4])); }
+double oracle_minmod4(double a, double b, double c, double d) { return dbl(minmod4(a, b, c, d)); }
+
+int oracle_fast_speeds(double alpha, double betad, double gudd, double vd, double v2, double a2, double* lp,
+                       double* lm) {
+  real p, m;
+  fast_speeds(alpha, betad, gudd, vd, v2, a2, &p, &m);
+  *lp = dbl(p);
+  *lm = dbl(m);
+  return 0;
+}
+
+// Pointwise flux vector along d at one point: U32 (32 evolved fields) and prim (NP).
+int oracle_flux_point(const oracle_params* P, const double* U32, const double* prim, int d, double* F10,
+                      double* lam) {
+  real F[10], l;
+  mhd_flux_point(P, U32, 1, prim, 1, d, F, &l);
+  for (int q = 0; q < 10; ++q) F10[q] = dbl(F[q]);
+  *lam = dbl(l);
+  return 0;
+}
+
+// Matter projections at one point: E, S_i, S_ij.
+int oracle_matter_point(const double* U32, const double* prim, double* E, double* Si, double* Sij) {
+  real e, s[3], sij[6], gdd[6], guu[6], sg;
+  matter_point(U32, 1, prim, 1, &e, s, sij, gdd, guu, &sg);
+  *E = dbl(e);
+  for (int q = 0; q < 3; ++q) Si[q] = dbl(s[q]);
+  for (int q = 0; q < 6; ++q) Sij[q] = dbl(sij[q]);
+  return 0;
+}
+
+}  // extern "C"

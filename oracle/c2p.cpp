@@ -1,0 +1,309 @@
+// Conservative-to-primitive recovery, following the paper's appendix
+// "Conversion from conserved to primitive fields" (Kastaun et al.'s scheme
+// extended to tabulated EOSs) step by step, with the error policy listed at
+// the end of that appendix.  Definitions of the conserved variables:
+// Sec. II B (eq. def_con2prim).
+#include "oracle.hpp"
+#include <cfloat>
+#include <cmath>
+
+// Undensitized (D, DYe, tau, S_i, B^i) from primitives; eq. def_con2prim
+// with h = rho (1 + eps) + p.
+void prim2con_point(const real prim[NP], const real B[3], const real gdd[6], real cons[9]) {
+  real v[3] = {prim[P_VX], prim[P_VY], prim[P_VZ]};
+  real vd[3], Bd[3];
+  for (int i = 0; i < 3; ++i) {
+    vd[i] = gdd[sym(i, 0)] * v[0] + gdd[sym(i, 1)] * v[1] + gdd[sym(i, 2)] * v[2];
+    Bd[i] = gdd[sym(i, 0)] * B[0] + gdd[sym(i, 1)] * B[1] + gdd[sym(i, 2)] * B[2];
+  }
+  real v2 = v[0] * vd[0] + v[1] * vd[1] + v[2] * vd[2];
+  real W = 1.0 / sqrt(1.0 - v2);
+  real rho = prim[P_RHO], eps = prim[P_EPS], p = prim[P_P];
+  real h = rho * (1.0 + eps) + p;
+  real B2 = B[0] * Bd[0] + B[1] * Bd[1] + B[2] * Bd[2];
+  real Bv = B[0] * vd[0] + B[1] * vd[1] + B[2] * vd[2];
+  real D = rho * W;
+  cons[0] = D;
+  cons[1] = D * prim[P_YE];
+  cons[2] = h * W * W - p + B2 - 0.5 * (Bv * Bv + B2 / (W * W)) - D;
+  for (int i = 0; i < 3; ++i) cons[3 + i] = (h * W * W + B2) * vd[i] - Bv * Bd[i];
+  for (int i = 0; i < 3; ++i) cons[6 + i] = B[i];
+}
+
+namespace {
+
+// Quantities fixed during the iterations (step 1 of the appendix).
+struct fixed_q {
+  real D, Ye, q, r2, rB, B2, B2rp2, v02, h0;
+};
+
+// Master-function evaluation and the intermediate values it produces.
+struct master_eval {
+  real f, chi, rbar2, qbar, v2, W, rho, rho_raw, eps, eps_raw, p, T, cs2;
+};
+
+// chi(mu) and rbar^2(mu), eqs. (chi) and (r_bar_sqr).
+inline void chi_rbar(const fixed_q& F, real mu, real* chi, real* rbar2) {
+  real c = 1.0 / (1.0 + mu * F.B2);
+  *chi = c;
+  *rbar2 = F.r2 * c * c + mu * c * (1.0 + c) * F.rB * F.rB;
+}
+
+// Auxiliary function f_a(mu) = mu sqrt(h0^2 + rbar^2(mu)) - 1  (step 2).
+inline real f_aux(const fixed_q& F, real mu) {
+  real chi, rbar2;
+  chi_rbar(F, mu, &chi, &rbar2);
+  return mu * sqrt(F.h0 * F.h0 + rbar2) - 1.0;
+}
+
+// Master function f(mu) of step 3 with the EOS validity clamps.
+master_eval f_master(const oracle_params* P, const oracle_eos_table* E, const fixed_q& F, real mu) {
+  master_eval m;
+  chi_rbar(F, mu, &m.chi, &m.rbar2);
+  m.qbar = F.q - 0.5 * F.B2 - 0.5 * mu * mu * m.chi * m.chi * F.B2rp2;
+  real v2 = mu * mu * m.rbar2;
+  m.v2 = fmin(v2, F.v02);
+  m.W = 1.0 / sqrt(1.0 - m.v2);
+  m.rho_raw = F.D / m.W;
+  m.rho = fmax(fmin(P->rho_max, m.rho_raw), P->rho_min);
+  m.eps_raw = m.W * (m.qbar - mu * m.rbar2) + m.v2 * m.W * m.W / (1.0 + m.W);
+  real emin = eos_eps_min(P, E, m.rho, F.Ye), emax = eos_eps_max(P, E, m.rho, F.Ye);
+  m.eps = fmax(fmin(emax, m.eps_raw), emin);
+  eos_state s = eos_from_eps(P, E, m.rho, m.eps, F.Ye);
+  m.p = s.p;
+  m.T = s.T;
+  m.cs2 = s.cs2;
+  real a = m.p / (m.rho * (1.0 + m.eps));
+  real nuA = (1.0 + a) * (1.0 + m.eps) / m.W;
+  real nuB = (1.0 + a) * (1.0 + m.qbar - mu * m.rbar2);
+  real nu = fmax(nuA, nuB);
+  m.f = mu - 1.0 / (nu + mu * m.rbar2);
+  return m;
+}
+
+// Brent's bracketing root finder (Brent 1973): keeps a bracket [b, c] with
+// f(b) f(c) <= 0 and |f(b)| <= |f(c)|, tries inverse quadratic interpolation
+// (secant when only two distinct points are known) and falls back to
+// bisection when the step is unsafe or the bracket shrinks too slowly.  Stops
+// when |c - b| <= 4 eps_mach |b| + xtol or f(b) = 0.
+template <class Fn>
+real brent(Fn fn, real a, real b, real fa, real fb, int max_iter, double xtol, int* iters, bool* ok) {
+  *ok = false;
+  *iters = 0;
+  if ((fa > 0.0 && fb > 0.0) || (fa < 0.0 && fb < 0.0)) return b;
+  real c = a, fc = fa;
+  real d = b - a, e = d;
+  for (int it = 0; it <= max_iter; ++it) {
+    if ((fb > 0.0 && fc > 0.0) || (fb < 0.0 && fc < 0.0)) {
+      c = a;
+      fc = fa;
+      d = b - a;
+      e = d;
+    }
+    if (fabs(fc) < fabs(fb)) {
+      a = b;
+      b = c;
+      c = a;
+      fa = fb;
+      fb = fc;
+      fc = fa;
+    }
+    real tol = 2.0 * DBL_EPSILON * fabs(b) + 0.5 * xtol;
+    real m = 0.5 * (c - b);
+    if (fabs(m) <= tol || fb == 0.0) {
+      *ok = true;
+      *iters = it;
+      return b;
+    }
+    if (it == max_iter) break;
+    if (fabs(e) >= tol && fabs(fa) > fabs(fb)) {
+      real s = fb / fa, p, q;
+      if (a == c) {
+        p = 2.0 * m * s;
+        q = 1.0 - s;
+      } else {
+        real qa = fa / fc, r = fb / fc;
+        p = s * (2.0 * m * qa * (qa - r) - (b - a) * (r - 1.0));
+        q = (qa - 1.0) * (r - 1.0) * (s - 1.0);
+      }
+      if (p > 0.0)
+        q = -q;
+      else
+        p = -p;
+      real lim1 = 3.0 * m * q - fabs(tol * q);
+      real lim2 = fabs(e * q);
+      if (2.0 * p < fmin(lim1, lim2)) {
+        e = d;
+        d = p / q;
+      } else {
+        d = m;
+        e = m;
+      }
+    } else {
+      d = m;
+      e = m;
+    }
+    a = b;
+    fa = fb;
+    if (fabs(d) > tol)
+      b = b + d;
+    else
+      b = b + (m > 0.0 ? tol : -tol);
+    fb = fn(b);
+  }
+  *iters = max_iter;
+  return b;
+}
+
+}  // namespace
+
+int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double cb[10], const double gtp[6],
+              double chip, double alpha, double prim[NP], double cons_out[10], int* iters_out) {
+  for (int n = 0; n < 10; ++n) cons_out[n] = cb[n];
+  *iters_out = 0;
+  // Metric: gamma_ij = gt_ij / chi, gamma^ij = chi gt^ij, sqrt(gamma) = sqrt(det gt) chi^{-3/2}.
+  real gt[6], gtu[6], gdd[6], guu[6];
+  for (int n = 0; n < 6; ++n) gt[n] = gtp[n];
+  real chi = chip;
+  real dgt = det_sym(gt);
+  inv_sym(gt, dgt, gtu);
+  for (int n = 0; n < 6; ++n) {
+    gdd[n] = gt[n] / chi;
+    guu[n] = chi * gtu[n];
+  }
+  real sqrtg = sqrt(dgt) / (chi * sqrt(chi));
+  bool finite = isfinite_r(sqrtg);
+  for (int n = 0; n < 9; ++n) finite = finite && std::isfinite(cb[n]);
+  for (int n = 0; n < NP; ++n) prim[n] = 0.0;
+  if (!finite || !(sqrtg > 0.0)) return -5;
+
+  real D = cb[0] / sqrtg, DYe = cb[1] / sqrtg, tau = cb[2] / sqrtg;
+  real S[3] = {cb[3] / sqrtg, cb[4] / sqrtg, cb[5] / sqrtg};
+  real B[3] = {cb[6] / sqrtg, cb[7] / sqrtg, cb[8] / sqrtg};
+  bool low_or_bh;
+  int status = 0;
+  real rho, eps, p, T, cs2, W, ye;
+  real v[3] = {0.0, 0.0, 0.0};
+
+  if (D < P->rho_min) {
+    // rho = D / W <= D < rho_min: atmosphere (policy item 1) without solving.
+    status = 1;
+  } else {
+    // Step 1: rescaled variables.
+    fixed_q F;
+    F.D = D;
+    F.Ye = DYe / D;
+    F.h0 = P->h0;
+    F.q = tau / D;
+    real r[3] = {S[0] / D, S[1] / D, S[2] / D};
+    real sD = sqrt(D);
+    real Bc[3] = {B[0] / sD, B[1] / sD, B[2] / sD};
+    real ru[3], Bcd[3];
+    for (int i = 0; i < 3; ++i) {
+      ru[i] = guu[sym(i, 0)] * r[0] + guu[sym(i, 1)] * r[1] + guu[sym(i, 2)] * r[2];
+      Bcd[i] = gdd[sym(i, 0)] * Bc[0] + gdd[sym(i, 1)] * Bc[1] + gdd[sym(i, 2)] * Bc[2];
+    }
+    F.r2 = ru[0] * r[0] + ru[1] * r[1] + ru[2] * r[2];
+    F.B2 = Bc[0] * Bcd[0] + Bc[1] * Bcd[1] + Bc[2] * Bcd[2];
+    F.rB = r[0] * Bc[0] + r[1] * Bc[1] + r[2] * Bc[2];
+    F.B2rp2 = F.B2 * F.r2 - F.rB * F.rB;
+    F.v02 = F.r2 / (F.h0 * F.h0 + F.r2);
+
+    // Step 2: mu_+ = root of f_a on (0, 1/h0].
+    int it1 = 0, it2 = 0;
+    bool ok1, ok2;
+    real mu_hi = 1.0 / F.h0;
+    real mu_plus = brent([&](real mu) { return f_aux(F, mu); }, 0.0, mu_hi, -1.0, f_aux(F, mu_hi),
+                         P->max_iter, P->c2p_xtol, &it1, &ok1);
+    // Step 3: root of the master function on (0, mu_+].
+    real f0 = f_master(P, E, F, 0.0).f;
+    real fplus = f_master(P, E, F, mu_plus).f;
+    real mu = brent([&](real x) { return f_master(P, E, F, x).f; }, 0.0, mu_plus, f0, fplus, P->max_iter,
+                    P->c2p_xtol, &it2, &ok2);
+    *iters_out = it1 + it2;
+    if (!ok1 || !ok2) return -5;
+    // Step 4: primitives from the root.
+    master_eval m = f_master(P, E, F, mu);
+    rho = m.rho;
+    eps = m.eps;
+    p = m.p;
+    T = m.T;
+    cs2 = m.cs2;
+    W = m.W;
+    ye = F.Ye;
+    for (int i = 0; i < 3; ++i) v[i] = mu * m.chi * (ru[i] + mu * F.rB * Bc[i]);
+
+    // Error policy.
+    low_or_bh = (rho < P->rho_low) || (alpha < P->alpha_bh);
+    if (m.rho_raw < P->rho_min) {
+      status = 1;
+    } else {
+      if (m.rho_raw > P->rho_max) return -1;
+      real emin = eos_eps_min(P, E, rho, ye), emax = eos_eps_max(P, E, rho, ye);
+      if (m.eps_raw < emin) status |= 2;
+      if (m.eps_raw > emax) {
+        if (!low_or_bh) return -2;
+        status |= 2;
+      }
+      if (W > P->W_max) {
+        if (!low_or_bh) return -3;
+        // Rescale v to v_max keeping D fixed.
+        real vmax = sqrt(1.0 - 1.0 / (P->W_max * P->W_max));
+        real vd2 = 0.0;
+        for (int i = 0; i < 3; ++i)
+          vd2 += v[i] * (gdd[sym(i, 0)] * v[0] + gdd[sym(i, 1)] * v[1] + gdd[sym(i, 2)] * v[2]);
+        real sc = vmax / sqrt(vd2);
+        for (int i = 0; i < 3; ++i) v[i] = v[i] * sc;
+        W = P->W_max;
+        rho = D / W;
+        status |= 4;
+      }
+      if (ye < P->ye_min || ye > P->ye_max) {
+        if (!low_or_bh) return -4;
+        ye = P->ye_atmo;
+        status |= 8;
+      }
+      if (status & (4 | 8)) {
+        // Thermodynamics at the corrected (rho, eps, ye).
+        real e2 = fmax(fmin(eos_eps_max(P, E, rho, ye), eps), eos_eps_min(P, E, rho, ye));
+        eos_state s = eos_from_eps(P, E, rho, e2, ye);
+        eps = e2;
+        p = s.p;
+        T = s.T;
+        cs2 = s.cs2;
+      }
+    }
+  }
+  if (status & 1) {
+    eos_state s = eos_atmosphere(P, E);
+    rho = P->rho_atmo;
+    eps = s.eps;
+    p = s.p;
+    T = s.T;
+    cs2 = s.cs2;
+    W = 1.0;
+    ye = P->ye_atmo;
+    v[0] = v[1] = v[2] = 0.0;
+    status = 1;
+  }
+  prim[P_RHO] = dbl(rho);
+  prim[P_EPS] = dbl(eps);
+  prim[P_P] = dbl(p);
+  prim[P_VX] = dbl(v[0]);
+  prim[P_VY] = dbl(v[1]);
+  prim[P_VZ] = dbl(v[2]);
+  prim[P_W] = dbl(W);
+  prim[P_YE] = dbl(ye);
+  prim[P_T] = dbl(T);
+  prim[P_CS2] = dbl(cs2);
+  if (status > 0) {
+    // A correction fired: the conserved variables are recomputed from the
+    // corrected primitives so that both stay consistent.
+    real pr[NP];
+    for (int n = 0; n < NP; ++n) pr[n] = prim[n];
+    real cons[9];
+    prim2con_point(pr, B, gdd, cons);
+    for (int n = 0; n < 6; ++n) cons_out[n] = dbl(cons[n] * sqrtg);
+  }
+  return status;
+}

@@ -1,0 +1,150 @@
+// Equations of state for the oracle.
+//
+// Ideal gas: p = (Gamma - 1) rho eps, the thermal part of the hybrid EOS of
+// Sec. II B with no cold part; c_s^2 = Gamma p / h with h = rho (1 + eps) + p
+// (the ideal-EOS sound speed quoted with the fast magnetosonic bound,
+// Appendix "Characteristic speeds").
+//
+// Table: p, eps, c_s^2 given at the nodes of a (log10 rho, log10 T, Ye) grid
+// and interpolated trilinearly (the tabulated finite-temperature EOS of
+// Sec. II B).  T(rho, eps, Ye) is inverted exactly: at fixed (rho, Ye) the
+// trilinear interpolant of eps is piecewise linear in log10 T, so a binary
+// search over the T nodes followed by one linear solve recovers it.
+#include "oracle.hpp"
+#include <cmath>
+
+static void locate(real x, double x0, double dx, int n, int* i, real* w) {
+  real f = (x - x0) / dx;
+  int ii = (int)std::floor(dbl(f));
+  if (ii < 0) ii = 0;
+  if (ii > n - 2) ii = n - 2;
+  real ww = f - (double)ii;
+  if (ww < 0.0) ww = 0.0;
+  if (ww > 1.0) ww = 1.0;
+  *i = ii;
+  *w = ww;
+}
+
+static inline real lerp(real a, real b, real w) { return a + w * (b - a); }
+
+static inline long node(const oracle_eos_table* E, int ir, int it, int iy) {
+  return ((long)iy * E->nt + it) * E->nr + ir;
+}
+
+// Bilinear value in (rho, Ye) of array A at temperature node it.
+static real bilin(const oracle_eos_table* E, const double* A, int ir, real wr, int it, int iy, real wy) {
+  real lo = lerp(A[node(E, ir, it, iy)], A[node(E, ir + 1, it, iy)], wr);
+  real hi = lerp(A[node(E, ir, it, iy + 1)], A[node(E, ir + 1, it, iy + 1)], wr);
+  return lerp(lo, hi, wy);
+}
+
+struct tab_loc {
+  int ir, iy;
+  real wr, wy;
+};
+
+static tab_loc tab_locate(const oracle_eos_table* E, real rho, real ye) {
+  tab_loc L;
+  locate(log10(rho), E->lr0, E->dlr, E->nr, &L.ir, &L.wr);
+  locate(ye, E->ye0, E->dye, E->ny, &L.iy, &L.wy);
+  return L;
+}
+
+real eos_eps_min(const oracle_params* P, const oracle_eos_table* E, real rho, real ye) {
+  if (P->eos_kind == 0) return 0.0;
+  tab_loc L = tab_locate(E, rho, ye);
+  return bilin(E, E->eps, L.ir, L.wr, 0, L.iy, L.wy);
+}
+
+real eos_eps_max(const oracle_params* P, const oracle_eos_table* E, real rho, real ye) {
+  if (P->eos_kind == 0) return P->eps_max;
+  tab_loc L = tab_locate(E, rho, ye);
+  return bilin(E, E->eps, L.ir, L.wr, E->nt - 1, L.iy, L.wy);
+}
+
+static eos_state ideal_from_eps(const oracle_params* P, real rho, real eps) {
+  eos_state s;
+  s.eps = eps;
+  s.p = (P->gamma_th - 1.0) * rho * eps;
+  s.T = 0.0;
+  s.cs2 = P->gamma_th * s.p / (rho * (1.0 + eps) + s.p);
+  return s;
+}
+
+eos_state eos_from_eps(const oracle_params* P, const oracle_eos_table* E, real rho, real eps, real ye) {
+  if (P->eos_kind == 0) return ideal_from_eps(P, rho, eps);
+  tab_loc L = tab_locate(E, rho, ye);
+  // Binary search for the T interval whose node values bracket eps.
+  int lo = 0, hi = E->nt - 1;
+  real elo = bilin(E, E->eps, L.ir, L.wr, lo, L.iy, L.wy);
+  real ehi = bilin(E, E->eps, L.ir, L.wr, hi, L.iy, L.wy);
+  if (eps <= elo) {
+    hi = 1;
+    ehi = bilin(E, E->eps, L.ir, L.wr, 1, L.iy, L.wy);
+  } else if (eps >= ehi) {
+    lo = E->nt - 2;
+    elo = bilin(E, E->eps, L.ir, L.wr, lo, L.iy, L.wy);
+  } else {
+    while (hi - lo > 1) {
+      int mid = (lo + hi) / 2;
+      real em = bilin(E, E->eps, L.ir, L.wr, mid, L.iy, L.wy);
+      if (em <= eps) {
+        lo = mid;
+        elo = em;
+      } else {
+        hi = mid;
+        ehi = em;
+      }
+    }
+  }
+  real wt = (eps - elo) / (ehi - elo);
+  if (wt < 0.0) wt = 0.0;
+  if (wt > 1.0) wt = 1.0;
+  eos_state s;
+  s.eps = eps;
+  real plo = bilin(E, E->p, L.ir, L.wr, lo, L.iy, L.wy);
+  real phi = bilin(E, E->p, L.ir, L.wr, lo + 1, L.iy, L.wy);
+  s.p = lerp(plo, phi, wt);
+  real clo = bilin(E, E->cs2, L.ir, L.wr, lo, L.iy, L.wy);
+  real chi = bilin(E, E->cs2, L.ir, L.wr, lo + 1, L.iy, L.wy);
+  s.cs2 = lerp(clo, chi, wt);
+  s.T = pow(10.0, E->lt0 + (lo + wt) * E->dlt);
+  return s;
+}
+
+eos_state eos_from_T(const oracle_params* P, const oracle_eos_table* E, real rho, real T, real ye) {
+  if (P->eos_kind == 0) {
+    // Ideal gas has no temperature: the cold polytrope p = K rho^Gamma is used.
+    real p = P->K_atmo * pow(rho, P->gamma_th);
+    return ideal_from_eps(P, rho, p / ((P->gamma_th - 1.0) * rho));
+  }
+  tab_loc L = tab_locate(E, rho, ye);
+  int it;
+  real wt;
+  locate(log10(T), E->lt0, E->dlt, E->nt, &it, &wt);
+  eos_state s;
+  s.T = T;
+  s.p = lerp(bilin(E, E->p, L.ir, L.wr, it, L.iy, L.wy), bilin(E, E->p, L.ir, L.wr, it + 1, L.iy, L.wy), wt);
+  s.eps = lerp(bilin(E, E->eps, L.ir, L.wr, it, L.iy, L.wy), bilin(E, E->eps, L.ir, L.wr, it + 1, L.iy, L.wy), wt);
+  s.cs2 = lerp(bilin(E, E->cs2, L.ir, L.wr, it, L.iy, L.wy), bilin(E, E->cs2, L.ir, L.wr, it + 1, L.iy, L.wy), wt);
+  return s;
+}
+
+eos_state eos_atmosphere(const oracle_params* P, const oracle_eos_table* E) {
+  return eos_from_T(P, E, P->rho_atmo, P->T_atmo, P->ye_atmo);
+}
+
+real det_sym(const real g[6]) {
+  return g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) +
+         g[2] * (g[1] * g[4] - g[3] * g[2]);
+}
+
+void inv_sym(const real g[6], real det, real gu[6]) {
+  real id = 1.0 / det;
+  gu[0] = (g[3] * g[5] - g[4] * g[4]) * id;
+  gu[1] = (g[2] * g[4] - g[1] * g[5]) * id;
+  gu[2] = (g[1] * g[4] - g[2] * g[3]) * id;
+  gu[3] = (g[0] * g[5] - g[2] * g[2]) * id;
+  gu[4] = (g[1] * g[2] - g[0] * g[4]) * id;
+  gu[5] = (g[0] * g[3] - g[1] * g[1]) * id;
+}
