@@ -1,0 +1,303 @@
+"""Benchmark: GRMHD zone-updates/s on the magnetised TOV star, 128^3 patch.
+
+One step = one full RK4 step (4 fused substeps: ghost fill, con2prim with the
+point-wise fluxes, interface fluxes, CCZ4 + MHD right-hand side with the RK
+epilogue) of the static TOV star (K = 100, Gamma = 2, rho_c = 1.28e-3) on a
+single 128^3 vertex-centred patch covering [-20, 20]^3, with a 1 % seeded
+pressure perturbation, a poloidal field and a 1e-10 atmosphere.  A zone-update
+is one interior point advanced by one RK4 step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl grmhd|reference]
+
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+method used by the tests) on a bounded sub-box of the same workload.  Under
+torchrun every rank advances its own star (replicas; no data-path collective).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GRMHD zone-updates/s (FP64, 1 GB300); con2prim solves/s plain vs NN-seeded"
+UNIT = "zone-updates/s"
+N_EDGE = 128
+DX = 0.3125
+X0 = -20.0
+WORKLOAD = "tov_magnetised_128^3_rk4_step"
+
+# Algorithmic FP64 flops per unit, counted by the oracle's flop-counting build
+# (python -m oracle.count_flops; one substep of a 24^3 sub-box of this workload
+# at the same grid spacing; checked by tests/test_flops_figures.py):
+#   right-hand side kernel: CCZ4 + gauge + KO + MHD sources + flux difference
+#   (6724 per interior point) plus the RK4 combination (128 for stages 0-2,
+#   64 for stage 3).
+RHS_FLOPS_PER_POINT = 6724.0
+RK_FLOPS_PER_POINT = (128.0 * 3 + 64.0) / 4.0
+# FP64 peak derived from the unit counts and clocks: 152 SMs x 4 FP64 flops per
+# clock per SM x 2070 MHz (nominal GB300 FP64 1.25 TFLOP/s = 152 x 2.07 GHz x 3.97).
+FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
+
+
+def _args():
+    a = argparse.ArgumentParser()
+    a.add_argument("--gpus", type=int, default=1)
+    a.add_argument("--steps", type=int, default=10)
+    a.add_argument("--warmup", type=int, default=3)
+    a.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
+    a.add_argument("--no-cpu-baseline", action="store_true")
+    a.add_argument("--e2e-steps", type=int, default=3)
+    a.add_argument("--edge", type=int, default=N_EDGE,
+                   help="interior points per axis (the same [-20,20]^3 star; 128 is the benchmark workload)")
+    return a.parse_args()
+
+
+def _workload_id(seed, edge=N_EDGE):
+    import synth
+    return synth.tov_id(n=(edge,) * 3, x0=(X0,) * 3, dx=40.0 / edge, seed=seed)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip() == "Active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(n=48, budget_s=12.0):
+    """The oracle as it stands, serial, on a sub-box of the workload (same dx, star centre)."""
+    import oracle
+    import synth
+    P = synth.ideal_params(bc=1)
+    nn = (n, n, n)
+    ID = synth.tov_id(n=nn, x0=(-(n // 2) * DX,) * 3, dx=DX, seed=1)
+    O = oracle.Oracle(P)
+    U = O.init_state(ID, nn, DX)
+    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    prim = np.zeros((oracle.NP,) + U.shape[1:])
+    st = np.zeros(U.shape[1:], dtype=np.int8)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        O.rk4_step(regs, prim, st, nn, DX, 0.4 * DX)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 50:
+            break
+    return {"value": steps * n ** 3 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d RK4 steps of a %d^3 sub-box of the TOV workload (same dx, star centre), serial C++ "
+                      "oracle, %.1f s" % (steps, n, el)}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    n = 32
+    P = synth.ideal_params(bc=1)
+    nn = (n, n, n)
+    ID = synth.tov_id(n=nn, x0=(-(n // 2) * DX,) * 3, dx=DX, seed=1)
+    O = oracle.Oracle(P)
+    U = O.init_state(ID, nn, DX)
+    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    prim = np.zeros((oracle.NP,) + U.shape[1:])
+    st = np.zeros(U.shape[1:], dtype=np.int8)
+    for _ in range(args.warmup):
+        O.rk4_step(regs, prim, st, nn, DX, 0.4 * DX)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.rk4_step(regs, prim, st, nn, DX, 0.4 * DX)
+    el = time.perf_counter() - t0
+    value = args.steps * n ** 3 / el
+    sample = "one RK4 step of a %d^3 sub-box of the TOV workload per step (same dx, star centre), serial oracle" % n
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_edge": n, "dx": DX},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_grmhd(args):
+    ws, rank, local = _dist()
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    _barrier(ws)
+    import paper_2510_13965_gb300 as g
+    import synth
+
+    P = synth.ideal_params(bc=1)
+    edge = args.edge
+    dx = 40.0 / edge
+    ID = torch.as_tensor(_workload_id(seed=1 + rank, edge=edge), device="cuda")
+    pt = g.Patches(P, [dict(n=(edge,) * 3, dx=dx, x0=(X0,) * 3)])
+    pt.init_state(0, ID)
+    del ID
+    dt = 0.4 * dx
+    for _ in range(max(args.warmup, 3)):
+        pt.step(dt)
+    pt.synchronize()
+    rc = pt.sync_status()
+    if rc != 0:
+        raise SystemExit("warm-up failed: status %d" % rc)
+
+    # ---- timed region: K RK4 steps, kernels bracketed by CUDA events ----------
+    clocks = Clocks(local) if rank == 0 else None
+    pt.profile(True)
+    launches0 = pt.launch_count()
+    s = pt.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        pt.step(dt)
+    e1.record(s)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    ms = e0.elapsed_time(e1)
+    launches = pt.launch_count() - launches0
+    prof = pt.profile_read()
+    pt.profile(False)
+    clk = clocks.stop() if clocks else None
+    ms_max = _max_over_ranks(ws, ms)
+    rc = pt.sync_status()
+    if rc != 0:
+        raise SystemExit("timed steps failed: status %d" % rc)
+    zones = edge ** 3
+    value = ws * args.steps * zones / (ms_max / 1e3)
+
+    # ---- end to end: state from pinned host memory, step, state back --------
+    host_in = pt.U[0][0].detach().to("cpu").pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    nbytes = host_in.numel() * host_in.element_size()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        with torch.cuda.stream(s):
+            pt.U[0][0].copy_(host_in, non_blocking=True)
+        pt.step(dt)
+        with torch.cuda.stream(s):
+            host_out.copy_(pt.U[0][0], non_blocking=True)
+        s.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = _max_over_ranks(ws, e2e_s)
+    e2e = {"value": ws * zones / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    if rank != 0:
+        return 0
+    rhs_ms, rhs_n = prof["rhs"]
+    avg_rhs_ms = rhs_ms / max(rhs_n, 1)
+    flops = (RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT) * zones
+    achieved = flops / (avg_rhs_ms / 1e3) / 1e12
+    tot = sum(v[0] for v in prof.values()) or 1.0
+    roofline = {"bound": "alu", "kernel": "k_rhs (CCZ4 + MHD RHS + RK epilogue)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz",
+                "flops_per_point": RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if edge == N_EDGE else "tov_magnetised_%d^3_rk4_step" % edge,
+                       "n": [edge] * 3, "dx": dx, "domain": "[-20,20]^3",
+                       "step": "one RK4 step (4 fused substeps)", "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (616 MB per RK register)"},
+            "substeps_per_s": 4 * args.steps * ws / (ms_max / 1e3),
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+            "kernel_share": {k: v[0] / tot for k, v in prof.items() if v[1]},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    if ws == 1 and not args.no_cpu_baseline and edge == N_EDGE:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_grmhd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,237 @@
+/*
+ * grmhd.h -- C ABI of the GB300 GRMHD substep library (libgrmhd.so).
+ *
+ * One Runge-Kutta substep of the GRMHD method of "MHDuet: a high-order GRRMHD
+ * code for CPU and GPU architectures" (arXiv 2510.13965) on ghosted,
+ * vertex-centred grid patches:
+ *   - CCZ4 spacetime right-hand side with 1+log slicing and the simplified
+ *     Gamma-freezing shift (Sec. II A, evolution equations and gauge),
+ *     4th-order centred / one-sided finite differences and Kreiss-Oliger
+ *     dissipation (Sec. III B);
+ *   - ideal-MHD balance laws with divergence cleaning (Sec. II B, MHD system),
+ *     Lax-Friedrichs flux splitting, MP5 reconstruction and the flux formula
+ *     Fhat = F^L + F^R (Sec. III C), fast-magnetosonic speed bound (appendix on
+ *     characteristic speeds);
+ *   - per-point conservative-to-primitive recovery, Kastaun's two Brent
+ *     root finds with the EOS validity clamps and the error policy (appendix on
+ *     the conversion from conserved to primitive fields);
+ *   - the explicit RK4 stage combination (Sec. III A, Table RK4 explicit part).
+ *
+ * Conventions
+ *   - All floating-point data are FP64.  Every compute step runs in the
+ *     library's CUDA kernels (sm_103a); there is no CPU path.
+ *   - Pointers marked "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them.  The library owns its context, the patch
+ *     descriptors copied to the device, its scratch arrays and CUDA graphs.
+ *   - Work is enqueued on the stream given at creation (a cudaStream_t passed
+ *     as void*; NULL means the legacy default stream).  Calls return after
+ *     enqueueing, except where a call says it synchronises.
+ *   - Every function returns a grmhd_status: 0 on success, a negative code on
+ *     failure.  Argument errors are detected on the host before any launch.
+ *     Device-side failures (a fatal con2prim point, a non-finite state) are
+ *     recorded in a device flag and reported by grmhd_sync_status.  No
+ *     function aborts, traps or exits.
+ *
+ * Patch layout
+ *   A patch has n[0] x n[1] x n[2] interior points and 3 ghost layers per side
+ *   (the width of the KO / one-sided stencils and of the 6-point MP5 interface
+ *   stencil).  Point (i, j, k), with i in [-3, n[0]+3) etc., sits at
+ *   x0 + (i, j, k) * dx.  Arrays are field-major, x fastest:
+ *       a[f][k + 3][j + 3][i + 3],  extents (n[2]+6, n[1]+6, px), px >= n[0]+6.
+ *   Evolved fields (32): 0-5 gt_ij (xx xy xz yy yz zz), 6-11 At_ij, 12 chi,
+ *   13 Khat, 14 Theta, 15-17 Gammahat^i, 18 alpha, 19-21 beta^i, 22 Dbar,
+ *   23 DYebar, 24 taubar, 25-27 Sbar_i, 28-30 Bbar^i, 31 phibar
+ *   (bar = densitized by sqrt(gamma)).
+ *   Primitives (10): rho, eps, p, v^x, v^y, v^z (contravariant), W, Ye, T, c_s^2.
+ *   Initial data (26): gamma_ij (6), K_ij (6), alpha, beta^i (3), rho, eps,
+ *   v^i (3), B^i (3, not densitized), Ye, T.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRMHD_NFIELDS 32
+#define GRMHD_NPRIM 10
+#define GRMHD_NID 26
+#define GRMHD_NGHOST 3
+
+typedef enum {
+  GRMHD_OK = 0,
+  GRMHD_ERR_ARG = -1,        /* invalid argument (checked on the host)          */
+  GRMHD_ERR_CUDA = -2,       /* a CUDA runtime call failed                       */
+  GRMHD_ERR_C2P_FATAL = -3,  /* a point hit a fatal con2prim policy branch        */
+  GRMHD_ERR_TIMEOUT = -4,    /* a bounded device wait ran out                     */
+  GRMHD_ERR_NONFINITE = -5,  /* a non-finite conserved state reached con2prim     */
+  GRMHD_ERR_NOMEM = -6       /* a library allocation failed                      */
+} grmhd_status;
+
+/* Per-point con2prim status codes written to grmhd_patch_desc.status:
+ *    0 ok; positive = corrections applied (bit mask): 1 atmosphere,
+ *    2 eps clamped to the EOS range, 4 velocity limited to W_max, 8 Ye reset;
+ *   -1 rho > rho_max, -2 eps > eps_max in a dense region, -3 W > W_max in a
+ *   dense region, -4 Ye out of range in a dense region (the paper's fatal
+ *   cases), -5 no bracketed root / non-finite input. */
+
+/* Physical and numerical parameters.  Constants the paper leaves open
+ * (kappa_2, damping and gauge constants, c_b, kappa_b, the error-policy
+ * thresholds, the Brent stop rule) are inputs. */
+typedef struct grmhd_params {
+  double kappa_z, kappa_c, kappa_2; /* CCZ4 constraint damping                         */
+  double eta;                       /* shift damping (beta_0 = 0, f_alpha = f_beta = 1) */
+  double sigma_ko;                  /* Kreiss-Oliger strength sigma                     */
+  double c_b, kappa_b;              /* divergence-cleaning speed and damping            */
+  double gamma_th;                  /* ideal-gas adiabatic index                        */
+  double K_atmo;                    /* polytropic K of the ideal-gas atmosphere         */
+  double rho_atmo, rho_min, rho_low, rho_max;
+  double alpha_bh, W_max;
+  double eps_max;                   /* ideal-gas eps upper bound                        */
+  double ye_min, ye_max, ye_atmo;
+  double T_atmo;                    /* tabulated EOS: atmosphere temperature [MeV]      */
+  double h0;                        /* lower bound of the specific enthalpy of the EOS  */
+  double c2p_xtol;                  /* absolute part of the Brent stop rule             */
+  int eos_kind;                     /* 0 ideal gas, 1 table                             */
+  int bc;                           /* outer ghosts: 0 periodic, 1 linear extrapolation */
+  int max_iter;                     /* Brent iteration cap per root find                */
+  int reserved;
+} grmhd_params;
+
+/* Tabulated EOS: p, eps, c_s^2 on the nodes of a uniform (log10 rho,
+ * log10 T[MeV], Ye) grid, rho fastest: node (ir, it, iy) is at
+ * (iy * nt + it) * nr + ir.  Arrays are device pointers owned by the caller
+ * and must stay valid while a context uses them. */
+typedef struct grmhd_eos_table {
+  int nr, nt, ny, reserved;
+  double lr0, dlr, lt0, dlt, ye0, dye;
+  const double* p;
+  const double* eps;
+  const double* cs2;
+} grmhd_eos_table;
+
+/* One patch.  U[0] holds U^n; U[1], U[2] hold RK stage values; U[3] holds the
+ * RK4 accumulator.  All arrays are device pointers with the layout above. */
+typedef struct grmhd_patch_desc {
+  int n[3];
+  int px;
+  int level;
+  int reserved;
+  double x0[3];
+  double dx;
+  double* U[4];
+  double* prim;
+  int8_t* status;
+} grmhd_patch_desc;
+
+typedef struct grmhd_c2p_stats {
+  long long points;      /* points processed                          */
+  long long iterations;  /* Brent iterations summed over both solves  */
+  long long corrected;   /* points with a positive status             */
+  long long failed;      /* points with a negative status             */
+} grmhd_c2p_stats;
+
+typedef struct grmhd_ctx grmhd_ctx;
+
+/* Version of this ABI (increases when a signature changes). */
+int grmhd_abi_version(void);
+
+/* Creates a context for npatch patches (init_patches).  Validates the
+ * descriptors (sizes >= 4 per axis, px >= n[0]+6, 8-byte-aligned non-NULL
+ * pointers, dx > 0), copies them to the device and allocates the library's
+ * scratch (pointwise and interface fluxes: 63 doubles per ghosted point).
+ * eos may be NULL when p->eos_kind == 0.  stream: cudaStream_t or NULL.
+ * Returns GRMHD_ERR_ARG / GRMHD_ERR_NOMEM / GRMHD_ERR_CUDA on failure, with
+ * *out set to NULL. */
+int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d,
+                       const grmhd_eos_table* eos, void* stream);
+
+/* Initial data -> evolved state in register U[0] of patch `patch`:
+ * chi = det(gamma)^(-1/3), gt = chi gamma, Khat = K, At = chi (K_ij - gamma_ij K/3),
+ * Theta = 0, conserved variables from the primitives (Sec. II B definitions),
+ * phibar = 0, then Gammahat^i = gt^ij gt^kl d_l gt_jk with the centred 4th-order
+ * derivative at interior points, then the ghost fill of all fields.
+ * id: device array [26][n2+6][n1+6][px] (ghosts included). */
+int grmhd_init_state(grmhd_ctx* ctx, int patch, const double* id);
+
+/* Fills the 3-deep ghost zones of register `reg` (0..3) of every patch
+ * (periodic copy or linear extrapolation, axis by axis). */
+int grmhd_ghost_fill(grmhd_ctx* ctx, int reg);
+
+/* con2prim at every point (ghosts included) of register `reg` of every patch:
+ * writes prim and status; where a correction fired, the conserved variables
+ * of `reg` are recomputed from the corrected primitives.  If stats is
+ * non-NULL the call synchronises the stream and fills it. */
+int grmhd_con2prim(grmhd_ctx* ctx, int reg, grmhd_c2p_stats* stats);
+
+/* Right-hand side L(U) of register `reg` at interior points, from the
+ * primitives of the last grmhd_con2prim call.  rhs[p] is a device array with
+ * the patch layout (32 fields); ghost entries are not written. */
+int grmhd_rhs_eval(grmhd_ctx* ctx, int reg, double* const* rhs);
+
+/* RK4 stage combination (unfused), interior points, with k = rhs[p]:
+ *   stage 0: U[1] = U[0] + dt/2 k, U[3] = U[0] + dt/6 k
+ *   stage 1: U[2] = U[0] + dt/2 k, U[3] += dt/3 k
+ *   stage 2: U[1] = U[0] + dt k,   U[3] += dt/3 k
+ *   stage 3: U[0] = U[3] + dt/6 k */
+int grmhd_rk_update(grmhd_ctx* ctx, int stage, double dt, double* const* rhs);
+
+/* One fused substep `stage` (0..3) of RK4: ghost fill of the stage input
+ * (U[0], U[1], U[2], U[1] for stages 0..3), con2prim, right-hand side and the
+ * stage combination of grmhd_rk_update, without storing k. */
+int grmhd_rhs_substep(grmhd_ctx* ctx, int stage, double dt);
+
+/* One full RK4 step (four fused substeps). */
+int grmhd_step(grmhd_ctx* ctx, double dt);
+
+/* Captures nsteps RK4 steps into a CUDA graph owned by the context
+ * (replacing a previous one); grmhd_graph_launch replays it on the stream. */
+int grmhd_capture_graph(grmhd_ctx* ctx, int nsteps, double dt);
+int grmhd_graph_launch(grmhd_ctx* ctx);
+
+/* Synchronises the stream and returns the worst device-side condition since
+ * the last call (GRMHD_OK, GRMHD_ERR_C2P_FATAL or GRMHD_ERR_NONFINITE), then
+ * clears it. */
+int grmhd_sync_status(grmhd_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * each eager launch (not inside graph capture).  grmhd_profile(ctx, 1)
+ * discards old records and starts recording; grmhd_profile(ctx, 0) stops.
+ * grmhd_profile_read synchronises the stream, writes the summed milliseconds
+ * and launch counts per kernel kind (0 ghost fill, 1 con2prim + pointwise
+ * fluxes, 2 interface fluxes, 3 right-hand side + RK epilogue, 4 unfused RK
+ * update, 5 initial data) into ms[0..nkinds) and count[0..nkinds), and
+ * discards the records. */
+int grmhd_profile(grmhd_ctx* ctx, int on);
+int grmhd_profile_read(grmhd_ctx* ctx, double* ms, long long* count, int nkinds);
+
+/* Number of kernel launches the context has enqueued so far. */
+long long grmhd_launch_count(grmhd_ctx* ctx);
+
+/* Last error message of the context (static storage, never NULL). */
+const char* grmhd_last_error(grmhd_ctx* ctx);
+
+/* Frees the context's own memory and graphs (not the caller's arrays). */
+void grmhd_destroy(grmhd_ctx* ctx);
+
+/* ---- con2prim on independent states (flat metric, alpha = 1) ------------ */
+
+/* Conserved (D, DYe, tau, S_i, B^i, phi) per state from primitives
+ * (rho, eps, p, v^i, W, Ye, T, cs2; eps and p are recomputed from (rho, T, Ye)
+ * with the EOS when p->eos_kind == 1) and B^i.
+ * prim: device [n][10]; B: device [n][3]; cons: device [n][10]. */
+int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* prim,
+                        const double* B, double* cons, void* stream);
+
+/* con2prim of n states with a flat metric (the isolated recovery workload).
+ * cons: device [n][10]; prim: device [n][10]; status: device [n];
+ * iters: device [n] or NULL. */
+int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
+                   double* prim, int8_t* status, int32_t* iters, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRMHD_H */

@@ -73,6 +73,7 @@ def lib(flops=False):
             "oracle_geom_point": (i, [vp, vp, i, d, vp, vp, i, i, i, vp, vp, vp, vp]),
             "oracle_substep": (i, [vp, vp, vp, i, d, i, d, vp, vp, vp, vp, vp, vp]),
             "oracle_rk4_step": (i, [vp, vp, vp, i, d, d, vp, vp, vp, vp, vp, vp]),
+            "oracle_substep_counted": (i, [vp, vp, vp, i, d, i, d, vp, vp, vp, vp, vp, vp, vp]),
             "oracle_c2p_point": (i, [vp, vp, vp, vp, d, d, vp, vp, vp]),
             "oracle_c2p_flat": (i, [vp, vp, l, vp, vp, vp, vp]),
             "oracle_prim2con_point": (i, [vp, vp, vp, vp]),
@@ -168,6 +169,14 @@ class Oracle:
         Un, Ua, Ub, acc = regs
         return self.L.oracle_substep(_ref(self.P), self.Tp, _n3(n), Un.shape[-1], dx, stage, dt, _p(Un), _p(Ua),
                                      _p(Ub), _p(acc), _p(prim), _p(status))
+
+    def substep_counted(self, regs, prim, status, n, dx, stage, dt):
+        """Substep plus flop counts [con2prim, pointwise fluxes, interface fluxes, local RHS, RK]."""
+        Un, Ua, Ub, acc = regs
+        c = np.zeros(5, dtype=np.int64)
+        self.L.oracle_substep_counted(_ref(self.P), self.Tp, _n3(n), Un.shape[-1], dx, stage, dt, _p(Un), _p(Ua),
+                                      _p(Ub), _p(acc), _p(prim), _p(status), _p(c))
+        return c
 
     def rk4_step(self, regs, prim, status, n, dx, dt):
         Un, Ua, Ub, acc = regs

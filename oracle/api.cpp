@@ -10,9 +10,10 @@ void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf);
 void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* ID, double* U);
 int c2p_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, double* U, double* prim,
               int8_t* status, long* iters_total);
-void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs);
+void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs,
+               long long* counts);
 int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, int stage, double dt, double* Un,
-            double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs);
+            double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs, long long* counts);
 
 #ifdef ORACLE_COUNT_FLOPS
 long long oracle_flops = 0;
@@ -49,7 +50,7 @@ int oracle_con2prim_patch(const oracle_params* P, const oracle_eos_table* E, con
 
 int oracle_rhs_patch(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
                      double* rhs) {
-  rhs_patch(P, make_grid(n, px, dx), U, prim, rhs);
+  rhs_patch(P, make_grid(n, px, dx), U, prim, rhs, nullptr);
   return 0;
 }
 
@@ -86,7 +87,18 @@ int oracle_substep(const oracle_params* P, const oracle_eos_table* E, const int*
                    double dt, double* Un, double* Ua, double* Ub, double* acc, double* prim, int8_t* status) {
   grid G = make_grid(n, px, dx);
   std::vector<double> k((size_t)NF * G.sf, 0.0);
-  return substep(P, E, G, stage, dt, Un, Ua, Ub, acc, prim, status, k.data());
+  return substep(P, E, G, stage, dt, Un, Ua, Ub, acc, prim, status, k.data(), nullptr);
+}
+
+// Same as oracle_substep; counts[5] receives the flops of [con2prim,
+// pointwise fluxes, interface fluxes, local right-hand side, RK combination]
+// (meaningful in the counting build only).
+int oracle_substep_counted(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx,
+                           int stage, double dt, double* Un, double* Ua, double* Ub, double* acc, double* prim,
+                           int8_t* status, long long* counts) {
+  grid G = make_grid(n, px, dx);
+  std::vector<double> k((size_t)NF * G.sf, 0.0);
+  return substep(P, E, G, stage, dt, Un, Ua, Ub, acc, prim, status, k.data(), counts);
 }
 
 int oracle_rk4_step(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx, double dt,
@@ -95,7 +107,7 @@ int oracle_rk4_step(const oracle_params* P, const oracle_eos_table* E, const int
   std::vector<double> k((size_t)NF * G.sf, 0.0);
   int worst = 0;
   for (int s = 0; s < 4; ++s) {
-    int w = substep(P, E, G, s, dt, Un, Ua, Ub, acc, prim, status, k.data());
+    int w = substep(P, E, G, s, dt, Un, Ua, Ub, acc, prim, status, k.data(), nullptr);
     if (w < worst) worst = w;
   }
   return worst;

@@ -164,7 +164,17 @@ int c2p_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, 
 // Right-hand side at every interior point (rhs has the layout of U; ghost
 // entries are left untouched).  Pointwise fluxes and interface fluxes are
 // computed once per point / interface, then differenced.
-void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs) {
+#ifdef ORACLE_COUNT_FLOPS
+static long long flops_now() { return oracle_flops; }
+#else
+static long long flops_now() { return 0; }
+#endif
+
+// counts (optional): flops of [pointwise fluxes, interface fluxes, local terms
+// (CCZ4 + sources + flux difference)] in the counting build.
+void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs,
+               long long* counts) {
+  long long c0 = flops_now(), c_pt = 0, c_if = 0;
   const long st[3] = {1, G.sy, G.sz};
   const long npts = G.sf;
   // Fhat[d][n][o]: flux at the interface between point o and o + st[d].
@@ -183,6 +193,8 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
           for (int n = 0; n < 10; ++n) Fp[(size_t)n * npts + o] = dbl(Fv[n]);
           Lp[o] = dbl(lam);
         }
+    long long c1 = flops_now();
+    c_pt += c1 - c0;
     lo[d] = -1;
     hi[d] = G.n[d];
     for (int k = lo[2]; k < hi[2]; ++k)
@@ -202,6 +214,8 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
           iface_flux(Fm, Um, lam, Fh);
           for (int n = 0; n < 10; ++n) Fhat[((size_t)d * 10 + n) * npts + o] = dbl(Fh[n]);
         }
+    c0 = flops_now();
+    c_if += c0 - c1;
   }
   real idx = 1.0 / G.dx;
   for (int k = 0; k < G.n[2]; ++k)
@@ -224,6 +238,11 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
         }
         for (int f = 0; f < NF; ++f) rhs[(long)f * G.sf + o] = dbl(r[f]);
       }
+  if (counts) {
+    counts[0] = c_pt;
+    counts[1] = c_if;
+    counts[2] = flops_now() - c0;
+  }
 }
 
 // One substep of explicit RK4 on registers Un, Ua, Ub (stage values) and acc:
@@ -232,13 +251,18 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
 //   stage 2: in Ub -> Ua = Un + dt k3,   acc += dt/3 k3
 //   stage 3: in Ua -> Un = acc + dt/6 k4
 // Each stage first fills ghosts and runs con2prim on its input register.
+// counts (optional, counting build): [con2prim, pointwise fluxes, interface
+// fluxes, local right-hand side, RK combination].
 int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, int stage, double dt, double* Un,
-            double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs) {
+            double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs, long long* counts) {
   double* in = stage == 0 ? Un : stage == 1 ? Ua : stage == 2 ? Ub : Ua;
   double* out = stage == 0 ? Ua : stage == 1 ? Ub : stage == 2 ? Ua : Un;
   ghost_fill(P, G, in, NF);
+  long long t0 = flops_now();
   int worst = c2p_patch(P, E, G, in, prim, status, nullptr);
-  rhs_patch(P, G, in, prim, krhs);
+  long long t1 = flops_now();
+  rhs_patch(P, G, in, prim, krhs, counts ? counts + 1 : nullptr);
+  long long t2 = flops_now();
   real hdt = 0.5 * dt, sdt = dt / 6.0, tdt = dt / 3.0;
   for (int f = 0; f < NF; ++f)
     for (int k = 0; k < G.n[2]; ++k)
@@ -259,5 +283,9 @@ int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, in
             out[o] = dbl(real(acc[o]) + sdt * kk);
           }
         }
+  if (counts) {
+    counts[0] = t1 - t0;
+    counts[4] = flops_now() - t2;
+  }
   return worst;
 }

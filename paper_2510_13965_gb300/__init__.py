@@ -1,0 +1,306 @@
+"""Python binding of libgrmhd.so, the GB300 GRMHD substep library.
+
+Argument marshalling only: every step of the substep runs in the library's
+CUDA kernels.  PyTorch provides device memory and a CUDA stream.  There is no
+CPU fallback: importing works anywhere, but every call that touches the
+library raises if libgrmhd.so cannot be loaded or no CUDA device is present.
+Names follow include/grmhd.h.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrmhd.so")
+
+NF, NP, NID, NG = 32, 10, 26, 3
+OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_C2P_FATAL", -4: "ERR_TIMEOUT", -5: "ERR_NONFINITE",
+          -6: "ERR_NOMEM"}
+
+_P_DOUBLES = ["kappa_z", "kappa_c", "kappa_2", "eta", "sigma_ko", "c_b", "kappa_b", "gamma_th", "K_atmo",
+              "rho_atmo", "rho_min", "rho_low", "rho_max", "alpha_bh", "W_max", "eps_max", "ye_min", "ye_max",
+              "ye_atmo", "T_atmo", "h0", "c2p_xtol"]
+_P_INTS = ["eos_kind", "bc", "max_iter", "reserved"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS]
+
+
+class EosTable(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int), ("nt", ctypes.c_int), ("ny", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("lr0", ctypes.c_double), ("dlr", ctypes.c_double), ("lt0", ctypes.c_double), ("dlt", ctypes.c_double),
+                ("ye0", ctypes.c_double), ("dye", ctypes.c_double),
+                ("p", ctypes.c_void_p), ("eps", ctypes.c_void_p), ("cs2", ctypes.c_void_p)]
+
+
+class PatchDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("px", ctypes.c_int), ("level", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("x0", ctypes.c_double * 3), ("dx", ctypes.c_double), ("U", ctypes.c_void_p * 4),
+                ("prim", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class C2PStats(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_longlong), ("iterations", ctypes.c_longlong), ("corrected", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong)]
+
+
+class GrmhdError(RuntimeError):
+    pass
+
+
+_lib = None
+
+_SIGS = {
+    "grmhd_abi_version": (ctypes.c_int, []),
+    "grmhd_init_patches": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_init_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "grmhd_ghost_fill": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_con2prim": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "grmhd_rhs_eval": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "grmhd_rk_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
+    "grmhd_rhs_substep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "grmhd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "grmhd_capture_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "grmhd_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
+    "grmhd_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "grmhd_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
+    "grmhd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "grmhd_destroy": (None, [ctypes.c_void_p]),
+    "grmhd_prim2con_flat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_c2p_flat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libgrmhd.so (raises GrmhdError if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise GrmhdError("libgrmhd.so not built (run __graft_entry__.build()): %s" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def make_params(d):
+    p = Params()
+    for n in _P_DOUBLES:
+        setattr(p, n, float(d.get(n, 0.0)))
+    for n in _P_INTS:
+        setattr(p, n, int(d.get(n, 0)))
+    return p
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise GrmhdError("no CUDA device: the GRMHD library has no CPU path")
+    return torch
+
+
+class Table:
+    """EOS table resident in device memory (numpy node arrays from synth.make_table)."""
+
+    def __init__(self, t, device="cuda"):
+        torch = _torch()
+        self.arrays = [torch.as_tensor(np.ascontiguousarray(t[k]), dtype=torch.float64, device=device)
+                       for k in ("p", "eps", "cs2")]
+        self.s = EosTable(t["nr"], t["nt"], t["ny"], 0, t["lr0"], t["dlr"], t["lt0"], t["dlt"], t["ye0"], t["dye"],
+                          *[a.data_ptr() for a in self.arrays])
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def _check(rc, ctx=None, what=""):
+    if rc != OK:
+        msg = ""
+        if ctx:
+            m = load().grmhd_last_error(ctx)
+            msg = m.decode() if m else ""
+        raise GrmhdError("%s failed: %s (%d) %s" % (what, STATUS.get(rc, "?"), rc, msg))
+
+
+class Patches:
+    """A set of patches with device-resident RK registers and a library context.
+
+    specs: list of dicts with n (3 ints), dx, x0 (3 floats), optional level.
+    Allocates U (4 registers of [32, n2+6, n1+6, px]), prim, status per patch
+    with torch on `device`, and works on its own CUDA stream.
+    """
+
+    def __init__(self, params, specs, table=None, device="cuda", pad=1):
+        torch = _torch()
+        self.torch = torch
+        L = load()
+        self.L = L
+        self.params = make_params(params)
+        self.table = table
+        self.stream = torch.cuda.Stream(device=device)
+        self.device = device
+        self.specs = []
+        self.U, self.prim, self.status = [], [], []
+        descs = (PatchDesc * len(specs))()
+        for i, s in enumerate(specs):
+            n = tuple(int(v) for v in s["n"])
+            px = n[0] + 2 * NG
+            px = (px + pad - 1) // pad * pad
+            shp = (n[2] + 2 * NG, n[1] + 2 * NG, px)
+            regs = [torch.zeros((NF,) + shp, dtype=torch.float64, device=device) for _ in range(4)]
+            prim = torch.zeros((NP,) + shp, dtype=torch.float64, device=device)
+            st = torch.zeros(shp, dtype=torch.int8, device=device)
+            self.U.append(regs)
+            self.prim.append(prim)
+            self.status.append(st)
+            d = descs[i]
+            d.n[:] = list(n)
+            d.px = px
+            d.level = int(s.get("level", 0))
+            d.x0[:] = [float(v) for v in s.get("x0", (0.0, 0.0, 0.0))]
+            d.dx = float(s["dx"])
+            for r in range(4):
+                d.U[r] = regs[r].data_ptr()
+            d.prim = prim.data_ptr()
+            d.status = st.data_ptr()
+            self.specs.append(dict(n=n, px=px, dx=float(s["dx"]), shape=shp))
+        self.descs = descs
+        torch.cuda.current_stream().synchronize()
+        ctx = ctypes.c_void_p()
+        rc = L.grmhd_init_patches(ctypes.byref(ctx), ctypes.byref(self.params), len(specs), descs,
+                                  table.ref if table is not None else None, ctypes.c_void_p(self.stream.cuda_stream))
+        _check(rc, None, "grmhd_init_patches")
+        self.ctx = ctx
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.stream.synchronize()
+                self.L.grmhd_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    def _enter(self):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def init_state(self, patch, id_tensor):
+        self._enter()
+        assert id_tensor.dtype == self.torch.float64 and id_tensor.is_contiguous()
+        assert tuple(id_tensor.shape) == (NID,) + self.specs[patch]["shape"]
+        _check(self.L.grmhd_init_state(self.ctx, patch, ctypes.c_void_p(id_tensor.data_ptr())), self.ctx,
+               "grmhd_init_state")
+
+    def ghost_fill(self, reg):
+        self._enter()
+        _check(self.L.grmhd_ghost_fill(self.ctx, reg), self.ctx, "grmhd_ghost_fill")
+
+    def con2prim(self, reg, stats=False):
+        self._enter()
+        s = C2PStats()
+        _check(self.L.grmhd_con2prim(self.ctx, reg, ctypes.byref(s) if stats else None), self.ctx, "grmhd_con2prim")
+        return dict(points=s.points, iterations=s.iterations, corrected=s.corrected, failed=s.failed) if stats else None
+
+    def rhs_eval(self, reg, out=None):
+        self._enter()
+        torch = self.torch
+        if out is None:
+            out = [torch.zeros((NF,) + sp["shape"], dtype=torch.float64, device=self.device) for sp in self.specs]
+        arr = (ctypes.c_void_p * len(out))(*[t.data_ptr() for t in out])
+        _check(self.L.grmhd_rhs_eval(self.ctx, reg, arr), self.ctx, "grmhd_rhs_eval")
+        return out
+
+    def rk_update(self, stage, dt, rhs):
+        self._enter()
+        arr = (ctypes.c_void_p * len(rhs))(*[t.data_ptr() for t in rhs])
+        _check(self.L.grmhd_rk_update(self.ctx, stage, float(dt), arr), self.ctx, "grmhd_rk_update")
+
+    def rhs_substep(self, stage, dt):
+        self._enter()
+        _check(self.L.grmhd_rhs_substep(self.ctx, stage, float(dt)), self.ctx, "grmhd_rhs_substep")
+
+    def step(self, dt):
+        self._enter()
+        _check(self.L.grmhd_step(self.ctx, float(dt)), self.ctx, "grmhd_step")
+
+    def capture_graph(self, nsteps, dt):
+        self.synchronize()
+        _check(self.L.grmhd_capture_graph(self.ctx, int(nsteps), float(dt)), self.ctx, "grmhd_capture_graph")
+
+    def graph_launch(self):
+        self._enter()
+        _check(self.L.grmhd_graph_launch(self.ctx), self.ctx, "grmhd_graph_launch")
+
+    def sync_status(self):
+        return self.L.grmhd_sync_status(self.ctx)
+
+    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init")
+
+    def profile(self, on=True):
+        _check(self.L.grmhd_profile(self.ctx, 1 if on else 0), self.ctx, "grmhd_profile")
+
+    def profile_read(self):
+        """Summed CUDA-event milliseconds and launch counts per kernel kind since profile(True)."""
+        k = len(self.KERNEL_KINDS)
+        ms = (ctypes.c_double * k)()
+        cnt = (ctypes.c_longlong * k)()
+        _check(self.L.grmhd_profile_read(self.ctx, ms, cnt, k), self.ctx, "grmhd_profile_read")
+        return {n: (ms[i], cnt[i]) for i, n in enumerate(self.KERNEL_KINDS)}
+
+    def launch_count(self):
+        return self.L.grmhd_launch_count(self.ctx)
+
+
+def prim2con_flat(params, prim, B, table=None, stream=None):
+    """Conserved (n, 10) from primitives (n, 10) and B (n, 3), device tensors."""
+    torch = _torch()
+    L = load()
+    n = prim.shape[0]
+    cons = torch.empty((n, 10), dtype=torch.float64, device=prim.device)
+    P = make_params(params)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.grmhd_prim2con_flat(ctypes.byref(P), table.ref if table is not None else None, n,
+                               ctypes.c_void_p(prim.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                               ctypes.c_void_p(cons.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    _check(rc, None, "grmhd_prim2con_flat")
+    return cons
+
+
+def c2p_flat(params, cons, table=None, iters=False, stream=None, out=None):
+    """con2prim of (n, 10) conserved states, flat metric; returns prim, status[, iters]."""
+    torch = _torch()
+    L = load()
+    n = cons.shape[0]
+    if out is None:
+        prim = torch.empty((n, NP), dtype=torch.float64, device=cons.device)
+        status = torch.empty((n,), dtype=torch.int8, device=cons.device)
+        it = torch.empty((n,), dtype=torch.int32, device=cons.device) if iters else None
+    else:
+        prim, status, it = out
+    P = make_params(params)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.grmhd_c2p_flat(ctypes.byref(P), table.ref if table is not None else None, n,
+                          ctypes.c_void_p(cons.data_ptr()), ctypes.c_void_p(prim.data_ptr()),
+                          ctypes.c_void_p(status.data_ptr()),
+                          ctypes.c_void_p(it.data_ptr()) if it is not None else None, ctypes.c_void_p(s.cuda_stream))
+    _check(rc, None, "grmhd_c2p_flat")
+    return (prim, status, it) if iters else (prim, status)

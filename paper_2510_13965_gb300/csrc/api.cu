@@ -1,0 +1,455 @@
+// Host side of the C ABI declared in include/grmhd.h.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include "kern.cuh"
+
+using namespace gk;
+
+struct grmhd_ctx {
+  grmhd_params P;
+  Eos E;
+  cudaStream_t st;
+  int np;
+  std::vector<grmhd_patch_desc> desc;
+  std::vector<PatchDev> pd_host;
+  PatchDev* pd = nullptr;
+  // work lists per domain
+  Work* work = nullptr;
+  int wofs[NDOM + 1];
+  double* scratch = nullptr;
+  DevFlags* flags = nullptr;
+  C2PStats* stats = nullptr;
+  double** rhs_ptrs = nullptr;  // device array of npatch pointers
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  long long launches = 0;
+  long long graph_kernels = 0;
+  std::string err;
+  // CUDA-event profiling per kernel kind (eager launches only).
+  bool profiling = false;
+  struct Rec {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, NKIND = 6 };
+
+static cudaEvent_t ev_get(grmhd_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch with events on the context's stream when profiling is
+// on and the stream is not being captured.
+struct ProfScope {
+  grmhd_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfScope(grmhd_ctx* c_, int k) : c(c_), kind(k) {
+    if (!c->profiling) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->st, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return;
+    a = ev_get(c);
+    cudaEventRecord(a, c->st);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = ev_get(c);
+    cudaEventRecord(b, c->st);
+    c->recs.push_back(grmhd_ctx::Rec{a, b, kind});
+  }
+};
+
+static const char* kNoCtx = "no context";
+
+static int fail(grmhd_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+static int cuda_ok(grmhd_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return GRMHD_OK;
+  return fail(c, GRMHD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static int check_launch(grmhd_ctx* c, const char* what) {
+  return cuda_ok(c, cudaGetLastError(), what);
+}
+
+static int block_size(int dom) {
+  return (dom == DOM_INT) ? BS_INT : ((dom >= DOM_IFX && dom <= DOM_IFZ) ? BS_IF : BS_ALL);
+}
+
+extern "C" {
+
+int grmhd_abi_version(void) { return 1; }
+
+const char* grmhd_last_error(grmhd_ctx* c) { return c ? c->err.c_str() : kNoCtx; }
+
+long long grmhd_launch_count(grmhd_ctx* c) { return c ? c->launches : -1; }
+
+void grmhd_destroy(grmhd_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  cudaFree(c->pd);
+  cudaFree(c->work);
+  cudaFree(c->scratch);
+  cudaFree(c->flags);
+  cudaFree(c->stats);
+  cudaFree(c->rhs_ptrs);
+  delete c;
+}
+
+int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d,
+                       const grmhd_eos_table* eos, void* stream) {
+  if (!out) return GRMHD_ERR_ARG;
+  *out = nullptr;
+  if (!p || !d || npatch <= 0) return GRMHD_ERR_ARG;
+  if (p->eos_kind != 0 && p->eos_kind != 1) return GRMHD_ERR_ARG;
+  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2 || eos->nr < 2 || eos->nt < 2 || eos->ny < 2))
+    return GRMHD_ERR_ARG;
+  if (p->bc != 0 && p->bc != 1) return GRMHD_ERR_ARG;
+  if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
+  for (int i = 0; i < npatch; ++i) {
+    const grmhd_patch_desc& q = d[i];
+    if (q.n[0] < 4 || q.n[1] < 4 || q.n[2] < 4 || q.px < q.n[0] + 6 || !(q.dx > 0.0)) return GRMHD_ERR_ARG;
+    for (int r = 0; r < 4; ++r)
+      if (!q.U[r] || ((uintptr_t)q.U[r] & 7)) return GRMHD_ERR_ARG;
+    if (!q.prim || ((uintptr_t)q.prim & 7) || !q.status) return GRMHD_ERR_ARG;
+  }
+  grmhd_ctx* c = new grmhd_ctx();
+  c->P = *p;
+  c->E = make_eos(*p, eos);
+  c->st = (cudaStream_t)stream;
+  c->np = npatch;
+  c->desc.assign(d, d + npatch);
+  c->pd_host.resize(npatch);
+  // scratch: Fp (30) + lam (3) + Fh (30) doubles per ghosted point
+  size_t total = 0;
+  std::vector<size_t> ofs(npatch);
+  for (int i = 0; i < npatch; ++i) {
+    Geo G;
+    G.n0 = d[i].n[0];
+    G.n1 = d[i].n[1];
+    G.n2 = d[i].n[2];
+    G.px = d[i].px;
+    G.sy = d[i].px;
+    G.sz = G.sy * (G.n1 + 6);
+    G.sf = G.sz * (G.n2 + 6);
+    G.dx = d[i].dx;
+    c->pd_host[i].G = G;
+    ofs[i] = total;
+    total += (size_t)63 * G.sf;
+  }
+  int rc;
+  if ((rc = cuda_ok(c, cudaMalloc(&c->scratch, total * sizeof(double)), "cudaMalloc scratch")) != GRMHD_OK) {
+    grmhd_destroy(c);
+    return GRMHD_ERR_NOMEM;
+  }
+  for (int i = 0; i < npatch; ++i) {
+    PatchDev& q = c->pd_host[i];
+    for (int r = 0; r < 4; ++r) q.U[r] = d[i].U[r];
+    q.prim = d[i].prim;
+    q.status = d[i].status;
+    q.Fp = c->scratch + ofs[i];
+    q.lam = q.Fp + 30 * q.G.sf;
+    q.Fh = q.lam + 3 * q.G.sf;
+  }
+  // work lists
+  std::vector<Work> wl;
+  for (int dom = 0; dom < NDOM; ++dom) {
+    c->wofs[dom] = (int)wl.size();
+    int bs = block_size(dom);
+    for (int i = 0; i < npatch; ++i) {
+      long long n = dom_count(dom, c->pd_host[i].G);
+      long long nb = (n + bs - 1) / bs;
+      for (long long b = 0; b < nb; ++b) wl.push_back(Work{i, (int)b});
+    }
+  }
+  c->wofs[NDOM] = (int)wl.size();
+  if ((rc = cuda_ok(c, cudaMalloc(&c->work, wl.size() * sizeof(Work)), "cudaMalloc work")) ||
+      (rc = cuda_ok(c, cudaMalloc(&c->pd, npatch * sizeof(PatchDev)), "cudaMalloc pd")) ||
+      (rc = cuda_ok(c, cudaMalloc(&c->flags, sizeof(DevFlags)), "cudaMalloc flags")) ||
+      (rc = cuda_ok(c, cudaMalloc(&c->stats, sizeof(C2PStats)), "cudaMalloc stats")) ||
+      (rc = cuda_ok(c, cudaMalloc(&c->rhs_ptrs, npatch * sizeof(double*)), "cudaMalloc rhs ptrs"))) {
+    grmhd_destroy(c);
+    return rc == GRMHD_ERR_CUDA ? GRMHD_ERR_NOMEM : rc;
+  }
+  if ((rc = cuda_ok(c, cudaMemcpyAsync(c->work, wl.data(), wl.size() * sizeof(Work), cudaMemcpyHostToDevice, c->st),
+                    "copy work")) ||
+      (rc = cuda_ok(c, cudaMemcpyAsync(c->pd, c->pd_host.data(), npatch * sizeof(PatchDev), cudaMemcpyHostToDevice,
+                                       c->st), "copy pd")) ||
+      (rc = cuda_ok(c, cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->st), "clear flags")) ||
+      (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync"))) {
+    grmhd_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return GRMHD_OK;
+}
+
+static int nblk(grmhd_ctx* c, int dom) { return c->wofs[dom + 1] - c->wofs[dom]; }
+static const Work* wl(grmhd_ctx* c, int dom) { return c->work + c->wofs[dom]; }
+
+int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (patch < 0 || patch >= c->np || !id) return fail(c, GRMHD_ERR_ARG, "init_state: bad patch or id");
+  const PatchDev& q = c->pd_host[patch];
+  {
+    ProfScope ps(c, K_INIT);
+    launch_init(c->pd, patch, q.G, c->P, c->E, id, q.U[0], c->st);
+  }
+  c->launches += 2;
+  int rc = check_launch(c, "init");
+  if (rc) return rc;
+  for (int ax = 0; ax < 3; ++ax) {
+    // ghost fill of this patch only: its own slice of the work list
+    int dom = DOM_GX + ax;
+    const Work* w = wl(c, dom);
+    int n = nblk(c, dom);
+    // find the contiguous range of this patch
+    int first = -1, cnt = 0;
+    {
+      // work items are grouped by patch in increasing order
+      long long before = 0;
+      for (int i = 0; i < patch; ++i) before += (dom_count(dom, c->pd_host[i].G) + BS_ALL - 1) / BS_ALL;
+      first = (int)before;
+      cnt = (int)((dom_count(dom, q.G) + BS_ALL - 1) / BS_ALL);
+    }
+    if (first + cnt > n) return fail(c, GRMHD_ERR_ARG, "init_state: work list");
+    launch_ghost(c->pd, w + first, cnt, 0, ax, c->P.bc, c->st);
+    c->launches += 1;
+  }
+  return check_launch(c, "init ghost");
+}
+
+int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (reg < 0 || reg > 3) return fail(c, GRMHD_ERR_ARG, "ghost_fill: reg");
+  for (int ax = 0; ax < 3; ++ax) {
+    ProfScope ps(c, K_GHOST);
+    launch_ghost(c->pd, wl(c, DOM_GX + ax), nblk(c, DOM_GX + ax), reg, ax, c->P.bc, c->st);
+    c->launches += 1;
+  }
+  return check_launch(c, "ghost");
+}
+
+static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats) {
+  ProfScope ps(c, K_C2P);
+  launch_c2p(c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->P, c->E, c->flags, stats ? c->stats : nullptr, c->st);
+  c->launches += 1;
+  return check_launch(c, "con2prim");
+}
+
+static int iflux(grmhd_ctx* c, int reg) {
+  for (int d = 0; d < 3; ++d) {
+    ProfScope ps(c, K_IFLUX);
+    launch_iflux(c->pd, wl(c, DOM_IFX + d), nblk(c, DOM_IFX + d), reg, d, c->st);
+    c->launches += 1;
+  }
+  return check_launch(c, "iflux");
+}
+
+int grmhd_con2prim(grmhd_ctx* c, int reg, grmhd_c2p_stats* s) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (reg < 0 || reg > 3) return fail(c, GRMHD_ERR_ARG, "con2prim: reg");
+  int rc;
+  if (s && (rc = cuda_ok(c, cudaMemsetAsync(c->stats, 0, sizeof(C2PStats), c->st), "clear stats"))) return rc;
+  if ((rc = c2p_and_fluxes(c, reg, s != nullptr))) return rc;
+  if (s) {
+    C2PStats h;
+    if ((rc = cuda_ok(c, cudaMemcpyAsync(&h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->st), "stats copy")) ||
+        (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
+      return rc;
+    s->points = (long long)h.points;
+    s->iterations = (long long)h.iters;
+    s->corrected = (long long)h.corrected;
+    s->failed = (long long)h.failed;
+  }
+  return GRMHD_OK;
+}
+
+int grmhd_rhs_eval(grmhd_ctx* c, int reg, double* const* rhs) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (reg < 0 || reg > 3 || !rhs) return fail(c, GRMHD_ERR_ARG, "rhs_eval: args");
+  for (int i = 0; i < c->np; ++i)
+    if (!rhs[i]) return fail(c, GRMHD_ERR_ARG, "rhs_eval: null rhs");
+  int rc;
+  if ((rc = cuda_ok(c, cudaMemcpyAsync(c->rhs_ptrs, rhs, c->np * sizeof(double*), cudaMemcpyHostToDevice, c->st),
+                    "rhs ptrs")) ||
+      (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
+    return rc;
+  if ((rc = iflux(c, reg))) return rc;
+  {
+    ProfScope ps(c, K_RHS);
+    launch_rhs(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st);
+  }
+  c->launches += 1;
+  return check_launch(c, "rhs");
+}
+
+int grmhd_rk_update(grmhd_ctx* c, int stage, double dt, double* const* rhs) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (stage < 0 || stage > 3 || !rhs) return fail(c, GRMHD_ERR_ARG, "rk_update: args");
+  int rc;
+  if ((rc = cuda_ok(c, cudaMemcpyAsync(c->rhs_ptrs, rhs, c->np * sizeof(double*), cudaMemcpyHostToDevice, c->st),
+                    "rhs ptrs")) ||
+      (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
+    return rc;
+  {
+    ProfScope ps(c, K_RK);
+    launch_rk(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), stage, dt, c->rhs_ptrs, c->st);
+  }
+  c->launches += 1;
+  return check_launch(c, "rk");
+}
+
+static const int kStageIn[4] = {0, 1, 2, 1};
+
+int grmhd_rhs_substep(grmhd_ctx* c, int stage, double dt) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (stage < 0 || stage > 3) return fail(c, GRMHD_ERR_ARG, "rhs_substep: stage");
+  int reg = kStageIn[stage];
+  int rc;
+  if ((rc = grmhd_ghost_fill(c, reg))) return rc;
+  if ((rc = c2p_and_fluxes(c, reg, false))) return rc;
+  if ((rc = iflux(c, reg))) return rc;
+  {
+    ProfScope ps(c, K_RHS);
+    launch_rhs(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), reg, 1, stage, dt, c->P, nullptr, c->st);
+  }
+  c->launches += 1;
+  return check_launch(c, "rhs fused");
+}
+
+int grmhd_step(grmhd_ctx* c, double dt) {
+  if (!c) return GRMHD_ERR_ARG;
+  for (int s = 0; s < 4; ++s) {
+    int rc = grmhd_rhs_substep(c, s, dt);
+    if (rc) return rc;
+  }
+  return GRMHD_OK;
+}
+
+int grmhd_capture_graph(grmhd_ctx* c, int nsteps, double dt) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (nsteps < 1) return fail(c, GRMHD_ERR_ARG, "capture: nsteps");
+  if (c->st == nullptr) return fail(c, GRMHD_ERR_ARG, "capture: needs a non-default stream");
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  if (c->graph) {
+    cudaGraphDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  int rc;
+  if ((rc = cuda_ok(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return rc;
+  long long before = c->launches;
+  int inner = GRMHD_OK;
+  for (int s = 0; s < nsteps && inner == GRMHD_OK; ++s) inner = grmhd_step(c, dt);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  c->graph_kernels = c->launches - before;
+  c->launches = before;  // captured launches run at replay
+  if (inner) {
+    if (g) cudaGraphDestroy(g);
+    return inner;
+  }
+  if ((rc = cuda_ok(c, e, "end capture"))) return rc;
+  c->graph = g;
+  if ((rc = cuda_ok(c, cudaGraphInstantiate(&c->gexec, g, 0), "instantiate"))) return rc;
+  return GRMHD_OK;
+}
+
+int grmhd_graph_launch(grmhd_ctx* c) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (!c->gexec) return fail(c, GRMHD_ERR_ARG, "graph_launch: no graph");
+  c->launches += c->graph_kernels;
+  return cuda_ok(c, cudaGraphLaunch(c->gexec, c->st), "graph launch");
+}
+
+int grmhd_profile(grmhd_ctx* c, int on) {
+  if (!c) return GRMHD_ERR_ARG;
+  int rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync");
+  for (auto& r : c->recs) {
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  c->profiling = on != 0;
+  return rc;
+}
+
+int grmhd_profile_read(grmhd_ctx* c, double* ms, long long* count, int nkinds) {
+  if (!c || !ms || !count || nkinds < 1) return GRMHD_ERR_ARG;
+  int rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync");
+  if (rc) return rc;
+  for (int k = 0; k < nkinds; ++k) {
+    ms[k] = 0.0;
+    count[k] = 0;
+  }
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return fail(c, GRMHD_ERR_CUDA, "event elapsed");
+    if (r.kind < nkinds) {
+      ms[r.kind] += t;
+      count[r.kind] += 1;
+    }
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  return GRMHD_OK;
+}
+
+int grmhd_sync_status(grmhd_ctx* c) {
+  if (!c) return GRMHD_ERR_ARG;
+  DevFlags h;
+  int rc;
+  if ((rc = cuda_ok(c, cudaMemcpyAsync(&h, c->flags, sizeof(h), cudaMemcpyDeviceToHost, c->st), "flags copy")) ||
+      (rc = cuda_ok(c, cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->st), "flags clear")) ||
+      (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
+    return rc;
+  if (h.flags & 2) return fail(c, GRMHD_ERR_NONFINITE, "non-finite state reached con2prim");
+  if (h.flags & 1) return fail(c, GRMHD_ERR_C2P_FATAL, "fatal con2prim point");
+  return GRMHD_OK;
+}
+
+int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* prim,
+                        const double* B, double* cons, void* stream) {
+  if (!p || n < 0 || (n > 0 && (!prim || !B || !cons))) return GRMHD_ERR_ARG;
+  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2)) return GRMHD_ERR_ARG;
+  launch_prim2con_flat(*p, make_eos(*p, eos), n, prim, B, cons, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}
+
+int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons, double* prim,
+                   int8_t* status, int32_t* iters, void* stream) {
+  if (!p || n < 0 || (n > 0 && (!cons || !prim || !status))) return GRMHD_ERR_ARG;
+  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2)) return GRMHD_ERR_ARG;
+  if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
+  launch_c2p_flat(*p, make_eos(*p, eos), n, cons, prim, status, iters, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+// Kernel declarations and the device-side patch descriptor shared by the
+// kernel translation units and the host API.
+#pragma once
+#include <cuda_runtime.h>
+#include "c2p.cuh"
+
+namespace gk {
+
+struct PatchDev {
+  Geo G;
+  double* U[4];
+  double* prim;
+  int8_t* status;
+  double* Fp;   // pointwise fluxes [3][10][sf]
+  double* lam;  // pointwise max |lambda_fast| [3][sf]
+  double* Fh;   // interface fluxes [3][10][sf] at the interface between o and o + s_d
+};
+
+// Work item of a launch: patch index and block index within that patch's domain.
+struct Work {
+  int patch;
+  int block;
+};
+
+enum Domain : int {
+  DOM_ALL = 0,  // every point, ghosts included
+  DOM_INT = 1,  // interior points
+  DOM_IFX = 2,  // interfaces i+1/2, i = -1 .. n0-1, interior in y, z (likewise IFY, IFZ)
+  DOM_IFY = 3,
+  DOM_IFZ = 4,
+  DOM_GX = 5,   // ghost-fill lines along x over interior (y, z)
+  DOM_GY = 6,   // lines along y over (x incl. ghosts, interior z)
+  DOM_GZ = 7,   // lines along z over (x, y incl. ghosts)
+  NDOM = 8
+};
+
+// Number of work items of a domain.
+inline __host__ __device__ long long dom_count(int dom, const Geo& G) {
+  long long a = G.n0, b = G.n1, c = G.n2;
+  switch (dom) {
+    case DOM_ALL: return (a + 6) * (b + 6) * (c + 6);
+    case DOM_INT: return a * b * c;
+    case DOM_IFX: return (a + 1) * b * c;
+    case DOM_IFY: return a * (b + 1) * c;
+    case DOM_IFZ: return a * b * (c + 1);
+    case DOM_GX: return b * c;
+    case DOM_GY: return (a + 6) * c;
+    default: return (a + 6) * (b + 6);
+  }
+}
+
+// Linear work index -> point (i, j, k) of the domain (for ghost lines: the line's base point).
+DI void dom_decode(int dom, const Geo& G, long long q, int& i, int& j, int& k) {
+  long long ex, ey;
+  int ox = 0, oy = 0, oz = 0;
+  switch (dom) {
+    case DOM_ALL: ex = G.n0 + 6; ey = G.n1 + 6; ox = oy = oz = -3; break;
+    case DOM_INT: ex = G.n0; ey = G.n1; break;
+    case DOM_IFX: ex = G.n0 + 1; ey = G.n1; ox = -1; break;
+    case DOM_IFY: ex = G.n0; ey = G.n1 + 1; oy = -1; break;
+    case DOM_IFZ: ex = G.n0; ey = G.n1; oz = -1; break;
+    case DOM_GX: i = 0; j = (int)(q % G.n1); k = (int)(q / G.n1); return;
+    case DOM_GY: i = (int)(q % (G.n0 + 6)) - 3; j = 0; k = (int)(q / (G.n0 + 6)); return;
+    default: i = (int)(q % (G.n0 + 6)) - 3; j = (int)(q / (G.n0 + 6)) - 3; k = 0; return;
+  }
+  i = (int)(q % ex) + ox;
+  q /= ex;
+  j = (int)(q % ey) + oy;
+  k = (int)(q / ey) + oz;
+}
+
+struct C2PStats {
+  unsigned long long points, iters, corrected, failed;
+};
+
+// Device error flags: bit 0 fatal con2prim point, bit 1 non-finite input.
+struct DevFlags {
+  int flags;
+  int worst_status;
+};
+
+Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T);
+
+// Launchers (host functions in the .cu files; all enqueue on `st`).
+void launch_init(const PatchDev* pd, int p, const Geo& G, const grmhd_params& P, const Eos& E, const double* id,
+                 double* U, cudaStream_t st);
+void launch_ghost(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int axis, int bc, cudaStream_t st);
+void launch_c2p(const PatchDev* pd_dev, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
+                DevFlags* flags, C2PStats* stats, cudaStream_t st);
+void launch_iflux(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int dir, cudaStream_t st);
+void launch_rhs(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int mode, int stage, double dt,
+                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st);
+void launch_rk(const PatchDev* pd_dev, const Work* w, int nblk, int stage, double dt, double* const* rhs_dev,
+               cudaStream_t st);
+void launch_c2p_flat(const grmhd_params& P, const Eos& E, long long n, const double* cons, double* prim,
+                     int8_t* status, int32_t* iters, cudaStream_t st);
+void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, const double* prim, const double* B,
+                          double* cons, cudaStream_t st);
+
+// Block sizes of the launches (threads per block).
+constexpr int BS_ALL = 128;
+constexpr int BS_INT = 128;
+constexpr int BS_IF = 128;
+
+}  // namespace gk

@@ -1,0 +1,436 @@
+// Point-wise and interface kernels of the substep: initial-data conversion,
+// ghost fill, con2prim with the point-wise MHD fluxes and speeds, interface
+// fluxes (Lax-Friedrichs split + MP5), the unfused RK4 stage combination and
+// the flat-metric con2prim of independent states.
+#include "kern.cuh"
+
+namespace gk {
+
+Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T) {
+  Eos E;
+  E.kind = P.eos_kind;
+  E.gam = P.gamma_th;
+  E.K = P.K_atmo;
+  E.eps_max = P.eps_max;
+  E.nr = E.nt = E.ny = 0;
+  E.lr0 = E.idlr = E.lt0 = E.dlt = E.idlt = E.ye0 = E.idye = 0.0;
+  E.p = E.e = E.c = nullptr;
+  if (T && P.eos_kind == 1) {
+    E.nr = T->nr;
+    E.nt = T->nt;
+    E.ny = T->ny;
+    E.lr0 = T->lr0;
+    E.idlr = 1.0 / T->dlr;
+    E.lt0 = T->lt0;
+    E.dlt = T->dlt;
+    E.idlt = 1.0 / T->dlt;
+    E.ye0 = T->ye0;
+    E.idye = 1.0 / T->dye;
+    E.p = T->p;
+    E.e = T->eps;
+    E.c = T->cs2;
+  }
+  return E;
+}
+
+// ---------------------------------------------------------------------------
+// Initial data -> CCZ4 variables and conserved variables at every point.
+__global__ void k_init(Geo G, grmhd_params P, Eos E, const double* __restrict__ id, double* __restrict__ U) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= dom_count(DOM_ALL, G)) return;
+  int i, j, k;
+  dom_decode(DOM_ALL, G, q, i, j, k);
+  long long o = at(G, i, j, k);
+  const long long sf = G.sf;
+  double g[6], K[6], gu[6];
+  for (int n = 0; n < 6; ++n) {
+    g[n] = id[(IG + n) * sf + o];
+    K[n] = id[(IK + n) * sf + o];
+  }
+  double det = det3(g);
+  inv3(g, 1.0 / det, gu);
+  double chi = 1.0 / cbrt(det);
+  double trK = tr6(gu, K);
+  for (int n = 0; n < 6; ++n) {
+    U[(GT + n) * sf + o] = chi * g[n];
+    U[(AT + n) * sf + o] = chi * fma(-g[n], trK * (1.0 / 3.0), K[n]);
+  }
+  U[CHI * sf + o] = chi;
+  U[KH * sf + o] = trK;
+  U[TH * sf + o] = 0.0;
+  U[ALP * sf + o] = id[IALP * sf + o];
+  for (int a = 0; a < 3; ++a) U[(BET + a) * sf + o] = id[(IBET + a) * sf + o];
+  double rho = id[IRHO * sf + o], ye = id[IYE * sf + o];
+  double eps, p;
+  if (P.eos_kind == 0) {
+    eps = id[IEPS * sf + o];
+    p = (P.gamma_th - 1.0) * rho * eps;
+  } else {
+    EosOut eo = eos_T(E, rho, id[IT * sf + o], ye);
+    eps = eo.eps;
+    p = eo.p;
+  }
+  double v[3] = {id[IV * sf + o], id[(IV + 1) * sf + o], id[(IV + 2) * sf + o]};
+  double B[3] = {id[IB * sf + o], id[(IB + 1) * sf + o], id[(IB + 2) * sf + o]};
+  double c6[6];
+  prim2con(g, rho, eps, p, v, ye, B, c6);
+  double sg = sqrt(det);
+  for (int n = 0; n < 6; ++n) U[(DD + n) * sf + o] = c6[n] * sg;
+  for (int a = 0; a < 3; ++a) U[(BB + a) * sf + o] = B[a] * sg;
+  U[PHI * sf + o] = 0.0;
+}
+
+// Gammahat^i = gt^ij gt^kl d_l gt_jk at interior points (same D_i as the RHS).
+__global__ void k_init_gh(Geo G, double* __restrict__ U) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= dom_count(DOM_INT, G)) return;
+  int i, j, k;
+  dom_decode(DOM_INT, G, q, i, j, k);
+  long long o = at(G, i, j, k);
+  const long long sf = G.sf;
+  const long long st[3] = {1, G.sy, G.sz};
+  const double i12 = 1.0 / (12.0 * G.dx);
+  double g[6], gu[6], dg[3][6];
+  for (int n = 0; n < 6; ++n) {
+    g[n] = U[(GT + n) * sf + o];
+    for (int a = 0; a < 3; ++a) dg[a][n] = fd1(U + (GT + n) * sf + o, st[a]) * i12;
+  }
+  inv3(g, 1.0 / det3(g), gu);
+  double t[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) s = fma(gu[S6(kk, l)], dg[l][S6(a, kk)], s);
+    t[a] = s;
+  }
+  for (int a = 0; a < 3; ++a)
+    U[(GH + a) * sf + o] = gu[S6(a, 0)] * t[0] + gu[S6(a, 1)] * t[1] + gu[S6(a, 2)] * t[2];
+}
+
+void launch_init(const PatchDev*, int, const Geo& G, const grmhd_params& P, const Eos& E, const double* id, double* U,
+                 cudaStream_t st) {
+  long long n = dom_count(DOM_ALL, G);
+  k_init<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(G, P, E, id, U);
+  long long m = dom_count(DOM_INT, G);
+  k_init_gh<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(G, U);
+}
+
+// ---------------------------------------------------------------------------
+// Ghost fill along one axis: each thread owns one line and fills its 3 + 3
+// ghost points for all 32 fields.
+template <int AX>
+__global__ void k_ghost(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg, int bc) {
+  Work wk = w[blockIdx.x];
+  const PatchDev& PD = pd[wk.patch];
+  const Geo& G = PD.G;
+  constexpr int dom = AX == 0 ? DOM_GX : (AX == 1 ? DOM_GY : DOM_GZ);
+  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
+  if (q >= dom_count(dom, G)) return;
+  int i, j, k;
+  dom_decode(dom, G, q, i, j, k);
+  long long o = at(G, i, j, k);
+  const long long s = AX == 0 ? 1 : (AX == 1 ? G.sy : G.sz);
+  const int n = AX == 0 ? G.n0 : (AX == 1 ? G.n1 : G.n2);
+  double* U = PD.U[reg];
+  for (int f = 0; f < NF; ++f) {
+    double* b = U + f * G.sf + o;
+    if (bc == 0) {
+#pragma unroll
+      for (int m = 1; m <= 3; ++m) {
+        b[-m * s] = b[(n - m) * s];
+        b[(n - 1 + m) * s] = b[(m - 1) * s];
+      }
+    } else {
+      double u0 = b[0], u1 = b[s], v0 = b[(n - 1) * s], v1 = b[(n - 2) * s];
+#pragma unroll
+      for (int m = 1; m <= 3; ++m) {
+        b[-m * s] = fma(1.0 + m, u0, -(double)m * u1);
+        b[(n - 1 + m) * s] = fma(1.0 + m, v0, -(double)m * v1);
+      }
+    }
+  }
+}
+
+void launch_ghost(const PatchDev* pd, const Work* w, int nblk, int reg, int axis, int bc, cudaStream_t st) {
+  if (nblk <= 0) return;
+  if (axis == 0) k_ghost<0><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc);
+  if (axis == 1) k_ghost<1><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc);
+  if (axis == 2) k_ghost<2><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc);
+}
+
+// ---------------------------------------------------------------------------
+// con2prim at every point, then the point-wise flux vectors F^d (10 fields)
+// and max |lambda^{+-}_fast| along d for the directions whose interface
+// stencils use this point.
+template <bool STATS>
+__global__ void __launch_bounds__(BS_ALL) k_c2p(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
+                                                 grmhd_params P, Eos E, DevFlags* flags, C2PStats* stats) {
+  Work wk = w[blockIdx.x];
+  const PatchDev& PD = pd[wk.patch];
+  const Geo G = PD.G;
+  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
+  bool active = q < dom_count(DOM_ALL, G);
+  int st_code = 0, iters = 0;
+  if (active) {
+    int i, j, k;
+    dom_decode(DOM_ALL, G, q, i, j, k);
+    const long long o = at(G, i, j, k), sf = G.sf;
+    double* U = PD.U[reg];
+    double gt[6], gtu[6], gdd[6], guu[6];
+    for (int n = 0; n < 6; ++n) gt[n] = U[(GT + n) * sf + o];
+    double chi = U[CHI * sf + o];
+    double det = det3(gt);
+    inv3(gt, 1.0 / det, gtu);
+    double ichi = 1.0 / chi;
+    for (int n = 0; n < 6; ++n) {
+      gdd[n] = gt[n] * ichi;
+      guu[n] = chi * gtu[n];
+    }
+    double sg = sqrt(det) * ichi * sqrt(ichi);
+    double cb[9];
+    for (int n = 0; n < 9; ++n) cb[n] = U[(DD + n) * sf + o];
+    double al = U[ALP * sf + o];
+    C2POut r;
+    c2p_point(P, E, cb, gdd, guu, sg, al, r);
+    st_code = r.status;
+    iters = r.iters;
+    for (int n = 0; n < NP; ++n) PD.prim[n * sf + o] = r.prim[n];
+    PD.status[o] = (int8_t)r.status;
+    if (r.status > 0)
+      for (int n = 0; n < 6; ++n) {
+        U[(DD + n) * sf + o] = r.cons[n];
+        cb[n] = r.cons[n];
+      }
+    if (r.status < 0) atomicOr(&flags->flags, r.status == -5 ? 2 : 1);
+
+    // Which directions need this point: interior in the two other axes.
+    bool inx = (i >= 0 && i < G.n0), iny = (j >= 0 && j < G.n1), inz = (k >= 0 && k < G.n2);
+    bool need[3] = {iny && inz, inx && inz, inx && iny};
+    if (need[0] || need[1] || need[2]) {
+      const double* pr = r.prim;
+      double v[3] = {pr[VX], pr[VY], pr[VZ]};
+      double isg = 1.0 / sg;
+      double B[3] = {cb[6] * isg, cb[7] * isg, cb[8] * isg};
+      double Sl[3] = {cb[3] * isg, cb[4] * isg, cb[5] * isg};
+      double vd[3], Bd[3];
+      lower3(gdd, v, vd);
+      lower3(gdd, B, Bd);
+      double v2 = v[0] * vd[0] + v[1] * vd[1] + v[2] * vd[2];
+      double B2 = B[0] * Bd[0] + B[1] * Bd[1] + B[2] * Bd[2];
+      double Bv = B[0] * vd[0] + B[1] * vd[1] + B[2] * vd[2];
+      double W = pr[WW];
+      double iW2 = 1.0 / (W * W);
+      double piso = pr[PRS] + 0.5 * fma(iW2, B2, Bv * Bv);
+      double Sij[6];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = a; b < 3; ++b) {
+          double t = 0.5 * fma(vd[a], Sl[b], vd[b] * Sl[a]) - iW2 * Bd[a] * Bd[b] -
+                     0.5 * Bv * fma(Bd[a], vd[b], Bd[b] * vd[a]);
+          Sij[S6(a, b)] = fma(gdd[S6(a, b)], piso, t);
+        }
+      double be[3] = {U[BET * sf + o], U[(BET + 1) * sf + o], U[(BET + 2) * sf + o]};
+      double phib = U[PHI * sf + o];
+      double b2 = fma(B2, iW2, Bv * Bv);
+      double h = fma(pr[RHO], 1.0 + pr[EPS], pr[PRS]);
+      double ca2 = b2 / (h + b2);
+      double cs2 = pr[CS2];
+      double a2 = cs2 + ca2 - cs2 * ca2;
+      double den = fma(-v2, a2, 1.0);
+      double pre = al / den;
+      double a2w = a2 * (1.0 - v2);
+      double oma2 = 1.0 - a2;
+      const double cb2 = P.c_b * P.c_b;
+      double avb[3];
+      for (int a = 0; a < 3; ++a) avb[a] = fma(al, v[a], -be[a]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!need[d]) continue;
+        double* F = PD.Fp + (long long)d * 10 * sf + o;
+        F[0 * sf] = avb[d] * cb[0];
+        F[1 * sf] = avb[d] * cb[1];
+        double Sbu = guu[S6(d, 0)] * cb[3] + guu[S6(d, 1)] * cb[4] + guu[S6(d, 2)] * cb[5];
+        F[2 * sf] = fma(-be[d], cb[2], al * fma(-cb[0], v[d], Sbu));
+        double asg = al * sg;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          double Sm = guu[S6(d, 0)] * Sij[S6(0, a)] + guu[S6(d, 1)] * Sij[S6(1, a)] + guu[S6(d, 2)] * Sij[S6(2, a)];
+          F[(3 + a) * sf] = fma(-be[d], cb[3 + a], asg * Sm);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          F[(6 + a) * sf] = fma(cb[6 + a], avb[d], fma(-cb[6 + d], avb[a], al * chi * gtu[S6(d, a)] * phib));
+        F[9 * sf] = fma(-be[d], phib, al * cb2 * cb[6 + d]);
+        double rad = sqrt(a2w * fma(den, guu[S6(d, d)], -oma2 * v[d] * v[d]));
+        double c = fma(pre * oma2, v[d], -be[d]);
+        PD.lam[(long long)d * sf + o] = fma(pre, rad, fabs(c));
+      }
+    }
+  }
+  if (STATS) {
+    unsigned long long it = iters, cor = st_code > 0, bad = st_code < 0, pts = active;
+    for (int off = 16; off > 0; off >>= 1) {
+      it += __shfl_down_sync(0xffffffffu, it, off);
+      cor += __shfl_down_sync(0xffffffffu, cor, off);
+      bad += __shfl_down_sync(0xffffffffu, bad, off);
+      pts += __shfl_down_sync(0xffffffffu, pts, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&stats->iters, it);
+      atomicAdd(&stats->corrected, cor);
+      atomicAdd(&stats->failed, bad);
+      atomicAdd(&stats->points, pts);
+    }
+  }
+}
+
+void launch_c2p(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
+                DevFlags* flags, C2PStats* stats, cudaStream_t st) {
+  if (nblk <= 0) return;
+  if (stats)
+    k_c2p<true><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, P, E, flags, stats);
+  else
+    k_c2p<false><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, P, E, flags, stats);
+}
+
+// ---------------------------------------------------------------------------
+// Interface fluxes along direction D: lambda = max over points i-2 .. i+3,
+// g^{+-} = F +- lambda U, F^L = MP5(g^+_{i-2..i+2}), F^R = MP5(g^-_{i+3..i-1}),
+// Fhat = (F^L + F^R) / 2 (MP5 commutes with the positive factor 1/2).
+template <int D>
+__global__ void __launch_bounds__(BS_IF) k_iflux(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg) {
+  Work wk = w[blockIdx.x];
+  const PatchDev& PD = pd[wk.patch];
+  const Geo G = PD.G;
+  constexpr int dom = D == 0 ? DOM_IFX : (D == 1 ? DOM_IFY : DOM_IFZ);
+  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
+  if (q >= dom_count(dom, G)) return;
+  int i, j, k;
+  dom_decode(dom, G, q, i, j, k);
+  const long long o = at(G, i, j, k), sf = G.sf;
+  const long long s = D == 0 ? 1 : (D == 1 ? G.sy : G.sz);
+  const double* lam = PD.lam + (long long)D * sf + o;
+  double L = ld(lam - 2 * s);
+#pragma unroll
+  for (int m = -1; m <= 3; ++m) L = fmax(L, ld(lam + m * s));
+  const double* Fp = PD.Fp + (long long)D * 10 * sf + o;
+  const double* Uc = PD.U[reg] + (long long)DD * sf + o;
+  double* Fh = PD.Fh + (long long)D * 10 * sf + o;
+#pragma unroll 1
+  for (int f = 0; f < 10; ++f) {
+    double gp[6], gm[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      double Fv = ld(Fp + f * sf + (m - 2) * s), Uv = ld(Uc + f * sf + (m - 2) * s);
+      gp[m] = fma(L, Uv, Fv);
+      gm[m] = fma(-L, Uv, Fv);
+    }
+    double FL = mp5(gp[0], gp[1], gp[2], gp[3], gp[4]);
+    double FR = mp5(gm[5], gm[4], gm[3], gm[2], gm[1]);
+    Fh[f * sf] = 0.5 * (FL + FR);
+  }
+}
+
+void launch_iflux(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st) {
+  if (nblk <= 0) return;
+  if (dir == 0) k_iflux<0><<<nblk, BS_IF, 0, st>>>(pd, w, reg);
+  if (dir == 1) k_iflux<1><<<nblk, BS_IF, 0, st>>>(pd, w, reg);
+  if (dir == 2) k_iflux<2><<<nblk, BS_IF, 0, st>>>(pd, w, reg);
+}
+
+// ---------------------------------------------------------------------------
+// Unfused RK4 stage combination at interior points.
+__global__ void k_rk(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int stage, double dt,
+                     double* const* __restrict__ rhs) {
+  Work wk = w[blockIdx.x];
+  const PatchDev& PD = pd[wk.patch];
+  const Geo G = PD.G;
+  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
+  if (q >= dom_count(DOM_INT, G)) return;
+  int i, j, k;
+  dom_decode(DOM_INT, G, q, i, j, k);
+  const long long o = at(G, i, j, k), sf = G.sf;
+  const double* K = rhs[wk.patch];
+  double *Un = PD.U[0], *Ua = PD.U[1], *Ub = PD.U[2], *acc = PD.U[3];
+  for (int f = 0; f < NF; ++f) {
+    long long x = f * sf + o;
+    double kk = K[x];
+    if (stage == 0) {
+      double u = Un[x];
+      Ua[x] = fma(0.5 * dt, kk, u);
+      acc[x] = fma(dt / 6.0, kk, u);
+    } else if (stage == 1) {
+      Ub[x] = fma(0.5 * dt, kk, Un[x]);
+      acc[x] = fma(dt / 3.0, kk, acc[x]);
+    } else if (stage == 2) {
+      Ua[x] = fma(dt, kk, Un[x]);
+      acc[x] = fma(dt / 3.0, kk, acc[x]);
+    } else {
+      Un[x] = fma(dt / 6.0, kk, acc[x]);
+    }
+  }
+}
+
+void launch_rk(const PatchDev* pd, const Work* w, int nblk, int stage, double dt, double* const* rhs, cudaStream_t st) {
+  if (nblk <= 0) return;
+  k_rk<<<nblk, BS_INT, 0, st>>>(pd, w, stage, dt, rhs);
+}
+
+// ---------------------------------------------------------------------------
+// con2prim of independent states with a flat metric (alpha = 1).
+__global__ void __launch_bounds__(128) k_c2p_flat(grmhd_params P, Eos E, long long n, const double* __restrict__ cons,
+                                                   double* __restrict__ prim, int8_t* __restrict__ status,
+                                                   int32_t* __restrict__ iters) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double g[6] = {1.0, 0.0, 0.0, 1.0, 0.0, 1.0};
+  double cb[9];
+  for (int m = 0; m < 9; ++m) cb[m] = ld(cons + q * 10 + m);
+  C2POut r;
+  c2p_point(P, E, cb, g, g, 1.0, 1.0, r);
+  for (int m = 0; m < NP; ++m) prim[q * NP + m] = r.prim[m];
+  status[q] = (int8_t)r.status;
+  if (iters) iters[q] = r.iters;
+}
+
+__global__ void k_prim2con_flat(grmhd_params P, Eos E, long long n, const double* __restrict__ prim,
+                                const double* __restrict__ B, double* __restrict__ cons) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double g[6] = {1.0, 0.0, 0.0, 1.0, 0.0, 1.0};
+  const double* pr = prim + q * NP;
+  double rho = pr[RHO], ye = pr[YE], eps, p;
+  if (P.eos_kind == 1) {
+    EosOut eo = eos_T(E, rho, pr[TT], ye);
+    eps = eo.eps;
+    p = eo.p;
+  } else {
+    eps = pr[EPS];
+    p = (P.gamma_th - 1.0) * rho * eps;
+  }
+  double v[3] = {pr[VX], pr[VY], pr[VZ]};
+  double b[3] = {B[q * 3], B[q * 3 + 1], B[q * 3 + 2]};
+  double c6[6];
+  prim2con(g, rho, eps, p, v, ye, b, c6);
+  for (int m = 0; m < 6; ++m) cons[q * 10 + m] = c6[m];
+  for (int m = 0; m < 3; ++m) cons[q * 10 + 6 + m] = b[m];
+  cons[q * 10 + 9] = 0.0;
+}
+
+void launch_c2p_flat(const grmhd_params& P, const Eos& E, long long n, const double* cons, double* prim,
+                     int8_t* status, int32_t* iters, cudaStream_t st) {
+  if (n <= 0) return;
+  k_c2p_flat<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(P, E, n, cons, prim, status, iters);
+}
+
+void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, const double* prim, const double* B,
+                          double* cons, cudaStream_t st) {
+  if (n <= 0) return;
+  k_prim2con_flat<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(P, E, n, prim, B, cons);
+}
+
+}  // namespace gk

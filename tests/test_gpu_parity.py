@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (normwise per field per patch, max |gpu - oracle| / max |oracle|):
+  initial-data conversion 1e-13, right-hand side 1e-11, primitives 1e-10
+  (rho, Ye relative; W v^i absolute; eps and p scaled by max(1, (1 + q) / |eps|)),
+  RK4 state after 100 steps 1e-9.  Integer outputs (con2prim status) are bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2510_13965_gb300 as g  # noqa: E402
+
+NF, NP = 32, 10
+INT = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
+
+
+def _interior(a, n):
+    return a[:, 3:3 + n[2], 3:3 + n[1], 3:3 + n[0]]
+
+
+def _field_err(got, want):
+    gg = got.reshape(got.shape[0], -1)
+    ww = want.reshape(want.shape[0], -1)
+    scale = np.maximum(np.abs(ww).max(axis=1), 1e-30)
+    return np.abs(gg - ww).max(axis=1) / scale
+
+
+def _setup(P, n, dx, ID, table=None):
+    T = g.Table(table) if table is not None else None
+    pt = g.Patches(P, [dict(n=n, dx=dx)], table=T)
+    pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    O = oracle.Oracle(P, table)
+    U = O.init_state(ID, n, dx)
+    return pt, O, U
+
+
+def _prim_check(gp, op, gst, ost, cons):
+    ok = (gst == 0) & (ost == 0)
+    assert np.array_equal(gst, ost)
+    rho_g, rho_o = gp[0][ok], op[0][ok]
+    assert np.all(np.abs(rho_g - rho_o) <= 1e-10 * rho_o)
+    assert np.all(np.abs(gp[7][ok] - op[7][ok]) <= 1e-10 * np.abs(op[7][ok]))
+    wv_g = gp[3:6][:, ok] * gp[6][ok]
+    wv_o = op[3:6][:, ok] * op[6][ok]
+    assert np.all(np.abs(wv_g - wv_o) <= 1e-10)
+    q = cons[2][ok] / cons[0][ok]
+    kap = np.maximum(1.0, (1.0 + np.abs(q)) / np.maximum(np.abs(op[1][ok]), 1e-300))
+    assert np.all(np.abs(gp[1][ok] - op[1][ok]) <= 1e-10 * kap * np.abs(op[1][ok]) + 1e-300)
+    assert np.all(np.abs(gp[2][ok] - op[2][ok]) <= 1e-10 * kap * np.abs(op[2][ok]) + 1e-300)
+
+
+CASES = {
+    "fourier_periodic_32": lambda: (synth.ideal_params(bc=0), (32, 32, 32), 1 / 32,
+                                     synth.config0_id(n=(32, 32, 32), seed=0)),
+    "fourier_ragged_extrap": lambda: (synth.ideal_params(bc=1), (20, 12, 17), 1 / 20,
+                                       synth.config0_id(n=(20, 12, 17), seed=5)),
+    "tov_40": lambda: (synth.ideal_params(bc=1), (40, 40, 40), 0.5,
+                       synth.tov_id(n=(40, 40, 40), x0=(-10, -10, -10), dx=0.5, seed=1)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_init_con2prim_rhs_parity(case):
+    P, n, dx, ID = CASES[case]()
+    pt, O, U = _setup(P, n, dx, ID)
+    pt.synchronize()
+    Ug = pt.U[0][0].cpu().numpy()
+    # Initial-data conversion, ghosts included.
+    assert np.all(_field_err(Ug, U) < 1e-13), _field_err(Ug, U)
+    # con2prim on both sides from each side's own state.
+    pt.con2prim(0)
+    rhs_g = pt.rhs_eval(0)[0]
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    prim_o, st_o, worst, its = O.con2prim_patch(U, n)
+    _prim_check(pt.prim[0].cpu().numpy(), prim_o, pt.status[0].cpu().numpy(), st_o, U[22:25])
+    rhs_o = O.rhs_patch(U, prim_o, n, dx)
+    err = _field_err(_interior(rhs_g.cpu().numpy(), n), _interior(rhs_o, n))
+    assert np.all(err < 1e-11), dict(enumerate(err))
+
+
+def test_flat_space_constant_gauge_exact_zero_on_gpu():
+    P = synth.ideal_params(bc=0, eta=0.0)
+    n = (8, 8, 8)
+    shp = synth.patch_shape(n)
+    ID = np.zeros((26,) + shp)
+    ID[0] = ID[3] = ID[5] = 1.0
+    ID[12] = 0.7
+    ID[13], ID[14], ID[15] = 0.1, -0.2, 0.3
+    ID[16], ID[17], ID[24] = 1e-3, 0.1, 0.1
+    ID[18:21] = np.array([0.2, -0.1, 0.05])[:, None, None, None]
+    ID[21:24] = np.array([0.01, 0.02, -0.01])[:, None, None, None]
+    pt = g.Patches(P, [dict(n=n, dx=0.1)])
+    pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    pt.con2prim(0)
+    r = pt.rhs_eval(0)[0].cpu().numpy()
+    # MHD of a uniform state: exactly zero.  Spacetime: zero except the matter sources.
+    assert np.all(r[22:][INT] == 0.0)
+    # No matter term enters gt_ij, chi or beta^i (eta = 0, Gammahat = 0).
+    for f in (0, 1, 2, 3, 4, 5, 12, 19, 20, 21):
+        assert np.all(r[f][INT[1:]] == 0.0), f
+
+
+def test_rk4_steps_parity_fourier():
+    P, n, dx, ID = synth.ideal_params(bc=0), (16, 16, 16), 1 / 16, synth.config0_id(n=(16, 16, 16), seed=2)
+    pt, O, U = _setup(P, n, dx, ID)
+    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    prim = np.zeros((NP,) + U.shape[1:])
+    st = np.zeros(U.shape[1:], dtype=np.int8)
+    dt = 0.4 * dx
+    for _ in range(5):
+        pt.step(dt)
+        O.rk4_step(regs, prim, st, n, dx, dt)
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    err = _field_err(_interior(pt.U[0][0].cpu().numpy(), n), _interior(regs[0], n))
+    assert np.all(err < 1e-10), err
+
+
+def test_unfused_rk_update_matches_fused():
+    P, n, dx, ID = synth.ideal_params(bc=0), (12, 12, 12), 1 / 12, synth.config0_id(n=(12, 12, 12), seed=4)
+    a = g.Patches(P, [dict(n=n, dx=dx)])
+    b = g.Patches(P, [dict(n=n, dx=dx)])
+    for pt in (a, b):
+        pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    dt = 0.4 * dx
+    a.step(dt)
+    reg_in = [0, 1, 2, 1]
+    for s in range(4):
+        b.ghost_fill(reg_in[s])
+        b.con2prim(reg_in[s])
+        k = b.rhs_eval(reg_in[s])
+        b.rk_update(s, dt, k)
+    a.synchronize()
+    b.synchronize()
+    ua, ub = _interior(a.U[0][0].cpu().numpy(), n), _interior(b.U[0][0].cpu().numpy(), n)
+    assert np.array_equal(ua, ub)
+
+
+def test_graph_replay_equals_eager_and_is_deterministic():
+    P, n, dx, ID = synth.ideal_params(bc=0), (16, 16, 16), 1 / 16, synth.config0_id(n=(16, 16, 16), seed=3)
+    a = g.Patches(P, [dict(n=n, dx=dx)])
+    b = g.Patches(P, [dict(n=n, dx=dx)])
+    c = g.Patches(P, [dict(n=n, dx=dx)])
+    for pt in (a, b, c):
+        pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    dt = 0.4 * dx
+    b.capture_graph(2, dt)
+    for _ in range(2):
+        a.step(dt)
+        c.step(dt)
+    b.graph_launch()
+    for pt in (a, b, c):
+        pt.synchronize()
+    ua, ub, uc = (pt.U[0][0].cpu().numpy() for pt in (a, b, c))
+    assert np.array_equal(_interior(ua, n), _interior(ub, n))
+    assert np.array_equal(ua, uc)
+
+
+def test_tov_100_steps_parity():
+    n, dx = (24, 24, 24), 0.8
+    P = synth.ideal_params(bc=1)
+    ID = synth.tov_id(n=n, x0=(-9.6, -9.6, -9.6), dx=dx, seed=1)
+    pt, O, U = _setup(P, n, dx, ID)
+    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    prim = np.zeros((NP,) + U.shape[1:])
+    st = np.zeros(U.shape[1:], dtype=np.int8)
+    dt = 0.4 * dx
+    pt.capture_graph(10, dt)
+    for _ in range(10):
+        pt.graph_launch()
+        for _ in range(10):
+            O.rk4_step(regs, prim, st, n, dx, dt)
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    err = _field_err(_interior(pt.U[0][0].cpu().numpy(), n), _interior(regs[0], n))
+    assert np.all(err < 1e-9), dict(enumerate(err))
+
+
+def test_full_size_tov_sampled_points():
+    """128^3 TOV star (the benchmark workload): the GPU right-hand side at sampled
+    points, each recomputed by the oracle from the full state."""
+    n, dx = (128, 128, 128), 0.3125
+    P = synth.ideal_params(bc=1)
+    ID = synth.tov_id(n=n, x0=(-20.0, -20.0, -20.0), dx=dx, seed=1)
+    pt = g.Patches(P, [dict(n=n, dx=dx)])
+    pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    pt.ghost_fill(0)
+    pt.con2prim(0)
+    rhs_g = pt.rhs_eval(0)[0]
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    Ug = pt.U[0][0].cpu().numpy()
+    pg = pt.prim[0].cpu().numpy()
+    O = oracle.Oracle(P)
+    U = O.init_state(ID, n, dx)
+    assert np.all(_field_err(Ug, U) < 1e-13)
+    prim_o, st_o, worst, its = O.con2prim_patch(U, n)
+    _prim_check(pg, prim_o, pt.status[0].cpu().numpy(), st_o, U[22:25])
+    rng = np.random.default_rng(0)
+    pts = [(0, 0, 0), (127, 127, 127), (64, 64, 64), (0, 64, 127), (63, 64, 65), (90, 40, 64)]
+    pts += [tuple(int(v) for v in rng.integers(0, 128, 3)) for _ in range(58)]
+    ijk = np.array(pts, dtype=np.int32)
+    want = O.rhs_points(U, prim_o, n, dx, ijk)
+    rg = rhs_g.cpu().numpy()
+    got = np.array([rg[:, k + 3, j + 3, i + 3] for (i, j, k) in pts])
+    scale = np.maximum(np.abs(_interior(rg, n)).reshape(NF, -1).max(axis=1), 1e-30)
+    err = np.abs(got - want).max(axis=0) / scale
+    assert np.all(err < 1e-11), dict(enumerate(err))
+
+
+@pytest.mark.parametrize("kind", ["ideal", "table"])
+def test_c2p_flat_parity(kind):
+    N = 1 << 14
+    if kind == "ideal":
+        table = None
+        P = synth.ideal_params()
+        rng = np.random.default_rng(9)
+        prim = np.zeros((N, NP))
+        prim[:, 0] = 10 ** rng.uniform(-6, -2, N)
+        prim[:, 1] = 10 ** rng.uniform(-3, 0.5, N)
+        v = rng.normal(size=(N, 3))
+        v *= (rng.uniform(0, 0.9, N) / np.linalg.norm(v, axis=1))[:, None]
+        prim[:, 3:6] = v
+        prim[:, 7] = 0.1
+        B = rng.normal(size=(N, 3)) * np.sqrt(prim[:, :1]) * 0.5
+    else:
+        table = synth.make_table(nr=64, nt=48, ny=16)
+        P = synth.table_params(table)
+        s = synth.c2p_states(N, seed=3)
+        prim = np.zeros((N, NP))
+        prim[:, 0], prim[:, 8], prim[:, 7] = s["rho"], s["T"], s["ye"]
+        prim[:, 3:6] = s["v"]
+        B = s["B"]
+    O = oracle.Oracle(P, table)
+    # Conserved states from the oracle's own prim2con; the same array feeds both sides.
+    cons = np.zeros((N, 10))
+    for q in range(N):
+        pr = prim[q].copy()
+        if kind == "table":
+            e = O.eos_from_T(pr[0], pr[8], pr[7])
+            pr[1], pr[2] = e[1], e[0]
+        else:
+            pr[2] = pr[0] * pr[1]
+        cons[q, :9] = oracle.prim2con_point(pr, B[q], [1.0, 0, 0, 1.0, 0, 1.0])
+    T = g.Table(table) if table is not None else None
+    cg = torch.as_tensor(cons, device="cuda")
+    pg, sg_, ig = g.c2p_flat(P, cg, table=T, iters=True)
+    torch.cuda.synchronize()
+    po, so, io = O.c2p_flat(cons)
+    _prim_check(pg.cpu().numpy().T, po.T, sg_.cpu().numpy(), so, cons[:, :3].T)
+
+
+def test_c2p_status_codes_match_oracle():
+    P = synth.ideal_params(eps_max=0.05, W_max=5.0, rho_max=1e-2)
+    O = oracle.Oracle(P)
+    states = []
+    for rho, eps, v, ye in [(1e-12, 0.1, 0.3, 0.1), (2e-2, 0.01, 0.0, 0.1), (1e-3, 0.1, 0.0, 0.1),
+                            (1e-9, 0.1, 0.0, 0.1), (1e-3, 0.01, 0.995, 0.1), (1e-9, 0.01, 0.995, 0.1),
+                            (1e-3, 0.01, 0.0, 0.9), (1e-9, 0.01, 0.0, 0.9), (1e-3, 0.01, 0.2, 0.1)]:
+        pr = np.zeros(NP)
+        pr[0], pr[1], pr[2], pr[3], pr[7] = rho, eps, rho * eps, v, ye
+        c = np.zeros(10)
+        c[:9] = oracle.prim2con_point(pr, [0, 0, 0], [1.0, 0, 0, 1.0, 0, 1.0])
+        states.append(c)
+    c = np.zeros(10)
+    c[0], c[1], c[2] = np.nan, 1e-5, 1e-4
+    states.append(c)
+    cons = np.array(states)
+    pg, sg_ = g.c2p_flat(P, torch.as_tensor(cons, device="cuda"))
+    po, so, io = O.c2p_flat(cons)
+    assert np.array_equal(sg_.cpu().numpy(), so)
+    assert sorted(set(so.tolist())) == [-5, -4, -3, -2, -1, 0, 1, 2, 4, 8]
