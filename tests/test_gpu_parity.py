@@ -43,13 +43,30 @@ def _setup(P, n, dx, ID, table=None):
     return pt, O, U
 
 
+NOISE = 1e-12  # RHS components below this norm vanish analytically (rounding noise only)
+
+
 def _init_ok(Ug, U):
-    """Initial-data conversion: 1e-13, except Gammahat (fields 15-17, a centred
-    derivative of gt_ij ~ delta_ij + 1e-4, conditioned like a right-hand side): 1e-11."""
+    """Initial-data conversion: 1e-13 per field, except Gammahat (fields 15-17, a
+    centred derivative of gt_ij, conditioned like a right-hand side): 1e-11, or
+    1e-13 absolute where it vanishes analytically (conformally flat data)."""
     e = _field_err(Ug, U)
     tol = np.full(NF, 1e-13)
     tol[15:18] = 1e-11
-    return np.all(e < tol), e
+    d = np.abs(Ug - U).reshape(NF, -1).max(axis=1)
+    small = np.abs(U).reshape(NF, -1).max(axis=1) < 1e-12
+    ok = (e < tol) | (small & (d < 1e-13))
+    return bool(np.all(ok)), {f: e[f] for f in range(NF) if not ok[f]}
+
+
+def _rhs_ok(got, want, tol=1e-11):
+    """Right-hand side: normwise relative error per field <= tol; a field whose
+    oracle norm is below NOISE vanishes analytically and is held to 1e-14 absolute."""
+    e = _field_err(got, want)
+    d = np.abs(got - want).reshape(NF, -1).max(axis=1)
+    small = np.abs(want).reshape(NF, -1).max(axis=1) < NOISE
+    ok = np.where(small, d < 1e-14, e < tol)
+    return bool(np.all(ok)), {f: (e[f], d[f]) for f in range(NF) if not ok[f]}
 
 
 def _prim_check(gp, op, gst, ost, cons):
@@ -94,8 +111,8 @@ def test_init_con2prim_rhs_parity(case):
     prim_o, st_o, worst, its = O.con2prim_patch(U, n)
     _prim_check(pt.prim[0].cpu().numpy(), prim_o, pt.status[0].cpu().numpy(), st_o, U[22:25])
     rhs_o = O.rhs_patch(U, prim_o, n, dx)
-    err = _field_err(_interior(rhs_g.cpu().numpy(), n), _interior(rhs_o, n))
-    assert np.all(err < 1e-11), dict(enumerate(err))
+    ok, bad = _rhs_ok(_interior(rhs_g.cpu().numpy(), n), _interior(rhs_o, n))
+    assert ok, bad
 
 
 def test_flat_space_constant_gauge_exact_zero_on_gpu():
@@ -225,9 +242,8 @@ def test_full_size_tov_sampled_points():
     want = O.rhs_points(U, prim_o, n, dx, ijk)
     rg = rhs_g.cpu().numpy()
     got = np.array([rg[:, k + 3, j + 3, i + 3] for (i, j, k) in pts])
-    scale = np.maximum(np.abs(_interior(rg, n)).reshape(NF, -1).max(axis=1), 1e-30)
-    err = np.abs(got - want).max(axis=0) / scale
-    assert np.all(err < 1e-11), dict(enumerate(err))
+    ok, bad = _rhs_ok(got.T.copy(), want.T.copy())
+    assert ok, bad
 
 
 @pytest.mark.parametrize("kind", ["ideal", "table"])
