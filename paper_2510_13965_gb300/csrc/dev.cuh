@@ -67,10 +67,12 @@ DI double ld(const double* p) { return __ldg(p); }
 DI double fd1(const double* u, long long s) {
   return fma(8.0, ld(u + s) - ld(u - s), -(ld(u + 2 * s) - ld(u - 2 * s)));
 }
-// d2:  16 ((u1 + u-1) - 2 u0) - ((u2 + u-2) - 2 u0)   [x 1/(12 dx^2)]
+// d2:  16 ((u1 - u0) + (u-1 - u0)) - ((u2 - u0) + (u-2 - u0))     [x 1/(12 dx^2)]
+// Differences against the centre are exact for nearby values (Sterbenz), so
+// the stencil keeps full relative accuracy on small variations of O(1) fields.
 DI double fd2(const double* u, long long s, double c) {
-  double a = fma(-2.0, c, ld(u + s) + ld(u - s));
-  double b = fma(-2.0, c, ld(u + 2 * s) + ld(u - 2 * s));
+  double a = (ld(u + s) - c) + (ld(u - s) - c);
+  double b = (ld(u + 2 * s) - c) + (ld(u - 2 * s) - c);
   return fma(16.0, a, -b);
 }
 // mixed: d1 along s2 of d1 along s1      [x 1/(144 dx^2)]
@@ -85,21 +87,38 @@ DI double fdup(const double* u, long long s, double c) {
   double t3 = ld(u + 3 * s) - c, t2 = ld(u + 2 * s) - c, t1 = ld(u + s) - c, tm = ld(u - s) - c;
   return fma(-3.0, tm, fma(18.0, t1, fma(-6.0, t2, t3)));
 }
-// KO 7-point stencil:  (u-3 + u3 - 2u0) - 6 (u-2 + u2 - 2u0) + 15 (u-1 + u1 - 2u0)   [x sigma/(64 dx)]
+// KO 7-point stencil:  ((u-3 - u0) + (u3 - u0)) - 6 ((u-2 - u0) + (u2 - u0)) + 15 ((u-1 - u0) + (u1 - u0))
+//                                                                       [x sigma/(64 dx)]
 DI double fdko(const double* u, long long s, double c) {
-  double a3 = fma(-2.0, c, ld(u + 3 * s) + ld(u - 3 * s));
-  double a2 = fma(-2.0, c, ld(u + 2 * s) + ld(u - 2 * s));
-  double a1 = fma(-2.0, c, ld(u + s) + ld(u - s));
+  double a3 = (ld(u + 3 * s) - c) + (ld(u - 3 * s) - c);
+  double a2 = (ld(u + 2 * s) - c) + (ld(u - 2 * s) - c);
+  double a1 = (ld(u + s) - c) + (ld(u - s) - c);
   return fma(15.0, a1, fma(-6.0, a2, a3));
 }
 
+// ---- comparisons on the integer pipe ----------------------------------------
+// FP64 min / max / compare issue on the same narrow pipe as DFMA on GB300
+// (measured: fmin 1.3, compare+select 1.6, DFMA 1.6 lanes/clk/SM), while a
+// 64-bit integer compare runs ~5x wider.  okey() maps doubles to int64 with
+// the same order (-0 sorts just below +0), so min/max/sign tests move off the
+// FP64 pipe and return the same values for every non-NaN input.
+DI long long okey(double x) {
+  long long k = __double_as_longlong(x);
+  return k ^ ((k >> 63) & 0x7fffffffffffffffLL);
+}
+DI bool ipos(double x) { return __double_as_longlong(x) > 0; }  // x > 0
+DI bool ineg(double x) { return okey(x) < -1; }                 // x < 0 (okey(-0) = -1)
+DI double imin(double a, double b) { return okey(a) <= okey(b) ? a : b; }
+DI double imax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
+
 // ---- MP5 (Suresh & Huynh) with alpha = 4 ------------------------------------
+// Minmod(a, b) = (sgn a + sgn b)/2 min(|a|, |b|).
 DI double mm2(double a, double b) {
-  return (a > 0.0 && b > 0.0) ? fmin(a, b) : ((a < 0.0 && b < 0.0) ? fmax(a, b) : 0.0);
+  return (ipos(a) && ipos(b)) ? imin(a, b) : ((ineg(a) && ineg(b)) ? imax(a, b) : 0.0);
 }
 DI double mm4(double a, double b, double c, double d) {
-  if (a > 0.0 && b > 0.0 && c > 0.0 && d > 0.0) return fmin(fmin(a, b), fmin(c, d));
-  if (a < 0.0 && b < 0.0 && c < 0.0 && d < 0.0) return fmax(fmax(a, b), fmax(c, d));
+  if (ipos(a) && ipos(b) && ipos(c) && ipos(d)) return imin(imin(a, b), imin(c, d));
+  if (ineg(a) && ineg(b) && ineg(c) && ineg(d)) return imax(imax(a, b), imax(c, d));
   return 0.0;
 }
 // Interface value between c and d from a..e (= F_{i-2} .. F_{i+2}).
@@ -108,15 +127,17 @@ DI double mp5(double a, double b, double c, double d, double e) {
   double f = fma(2.0 / 60.0, a, fma(-13.0 / 60.0, b, fma(47.0 / 60.0, c, fma(27.0 / 60.0, d, (-3.0 / 60.0) * e))));
   double dp = d - c, dm = c - b;
   double fmp = c + mm2(dp, al * dm);
-  if ((f - c) * (f - fmp) < 0.0) return f;
+  // (f - c)(f - f_MP) < 0 as a sign test (no product, no FP64 compare).
+  double s1 = f - c, s2 = f - fmp;
+  if ((ipos(s1) && ineg(s2)) || (ineg(s1) && ipos(s2))) return f;
   double d_m = dm - (b - a), d_0 = dp - dm, d_p = (e - d) - dp;
   double m4p = mm4(fma(4.0, d_0, -d_p), fma(4.0, d_p, -d_0), d_0, d_p);
   double m4m = mm4(fma(4.0, d_0, -d_m), fma(4.0, d_m, -d_0), d_0, d_m);
   double ful = fma(al, dm, c);
-  double fmd = 0.5 * (c + d) - 0.5 * m4p;
-  double flc = c + 0.5 * dm + (4.0 / 3.0) * m4m;
-  double fmn = fmax(fmin(fmin(c, d), fmd), fmin(fmin(c, ful), flc));
-  double fmx = fmin(fmax(fmax(c, d), fmd), fmax(fmax(c, ful), flc));
+  double fmd = fma(-0.5, m4p, 0.5 * (c + d));
+  double flc = fma(4.0 / 3.0, m4m, fma(0.5, dm, c));
+  double fmn = imax(imin(imin(c, d), fmd), imin(imin(c, ful), flc));
+  double fmx = imin(imax(imax(c, d), fmd), imax(imax(c, ful), flc));
   return fmn + mm2(f - fmn, fmx - fmn);
 }
 

@@ -24,7 +24,7 @@ def ideal_params(bc=0, **over):
     p = dict(_COMMON)
     p.update(
         gamma_th=2.0, K_atmo=100.0,
-        rho_atmo=1e-10, rho_min=1e-10, rho_low=1e-8, rho_max=1.0,
+        rho_atmo=1e-10, rho_min=1.1e-10, rho_low=1e-8, rho_max=1.0,
         eps_max=1e6, T_atmo=0.0, h0=1.0,
         ye_atmo=0.1,  # Ye is a passive scalar for the ideal gas: the fluid's own value
         eos_kind=0, bc=bc,
@@ -38,7 +38,7 @@ def table_params(table, bc=0, **over):
     p = dict(_COMMON)
     p.update(
         gamma_th=2.0, K_atmo=100.0,
-        rho_atmo=1e-13, rho_min=1e-13, rho_low=1e-11, rho_max=10.0 ** table["lr_max"],
+        rho_atmo=1e-13, rho_min=1.1e-13, rho_low=1e-11, rho_max=10.0 ** table["lr_max"],
         eps_max=0.0, T_atmo=10.0 ** table["lt0"], h0=table["h0"],
         ye_atmo=0.315,  # midpoint of the Ye range (no beta-equilibrium data)
         eos_kind=1, bc=bc,
