@@ -156,6 +156,10 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     G.sz = G.sy * (G.n1 + 6);
     G.sf = G.sz * (G.n2 + 6);
     G.dx = d[i].dx;
+    G.i12 = 1.0 / (12.0 * G.dx);
+    G.i12s = 1.0 / (12.0 * G.dx * G.dx);
+    G.i144 = 1.0 / (144.0 * G.dx * G.dx);
+    G.idx = 1.0 / G.dx;
     c->pd_host[i].G = G;
     ofs[i] = total;
     total += (size_t)63 * G.sf;

@@ -32,6 +32,7 @@ struct Geo {
   int n0, n1, n2, px;
   long long sy, sz, sf;  // strides (x stride 1)
   double dx;
+  double i12, i12s, i144, idx;  // 1/(12 dx), 1/(12 dx^2), 1/(144 dx^2), 1/dx
 };
 
 DI long long at(const Geo& G, int i, int j, int k) {
@@ -122,13 +123,20 @@ DI double mm4(double a, double b, double c, double d) {
   return 0.0;
 }
 // Interface value between c and d from a..e (= F_{i-2} .. F_{i+2}).
+// The 5th-order value is formed from differences to c,
+//   f = c + (2 (a - c) - 13 (b - c) + 27 (d - c) - 3 (e - c)) / 60,
+// which is exact on constant data.  When f == c the limited value is f
+// itself (f_min <= c <= f_max always), so that case returns at once.
 DI double mp5(double a, double b, double c, double d, double e) {
   const double al = 4.0;
-  double f = fma(2.0 / 60.0, a, fma(-13.0 / 60.0, b, fma(47.0 / 60.0, c, fma(27.0 / 60.0, d, (-3.0 / 60.0) * e))));
   double dp = d - c, dm = c - b;
+  double t = fma(-3.0, e - c, fma(27.0, dp, fma(2.0, a - c, 13.0 * dm)));
+  double f = fma(t, 1.0 / 60.0, c);
+  double s1 = f - c;
+  if ((__double_as_longlong(s1) << 1) == 0) return f;
   double fmp = c + mm2(dp, al * dm);
   // (f - c)(f - f_MP) < 0 as a sign test (no product, no FP64 compare).
-  double s1 = f - c, s2 = f - fmp;
+  double s2 = f - fmp;
   if ((ipos(s1) && ineg(s2)) || (ineg(s1) && ipos(s2))) return f;
   double d_m = dm - (b - a), d_0 = dp - dm, d_p = (e - d) - dp;
   double m4p = mm4(fma(4.0, d_0, -d_p), fma(4.0, d_p, -d_0), d_0, d_p);

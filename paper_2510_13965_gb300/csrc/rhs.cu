@@ -25,11 +25,8 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
   const long long o = at(G, pi, pj, pk), sf = G.sf;
   const long long st[3] = {1, G.sy, G.sz};
   const double* U = PD.U[reg] + o;
-  const double dx = G.dx;
-  const double i12 = 1.0 / (12.0 * dx);
-  const double i12s = i12 / dx;
-  const double i144 = i12 * i12;
-  const double kof = P.sigma_ko / (64.0 * dx);
+  const double i12 = G.i12, i12s = G.i12s, i144 = G.i144;
+  const double kof = P.sigma_ko * (12.0 / 64.0) * i12;  // sigma / (64 dx)
 #define FP(f) (U + (long long)(f) * sf)
 
   double r[NF];
@@ -47,49 +44,90 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
     Gh[a] = ld(FP(GH + a));
     be[a] = ld(FP(BET + a));
   }
-
-  // ---- advection (one-sided by the sign of beta^k) and KO dissipation ----
-  {
-    long long su[3];
-    double sgn[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      su[a] = be[a] > 0.0 ? st[a] : -st[a];
-      sgn[a] = be[a] > 0.0 ? be[a] * i12 : -be[a] * i12;
-    }
-#pragma unroll 2
-    for (int f = 0; f < NST; ++f) {
-      const double* u = FP(f);
-      double c = ld(u);
-      double adv = sgn[0] * fdup(u, su[0], c);
-      adv = fma(sgn[1], fdup(u, su[1], c), adv);
-      adv = fma(sgn[2], fdup(u, su[2], c), adv);
-      double ko = fdko(u, st[0], c) + fdko(u, st[1], c) + fdko(u, st[2], c);
-      r[f] = fma(kof, ko, adv);
-    }
-  }
-
-  // ---- first derivatives ------------------------------------------------
-  double dg[3][6], dchi[3], dK[3], dTh[3], dGh[3][3], dal[3], dbe[3][3];  // dGh[c][a] = d_a Gh^c
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-#pragma unroll
-    for (int n = 0; n < 6; ++n) dg[a][n] = fd1(FP(GT + n), st[a]) * i12;
-    dchi[a] = fd1(FP(CHI), st[a]) * i12;
-    dK[a] = fd1(FP(KH), st[a]) * i12;
-    dTh[a] = fd1(FP(TH), st[a]) * i12;
-    dal[a] = fd1(FP(ALP), st[a]) * i12;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      dGh[c][a] = fd1(FP(GH + c), st[a]) * i12;
-      dbe[c][a] = fd1(FP(BET + c), st[a]) * i12;
-    }
-  }
-
-  // ---- conformal metric inverse, Christoffels ----------------------------
   const double detg = det3(g);
   double gu[6];
   inv3(g, 1.0 / detg, gu);
+
+  // ---- one pass over fields and axes: the six centre differences of each
+  // (field, axis) feed the one-sided advection derivative, the KO operator
+  // and, where the equations need them, D_a and D_aa. ------------------------
+  double dg[3][6], dchi[3], dK[3], dTh[3], dGh[3][3], dal[3], dbe[3][3];  // dGh[c][a] = d_a Gh^c
+  double Rs[6];               // Rhat_ij, starting with -1/2 gt^mn d_m d_n gt_ij
+  double ddchi[6], ddal[6];
+  double lb[3], ddb[3];       // gt^jk d_j d_k beta^i ; d_j d_k beta^k
+#pragma unroll
+  for (int n = 0; n < 6; ++n) Rs[n] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) lb[c] = ddb[c] = 0.0;
+  bool upw[3];
+  double wadv[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    upw[a] = ipos(be[a]);
+    wadv[a] = __longlong_as_double(__double_as_longlong(be[a]) & 0x7fffffffffffffffLL) * i12;  // |beta^a| / (12 dx)
+  }
+#pragma unroll
+  for (int f = 0; f < NST; ++f) {
+    const double* u = FP(f);
+    const double c = ld(u);
+    const bool need_d1 = !(f >= AT && f < AT + 6);
+    const bool need_d2 = (f < GT + 6) || f == CHI || f == ALP || (f >= BET && f < BET + 3);
+    double adv = 0.0, ko = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long s = st[a];
+      const double t1p = ld(u + s) - c, t1m = ld(u - s) - c;
+      const double t2p = ld(u + 2 * s) - c, t2m = ld(u - 2 * s) - c;
+      const double t3p = ld(u + 3 * s) - c, t3m = ld(u - 3 * s) - c;
+      const double s1 = t1p + t1m, s2 = t2p + t2m, s3 = t3p + t3m;
+      ko += fma(15.0, s1, fma(-6.0, s2, s3));
+      const double x3 = upw[a] ? t3p : t3m, x2 = upw[a] ? t2p : t2m;
+      const double x1 = upw[a] ? t1p : t1m, y1 = upw[a] ? t1m : t1p;
+      adv = fma(wadv[a], fma(-3.0, y1, fma(18.0, x1, fma(-6.0, x2, x3))), adv);
+      if (need_d1) {
+        const double d1 = fma(8.0, t1p - t1m, -(t2p - t2m)) * i12;
+        if (f < GT + 6) dg[a][f - GT] = d1;
+        if (f == CHI) dchi[a] = d1;
+        if (f == KH) dK[a] = d1;
+        if (f == TH) dTh[a] = d1;
+        if (f >= GH && f < GH + 3) dGh[f - GH][a] = d1;
+        if (f == ALP) dal[a] = d1;
+        if (f >= BET && f < BET + 3) dbe[f - BET][a] = d1;
+      }
+      if (need_d2) {
+        const double d2 = fma(16.0, s1, -s2) * i12s;
+        if (f < GT + 6) Rs[f - GT] = fma(-0.5 * gu[S6(a, a)], d2, Rs[f - GT]);
+        if (f == CHI) ddchi[S6(a, a)] = d2;
+        if (f == ALP) ddal[S6(a, a)] = d2;
+        if (f >= BET && f < BET + 3) {
+          lb[f - BET] = fma(gu[S6(a, a)], d2, lb[f - BET]);
+          if (f - BET == a) ddb[a] += d2;
+        }
+      }
+    }
+    r[f] = fma(kof, ko, adv);
+  }
+  // Mixed second derivatives D_ab = D_b(D_a).
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 3; ++b) {
+      const int ab = S6(a, b);
+      const double wgt = -gu[ab] * i144;
+#pragma unroll
+      for (int n = 0; n < 6; ++n) Rs[n] = fma(wgt, fd11(FP(GT + n), st[a], st[b]), Rs[n]);
+      ddchi[ab] = fd11(FP(CHI), st[a], st[b]) * i144;
+      ddal[ab] = fd11(FP(ALP), st[a], st[b]) * i144;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double d2 = fd11(FP(BET + c), st[a], st[b]) * i144;
+        lb[c] = fma(2.0 * gu[ab], d2, lb[c]);
+        if (c == b) ddb[a] += d2;
+        if (c == a) ddb[b] += d2;
+      }
+    }
+
+  // ---- Christoffels ---------------------------------------------------------------
   double Gl[3][6], Gu[3][6];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -106,12 +144,12 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
     double t[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double s = 0.0;
+      double sacc = 0.0;
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int l = 0; l < 3; ++l) s = fma(gu[S6(k, l)], dg[l][S6(a, k)], s);
-      t[a] = s;
+        for (int l = 0; l < 3; ++l) sacc = fma(gu[S6(k, l)], dg[l][S6(a, k)], sacc);
+      t[a] = sacc;
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -120,24 +158,8 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
     }
   }
 
-  // ---- Rhat_ij ------------------------------------------------------------
-  double Rs[6];
+  // ---- rest of Rhat_ij: Gammahat terms and Christoffel products --------------------
   {
-    // t1 = -1/2 gt^mn d_m d_n gt_ij, second derivatives contracted immediately.
-#pragma unroll
-    for (int n = 0; n < 6; ++n) Rs[n] = 0.0;
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int l = m; l < 3; ++l) {
-        double wgt = (m == l ? -0.5 : -1.0) * gu[S6(m, l)] * (m == l ? i12s : i144);
-#pragma unroll
-        for (int n = 0; n < 6; ++n) {
-          const double* u = FP(GT + n);
-          double d2 = (m == l) ? fd2(u, st[m], g[n]) : fd11(u, st[m], st[l]);
-          Rs[n] = fma(wgt, d2, Rs[n]);
-        }
-      }
     // C[n][k][a] = gt^{mn} Gt^k_{ma}
     double C[3][3][3];
 #pragma unroll
@@ -153,12 +175,12 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        double s = 0.0;
+        double sacc = 0.0;
 #pragma unroll
         for (int n = 0; n < 3; ++n)
 #pragma unroll
-          for (int k = 0; k < 3; ++k) s = fma(C[n][k][a], Gl[b][S6(k, n)], s);
-        X[a][b] = s;
+          for (int k = 0; k < 3; ++k) sacc = fma(C[n][k][a], Gl[b][S6(k, n)], sacc);
+        X[a][b] = sacc;
       }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -180,19 +202,6 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
 
   // ---- R^chi_ij, D_i D_j alpha ------------------------------------------------
   const double ichi = 1.0 / chi;
-  double ddchi[6], ddal[6];
-#pragma unroll
-  for (int m = 0; m < 3; ++m)
-#pragma unroll
-    for (int l = m; l < 3; ++l) {
-      if (m == l) {
-        ddchi[S6(m, l)] = fd2(FP(CHI), st[m], chi) * i12s;
-        ddal[S6(m, l)] = fd2(FP(ALP), st[m], al) * i12s;
-      } else {
-        ddchi[S6(m, l)] = fd11(FP(CHI), st[m], st[l]) * i144;
-        ddal[S6(m, l)] = fd11(FP(ALP), st[m], st[l]) * i144;
-      }
-    }
   double gdchi[3], gdal[3];  // gt^ij d_j chi, gt^ij d_j alpha
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -315,24 +324,6 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
 
   // ---- d_t Gammahat^i ---------------------------------------------------------
   {
-    // gt^jk d_j d_k beta^i and d_j d_k beta^k.
-    double lb[3] = {0.0, 0.0, 0.0}, ddb[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int l = m; l < 3; ++l) {
-        double sc = (m == l) ? i12s : i144;
-        double wgt = (m == l ? 1.0 : 2.0) * gu[S6(m, l)];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const double* u = FP(BET + c);
-          double d2 = ((m == l) ? fd2(u, st[m], be[c]) : fd11(u, st[m], st[l])) * sc;
-          lb[c] = fma(wgt, d2, lb[c]);
-          // d_j d_k beta^k for j = m (k = l == c) and j = l (k = m == c)
-          if (c == l) ddb[m] += d2;
-          if (m != l && c == m) ddb[l] += d2;
-        }
-      }
     const double k23 = (2.0 / 3.0) * divb;
     const double zfac = -2.0 * al * ichi * (P.kappa_z + (2.0 / 3.0) * Kt);
     const double thfac = 2.0 * Th;  // 2 alpha (Theta / alpha) d_j alpha = 2 Theta d_j alpha
@@ -362,7 +353,7 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
 
   // ---- MHD: flux divergence and sources -------------------------------------------
   {
-    const double idx = 1.0 / dx;
+    const double idx = G.idx;
 #pragma unroll
     for (int n = 0; n < 10; ++n) r[NST + n] = 0.0;
 #pragma unroll

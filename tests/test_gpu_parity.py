@@ -69,6 +69,7 @@ def _rhs_ok(got, want, tol=1e-11, U=None, dx=None):
     scale = np.maximum(want_n, 1e-30)
     if U is not None:
         un = np.abs(U).reshape(NF, -1).max(axis=1)
+        un[28:32] = un[28:32].max()  # the B and phi fluxes carry each other (alpha c_b^2 Bbar, alpha chi gt phibar)
         scale[22:] = np.maximum(scale[22:], un[22:] / dx)
     d = np.abs(got - want).reshape(NF, -1).max(axis=1)
     e = d / scale
