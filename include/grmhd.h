@@ -67,7 +67,8 @@ typedef enum {
   GRMHD_ERR_C2P_FATAL = -3,  /* a point hit a fatal con2prim policy branch        */
   GRMHD_ERR_TIMEOUT = -4,    /* a bounded device wait ran out                     */
   GRMHD_ERR_NONFINITE = -5,  /* a non-finite conserved state reached con2prim     */
-  GRMHD_ERR_NOMEM = -6       /* a library allocation failed                      */
+  GRMHD_ERR_NOMEM = -6,      /* a library allocation failed                      */
+  GRMHD_ERR_SIZE = -7        /* a patch exceeds a fixed maximum size             */
 } grmhd_status;
 
 /* Per-point con2prim status codes written to grmhd_patch_desc.status:
@@ -230,6 +231,36 @@ int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long 
  * iters: device [n] or NULL. */
 int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
                    double* prim, int8_t* status, int32_t* iters, void* stream);
+
+/* ---- allocation-free right-hand side -------------------------------------- */
+
+/* No counterpart in the paper; this is a service for callers that must not
+ * have the library allocate device memory (an application whose device memory
+ * all belongs to its own pool allocator, a code path that cannot afford the
+ * device synchronisation cudaMalloc / cudaFree may imply, a host framework
+ * that allows allocation only through its own allocator).
+ *
+ * Same result as grmhd_con2prim(ctx, reg, NULL) followed by
+ * grmhd_rhs_eval(ctx, reg, &rhs) on a context holding this single patch: con2prim
+ * on U[reg] (writing prim, status and the corrected conserved variables into
+ * U[reg]) and L(U) into rhs (device, patch layout, ghost entries untouched).
+ * U[reg] must already hold filled ghost zones; only U[reg], prim and status
+ * of the descriptor are used.  eos may be NULL for the ideal gas.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its working
+ * memory (pointwise and interface fluxes, descriptor, work list, flags) is a
+ * file-scope static device array of about 27.7 MB that every GPU which loads
+ * the library holds until the process exits.  Patches are limited to
+ * px * (n[1]+6) * (n[2]+6) <= 54872 ghosted points (a 32^3 patch); larger ones
+ * return GRMHD_ERR_SIZE before any work is enqueued.  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.  All calls on a device share the
+ * array and it keeps the last call's contents, so calls that may overlap on
+ * the GPU (two streams of one device) race and must be serialised by the
+ * caller; calls on one stream are ordered.  Work is enqueued on `stream`.
+ * Fatal con2prim points are reported only through the status array. */
+int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_desc* d, const grmhd_eos_table* eos, int reg,
+                          double* rhs, void* stream);
 
 #ifdef __cplusplus
 }

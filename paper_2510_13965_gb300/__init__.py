@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgrmhd.so")
 NF, NP, NID, NG = 32, 10, 26, 3
 OK = 0
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_C2P_FATAL", -4: "ERR_TIMEOUT", -5: "ERR_NONFINITE",
-          -6: "ERR_NOMEM"}
+          -6: "ERR_NOMEM", -7: "ERR_SIZE"}
 
 _P_DOUBLES = ["kappa_z", "kappa_c", "kappa_2", "eta", "sigma_ko", "c_b", "kappa_b", "gamma_th", "K_atmo",
               "rho_atmo", "rho_min", "rho_low", "rho_max", "alpha_bh", "W_max", "eps_max", "ye_min", "ye_max",
@@ -76,6 +76,8 @@ _SIGS = {
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_c2p_flat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_rhs_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
