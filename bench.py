@@ -54,6 +54,8 @@ def _args():
     a.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--e2e-steps", type=int, default=3)
+    a.add_argument("--workload", default="tov", choices=["tov", "batched"],
+                   help="tov: the 128^3 TOV star (default); batched: 256 uneven patches over 5 levels")
     a.add_argument("--edge", type=int, default=N_EDGE,
                    help="interior points per axis (the same [-20,20]^3 star; 128 is the benchmark workload)")
     return a.parse_args()
@@ -292,10 +294,93 @@ def run_grmhd(args):
     return 0
 
 
+def run_batched(args):
+    """256 uneven patches (edges in {16,24,32,48,64} per axis, 5 levels, frozen
+    ghosts): batched (one launch per kernel over all patches) with and without
+    the autotuner and a CUDA graph, against plain per-patch launches."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_13965_gb300 as g
+    import synth
+
+    P = synth.ideal_params(bc=2)
+    specs = synth.batched_specs(npatch=256, seed=2)
+    _, norm = synth.config0_id(n=(32, 32, 32), seed=0, return_norm=True)
+    zones = int(sum(np.prod(s["n"]) for s in specs))
+    dt = 0.4 * min(s["dx"] for s in specs)
+    stream = torch.cuda.Stream()
+    batched = g.Patches(P, specs, stream=stream)
+    t0 = time.perf_counter()
+    for p_, s_ in enumerate(specs):
+        batched.init_state(p_, torch.as_tensor(synth.batched_id(s_, seed=0, norm=norm), device="cuda"))
+    batched.synchronize()
+    gen_s = time.perf_counter() - t0
+    init = [u[0].clone() for u in batched.U]
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def reset(pt):
+        for p_ in range(len(specs)):
+            pt.U[p_][0].copy_(init[p_])
+        torch.cuda.synchronize()
+
+    K = args.steps
+    for _ in range(max(args.warmup, 3)):
+        batched.step(dt)
+    reset(batched)
+    ms_default = timed(lambda: batched.step(dt), K)
+    reset(batched)
+    chosen = batched.autotune(dt, reps=2)
+    reset(batched)
+    ms_tuned = timed(lambda: batched.step(dt), K)
+    reset(batched)
+    batched.capture_graph(1, dt)
+    launches0 = batched.launch_count()
+    ms_graph = timed(batched.graph_launch, K)
+    launches = batched.launch_count() - launches0
+    rc = batched.sync_status()
+    # plain per-patch launches: one context per patch, all on the same stream
+    plain = []
+    for p_, s_ in enumerate(specs):
+        q = g.Patches(P, [s_], stream=stream)
+        q.U[0][0].copy_(init[p_])
+        plain.append(q)
+    torch.cuda.synchronize()
+    for q in plain:
+        q.step(dt)
+    for p_, q in enumerate(plain):
+        q.U[0][0].copy_(init[p_])
+    ms_plain = timed(lambda: [q.step(dt) for q in plain], K)
+    line = {"metric": METRIC, "value": zones / (ms_graph / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched_256_uneven_patches_5_levels_rk4_step", "patches": len(specs),
+                       "interior_points": zones, "edges": list(synth.EDGES), "levels": 5, "ghosts": "frozen",
+                       "l2": "inputs larger than L2"},
+            "variants_ms_per_step": {"plain_per_patch": ms_plain, "batched_default_bs128": ms_default,
+                                     "batched_autotuned": ms_tuned, "batched_autotuned_graph": ms_graph},
+            "speedup_batched_graph_vs_plain": ms_plain / ms_graph, "autotuned_block_sizes": list(chosen),
+            "gpu_launches": int(launches), "status": rc, "setup_s": gen_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_grmhd(args)
 
 

@@ -96,7 +96,8 @@ typedef struct grmhd_params {
   double h0;                        /* lower bound of the specific enthalpy of the EOS  */
   double c2p_xtol;                  /* absolute part of the Brent stop rule             */
   int eos_kind;                     /* 0 ideal gas, 1 table                             */
-  int bc;                           /* outer ghosts: 0 periodic, 1 linear extrapolation */
+  int bc;                           /* ghosts: 0 periodic, 1 linear extrapolation,
+                                       2 frozen (the initial data's ghost values)       */
   int max_iter;                     /* Brent iteration cap per root find                */
   int reserved;
 } grmhd_params;
@@ -196,6 +197,19 @@ int grmhd_graph_launch(grmhd_ctx* ctx);
  * the last call (GRMHD_OK, GRMHD_ERR_C2P_FATAL or GRMHD_ERR_NONFINITE), then
  * clears it. */
 int grmhd_sync_status(grmhd_ctx* ctx);
+
+/* Threads per block of the con2prim, interface-flux and right-hand-side
+ * kernels (each 64, 128 or 256; 128 at creation). */
+int grmhd_set_block_sizes(grmhd_ctx* ctx, int bs_c2p, int bs_iflux, int bs_rhs);
+
+/* Autotuner: runs reps fused stage-0 substeps (after one warm-up) with each
+ * candidate block size on this context's own patches, times every kernel kind
+ * with CUDA events and keeps the fastest size per kind.  It overwrites the
+ * stage registers U[1] and U[3] and may apply con2prim corrections to U[0], so
+ * call it before stepping or between steps.  chosen (3 ints, may be NULL)
+ * receives the sizes kept for con2prim, interface fluxes and right-hand side.
+ * Synchronises the stream. */
+int grmhd_autotune(grmhd_ctx* ctx, double dt, int reps, int* chosen);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around
  * each eager launch (not inside graph capture).  grmhd_profile(ctx, 1)

@@ -26,7 +26,7 @@ struct oracle_params {
   double h0;                                        // specific-enthalpy lower bound of the EOS
   double c2p_xtol;                                  // absolute part of the Brent stop rule
   int eos_kind;                                     // 0 ideal gas, 1 table
-  int bc;                                           // 0 periodic, 1 linear extrapolation
+  int bc;                                           // 0 periodic, 1 linear extrapolation, 2 frozen
   int max_iter;                                     // Brent iteration cap
   int pad_;
 };

@@ -25,7 +25,16 @@ grid make_grid(const int n[3], int px, double dx) {
 // bc 0: periodic copy.  bc 1: linear extrapolation from the two outermost
 // interior points, U_{-m} = (1+m) U_0 - m U_1 (the outer-boundary ghost
 // extrapolation of Sec. IV B, taken at first order).
+// bc 2: frozen ghosts (the initial data's ghost values, kept by every
+// register; see substep) -- nothing to fill here.
+static void ghost_fill_bc(int bc, const grid& G, double* U, int nf);
+
 void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf) {
+  if (P->bc == 2) return;
+  ghost_fill_bc(P->bc, G, U, nf);
+}
+
+static void ghost_fill_bc(int bc, const grid& G, double* U, int nf) {
   const long st[3] = {1, G.sy, G.sz};
   for (int ax = 0; ax < 3; ++ax) {
     int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
@@ -42,7 +51,7 @@ void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf) {
           double* base = U + (long)f * G.sf + G.at(idx[0], idx[1], idx[2]);
           long s = st[ax];
           for (int m = 1; m <= NG; ++m) {
-            if (P->bc == 0) {
+            if (bc == 0) {
               base[-m * s] = base[(n - m) * s];
               base[(n - 1 + m) * s] = base[(m - 1) * s];
             } else {
@@ -132,7 +141,10 @@ void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G
         for (int a = 0; a < 3; ++a)
           U[(F_GH + a) * G.sf + o] = dbl(gu[sym(a, 0)] * tj[0] + gu[sym(a, 1)] * tj[1] + gu[sym(a, 2)] * tj[2]);
       }
-  ghost_fill(P, G, U, NF);
+  if (P->bc == 2)  // frozen ghosts keep the initial data; Gammahat is extrapolated into them
+    ghost_fill_bc(1, G, U + (long)F_GH * G.sf, 3);
+  else
+    ghost_fill(P, G, U, NF);
 }
 
 // con2prim at every point of the patch, ghosts included; corrected conserved
@@ -258,6 +270,16 @@ int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, in
   double* in = stage == 0 ? Un : stage == 1 ? Ua : stage == 2 ? Ub : Ua;
   double* out = stage == 0 ? Ua : stage == 1 ? Ub : stage == 2 ? Ua : Un;
   ghost_fill(P, G, in, NF);
+  if (P->bc == 2 && in != Un) {
+    // Frozen ghosts: the stage register carries U^n's ghost values.
+    for (int f = 0; f < NF; ++f)
+      for (int k = -NG; k < G.n[2] + NG; ++k)
+        for (int j = -NG; j < G.n[1] + NG; ++j)
+          for (int i = -NG; i < G.n[0] + NG; ++i) {
+            bool inner = i >= 0 && i < G.n[0] && j >= 0 && j < G.n[1] && k >= 0 && k < G.n[2];
+            if (!inner) in[(long)f * G.sf + G.at(i, j, k)] = Un[(long)f * G.sf + G.at(i, j, k)];
+          }
+  }
   long long t0 = flops_now();
   int worst = c2p_patch(P, E, G, in, prim, status, nullptr);
   long long t1 = flops_now();

@@ -68,6 +68,8 @@ _SIGS = {
     "grmhd_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
     "grmhd_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
     "grmhd_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_set_block_sizes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "grmhd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "grmhd_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "grmhd_launch_count": (ctypes.c_longlong, [ctypes.c_void_p]),
     "grmhd_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -148,14 +150,14 @@ class Patches:
     with torch on `device`, and works on its own CUDA stream.
     """
 
-    def __init__(self, params, specs, table=None, device="cuda", pad=1):
+    def __init__(self, params, specs, table=None, device="cuda", pad=1, stream=None):
         torch = _torch()
         self.torch = torch
         L = load()
         self.L = L
         self.params = make_params(params)
         self.table = table
-        self.stream = torch.cuda.Stream(device=device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         self.device = device
         self.specs = []
         self.U, self.prim, self.status = [], [], []
@@ -256,6 +258,16 @@ class Patches:
         return self.L.grmhd_sync_status(self.ctx)
 
     KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init")
+
+    def set_block_sizes(self, bs_c2p, bs_iflux, bs_rhs):
+        _check(self.L.grmhd_set_block_sizes(self.ctx, bs_c2p, bs_iflux, bs_rhs), self.ctx, "grmhd_set_block_sizes")
+
+    def autotune(self, dt, reps=2):
+        """Pick the fastest block size per kernel kind on these patches; returns (c2p, iflux, rhs)."""
+        self._enter()
+        ch = (ctypes.c_int * 3)()
+        _check(self.L.grmhd_autotune(self.ctx, float(dt), int(reps), ch), self.ctx, "grmhd_autotune")
+        return tuple(ch)
 
     def profile(self, on=True):
         _check(self.L.grmhd_profile(self.ctx, 1 if on else 0), self.ctx, "grmhd_profile")

@@ -15,9 +15,10 @@ struct grmhd_ctx {
   std::vector<grmhd_patch_desc> desc;
   std::vector<PatchDev> pd_host;
   PatchDev* pd = nullptr;
-  // work lists per domain
+  // work lists per block size and domain, concatenated
   Work* work = nullptr;
-  int wofs[NDOM + 1];
+  int wofs[NBS][NDOM + 1];
+  int bs_c2p = 128, bs_if = 128, bs_rhs = 128;  // chosen block sizes
   double* scratch = nullptr;
   DevFlags* flags = nullptr;
   C2PStats* stats = nullptr;
@@ -88,9 +89,7 @@ static int check_launch(grmhd_ctx* c, const char* what) {
   return cuda_ok(c, cudaGetLastError(), what);
 }
 
-static int block_size(int dom) {
-  return (dom == DOM_INT) ? BS_INT : ((dom >= DOM_IFX && dom <= DOM_IFZ) ? BS_IF : BS_ALL);
-}
+static int bs_index(int bs) { return bs == 64 ? 0 : (bs == 256 ? 2 : 1); }
 
 extern "C" {
 
@@ -127,7 +126,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   if (p->eos_kind != 0 && p->eos_kind != 1) return GRMHD_ERR_ARG;
   if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2 || eos->nr < 2 || eos->nt < 2 || eos->ny < 2))
     return GRMHD_ERR_ARG;
-  if (p->bc != 0 && p->bc != 1) return GRMHD_ERR_ARG;
+  if (p->bc < 0 || p->bc > 2) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   for (int i = 0; i < npatch; ++i) {
     const grmhd_patch_desc& q = d[i];
@@ -178,18 +177,20 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     q.lam = q.Fp + 30 * q.G.sf;
     q.Fh = q.lam + 3 * q.G.sf;
   }
-  // work lists
+  // work lists: for each block size and domain, the blocks of patch 0, then patch 1, ...
   std::vector<Work> wl;
-  for (int dom = 0; dom < NDOM; ++dom) {
-    c->wofs[dom] = (int)wl.size();
-    int bs = block_size(dom);
-    for (int i = 0; i < npatch; ++i) {
-      long long n = dom_count(dom, c->pd_host[i].G);
-      long long nb = (n + bs - 1) / bs;
-      for (long long b = 0; b < nb; ++b) wl.push_back(Work{i, (int)b});
+  for (int b = 0; b < NBS; ++b) {
+    int bs = BS_CAND[b];
+    for (int dom = 0; dom < NDOM; ++dom) {
+      c->wofs[b][dom] = (int)wl.size();
+      for (int i = 0; i < npatch; ++i) {
+        long long n = dom_count(dom, c->pd_host[i].G);
+        long long nb = (n + bs - 1) / bs;
+        for (long long k = 0; k < nb; ++k) wl.push_back(Work{i, (int)k});
+      }
     }
+    c->wofs[b][NDOM] = (int)wl.size();
   }
-  c->wofs[NDOM] = (int)wl.size();
   if ((rc = cuda_ok(c, cudaMalloc(&c->work, wl.size() * sizeof(Work)), "cudaMalloc work")) ||
       (rc = cuda_ok(c, cudaMalloc(&c->pd, npatch * sizeof(PatchDev)), "cudaMalloc pd")) ||
       (rc = cuda_ok(c, cudaMalloc(&c->flags, sizeof(DevFlags)), "cudaMalloc flags")) ||
@@ -211,8 +212,11 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   return GRMHD_OK;
 }
 
-static int nblk(grmhd_ctx* c, int dom) { return c->wofs[dom + 1] - c->wofs[dom]; }
-static const Work* wl(grmhd_ctx* c, int dom) { return c->work + c->wofs[dom]; }
+static int nblk(grmhd_ctx* c, int dom, int bs = 128) {
+  int b = bs_index(bs);
+  return c->wofs[b][dom + 1] - c->wofs[b][dom];
+}
+static const Work* wl(grmhd_ctx* c, int dom, int bs = 128) { return c->work + c->wofs[bs_index(bs)][dom]; }
 
 int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
   if (!c) return GRMHD_ERR_ARG;
@@ -240,7 +244,10 @@ int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
       cnt = (int)((dom_count(dom, q.G) + BS_ALL - 1) / BS_ALL);
     }
     if (first + cnt > n) return fail(c, GRMHD_ERR_ARG, "init_state: work list");
-    launch_ghost(c->pd, w + first, cnt, 0, ax, c->P.bc, c->st);
+    if (c->P.bc == 2)  // frozen ghosts keep the initial data; only Gammahat is extrapolated
+      launch_ghost(c->pd, w + first, cnt, 0, ax, 1, c->st, GH, GH + 3);
+    else
+      launch_ghost(c->pd, w + first, cnt, 0, ax, c->P.bc, c->st);
     c->launches += 1;
   }
   return check_launch(c, "init ghost");
@@ -249,6 +256,14 @@ int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
 int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
   if (!c) return GRMHD_ERR_ARG;
   if (reg < 0 || reg > 3) return fail(c, GRMHD_ERR_ARG, "ghost_fill: reg");
+  if (c->P.bc == 2) {
+    if (reg != 0) {
+      ProfScope ps(c, K_GHOST);
+      launch_ghost_copy(c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->st);
+      c->launches += 1;
+    }
+    return check_launch(c, "ghost copy");
+  }
   for (int ax = 0; ax < 3; ++ax) {
     ProfScope ps(c, K_GHOST);
     launch_ghost(c->pd, wl(c, DOM_GX + ax), nblk(c, DOM_GX + ax), reg, ax, c->P.bc, c->st);
@@ -259,7 +274,8 @@ int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
 
 static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats) {
   ProfScope ps(c, K_C2P);
-  launch_c2p(c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->P, c->E, c->flags, stats ? c->stats : nullptr, c->st);
+  launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p), nblk(c, DOM_ALL, c->bs_c2p), reg, c->P, c->E, c->flags,
+             stats ? c->stats : nullptr, c->st, c->bs_c2p);
   c->launches += 1;
   return check_launch(c, "con2prim");
 }
@@ -267,7 +283,7 @@ static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats) {
 static int iflux(grmhd_ctx* c, int reg) {
   for (int d = 0; d < 3; ++d) {
     ProfScope ps(c, K_IFLUX);
-    launch_iflux(c->pd, wl(c, DOM_IFX + d), nblk(c, DOM_IFX + d), reg, d, c->st);
+    launch_iflux(c->pd, wl(c, DOM_IFX + d, c->bs_if), nblk(c, DOM_IFX + d, c->bs_if), reg, d, c->st, c->bs_if);
     c->launches += 1;
   }
   return check_launch(c, "iflux");
@@ -305,7 +321,8 @@ int grmhd_rhs_eval(grmhd_ctx* c, int reg, double* const* rhs) {
   if ((rc = iflux(c, reg))) return rc;
   {
     ProfScope ps(c, K_RHS);
-    launch_rhs(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st);
+    launch_rhs(c->pd, wl(c, DOM_INT, c->bs_rhs), nblk(c, DOM_INT, c->bs_rhs), reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st,
+               c->bs_rhs);
   }
   c->launches += 1;
   return check_launch(c, "rhs");
@@ -339,7 +356,8 @@ int grmhd_rhs_substep(grmhd_ctx* c, int stage, double dt) {
   if ((rc = iflux(c, reg))) return rc;
   {
     ProfScope ps(c, K_RHS);
-    launch_rhs(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), reg, 1, stage, dt, c->P, nullptr, c->st);
+    launch_rhs(c->pd, wl(c, DOM_INT, c->bs_rhs), nblk(c, DOM_INT, c->bs_rhs), reg, 1, stage, dt, c->P, nullptr, c->st,
+               c->bs_rhs);
   }
   c->launches += 1;
   return check_launch(c, "rhs fused");
@@ -390,6 +408,51 @@ int grmhd_graph_launch(grmhd_ctx* c) {
   if (!c->gexec) return fail(c, GRMHD_ERR_ARG, "graph_launch: no graph");
   c->launches += c->graph_kernels;
   return cuda_ok(c, cudaGraphLaunch(c->gexec, c->st), "graph launch");
+}
+
+int grmhd_set_block_sizes(grmhd_ctx* c, int bs_c2p, int bs_iflux, int bs_rhs) {
+  if (!c) return GRMHD_ERR_ARG;
+  auto ok = [](int b) { return b == 64 || b == 128 || b == 256; };
+  if (!ok(bs_c2p) || !ok(bs_iflux) || !ok(bs_rhs)) return fail(c, GRMHD_ERR_ARG, "block sizes: 64, 128 or 256");
+  c->bs_c2p = bs_c2p;
+  c->bs_if = bs_iflux;
+  c->bs_rhs = bs_rhs;
+  return GRMHD_OK;
+}
+
+int grmhd_autotune(grmhd_ctx* c, double dt, int reps, int* chosen) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (reps < 1) return fail(c, GRMHD_ERR_ARG, "autotune: reps");
+  bool was = c->profiling;
+  double best[3] = {1e300, 1e300, 1e300};
+  int pick[3] = {128, 128, 128};
+  int rc = GRMHD_OK;
+  for (int b = 0; b < NBS && rc == GRMHD_OK; ++b) {
+    c->bs_c2p = c->bs_if = c->bs_rhs = BS_CAND[b];
+    if ((rc = grmhd_rhs_substep(c, 0, dt))) break;  // warm-up of this variant
+    if ((rc = grmhd_profile(c, 1))) break;
+    for (int r = 0; r < reps && rc == GRMHD_OK; ++r) rc = grmhd_rhs_substep(c, 0, dt);
+    if (rc) break;
+    double ms[NKIND];
+    long long cnt[NKIND];
+    if ((rc = grmhd_profile_read(c, ms, cnt, NKIND))) break;
+    const int kinds[3] = {K_C2P, K_IFLUX, K_RHS};
+    for (int k = 0; k < 3; ++k)
+      if (ms[kinds[k]] < best[k]) {
+        best[k] = ms[kinds[k]];
+        pick[k] = BS_CAND[b];
+      }
+  }
+  grmhd_profile(c, was ? 1 : 0);
+  c->bs_c2p = pick[0];
+  c->bs_if = pick[1];
+  c->bs_rhs = pick[2];
+  if (chosen) {
+    chosen[0] = pick[0];
+    chosen[1] = pick[1];
+    chosen[2] = pick[2];
+  }
+  return rc;
 }
 
 int grmhd_profile(grmhd_ctx* c, int on) {

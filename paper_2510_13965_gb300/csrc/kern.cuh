@@ -84,12 +84,16 @@ Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T);
 // Launchers (host functions in the .cu files; all enqueue on `st`).
 void launch_init(const PatchDev* pd, int p, const Geo& G, const grmhd_params& P, const Eos& E, const double* id,
                  double* U, cudaStream_t st);
-void launch_ghost(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int axis, int bc, cudaStream_t st);
+void launch_ghost(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int axis, int bc, cudaStream_t st,
+                  int f0 = 0, int f1 = NF);
+// bs: threads per block of the launch (64, 128 or 256); the work list must
+// have been built for the same block size.
 void launch_c2p(const PatchDev* pd_dev, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                DevFlags* flags, C2PStats* stats, cudaStream_t st);
-void launch_iflux(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int dir, cudaStream_t st);
+                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs = 128);
+void launch_iflux(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs = 128);
 void launch_rhs(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int mode, int stage, double dt,
-                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st);
+                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs = 128);
+void launch_ghost_copy(const PatchDev* pd_dev, const Work* w, int nblk, int reg, cudaStream_t st);
 void launch_rk(const PatchDev* pd_dev, const Work* w, int nblk, int stage, double dt, double* const* rhs_dev,
                cudaStream_t st);
 void launch_c2p_flat(const grmhd_params& P, const Eos& E, long long n, const double* cons, double* prim,
@@ -101,5 +105,8 @@ void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, cons
 constexpr int BS_ALL = 128;
 constexpr int BS_INT = 128;
 constexpr int BS_IF = 128;
+// Block sizes the autotuner chooses from.
+constexpr int NBS = 3;
+constexpr int BS_CAND[NBS] = {64, 128, 256};
 
 }  // namespace gk

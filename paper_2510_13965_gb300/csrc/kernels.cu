@@ -122,7 +122,7 @@ void launch_init(const PatchDev*, int, const Geo& G, const grmhd_params& P, cons
 // Ghost fill along one axis: each thread owns one line and fills its 3 + 3
 // ghost points for all 32 fields.
 template <int AX>
-__global__ void k_ghost(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg, int bc) {
+__global__ void k_ghost(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg, int bc, int f0, int f1) {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
   const Geo& G = PD.G;
@@ -135,7 +135,7 @@ __global__ void k_ghost(const PatchDev* __restrict__ pd, const Work* __restrict_
   const long long s = AX == 0 ? 1 : (AX == 1 ? G.sy : G.sz);
   const int n = AX == 0 ? G.n0 : (AX == 1 ? G.n1 : G.n2);
   double* U = PD.U[reg];
-  for (int f = 0; f < NF; ++f) {
+  for (int f = f0; f < f1; ++f) {
     double* b = U + f * G.sf + o;
     if (bc == 0) {
 #pragma unroll
@@ -154,19 +154,20 @@ __global__ void k_ghost(const PatchDev* __restrict__ pd, const Work* __restrict_
   }
 }
 
-void launch_ghost(const PatchDev* pd, const Work* w, int nblk, int reg, int axis, int bc, cudaStream_t st) {
+void launch_ghost(const PatchDev* pd, const Work* w, int nblk, int reg, int axis, int bc, cudaStream_t st, int f0,
+                  int f1) {
   if (nblk <= 0) return;
-  if (axis == 0) k_ghost<0><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc);
-  if (axis == 1) k_ghost<1><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc);
-  if (axis == 2) k_ghost<2><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc);
+  if (axis == 0) k_ghost<0><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc, f0, f1);
+  if (axis == 1) k_ghost<1><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc, f0, f1);
+  if (axis == 2) k_ghost<2><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, bc, f0, f1);
 }
 
 // ---------------------------------------------------------------------------
 // con2prim at every point, then the point-wise flux vectors F^d (10 fields)
 // and max |lambda^{+-}_fast| along d for the directions whose interface
 // stencils use this point.
-template <bool STATS>
-__global__ void __launch_bounds__(BS_ALL) k_c2p(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
+template <bool STATS, int BS>
+__global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
                                                  grmhd_params P, Eos E, DevFlags* flags, C2PStats* stats) {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
@@ -288,21 +289,29 @@ __global__ void __launch_bounds__(BS_ALL) k_c2p(const PatchDev* __restrict__ pd,
   }
 }
 
-void launch_c2p(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                DevFlags* flags, C2PStats* stats, cudaStream_t st) {
-  if (nblk <= 0) return;
+template <int BS>
+static void launch_c2p_bs(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
+                          DevFlags* flags, C2PStats* stats, cudaStream_t st) {
   if (stats)
-    k_c2p<true><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, P, E, flags, stats);
+    k_c2p<true, BS><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats);
   else
-    k_c2p<false><<<nblk, BS_ALL, 0, st>>>(pd, w, reg, P, E, flags, stats);
+    k_c2p<false, BS><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats);
+}
+
+void launch_c2p(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
+                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs) {
+  if (nblk <= 0) return;
+  if (bs == 64) launch_c2p_bs<64>(pd, w, nblk, reg, P, E, flags, stats, st);
+  else if (bs == 256) launch_c2p_bs<256>(pd, w, nblk, reg, P, E, flags, stats, st);
+  else launch_c2p_bs<128>(pd, w, nblk, reg, P, E, flags, stats, st);
 }
 
 // ---------------------------------------------------------------------------
 // Interface fluxes along direction D: lambda = max over points i-2 .. i+3,
 // g^{+-} = F +- lambda U, F^L = MP5(g^+_{i-2..i+2}), F^R = MP5(g^-_{i+3..i-1}),
 // Fhat = (F^L + F^R) / 2 (MP5 commutes with the positive factor 1/2).
-template <int D>
-__global__ void __launch_bounds__(BS_IF) k_iflux(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg) {
+template <int D, int BS>
+__global__ void __launch_bounds__(BS) k_iflux(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg) {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
@@ -335,11 +344,38 @@ __global__ void __launch_bounds__(BS_IF) k_iflux(const PatchDev* __restrict__ pd
   }
 }
 
-void launch_iflux(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st) {
+template <int BS>
+static void launch_iflux_bs(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st) {
+  if (dir == 0) k_iflux<0, BS><<<nblk, BS, 0, st>>>(pd, w, reg);
+  if (dir == 1) k_iflux<1, BS><<<nblk, BS, 0, st>>>(pd, w, reg);
+  if (dir == 2) k_iflux<2, BS><<<nblk, BS, 0, st>>>(pd, w, reg);
+}
+
+void launch_iflux(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs) {
   if (nblk <= 0) return;
-  if (dir == 0) k_iflux<0><<<nblk, BS_IF, 0, st>>>(pd, w, reg);
-  if (dir == 1) k_iflux<1><<<nblk, BS_IF, 0, st>>>(pd, w, reg);
-  if (dir == 2) k_iflux<2><<<nblk, BS_IF, 0, st>>>(pd, w, reg);
+  if (bs == 64) launch_iflux_bs<64>(pd, w, nblk, reg, dir, st);
+  else if (bs == 256) launch_iflux_bs<256>(pd, w, nblk, reg, dir, st);
+  else launch_iflux_bs<128>(pd, w, nblk, reg, dir, st);
+}
+
+// Frozen ghosts (bc 2): the ghost zones of every register hold the ghost values
+// of U^n, which no step changes.
+__global__ void k_ghost_copy(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg) {
+  Work wk = w[blockIdx.x];
+  const PatchDev& PD = pd[wk.patch];
+  const Geo& G = PD.G;
+  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
+  if (q >= dom_count(DOM_ALL, G)) return;
+  int i, j, k;
+  dom_decode(DOM_ALL, G, q, i, j, k);
+  if (i >= 0 && i < G.n0 && j >= 0 && j < G.n1 && k >= 0 && k < G.n2) return;
+  const long long o = at(G, i, j, k);
+  for (int f = 0; f < NF; ++f) PD.U[reg][f * G.sf + o] = PD.U[0][f * G.sf + o];
+}
+
+void launch_ghost_copy(const PatchDev* pd, const Work* w, int nblk, int reg, cudaStream_t st) {
+  if (nblk <= 0 || reg == 0) return;
+  k_ghost_copy<<<nblk, BS_ALL, 0, st>>>(pd, w, reg);
 }
 
 // ---------------------------------------------------------------------------

@@ -12,8 +12,8 @@ namespace gk {
 
 constexpr double PI = 3.14159265358979323846;
 
-template <int MODE>  // 0: write L(U) to rhs[patch]; 1: fused RK4 stage combination
-__global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
+template <int MODE, int BS>  // MODE 0: write L(U) to rhs[patch]; 1: fused RK4 stage combination
+__global__ void __launch_bounds__(BS) k_rhs(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
                                                  int stage, double dt, grmhd_params P, double* const* rhs_out) {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
@@ -426,13 +426,21 @@ __global__ void __launch_bounds__(BS_INT) k_rhs(const PatchDev* __restrict__ pd,
 #undef FP
 }
 
-void launch_rhs(const PatchDev* pd, const Work* w, int nblk, int reg, int mode, int stage, double dt,
-                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st) {
-  if (nblk <= 0) return;
+template <int BS>
+static void launch_rhs_bs(const PatchDev* pd, const Work* w, int nblk, int reg, int mode, int stage, double dt,
+                          const grmhd_params& P, double* const* rhs_dev, cudaStream_t st) {
   if (mode == 0)
-    k_rhs<0><<<nblk, BS_INT, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
+    k_rhs<0, BS><<<nblk, BS, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
   else
-    k_rhs<1><<<nblk, BS_INT, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
+    k_rhs<1, BS><<<nblk, BS, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
+}
+
+void launch_rhs(const PatchDev* pd, const Work* w, int nblk, int reg, int mode, int stage, double dt,
+                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs) {
+  if (nblk <= 0) return;
+  if (bs == 64) launch_rhs_bs<64>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  else if (bs == 256) launch_rhs_bs<256>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  else launch_rhs_bs<128>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
 }
 
 }  // namespace gk

@@ -56,8 +56,12 @@ def _lower(g, v):
     return [sum(g[S[i][j]] * v[j] for j in range(3)) for i in range(3)]
 
 
-def config0_id(n=(32, 32, 32), seed=0, pad=1, amp=1e-4, dx=None, x0=(0.0, 0.0, 0.0)):
-    """Fourier-mode initial data on the periodic unit cube (dx = 1/n0 unless given)."""
+def config0_id(n=(32, 32, 32), seed=0, pad=1, amp=1e-4, dx=None, x0=(0.0, 0.0, 0.0), norm=None, return_norm=False):
+    """Fourier-mode initial data on the periodic unit cube (dx = 1/n0 unless given).
+
+    The density, velocity and field amplitudes are normalised on the patch's own
+    points unless `norm` (as returned with return_norm=True) fixes them, which
+    keeps one global field across patches of different size and resolution."""
     n = tuple(int(v) for v in n)
     if dx is None:
         dx = 1.0 / n[0]
@@ -77,7 +81,8 @@ def config0_id(n=(32, 32, 32), seed=0, pad=1, amp=1e-4, dx=None, x0=(0.0, 0.0, 0
     # Density.
     ks, ph = _modes(rng)
     m = full(_mode_sum(x, y, z, ks, ph))
-    m = m / np.max(np.abs(m))
+    m_max = norm["m_max"] if norm else np.max(np.abs(m))
+    m = m / m_max
     rho = 1e-3 * (1.0 + 0.1 * m)
     ID[16] = rho
     ID[17] = 100.0 * rho  # eps = P / ((Gamma - 1) rho) with P = 100 rho^2, Gamma = 2
@@ -87,7 +92,7 @@ def config0_id(n=(32, 32, 32), seed=0, pad=1, amp=1e-4, dx=None, x0=(0.0, 0.0, 0
         ks, ph = _modes(rng)
         v.append(full(_mode_sum(x, y, z, ks, ph)))
     vmag = np.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
-    sc = 0.1 / np.max(vmag)
+    sc = norm["v_scale"] if norm else 0.1 / np.max(vmag)
     for a in range(3):
         ID[18 + a] = v[a] * sc
     # Magnetic field: Bbar = curl A (densitized, analytically divergence free).
@@ -106,11 +111,36 @@ def config0_id(n=(32, 32, 32), seed=0, pad=1, amp=1e-4, dx=None, x0=(0.0, 0.0, 0
     B2 = sum(B[a] * Bd[a] for a in range(3))
     Bv = sum(B[a] * vd[a] for a in range(3))
     b2 = B2 * (1.0 - v2) + Bv ** 2
-    s = np.sqrt(1.0 / np.max(b2 / rho))
+    s = norm["b_scale"] if norm else np.sqrt(1.0 / np.max(b2 / rho))
     for a in range(3):
         ID[21 + a] = B[a] * s
     ID[24] = 0.1
+    if return_norm:
+        return np.ascontiguousarray(ID), dict(m_max=m_max, v_scale=sc, b_scale=s)
     return np.ascontiguousarray(ID)
+
+
+EDGES = (16, 24, 32, 48, 64)
+
+
+def batched_specs(npatch=256, seed=2, levels=5, edges=EDGES, dx0=1.0 / 32):
+    """Uneven patches: each axis edge uniform over `edges`, level uniform in
+    0..levels-1 with dx = dx0 / 2^level, origin uniform in [0, 1)^3."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    out = []
+    for _ in range(npatch):
+        n = tuple(int(v) for v in rng.choice(edges, size=3))
+        lev = int(rng.integers(0, levels))
+        out.append(dict(n=n, level=lev, dx=dx0 / 2 ** lev, x0=tuple(float(v) for v in rng.uniform(0.0, 1.0, 3))))
+    return out
+
+
+def batched_id(spec, seed=0, norm=None):
+    """Initial data of one batched patch: the periodic Fourier field of seed
+    `seed` sampled on the patch's points (ghosts from the same field)."""
+    if norm is None:
+        _, norm = config0_id(n=(32, 32, 32), seed=seed, return_norm=True)
+    return config0_id(n=spec["n"], seed=seed, dx=spec["dx"], x0=spec["x0"], norm=norm)
 
 
 # ---------------------------------------------------------------------------
