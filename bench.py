@@ -41,6 +41,11 @@ WORKLOAD = "tov_magnetised_128^3_rk4_step"
 #   64 for stage 3).
 RHS_FLOPS_PER_POINT = 6724.0
 RK_FLOPS_PER_POINT = (128.0 * 3 + 64.0) / 4.0
+# DRAM bytes (read + write) per interior point of one k_rhs launch, from the
+# ncu capture in profiles/substep_kernels_tov64_ncu_full.md (64^3 case,
+# 195.1 + 232.1 MB over 262,144 points), scaled to a launch by its points;
+# set to None whenever k_rhs changes until it is captured again.
+RHS_TRAFFIC_BYTES_PER_POINT = (195.1e6 + 232.1e6) / 64 ** 3
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 4 FP64 flops per
 # clock per SM x 2070 MHz (nominal GB300 FP64 1.25 TFLOP/s = 152 x 2.07 GHz x 3.97).
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
@@ -273,8 +278,9 @@ def run_grmhd(args):
     flops = (RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT) * zones
     achieved = flops / (avg_rhs_ms / 1e3) / 1e12
     tot = sum(v[0] for v in prof.values()) or 1.0
+    traffic = RHS_TRAFFIC_BYTES_PER_POINT * zones if RHS_TRAFFIC_BYTES_PER_POINT else None
     roofline = {"bound": "alu", "kernel": "k_rhs (CCZ4 + MHD RHS + RK epilogue)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz",
                 "flops_per_point": RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
