@@ -76,6 +76,11 @@ def lib(flops=False):
             "oracle_substep_counted": (i, [vp, vp, vp, i, d, i, d, vp, vp, vp, vp, vp, vp, vp]),
             "oracle_c2p_point": (i, [vp, vp, vp, vp, d, d, vp, vp, vp]),
             "oracle_c2p_flat": (i, [vp, vp, l, vp, vp, vp, vp]),
+            "oracle_c2p_flat_ext": (i, [vp, vp, l, vp, vp, vp, vp, vp, d, vp, vp]),
+            "oracle_mlp_nparams": (i, []),
+            "oracle_mlp_forward": (i, [vp, l, vp, vp, i]),
+            "oracle_mlp_grad": (d, [vp, l, vp, vp, vp, i]),
+            "oracle_adam": (i, [vp, vp, vp, vp, l, d, d, d, d, i]),
             "oracle_prim2con_point": (i, [vp, vp, vp, vp]),
             "oracle_eos_from_eps": (i, [vp, vp, d, d, d, vp]),
             "oracle_eos_from_T": (i, [vp, vp, d, d, d, vp]),
@@ -203,6 +208,20 @@ class Oracle:
         self.L.oracle_c2p_flat(_ref(self.P), self.Tp, n, _p(cons), _p(prim), _p(status), _p(iters))
         return prim, status, iters
 
+    def c2p_flat_ext(self, cons, seeds=None, delta=0.0):
+        """Flat-metric con2prim with optional seeds (n, 3): prim, status, iters, roots (n, 3), seeded mask."""
+        cons = np.ascontiguousarray(cons, dtype=np.float64)
+        n = cons.shape[0]
+        prim = np.zeros((n, NP))
+        status = np.zeros(n, dtype=np.int8)
+        iters = np.zeros(n, dtype=np.int32)
+        roots = np.zeros((n, 3))
+        seeded = np.zeros(n, dtype=np.int8)
+        sd = None if seeds is None else np.ascontiguousarray(seeds, dtype=np.float64)
+        self.L.oracle_c2p_flat_ext(_ref(self.P), self.Tp, n, _p(cons), _p(prim), _p(status), _p(iters), _p(sd),
+                                   float(delta), _p(roots), _p(seeded))
+        return prim, status, iters, roots, seeded
+
     def eos_from_eps(self, rho, eps, ye):
         out = np.zeros(4)
         self.L.oracle_eos_from_eps(_ref(self.P), self.Tp, rho, eps, ye, _p(out))
@@ -264,6 +283,34 @@ def fd_d11(u2d, dx):
     cy, cx = u.shape[0] // 2, u.shape[1] // 2
     ptr = u.ctypes.data + 8 * (cy * u.shape[1] + cx)
     return lib().oracle_fd_d11(ptr, u.shape[1], dx)
+
+
+def mlp_forward(params, x, bf16=True):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.zeros((x.shape[0], 3))
+    lib().oracle_mlp_forward(_p(p), x.shape[0], _p(x), _p(y), 1 if bf16 else 0)
+    return y
+
+
+def mlp_grad(params, x, t, bf16=True):
+    """(loss, grad) of the mean-squared error; grad has the parameter layout."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(p.size)
+    loss = lib().oracle_mlp_grad(_p(p), x.shape[0], _p(x), _p(t), _p(g), 1 if bf16 else 0)
+    return loss, g
+
+
+def adam(w, m, v, g, lr, b1, b2, eps, t):
+    w, m, v = (np.ascontiguousarray(a, dtype=np.float64) for a in (w, m, v))
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().oracle_adam(_p(w), _p(m), _p(v), _p(g), w.size, lr, b1, b2, eps, t)
+    return w, m, v
+
+
+MLP_NPARAMS = 9091
 
 
 def mp5(f5):

@@ -136,6 +136,26 @@ int oracle_c2p_flat(const oracle_params* P, const oracle_eos_table* E, long n, c
   return worst;
 }
 
+// Flat-metric con2prim with optional seeds [n][3] (NULL: plain) and bracket
+// half-width delta; roots [n][3] (mu_+, mu, T) and seeded [n] (bit mask of
+// seed brackets used) may be NULL.
+int oracle_c2p_flat_ext(const oracle_params* P, const oracle_eos_table* E, long n, const double* cons, double* prim,
+                        int8_t* status, int* iters, const double* seeds, double delta, double* roots, int8_t* seeded) {
+  const double gt[6] = {1, 0, 0, 1, 0, 1};
+  int worst = 0;
+  for (long q = 0; q < n; ++q) {
+    double co[10];
+    int it = 0, sd = 0;
+    int st = c2p_point_ext(P, E, cons + q * 10, gt, 1.0, 1.0, prim + q * NP, co, &it, seeds ? seeds + 3 * q : nullptr,
+                           delta, roots ? roots + 3 * q : nullptr, &sd);
+    if (status) status[q] = (int8_t)st;
+    if (iters) iters[q] = it;
+    if (seeded) seeded[q] = (int8_t)sd;
+    if (st < worst) worst = st;
+  }
+  return worst;
+}
+
 // Undensitized conserved variables (D, DYe, tau, S_i, B^i) from primitives
 // (rho, eps, p, v^i, ..., Ye) and the physical metric gamma_ij.
 int oracle_prim2con_point(const double* prim, const double* B, const double* gdd, double* cons) {

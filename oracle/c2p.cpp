@@ -159,7 +159,36 @@ real brent(Fn fn, real a, real b, real fa, real fb, int max_iter, double xtol, i
 
 int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double cb[10], const double gtp[6],
               double chip, double alpha, double prim[NP], double cons_out[10], int* iters_out) {
+  return c2p_point_ext(P, E, cb, gtp, chip, alpha, prim, cons_out, iters_out, nullptr, 0.0, nullptr, nullptr);
+}
+
+namespace {
+// Seeded bracket (learned seeder, not part of the paper): [s(1 - d), s(1 + d)]
+// clipped to the plain bracket (0, hi].  Returns true (and the end values) when
+// it brackets a root of fn; otherwise the caller keeps the plain bracket.
+template <class Fn>
+bool seed_bracket(Fn fn, double s, double d, real hi, real* a, real* b, real* fa, real* fb, int* ev) {
+  if (!std::isfinite(s) || !(s > 0.0) || !(d > 0.0)) return false;
+  real lo = s * (1.0 - d);
+  real up = fmin(real(s * (1.0 + d)), hi);
+  if (!(lo > 0.0) || !(lo < up)) return false;
+  real flo = fn(lo), fup = fn(up);
+  *ev += 2;
+  if (!(flo <= 0.0 && fup >= 0.0)) return false;
+  *a = lo;
+  *b = up;
+  *fa = flo;
+  *fb = fup;
+  return true;
+}
+}  // namespace
+
+int c2p_point_ext(const oracle_params* P, const oracle_eos_table* E, const double cb[10], const double gtp[6],
+                  double chip, double alpha, double prim[NP], double cons_out[10], int* iters_out, const double* seed3,
+                  double delta, double* roots3, int* seeded_ok) {
   for (int n = 0; n < 10; ++n) cons_out[n] = cb[n];
+  if (roots3) roots3[0] = roots3[1] = roots3[2] = 0.0;
+  if (seeded_ok) *seeded_ok = 0;
   *iters_out = 0;
   // Metric: gamma_ij = gt_ij / chi, gamma^ij = chi gt^ij, sqrt(gamma) = sqrt(det gt) chi^{-3/2}.
   real gt[6], gtu[6], gdd[6], guu[6];
@@ -211,28 +240,48 @@ int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double cb
 
     // Step 2: mu_+ = root of f_a on (0, 1/h0].  f_a(1/h0) >= 0 analytically;
     // when rounding makes it <= 0 the root is the end point itself.
-    int it1 = 0, it2 = 0;
+    // iters counts every evaluation of f_a and of the master function.
+    int it1 = 0, it2 = 0, ev = 0;
     bool ok1 = true, ok2 = true;
     real mu_hi = 1.0 / F.h0;
-    real fa_hi = f_aux(F, mu_hi);
+    auto fa_fn = [&](real mu) { return f_aux(F, mu); };
+    auto fm_fn = [&](real x) { return f_master(P, E, F, x).f; };
     real mu_plus = mu_hi;
-    if (fa_hi > 0.0)
-      mu_plus = brent([&](real mu) { return f_aux(F, mu); }, 0.0, mu_hi, -1.0, fa_hi, P->max_iter, P->c2p_xtol, &it1,
-                      &ok1);
+    int sd = 0;
+    real sa, sb, sfa, sfb;
+    if (seed3 && seed_bracket(fa_fn, seed3[0], delta, mu_hi, &sa, &sb, &sfa, &sfb, &ev)) {
+      mu_plus = brent(fa_fn, sa, sb, sfa, sfb, P->max_iter, P->c2p_xtol, &it1, &ok1);
+      sd |= 1;
+    } else {
+      real fa_hi = f_aux(F, mu_hi);
+      ev += 1;
+      if (fa_hi > 0.0) mu_plus = brent(fa_fn, 0.0, mu_hi, -1.0, fa_hi, P->max_iter, P->c2p_xtol, &it1, &ok1);
+    }
     // Step 3: root of the master function on (0, mu_+].  f(mu_+) >= 0
     // analytically (it is exactly 0 when the velocity bound v_0 is reached, as
     // for states with tau below the kinetic energy); a rounding-negative
     // value means the root is mu_+.
-    real f0 = f_master(P, E, F, 0.0).f;
-    real fplus = f_master(P, E, F, mu_plus).f;
     real mu = mu_plus;
-    if (fplus > 0.0)
-      mu = brent([&](real x) { return f_master(P, E, F, x).f; }, 0.0, mu_plus, f0, fplus, P->max_iter, P->c2p_xtol,
-                 &it2, &ok2);
-    *iters_out = it1 + it2;
+    if (seed3 && seed_bracket(fm_fn, seed3[1], delta, mu_plus, &sa, &sb, &sfa, &sfb, &ev)) {
+      mu = brent(fm_fn, sa, sb, sfa, sfb, P->max_iter, P->c2p_xtol, &it2, &ok2);
+      sd |= 2;
+    } else {
+      real f0 = f_master(P, E, F, 0.0).f;
+      real fplus = f_master(P, E, F, mu_plus).f;
+      ev += 2;
+      if (fplus > 0.0)
+        mu = brent(fm_fn, 0.0, mu_plus, f0, fplus, P->max_iter, P->c2p_xtol, &it2, &ok2);
+    }
+    if (seeded_ok) *seeded_ok = sd;
+    *iters_out = it1 + it2 + ev;
     if (!ok1 || !ok2) return -5;
     // Step 4: primitives from the root.
     master_eval m = f_master(P, E, F, mu);
+    if (roots3) {
+      roots3[0] = dbl(mu_plus);
+      roots3[1] = dbl(mu);
+      roots3[2] = dbl(m.T);
+    }
     rho = m.rho;
     eps = m.eps;
     p = m.p;

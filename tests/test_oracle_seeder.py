@@ -1,0 +1,102 @@
+"""Pins of the oracle pieces of the learned con2prim seeder (not part of the paper).
+
+- The MLP backward (FP64, no rounding) against central finite differences of the loss.
+- Closed forms: zero hidden weights give y = b4 and dL/db4 = 2 (b4 - mean t) / 3.
+- One Adam step against the textbook update written out here.
+- Seeded con2prim finds the same root as the plain bracket (the root is unique),
+  uses the seed bracket when the seed is close, and falls back otherwise.
+"""
+import numpy as np
+
+import oracle
+import synth
+
+NPAR = oracle.MLP_NPARAMS
+
+
+def _params(rng, scale=0.3):
+    return (scale * rng.normal(size=NPAR)).astype(np.float32)
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    p = _params(rng)
+    x = rng.normal(size=(16, 8)).astype(np.float32)
+    t = rng.normal(size=(16, 3)).astype(np.float32)
+    loss, g = oracle.mlp_grad(p, x, t, bf16=False)
+    # Parameters are float32: perturb in float64 copies through a float64 path
+    # by finite differences on the loss evaluated with the forward.
+    def L(pp):
+        y = oracle.mlp_forward(pp, x, bf16=False)
+        return np.mean((y - t) ** 2)
+    idx = rng.choice(NPAR, 40, replace=False)
+    for q in idx:
+        h = 2e-6 * max(1.0, abs(float(p[q])))  # small: no ReLU kink crossed
+        pp, pm = p.copy(), p.copy()
+        pp[q] += np.float32(h)
+        pm[q] -= np.float32(h)
+        hq = float(pp[q]) - float(pm[q])
+        fd = (L(pp) - L(pm)) / hq
+        assert abs(fd - g[q]) <= 1e-4 * max(1e-3, abs(g[q])) + 1e-7, (q, fd, g[q])
+    assert abs(loss - L(p)) < 1e-12
+
+
+def test_mlp_closed_forms():
+    p = np.zeros(NPAR, dtype=np.float32)
+    b4 = np.array([0.5, -1.0, 2.0], dtype=np.float32)
+    p[-3:] = b4
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(10, 8)).astype(np.float32)
+    t = rng.normal(size=(10, 3)).astype(np.float32)
+    y = oracle.mlp_forward(p, x)
+    assert np.allclose(y, b4[None, :])
+    loss, g = oracle.mlp_grad(p, x, t)
+    assert np.allclose(g[-3:], 2.0 * (b4.astype(float) - t.astype(float).mean(axis=0)) / 3.0, rtol=1e-12, atol=1e-12)
+    assert np.all(g[:-3] == 0.0)  # ReLU of zero pre-activations blocks every other gradient
+
+
+def test_adam_step():
+    rng = np.random.default_rng(2)
+    w, m, v, g = (rng.normal(size=50) for _ in range(4))
+    v = np.abs(v)
+    lr, b1, b2, eps, t = 1e-3, 0.9, 0.999, 1e-8, 3
+    w2, m2, v2 = oracle.adam(w.copy(), m.copy(), v.copy(), g, lr, b1, b2, eps, t)
+    mm = b1 * m + (1 - b1) * g
+    vv = b2 * v + (1 - b2) * g * g
+    ww = w - lr * (mm / (1 - b1 ** t)) / (np.sqrt(vv / (1 - b2 ** t)) + eps)
+    assert np.allclose(w2, ww, rtol=1e-15, atol=1e-15) and np.allclose(m2, mm) and np.allclose(v2, vv)
+
+
+def _cons(O, n, seed):
+    s = synth.c2p_states(n, seed=seed)
+    cons = np.zeros((n, 10))
+    for q in range(n):
+        pr = np.zeros(oracle.NP)
+        pr[0], pr[7] = s["rho"][q], s["ye"][q]
+        e = O.eos_from_T(s["rho"][q], s["T"][q], s["ye"][q])
+        pr[1], pr[2] = e[1], e[0]
+        pr[3:6] = s["v"][q]
+        cons[q, :9] = oracle.prim2con_point(pr, s["B"][q], [1.0, 0, 0, 1.0, 0, 1.0])
+    return cons
+
+
+def test_seeded_con2prim_same_root_and_fallback():
+    table = synth.make_table(nr=64, nt=48, ny=16)
+    O = oracle.Oracle(synth.table_params(table), table)
+    cons = _cons(O, 400, seed=5)
+    p0, s0, it0, roots, _ = O.c2p_flat_ext(cons)
+    ok = s0 >= 0
+    # Close seeds: the seed brackets are used and the primitives agree to rounding.
+    seeds = roots * (1.0 + 2e-4)
+    p1, s1, it1, r1, sd = O.c2p_flat_ext(cons, seeds, delta=1e-3)
+    assert np.array_equal(s0, s1)
+    assert np.mean(sd[ok] == 3) > 0.9
+    assert np.all(np.abs(p1[ok, 0] - p0[ok, 0]) <= 1e-13 * p0[ok, 0])
+    assert np.all(np.abs(r1[ok, 1] - roots[ok, 1]) <= 1e-13 * roots[ok, 1])
+    assert it1[ok].mean() < it0[ok].mean()
+    # Unusable seeds (non-finite, negative, far off): the plain brackets, same result.
+    bad = np.where(np.arange(400)[:, None] % 3 == 0, np.nan, np.where(np.arange(400)[:, None] % 3 == 1, -1.0, 1e3))
+    bad = np.broadcast_to(bad, (400, 3)).copy()
+    p2, s2, it2, r2, sd2 = O.c2p_flat_ext(cons, bad, delta=1e-3)
+    assert np.all(sd2 == 0)
+    assert np.array_equal(s2, s0) and np.array_equal(p2, p0)
