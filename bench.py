@@ -59,8 +59,12 @@ def _args():
     a.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--e2e-steps", type=int, default=3)
-    a.add_argument("--workload", default="tov", choices=["tov", "batched"],
-                   help="tov: the 128^3 TOV star (default); batched: 256 uneven patches over 5 levels")
+    a.add_argument("--workload", default="tov", choices=["tov", "batched", "c2p"],
+                   help="tov: the 128^3 TOV star (default); batched: 256 uneven patches over 5 levels; "
+                        "c2p: con2prim of 2^24 tabulated-EOS states, plain vs NN-seeded")
+    a.add_argument("--c2p-states", type=int, default=1 << 24)
+    a.add_argument("--train-pairs", type=int, default=1 << 20)
+    a.add_argument("--train-epochs", type=int, default=40)
     a.add_argument("--edge", type=int, default=N_EDGE,
                    help="interior points per axis (the same [-20,20]^3 star; 128 is the benchmark workload)")
     return a.parse_args()
@@ -381,12 +385,172 @@ def run_batched(args):
     return 0
 
 
+def _c2p_cons(g, P, T, n, seed):
+    """Conserved states of the isolated con2prim workload, made on the GPU from
+    seeded primitives (rho, T, Ye, v, B) by the library's prim2con."""
+    import torch
+    import synth
+    st = synth.c2p_states(n, seed=seed)
+    prim = torch.zeros((n, 10), dtype=torch.float64)
+    prim[:, 0] = torch.from_numpy(st["rho"])
+    prim[:, 7] = torch.from_numpy(st["ye"])
+    prim[:, 8] = torch.from_numpy(st["T"])
+    prim[:, 3:6] = torch.from_numpy(st["v"])
+    B = torch.from_numpy(st["B"]).cuda()
+    prim = prim.cuda()
+    del st
+    cons = g.prim2con_flat(P, prim, B, table=T)
+    del prim, B
+    return cons
+
+
+def run_c2p(args):
+    """con2prim in isolation: 2^24 states, synthetic 256 x 128 x 64 table; the
+    seeder trained on 2^20 pairs (seed 13) made on the GPU; plain brackets
+    against network seeds (inference included in the seeded time)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_13965_gb300 as g
+    import synth
+
+    table = synth.make_table()
+    P = synth.table_params(table)
+    T = g.Table(table)
+    n = args.c2p_states
+    s = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    cons = _c2p_cons(g, P, T, n, seed=3)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    # ---- training pairs and training -------------------------------------
+    ntr = args.train_pairs
+    ctr = _c2p_cons(g, P, T, ntr, seed=13)
+    _, st, _, roots, _ = g.c2p_flat_seeded(P, ctr, None, table=T)
+    keep = st >= 0
+    f = g.seeder_features(ctr)[keep].contiguous()
+    t = g.seeder_targets(ctr, roots)[keep].contiguous()
+    del ctr, roots
+    S = g.Seeder(seed=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    hist = S.train(f, t, batch=4096, epochs=args.train_epochs, lr=3e-3, lr_final=3e-5)
+    e1.record(s)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    hist = hist.cpu().numpy()
+
+    # ---- bracket half-width from a validation slice ----------------------
+    nval = min(n, 1 << 20)
+    cv = cons[:nval]
+    sv = S.infer(cv)
+    _, _, it_plain_v, _, _ = g.c2p_flat_seeded(P, cv, None, table=T)
+    sweep = {}
+
+    def _ms(fn, k=3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record(s)
+        for _ in range(k):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    plain_ms_v = _ms(lambda: g.c2p_flat_seeded(P, cv, None, table=T))
+    for d in (3e-3, 1e-2, 3e-2, 1e-1):
+        _, _, itv, _, sdv = g.c2p_flat_seeded(P, cv, sv, d, table=T)
+        sweep[d] = (float(itv.double().mean()), float(((sdv & 2) > 0).double().mean()),
+                    _ms(lambda: g.c2p_flat_seeded(P, cv, sv, d, table=T)))
+    delta = min(sweep, key=lambda d: sweep[d][2])  # fastest, not fewest evaluations
+    del sv, cv
+
+    # ---- timed: plain and seeded over all n states -------------------------
+    out_p = [torch.empty((n, 10), dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.int8, device="cuda"),
+             torch.empty(n, dtype=torch.int32, device="cuda")]
+    out_s = [torch.empty_like(x) for x in out_p] + [torch.empty(n, dtype=torch.int8, device="cuda")]
+    seeds = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    L = g.load()
+    Pp = g.make_params(P)
+    import ctypes
+
+    def plain():
+        rc = L.grmhd_c2p_flat_seeded(ctypes.byref(Pp), T.ref, n, g._vp(cons), None, 0.0, g._vp(out_p[0]),
+                                     g._vp(out_p[1]), g._vp(out_p[2]), None, None, ctypes.c_void_p(s.cuda_stream))
+        assert rc == 0
+
+    def seeded():
+        rc = L.grmhd_seeder_infer(S.h, n, g._vp(cons), g._vp(seeds), ctypes.c_void_p(s.cuda_stream))
+        rc |= L.grmhd_c2p_flat_seeded(ctypes.byref(Pp), T.ref, n, g._vp(cons), g._vp(seeds), delta, g._vp(out_s[0]),
+                                      g._vp(out_s[1]), g._vp(out_s[2]), None, g._vp(out_s[3]),
+                                      ctypes.c_void_p(s.cuda_stream))
+        assert rc == 0
+
+    def infer_only():
+        assert L.grmhd_seeder_infer(S.h, n, g._vp(cons), g._vp(seeds), ctypes.c_void_p(s.cuda_stream)) == 0
+
+    def timed(fn, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(s)
+        for _ in range(k):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    for _ in range(max(args.warmup, 3)):
+        plain()
+        seeded()
+    K = args.steps
+    clocks = Clocks(0)
+    ms_plain = timed(plain, K)
+    ms_seeded = timed(seeded, K)
+    ms_infer = timed(infer_only, K)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    st_p, st_s = out_p[1], out_s[1]
+    same_status = bool(torch.equal(st_p, st_s))
+    ok = (st_p == 0) & (st_s == 0)
+    rel_rho = float(((out_s[0][:, 0] - out_p[0][:, 0]).abs() / out_p[0][:, 0]).masked_fill(~ok, 0).max())
+    ev_plain = float(out_p[2].double().mean())
+    ev_seeded = float(out_s[2].double().mean())
+    line = {"metric": METRIC, "value": n / (ms_seeded / 1e3), "unit": "con2prim solves/s", "n_gpus": 1, "steps": K,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_seeded, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (network bf16/fp32)", "data": "synthetic",
+            "config": {"workload": "con2prim_2^24_states_table_256x128x64" if n == 1 << 24 else
+                       "con2prim_%d_states_table_256x128x64" % n, "states": n, "metric": "flat",
+                       "train_pairs": ntr, "train_seed": 13, "state_seed": 3,
+                       "l2": "inputs larger than L2 (1.34 GB of conserved states)"},
+            "plain": {"solves_per_s": n / (ms_plain / 1e3), "ms": ms_plain, "evaluations_per_state": ev_plain},
+            "seeded": {"solves_per_s": n / (ms_seeded / 1e3), "ms": ms_seeded, "inference_ms": ms_infer,
+                       "evaluations_per_state": ev_seeded, "delta": delta,
+                       "mu_seed_bracket_used": float(((out_s[3] & 2) > 0).double().mean()),
+                       "mu_plus_not_solved": float(((out_s[3] & 4) > 0).double().mean())},
+            "speedup_seeded_vs_plain": ms_plain / ms_seeded,
+            "delta_sweep_on_2^20_states": {str(k): {"evaluations": v[0], "mu_seeded": v[1], "ms": v[2]}
+                                           for k, v in sweep.items()},
+            "plain_on_sweep_slice": {"evaluations": float(it_plain_v.double().mean()), "ms": plain_ms_v},
+            "training": {"ms": train_ms, "pairs": int(f.shape[0]), "epochs": args.train_epochs, "batch": 4096,
+                         "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1])},
+            "seeded_vs_plain": {"same_status": same_status, "max_rel_rho_diff": rel_rho},
+            "gpu_launches": 4 * K, "clocks": clk, "setup_s": gen_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "c2p":
+        return run_c2p(args)
     return run_grmhd(args)
 
 

@@ -276,6 +276,128 @@ int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long 
 int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_desc* d, const grmhd_eos_table* eos, int reg,
                           double* rhs, void* stream);
 
+/* ---- learned con2prim seeder ----------------------------------------------
+ *
+ * Not part of the paper's method: a small network that supplies starting
+ * guesses for the two Brent root finds of the con2prim appendix.  The FP64
+ * root finder still polishes every state with the paper's stop rule, and a
+ * guess that does not bracket the root falls back to the plain bracket, so
+ * the seeder changes evaluation counts, not results.
+ *
+ * Network: multilayer perceptron 8 -> 64 -> 64 -> 64 -> 3 with ReLU on the
+ * hidden layers.  Products run on the tensor cores with BF16 operands (inputs,
+ * weights, hidden activations and back-propagated gradients rounded to BF16,
+ * round to nearest even) and FP32 accumulation; biases, master weights and
+ * the Adam moments are FP32.
+ *
+ * Parameter vector (GRMHD_SEEDER_NPARAMS floats): W1[8][64], b1[64],
+ * W2[64][64], b2[64], W3[64][64], b3[64], W4[64][3], b4[3]; W[k][j] multiplies
+ * input k into unit j.  Normalisation vector (GRMHD_SEEDER_NNORM floats):
+ * feature mean[8], feature scale[8], target mean[3], target scale[3]; the
+ * network sees x = (f - mean) / scale and its output y maps to the target
+ * y * scale + mean.
+ *
+ * Features f of a conserved state (flat metric; D, DYe, tau, S_i, B^i as in
+ * the cons arrays of grmhd_c2p_flat), with q = tau / D, r = |S| / D,
+ * b2 = |B|^2 / D (Kastaun's scalars of the con2prim appendix) and
+ * Q = max(1 + q, 1e-30).  q, r, b2, Q and (1 + q - r)(1 + q + r) are formed in
+ * FP64; the logarithms of those quantities are taken in FP32:
+ *   f0 = log10 D,      f1 = DYe / D,      f2 = ln Q,
+ *   f3 = ln max((1 + q - r)(1 + q + r), 1e-30),   f4 = r / Q,
+ *   f5 = log10 max(b2, 1e-30),   f6 = S.B / (|S| |B|) (0 if S or B is 0),
+ *   f7 = b2 / Q.
+ * Targets t from the roots (mu_+, mu) and the Lorentz factor W at mu:
+ *   t0 = ln(mu_+ sqrt(1 + r^2)),  t1 = ln(mu Q),  t2 = ln W
+ * (corrections to the unmagnetised closed forms mu_+ = 1 / sqrt(h0^2 + r^2)
+ * and mu (1 + q) = 1 - p / (rho h W^2), with h0 ~ 1).
+ * Seeds from targets: mu_+ = exp(t0) / sqrt(1 + r^2), mu = exp(t1) / Q,
+ * W = exp(t2).
+ */
+#define GRMHD_SEEDER_NPARAMS 9091
+#define GRMHD_SEEDER_NNORM 22
+
+typedef struct grmhd_seeder grmhd_seeder; /* opaque: weights, Adam state, scratch */
+
+typedef struct {
+  int batch;       /* samples per Adam step: a multiple of 128 in [128, 65536] */
+  int epochs;      /* passes over the training set (floor(n / batch) steps each) */
+  float lr;        /* learning rate at the first step ... */
+  float lr_final;  /* ... decaying as a half cosine to this value at the last */
+  float beta1, beta2, eps; /* Adam constants */
+  int fit_norm;    /* 1: first set the normalisation to the training set's
+                      per-channel mean and standard deviation */
+} grmhd_train_cfg;
+
+/* Creates a seeder on the current device: weights uniform in
+ * +-sqrt(6 / fan_in) from a splitmix64 stream of `seed`, zero biases, identity
+ * normalisation (mean 0, scale 1), zero Adam state.  Synchronous. */
+int grmhd_seeder_create(grmhd_seeder** out, unsigned long long seed);
+
+/* Host copies of the parameters and/or the normalisation (either may be NULL).
+ * set resets the Adam state; both synchronise the device. */
+int grmhd_seeder_set_params(grmhd_seeder* s, const float* params, const float* norm);
+int grmhd_seeder_get_params(grmhd_seeder* s, float* params, float* norm);
+
+/* Features f (device float [n][8]) of the conserved states cons (device
+ * double [n][10], as grmhd_c2p_flat). */
+int grmhd_seeder_features(long long n, const double* cons, float* f, void* stream);
+
+/* Targets t (device float [n][3]) of the states cons (device double [n][10])
+ * from their roots (device double [n][3], as written by grmhd_c2p_flat_seeded
+ * without seeds). */
+int grmhd_seeder_targets(long long n, const double* cons, const double* roots, float* t, void* stream);
+
+/* Network output mapped to targets: t = net((f - mean) / scale) * scale + mean.
+ * f: device float [n][8]; t: device float [n][3]. */
+int grmhd_seeder_forward(grmhd_seeder* s, long long n, const float* f, float* t_out, void* stream);
+
+/* Gradient of the loss L = mean over the n samples and 3 outputs of
+ * (net(x) - (t - mean) / scale)^2 with respect to the parameter vector
+ * (device float [GRMHD_SEEDER_NPARAMS]), and L itself (device double [1]).
+ * Uses the same kernels as the training step.  1 <= n <= 65536. */
+int grmhd_seeder_grad(grmhd_seeder* s, long long n, const float* f, const float* t, float* grad, double* loss,
+                      void* stream);
+
+/* One Adam step with the gradient grad (device float [GRMHD_SEEDER_NPARAMS]),
+ * as step number `step` (>= 1; sets the bias corrections), learning rate lr. */
+int grmhd_seeder_adam(grmhd_seeder* s, const float* grad, long long step, float lr, float beta1, float beta2,
+                      float eps, void* stream);
+
+/* Trains on n pairs (f: device float [n][8], t: device float [n][3]): every
+ * step a forward and backward pass over one batch, partial gradients per
+ * 128-sample tile summed in a fixed order, then Adam; batches walk through the
+ * set in order.  The epoch's steps are captured once in a CUDA graph that is
+ * launched `epochs` times on `stream`.  loss_hist (device double [epochs] or
+ * NULL) receives each epoch's mean loss.  Resets the Adam state first; keeps
+ * the current weights as the starting point. */
+int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float* t, const grmhd_train_cfg* cfg,
+                       double* loss_hist, void* stream);
+
+/* Seeds (device double [n][3]: mu_+, mu, W) for the conserved states cons
+ * (device double [n][10]): features, network and the seed map in one kernel. */
+int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double* seeds, void* stream);
+
+void grmhd_seeder_destroy(grmhd_seeder* s);
+
+/* grmhd_c2p_flat with optional seeds (device double [n][3] or NULL).  The
+ * mu seed s gives the bracket [s (1 - delta), min(s (1 + delta), 1 / h0)]:
+ * (a) when f_a < 0 at its upper end the bracket lies below mu_+ (f_a changes
+ * sign once, at mu_+) and the master root is found on it without solving for
+ * mu_+; (b) otherwise mu_+ is solved, from the bracket
+ * [s_+ (1 - delta), s_+ (1 + delta)] of the mu_+ seed when f_a changes sign on
+ * it, and the mu seed bracket is clipped to mu_+.  A seed bracket on which the
+ * function keeps its sign (or a seed that is not finite and positive) falls
+ * back to the plain bracket of that step; results agree with the plain solve
+ * to the root finder's tolerance.  iters counts every evaluation of the
+ * auxiliary and master functions.  roots (device double [n][3] or NULL)
+ * receives (mu_+, mu, W at mu), zeros where a root find failed and mu_+ = 0
+ * when it was not solved; seeded (device int8 [n] or NULL): bit 0 the mu_+
+ * seed bracket was used, bit 1 the mu seed bracket, bit 2 mu_+ was not solved.
+ * The third seed (W) is not used. */
+int grmhd_c2p_flat_seeded(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
+                          const double* seeds, double delta, double* prim, int8_t* status, int32_t* iters,
+                          double* roots, int8_t* seeded, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

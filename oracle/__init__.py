@@ -81,6 +81,8 @@ def lib(flops=False):
             "oracle_mlp_forward": (i, [vp, l, vp, vp, i]),
             "oracle_mlp_grad": (d, [vp, l, vp, vp, vp, i]),
             "oracle_adam": (i, [vp, vp, vp, vp, l, d, d, d, d, i]),
+            "oracle_seeder_features": (i, [l, vp, vp]),
+            "oracle_seeder_targets": (i, [l, vp, vp, vp]),
             "oracle_prim2con_point": (i, [vp, vp, vp, vp]),
             "oracle_eos_from_eps": (i, [vp, vp, d, d, d, vp]),
             "oracle_eos_from_T": (i, [vp, vp, d, d, d, vp]),
@@ -311,6 +313,23 @@ def adam(w, m, v, g, lr, b1, b2, eps, t):
 
 
 MLP_NPARAMS = 9091
+
+
+def seeder_features(cons):
+    """Seeder features [n][8] (float64) of flat-metric conserved states [n][10]."""
+    c = np.ascontiguousarray(cons, dtype=np.float64)
+    f = np.zeros((c.shape[0], 8))
+    lib().oracle_seeder_features(c.shape[0], _p(c), _p(f))
+    return f
+
+
+def seeder_targets(cons, roots):
+    """Seeder targets [n][3] (float64) of states [n][10] from roots [n][3] = (mu_+, mu, W)."""
+    c = np.ascontiguousarray(cons, dtype=np.float64)
+    r = np.ascontiguousarray(roots, dtype=np.float64)
+    t = np.zeros((r.shape[0], 3))
+    lib().oracle_seeder_targets(r.shape[0], _p(c), _p(r), _p(t))
+    return t
 
 
 def mp5(f5):

@@ -137,7 +137,7 @@ int oracle_c2p_flat(const oracle_params* P, const oracle_eos_table* E, long n, c
 }
 
 // Flat-metric con2prim with optional seeds [n][3] (NULL: plain) and bracket
-// half-width delta; roots [n][3] (mu_+, mu, T) and seeded [n] (bit mask of
+// half-width delta; roots [n][3] (mu_+, mu, W) and seeded [n] (bit mask of
 // seed brackets used) may be NULL.
 int oracle_c2p_flat_ext(const oracle_params* P, const oracle_eos_table* E, long n, const double* cons, double* prim,
                         int8_t* status, int* iters, const double* seeds, double delta, double* roots, int8_t* seeded) {

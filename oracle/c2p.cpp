@@ -162,26 +162,6 @@ int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double cb
   return c2p_point_ext(P, E, cb, gtp, chip, alpha, prim, cons_out, iters_out, nullptr, 0.0, nullptr, nullptr);
 }
 
-namespace {
-// Seeded bracket (learned seeder, not part of the paper): [s(1 - d), s(1 + d)]
-// clipped to the plain bracket (0, hi].  Returns true (and the end values) when
-// it brackets a root of fn; otherwise the caller keeps the plain bracket.
-template <class Fn>
-bool seed_bracket(Fn fn, double s, double d, real hi, real* a, real* b, real* fa, real* fb, int* ev) {
-  if (!std::isfinite(s) || !(s > 0.0) || !(d > 0.0)) return false;
-  real lo = s * (1.0 - d);
-  real up = fmin(real(s * (1.0 + d)), hi);
-  if (!(lo > 0.0) || !(lo < up)) return false;
-  real flo = fn(lo), fup = fn(up);
-  *ev += 2;
-  if (!(flo <= 0.0 && fup >= 0.0)) return false;
-  *a = lo;
-  *b = up;
-  *fa = flo;
-  *fb = fup;
-  return true;
-}
-}  // namespace
 
 int c2p_point_ext(const oracle_params* P, const oracle_eos_table* E, const double cb[10], const double gtp[6],
                   double chip, double alpha, double prim[NP], double cons_out[10], int* iters_out, const double* seed3,
@@ -241,46 +221,93 @@ int c2p_point_ext(const oracle_params* P, const oracle_eos_table* E, const doubl
     // Step 2: mu_+ = root of f_a on (0, 1/h0].  f_a(1/h0) >= 0 analytically;
     // when rounding makes it <= 0 the root is the end point itself.
     // iters counts every evaluation of f_a and of the master function.
+    //
+    // With a seed s for mu (learned seeder, not part of the paper) the seed
+    // bracket is [lo, up] = [s (1 - delta), min(s (1 + delta), 1/h0)].  mu_+
+    // only bounds the bracket of Step 3, and f_a changes sign once, at mu_+:
+    //  (a) f_a(up) < 0: [lo, up] lies below mu_+; Step 3 runs on it and mu_+
+    //      is not solved;
+    //  (b) f_a(up) >= 0: mu_+ lies in (0, up] and is solved there; Step 3
+    //      runs on [lo, mu_+] when lo < mu_+, else on (0, mu_+].
+    // When the master function keeps its sign on the seed bracket, its signs
+    // narrow the plain bracket: f(lo) > 0 gives (0, lo]; in case (a) f(up) < 0
+    // gives [up, mu_+], with mu_+ solved on [up, 1/h0].
     int it1 = 0, it2 = 0, ev = 0;
     bool ok1 = true, ok2 = true;
     real mu_hi = 1.0 / F.h0;
     auto fa_fn = [&](real mu) { return f_aux(F, mu); };
     auto fm_fn = [&](real x) { return f_master(P, E, F, x).f; };
-    real mu_plus = mu_hi;
     int sd = 0;
-    real sa, sb, sfa, sfb;
-    if (seed3 && seed_bracket(fa_fn, seed3[0], delta, mu_hi, &sa, &sb, &sfa, &sfb, &ev)) {
-      mu_plus = brent(fa_fn, sa, sb, sfa, sfb, P->max_iter, P->c2p_xtol, &it1, &ok1);
-      sd |= 1;
-    } else {
-      real fa_hi = f_aux(F, mu_hi);
-      ev += 1;
-      if (fa_hi > 0.0) mu_plus = brent(fa_fn, 0.0, mu_hi, -1.0, fa_hi, P->max_iter, P->c2p_xtol, &it1, &ok1);
+    real lo = 0.0, up = mu_hi;
+    bool seeded = false;
+    if (seed3 && std::isfinite(seed3[1]) && seed3[1] > 0.0 && delta > 0.0) {
+      real l = seed3[1] * (1.0 - delta);
+      real u = fmin(real(seed3[1] * (1.0 + delta)), mu_hi);
+      if (l > 0.0 && l < u) {
+        seeded = true;
+        lo = l;
+        up = u;
+        sd |= 1;
+      }
     }
+    real fa_top = f_aux(F, up);
+    ev += 1;
+    bool case_a = seeded && fa_top < 0.0;
+    bool have_plus = !case_a;
+    real mu_plus = up;
+    if (!case_a && fa_top > 0.0)
+      mu_plus = brent(fa_fn, 0.0, up, -1.0, fa_top, P->max_iter, P->c2p_xtol, &it1, &ok1);
     // Step 3: root of the master function on (0, mu_+].  f(mu_+) >= 0
     // analytically (it is exactly 0 when the velocity bound v_0 is reached, as
     // for states with tau below the kinetic energy); a rounding-negative
     // value means the root is mu_+.
-    real mu = mu_plus;
-    if (seed3 && seed_bracket(fm_fn, seed3[1], delta, mu_plus, &sa, &sb, &sfa, &sfb, &ev)) {
-      mu = brent(fm_fn, sa, sb, sfa, sfb, P->max_iter, P->c2p_xtol, &it2, &ok2);
-      sd |= 2;
-    } else {
-      real f0 = f_master(P, E, F, 0.0).f;
-      real fplus = f_master(P, E, F, mu_plus).f;
-      ev += 2;
-      if (fplus > 0.0)
-        mu = brent(fm_fn, 0.0, mu_plus, f0, fplus, P->max_iter, P->c2p_xtol, &it2, &ok2);
+    real x_lo = 0.0, x_hi = mu_plus;
+    if (case_a) {
+      x_lo = lo;
+      x_hi = up;
+    } else if (seeded && lo < mu_plus) {
+      x_lo = lo;
     }
+    real f_lo = fm_fn(x_lo), f_hi = fm_fn(x_hi);
+    ev += 2;
+    bool from_seed = x_lo > 0.0;
+    if (x_lo > 0.0 && f_lo > 0.0) {
+      x_hi = x_lo;
+      f_hi = f_lo;
+      x_lo = 0.0;
+      f_lo = fm_fn(0.0);
+      ev += 1;
+      from_seed = false;
+    } else if (case_a && f_hi < 0.0) {
+      real fa_max = f_aux(F, mu_hi);
+      ev += 1;
+      mu_plus = mu_hi;
+      if (fa_max > 0.0) {
+        int itx = 0;
+        mu_plus = brent(fa_fn, up, mu_hi, fa_top, fa_max, P->max_iter, P->c2p_xtol, &itx, &ok1);
+        it1 += itx;
+      }
+      have_plus = true;
+      x_lo = up;
+      f_lo = f_hi;
+      x_hi = mu_plus;
+      f_hi = fm_fn(mu_plus);
+      ev += 1;
+      from_seed = false;
+    }
+    real mu = x_hi;
+    if (f_hi > 0.0) mu = brent(fm_fn, x_lo, x_hi, f_lo, f_hi, P->max_iter, P->c2p_xtol, &it2, &ok2);
+    if (from_seed) sd |= 2;
+    if (!have_plus) sd |= 4;
     if (seeded_ok) *seeded_ok = sd;
     *iters_out = it1 + it2 + ev;
     if (!ok1 || !ok2) return -5;
     // Step 4: primitives from the root.
     master_eval m = f_master(P, E, F, mu);
     if (roots3) {
-      roots3[0] = dbl(mu_plus);
+      roots3[0] = have_plus ? dbl(mu_plus) : 0.0;
       roots3[1] = dbl(mu);
-      roots3[2] = dbl(m.T);
+      roots3[2] = dbl(m.W);
     }
     rho = m.rho;
     eps = m.eps;

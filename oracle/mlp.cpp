@@ -7,6 +7,7 @@
 //
 // Parameter layout (floats, 9091): W1[8][64], b1[64], W2[64][64], b2[64],
 // W3[64][64], b3[64], W4[64][3], b4[3]; W[k][j] multiplies input k into unit j.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -131,6 +132,50 @@ double oracle_mlp_grad(const float* params, long n, const float* x, const float*
   }
   for (int q = 0; q < NPAR; ++q) grad[q] = g[q];
   return loss / (3.0 * (double)n);
+}
+
+// Seeder features of flat-metric conserved states cons[n][10] (D, DYe, tau,
+// S_i, B^i): with q = tau / D, r = |S| / D, b2 = |B|^2 / D and
+// Q = max(1 + q, 1e-30),
+//   (log10 D, DYe / D, ln Q, ln max((1 + q - r)(1 + q + r), 1e-30), r / Q,
+//    log10 max(b2, 1e-30), S.B / (|S| |B|) or 0, b2 / Q).
+int oracle_seeder_features(long n, const double* cons, double* f) {
+  for (long s = 0; s < n; ++s) {
+    const double* c = cons + 10 * s;
+    double D = c[0];
+    double Smag = std::sqrt(c[3] * c[3] + c[4] * c[4] + c[5] * c[5]);
+    double Bmag = std::sqrt(c[6] * c[6] + c[7] * c[7] + c[8] * c[8]);
+    double q = c[2] / D, r = Smag / D, b2 = Bmag * Bmag / D;
+    double Q = std::max(1.0 + q, 1e-30);
+    double* o = f + NI * s;
+    o[0] = std::log10(D);
+    o[1] = c[1] / D;
+    o[2] = std::log(Q);
+    o[3] = std::log(std::max((1.0 + q - r) * (1.0 + q + r), 1e-30));
+    o[4] = r / Q;
+    o[5] = std::log10(std::max(b2, 1e-30));
+    o[6] = (Smag > 0.0 && Bmag > 0.0) ? (c[3] * c[6] + c[4] * c[7] + c[5] * c[8]) / (Smag * Bmag) : 0.0;
+    o[7] = b2 / Q;
+  }
+  return 0;
+}
+
+// Seeder targets from the states cons[n][10] and roots[n][3] = (mu_+, mu, W):
+//   (ln(mu_+ sqrt(1 + r^2)), ln(mu max(1 + q, 1e-30)), ln W).
+// For B = 0 and h0 = 1, mu_+ = 1 / sqrt(1 + r^2) and mu (1 + q) = 1 - p / (rho h W^2),
+// so the targets are corrections to those closed forms.
+int oracle_seeder_targets(long n, const double* cons, const double* roots, double* t) {
+  for (long s = 0; s < n; ++s) {
+    const double* c = cons + 10 * s;
+    const double* r = roots + 3 * s;
+    double D = c[0];
+    double rr = std::sqrt(c[3] * c[3] + c[4] * c[4] + c[5] * c[5]) / D;
+    double Q = std::max(1.0 + c[2] / D, 1e-30);
+    t[3 * s] = std::log(r[0] * std::sqrt(1.0 + rr * rr));
+    t[3 * s + 1] = std::log(r[1] * Q);
+    t[3 * s + 2] = std::log(r[2]);
+  }
+  return 0;
 }
 
 // One Adam step (step number t >= 1) on FP64 copies of the state.

@@ -119,10 +119,11 @@ void prim2con_point(const real prim[NP], const real B[3], const real gdd[6], rea
 int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double cons_bar[10],
               const double gt[6], double chi, double alpha, double prim[NP], double cons_out[10],
               int* iters);
-// Same, optionally starting from seeds (mu_+, mu, T) with relative bracket
-// half-width delta (fallback to the plain brackets when a seed does not
-// bracket the root), and returning the roots (mu_+, mu, T).  seeded_ok gets
-// bit 0 / bit 1 set when the mu_+ / mu seed bracket was used.
+// Same, optionally starting from seeds (mu_+, mu, W) with relative bracket
+// half-width delta (only the mu seed is used), and returning (mu_+, mu, W at
+// mu) in roots3 (mu_+ is 0 when the seeded start made it unnecessary).
+// seeded_ok: bit 0 the seed was usable, bit 1 the final master bracket came
+// from the seed, bit 2 mu_+ was not solved.
 int c2p_point_ext(const oracle_params* P, const oracle_eos_table* E, const double cons_bar[10],
                   const double gt[6], double chi, double alpha, double prim[NP], double cons_out[10],
                   int* iters, const double* seed3, double delta, double* roots3, int* seeded_ok);

@@ -47,6 +47,12 @@ class C2PStats(ctypes.Structure):
                 ("failed", ctypes.c_longlong)]
 
 
+class TrainCfg(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int), ("epochs", ctypes.c_int), ("lr", ctypes.c_float),
+                ("lr_final", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("fit_norm", ctypes.c_int)]
+
+
 class GrmhdError(RuntimeError):
     pass
 
@@ -80,6 +86,26 @@ _SIGS = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_rhs_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                              ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong]),
+    "grmhd_seeder_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_features": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_targets": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "grmhd_seeder_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "grmhd_seeder_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_void_p]),
+    "grmhd_seeder_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_infer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "grmhd_seeder_destroy": (None, [ctypes.c_void_p]),
+    "grmhd_c2p_flat_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -318,3 +344,119 @@ def c2p_flat(params, cons, table=None, iters=False, stream=None, out=None):
                           ctypes.c_void_p(it.data_ptr()) if it is not None else None, ctypes.c_void_p(s.cuda_stream))
     _check(rc, None, "grmhd_c2p_flat")
     return (prim, status, it) if iters else (prim, status)
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(torch, stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def c2p_flat_seeded(params, cons, seeds=None, delta=1e-2, table=None, stream=None):
+    """Flat-metric con2prim with optional seeds (n, 3); returns
+    (prim, status, iters, roots, seeded) as device tensors."""
+    torch = _torch()
+    L = load()
+    n = cons.shape[0]
+    dev = cons.device
+    prim = torch.empty((n, NP), dtype=torch.float64, device=dev)
+    status = torch.empty((n,), dtype=torch.int8, device=dev)
+    it = torch.empty((n,), dtype=torch.int32, device=dev)
+    roots = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    sd = torch.empty((n,), dtype=torch.int8, device=dev)
+    P = make_params(params)
+    rc = L.grmhd_c2p_flat_seeded(ctypes.byref(P), table.ref if table is not None else None, n, _vp(cons),
+                                 _vp(seeds), float(delta), _vp(prim), _vp(status), _vp(it), _vp(roots), _vp(sd),
+                                 _stream(torch, stream))
+    _check(rc, None, "grmhd_c2p_flat_seeded")
+    return prim, status, it, roots, sd
+
+
+class Seeder:
+    """The learned con2prim seeder (weights, Adam state and scratch on the device)."""
+
+    NPARAMS = 9091
+    NNORM = 22
+
+    def __init__(self, seed=0):
+        self._torch = _torch()
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.grmhd_seeder_create(ctypes.byref(h), int(seed)), None, "grmhd_seeder_create")
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            load().grmhd_seeder_destroy(self.h)
+            self.h = None
+
+    def set_params(self, params=None, norm=None):
+        p = np.ascontiguousarray(params, dtype=np.float32) if params is not None else None
+        m = np.ascontiguousarray(norm, dtype=np.float32) if norm is not None else None
+        rc = load().grmhd_seeder_set_params(self.h, p.ctypes.data if p is not None else None,
+                                            m.ctypes.data if m is not None else None)
+        _check(rc, None, "grmhd_seeder_set_params")
+
+    def get_params(self):
+        p = np.zeros(self.NPARAMS, dtype=np.float32)
+        m = np.zeros(self.NNORM, dtype=np.float32)
+        _check(load().grmhd_seeder_get_params(self.h, p.ctypes.data, m.ctypes.data), None, "grmhd_seeder_get_params")
+        return p, m
+
+    def forward(self, f, stream=None):
+        torch = self._torch
+        t = torch.empty((f.shape[0], 3), dtype=torch.float32, device=f.device)
+        rc = load().grmhd_seeder_forward(self.h, f.shape[0], _vp(f), _vp(t), _stream(torch, stream))
+        _check(rc, None, "grmhd_seeder_forward")
+        return t
+
+    def grad(self, f, t, stream=None):
+        torch = self._torch
+        g = torch.empty((self.NPARAMS,), dtype=torch.float32, device=f.device)
+        loss = torch.empty((1,), dtype=torch.float64, device=f.device)
+        rc = load().grmhd_seeder_grad(self.h, f.shape[0], _vp(f), _vp(t), _vp(g), _vp(loss), _stream(torch, stream))
+        _check(rc, None, "grmhd_seeder_grad")
+        return loss, g
+
+    def adam(self, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        rc = load().grmhd_seeder_adam(self.h, _vp(grad), int(step), lr, beta1, beta2, eps,
+                                      _stream(self._torch, stream))
+        _check(rc, None, "grmhd_seeder_adam")
+
+    def train(self, f, t, batch=4096, epochs=10, lr=3e-3, lr_final=3e-5, beta1=0.9, beta2=0.999, eps=1e-8,
+              fit_norm=True, stream=None):
+        """Trains on (f, t); returns the per-epoch mean losses (device float64 tensor)."""
+        torch = self._torch
+        hist = torch.zeros((epochs,), dtype=torch.float64, device=f.device)
+        cfg = TrainCfg(batch, epochs, lr, lr_final, beta1, beta2, eps, 1 if fit_norm else 0)
+        rc = load().grmhd_seeder_train(self.h, f.shape[0], _vp(f), _vp(t), ctypes.byref(cfg), _vp(hist),
+                                       _stream(torch, stream))
+        _check(rc, None, "grmhd_seeder_train")
+        return hist
+
+    def infer(self, cons, stream=None):
+        """Seeds (n, 3) = (mu_+, mu, W) for flat-metric conserved states (n, 10)."""
+        torch = self._torch
+        s = torch.empty((cons.shape[0], 3), dtype=torch.float64, device=cons.device)
+        rc = load().grmhd_seeder_infer(self.h, cons.shape[0], _vp(cons), _vp(s), _stream(torch, stream))
+        _check(rc, None, "grmhd_seeder_infer")
+        return s
+
+
+def seeder_features(cons, stream=None):
+    torch = _torch()
+    f = torch.empty((cons.shape[0], 8), dtype=torch.float32, device=cons.device)
+    _check(load().grmhd_seeder_features(cons.shape[0], _vp(cons), _vp(f), _stream(torch, stream)), None,
+           "grmhd_seeder_features")
+    return f
+
+
+def seeder_targets(cons, roots, stream=None):
+    torch = _torch()
+    t = torch.empty((roots.shape[0], 3), dtype=torch.float32, device=roots.device)
+    _check(load().grmhd_seeder_targets(roots.shape[0], _vp(cons), _vp(roots), _vp(t), _stream(torch, stream)), None,
+           "grmhd_seeder_targets")
+    return t

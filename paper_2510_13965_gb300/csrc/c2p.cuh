@@ -111,6 +111,81 @@ DI EosOut eos_eps(const Eos& E, double rho, double eps, double ye) {
   return o;
 }
 
+// The master function's EOS step in one table location: eps clamped to
+// [eps_min(rho), eps_max(rho)], then (p, T, cs2) at the clamped eps.  For the
+// table the temperature cell search starts at *cell (the previous
+// evaluation's cell, or -1): eps increases strictly along T at fixed
+// (rho, Ye), so the cell with e_k <= eps < e_{k+1} is unique and the result
+// equals that of the full binary search.  *cell receives the cell used.
+struct EosClamp {
+  double eps, p, T, cs2, emin, emax;
+};
+template <bool FULL>
+DI EosClamp eos_clamped(const Eos& E, double rho, double eps_raw, double ye, int* cell) {
+  EosClamp o;
+  if (E.kind == 0) {
+    o.emin = 0.0;
+    o.emax = E.eps_max;
+    o.eps = fmax(fmin(o.emax, eps_raw), o.emin);
+    o.p = (E.gam - 1.0) * rho * o.eps;
+    o.T = 0.0;
+    o.cs2 = FULL ? E.gam * o.p / fma(rho, 1.0 + o.eps, o.p) : 0.0;
+    return o;
+  }
+  TabPos t = tab_pos(E, rho, ye);
+  double elo = tab_bl(t, E.e, 0), ehi = tab_bl(t, E.e, E.nt - 1);
+  o.emin = elo;
+  o.emax = ehi;
+  const double eps = fmax(fmin(ehi, eps_raw), elo);
+  o.eps = eps;
+  int lo = 0, hi = E.nt - 1;
+  if (eps <= elo) {
+    hi = 1;
+    ehi = tab_bl(t, E.e, 1);
+  } else if (eps >= ehi) {
+    lo = E.nt - 2;
+    elo = tab_bl(t, E.e, lo);
+  } else {
+    bool found = false;
+    int k = *cell;
+    if (k >= 0 && k <= E.nt - 2) {
+      double ek = tab_bl(t, E.e, k), ek1 = tab_bl(t, E.e, k + 1);
+      if (ek <= eps && eps < ek1) {
+        lo = k;
+        hi = k + 1;
+        elo = ek;
+        ehi = ek1;
+        found = true;
+      }
+    }
+    if (!found) {
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        double em = tab_bl(t, E.e, mid);
+        if (em <= eps) {
+          lo = mid;
+          elo = em;
+        } else {
+          hi = mid;
+          ehi = em;
+        }
+      }
+    }
+  }
+  *cell = lo;
+  double w = fmin(fmax((eps - elo) / (ehi - elo), 0.0), 1.0);
+  double p0 = tab_bl(t, E.p, lo), p1 = tab_bl(t, E.p, lo + 1);
+  o.p = fma(w, p1 - p0, p0);
+  if (FULL) {
+    double c0 = tab_bl(t, E.c, lo), c1 = tab_bl(t, E.c, lo + 1);
+    o.cs2 = fma(w, c1 - c0, c0);
+    o.T = exp10(fma((double)lo + w, E.dlt, E.lt0));
+  } else {
+    o.cs2 = o.T = 0.0;
+  }
+  return o;
+}
+
 // (p, eps, cs2) from (rho, T, ye) (table), or the cold polytrope (ideal gas).
 DI EosOut eos_T(const Eos& E, double rho, double T, double ye) {
   EosOut o;
@@ -182,7 +257,7 @@ DI double c2p_faux(const C2PFix& F, double mu) {
 }
 
 template <bool FULL>
-DI C2PEval c2p_master(const grmhd_params& P, const Eos& E, const C2PFix& F, double mu) {
+DI C2PEval c2p_master(const grmhd_params& P, const Eos& E, const C2PFix& F, double mu, int* cell) {
   C2PEval m;
   double rbar2;
   c2p_chi_rbar(F, mu, &m.chi, &rbar2);
@@ -196,9 +271,8 @@ DI C2PEval c2p_master(const grmhd_params& P, const Eos& E, const C2PFix& F, doub
   m.rho = fmax(fmin(P.rho_max, m.rho_raw), P.rho_min);
   double x = fma(-mu, rbar2, qbar);  // qbar - mu rbar^2
   m.eps_raw = fma(m.W, x + 1.0, -1.0);
-  double emin = eos_emin(E, m.rho, F.ye), emax = eos_emax(E, m.rho, F.ye);
-  m.eps = fmax(fmin(emax, m.eps_raw), emin);
-  EosOut eo = eos_eps(E, m.rho, m.eps, F.ye);
+  EosClamp eo = eos_clamped<FULL>(E, m.rho, m.eps_raw, F.ye, cell);
+  m.eps = eo.eps;
   m.p = eo.p;
   if (FULL) {
     m.T = eo.T;
@@ -284,15 +358,19 @@ struct C2POut {
   double prim[NP];
   double cons[6];  // corrected densitized D, DYe, tau, S_i (valid when status > 0)
   int status;
-  int iters;
+  int iters;       // evaluations of f_a and of the master function
+  int seeded;      // bit 0: seed usable; bit 1: master bracket from the seed; bit 2: mu_+ not solved
+  double mu_plus, mu, W_root;  // roots and W at mu (0 unless the root finds converged; mu_+ 0 if not solved)
 };
 
 // con2prim at one point.  cb: densitized (D, DYe, tau, S_i, B^i); gdd/guu:
 // physical metric and inverse; sg = sqrt(gamma); alpha for the BH test.
 DI void c2p_point(const grmhd_params& P, const Eos& E, const double cb[9], const double gdd[6], const double guu[6],
-                  double sg, double alpha, C2POut& o) {
+                  double sg, double alpha, C2POut& o, const double* seed = nullptr, double delta = 0.0) {
   for (int n = 0; n < NP; ++n) o.prim[n] = 0.0;
   o.iters = 0;
+  o.seeded = 0;
+  o.mu_plus = o.mu = o.W_root = 0.0;
   bool finite = isfinite(sg) && sg > 0.0;
   for (int n = 0; n < 9; ++n) finite = finite && isfinite(cb[n]);
   if (!finite) {
@@ -326,26 +404,91 @@ DI void c2p_point(const grmhd_params& P, const Eos& E, const double cb[9], const
     F.rB = r[0] * Bc[0] + r[1] * Bc[1] + r[2] * Bc[2];
     F.B2rp2 = fma(F.B2, F.r2, -F.rB * F.rB);
     F.v02 = F.r2 / fma(F.h0, F.h0, F.r2);
-    int it1 = 0, it2 = 0, ok1 = 1, ok2 = 1;
-    double muh = 1.0 / F.h0;
-    // A non-positive f at the upper end of either bracket (zero analytically,
-    // negative by rounding) makes that end point the root.
-    double fah = c2p_faux(F, muh);
-    double mup = muh;
-    if (fah > 0.0)
-      mup = brent([&](double mu) { return c2p_faux(F, mu); }, 0.0, muh, -1.0, fah, P.max_iter, P.c2p_xtol, &it1, &ok1);
-    double f0 = c2p_master<false>(P, E, F, 0.0).f;
-    double fp = c2p_master<false>(P, E, F, mup).f;
-    double mu = mup;
-    if (fp > 0.0)
-      mu = brent([&](double x) { return c2p_master<false>(P, E, F, x).f; }, 0.0, mup, f0, fp, P.max_iter, P.c2p_xtol,
-                 &it2, &ok2);
-    o.iters = it1 + it2;
+    // With a seed s for mu (learned seeder, not part of the paper) the seed
+    // bracket is [lo, up] = [s (1 - delta), min(s (1 + delta), 1/h0)].  mu_+
+    // only bounds the master root's bracket, and f_a changes sign once, at
+    // mu_+: (a) f_a(up) < 0: [lo, up] lies below mu_+, which is not solved;
+    // (b) f_a(up) >= 0: mu_+ is solved on (0, up] and the master bracket is
+    // [lo, mu_+] (or (0, mu_+] when lo >= mu_+).  A master bracket without a
+    // sign change is narrowed by the signs found: f(lo) > 0 gives (0, lo]; in
+    // case (a) f(up) < 0 gives [up, mu_+] with mu_+ solved on [up, 1/h0].
+    // Every lane goes through the same call sites (one f_a and one master
+    // Brent, two bracket evaluations), so mixed warps do not serialise.
+    // o.iters counts every evaluation of f_a and of the master function.
+    int it1 = 0, it2 = 0, ok1 = 1, ok2 = 1, ev = 0, sd = 0;
+    const double muh = 1.0 / F.h0;
+    auto fa_fn = [&](double mu) { return c2p_faux(F, mu); };
+    int tcell = -1;  // temperature cell of the previous master evaluation
+    auto fm_fn = [&](double x) { return c2p_master<false>(P, E, F, x, &tcell).f; };
+    double lo = 0.0, up = muh;
+    bool seeded = false;
+    if (seed && isfinite(seed[1]) && seed[1] > 0.0 && delta > 0.0) {
+      double l = seed[1] * (1.0 - delta);
+      double u = fmin(seed[1] * (1.0 + delta), muh);
+      if (l > 0.0 && l < u) {
+        seeded = true;
+        lo = l;
+        up = u;
+        sd |= 1;
+      }
+    }
+    double fa_top = c2p_faux(F, up);
+    ev += 1;
+    const bool case_a = seeded && fa_top < 0.0;
+    bool have_plus = !case_a;
+    double mup = up;
+    // A non-positive f_a at the upper end (zero analytically, negative by
+    // rounding at 1/h0) makes that end point the root.
+    if (!case_a && fa_top > 0.0) mup = brent(fa_fn, 0.0, up, -1.0, fa_top, P.max_iter, P.c2p_xtol, &it1, &ok1);
+    double x_lo = 0.0, x_hi = mup;
+    if (case_a) {
+      x_lo = lo;
+      x_hi = up;
+    } else if (seeded && lo < mup) {
+      x_lo = lo;
+    }
+    double f_lo = fm_fn(x_lo), f_hi = fm_fn(x_hi);
+    ev += 2;
+    bool from_seed = x_lo > 0.0;
+    if (x_lo > 0.0 && f_lo > 0.0) {
+      x_hi = x_lo;
+      f_hi = f_lo;
+      x_lo = 0.0;
+      f_lo = fm_fn(0.0);
+      ev += 1;
+      from_seed = false;
+    } else if (case_a && f_hi < 0.0) {
+      double fa_max = c2p_faux(F, muh);
+      ev += 1;
+      mup = muh;
+      if (fa_max > 0.0) {
+        int itx = 0;
+        mup = brent(fa_fn, up, muh, fa_top, fa_max, P.max_iter, P.c2p_xtol, &itx, &ok1);
+        it1 += itx;
+      }
+      have_plus = true;
+      x_lo = up;
+      f_lo = f_hi;
+      x_hi = mup;
+      f_hi = fm_fn(mup);
+      ev += 1;
+      from_seed = false;
+    }
+    // f(mu_+) >= 0 analytically; a rounding-negative value makes mu_+ the root.
+    double mu = x_hi;
+    if (f_hi > 0.0) mu = brent(fm_fn, x_lo, x_hi, f_lo, f_hi, P.max_iter, P.c2p_xtol, &it2, &ok2);
+    if (from_seed) sd |= 2;
+    if (!have_plus) sd |= 4;
+    o.iters = it1 + it2 + ev;
+    o.seeded = sd;
     if (!ok1 || !ok2) {
       o.status = -5;
       return;
     }
-    C2PEval m = c2p_master<true>(P, E, F, mu);
+    C2PEval m = c2p_master<true>(P, E, F, mu, &tcell);
+    o.mu_plus = have_plus ? mup : 0.0;
+    o.mu = mu;
+    o.W_root = m.W;
     rho = m.rho;
     eps = m.eps;
     p = m.p;

@@ -1,0 +1,897 @@
+// Learned con2prim seeder (no counterpart in the paper) and the seeded flat
+// con2prim.
+//
+// Network 8 -> 64 -> 64 -> 64 -> 3 (ReLU).  One CTA of 128 threads (4 warps)
+// owns a tile of 128 samples.  Weights are converted to BF16 in shared memory;
+// activations stay in shared memory as BF16.  Every product is
+// mma.sync.m16n8k16 (BF16 operands, FP32 accumulate):
+//   forward        H_l = relu(H_{l-1} W_l + b_l)      warp w: sample rows 32w..32w+31
+//   backward       dZ_l = [H_l > 0] (dZ_{l+1} W_{l+1}^T)    same rows
+//   weight grads   dW_l = H_{l-1}^T dZ_l             warp w: 16 rows of dW_l, K = 128 samples
+// The tile's partial gradient goes to its own slot of a partial-gradient
+// array; the Adam kernel sums the slots in a fixed order, so training is
+// deterministic.
+#include <cuda_bf16.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include "kern.cuh"
+
+namespace gk {
+namespace sd {
+
+constexpr int NI = 8, NH = 64, NO = 3;
+constexpr int OW1 = 0, OB1 = OW1 + NI * NH, OW2 = OB1 + NH, OB2 = OW2 + NH * NH, OW3 = OB2 + NH,
+              OB3 = OW3 + NH * NH, OW4 = OB3 + NH, OB4 = OW4 + NH * NO, NPAR = OB4 + NO;
+static_assert(NPAR == GRMHD_SEEDER_NPARAMS, "parameter count");
+constexpr int NNORM = 2 * NI + 2 * NO;
+static_assert(NNORM == GRMHD_SEEDER_NNORM, "normalisation count");
+constexpr int TM = 128;    // samples per CTA
+constexpr int LDH = 72;    // row stride (BF16 elements) of 64-wide tiles: conflict-free fragment loads
+constexpr int LDX = 24;    // row stride of 16-wide tiles
+constexpr int MAX_BATCH = 65536;
+constexpr int MAX_TILES = MAX_BATCH / TM;
+
+typedef unsigned short u16;
+
+// Shared-memory layout (BF16 tiles as raw 16-bit words).
+constexpr int S_W1 = 0;                      // [16][LDH]   rows 8..15 zero
+constexpr int S_W2 = S_W1 + 16 * LDH;        // [64][LDH]
+constexpr int S_W3 = S_W2 + 64 * LDH;        // [64][LDH]
+constexpr int S_W4 = S_W3 + 64 * LDH;        // [64][LDX]   cols 3.. zero
+constexpr int S_X = S_W4 + 64 * LDX;         // [128][LDX]  cols 8.. zero
+constexpr int S_H1 = S_X + TM * LDX;         // [128][LDH]
+constexpr int S_H2 = S_H1 + TM * LDH;
+constexpr int S_H3 = S_H2 + TM * LDH;        // training only (inference ping-pongs H1 / H2)
+constexpr int S_DZ = S_H3 + TM * LDH;        // training only
+constexpr int S_DY = S_DZ + TM * LDH;        // [128][LDX]  training only
+constexpr int S_END_INFER = S_H3;
+constexpr int S_END_TRAIN = S_DY + TM * LDX;
+// FP32 area after the BF16 words: biases (3 x 64 + 4), normalisation (22),
+// outputs Y[128][4], per-warp bias-gradient partials [4][64 * 3 + 4], loss partials [4].
+constexpr int F_B = 0;
+constexpr int F_NORM = F_B + 3 * NH + 4;
+constexpr int F_Y = F_NORM + NNORM + 2;
+constexpr int F_GB = F_Y + TM * 4;
+constexpr int F_LOSS = F_GB + 4 * (3 * NH + 4);
+constexpr int F_END = F_LOSS + 4 * 2;  // doubles stored as float pairs
+constexpr size_t smem_bytes(bool train) {
+  return (size_t)(train ? S_END_TRAIN : S_END_INFER) * 2 + (size_t)F_END * 4;
+}
+
+DI u16 bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+DI bool pos(u16 h) { return h != 0 && !(h & 0x8000u); }
+DI uint32_t pk(u16 lo, u16 hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
+DI uint32_t pkf(float lo, float hi) { return pk(bf(lo), bf(hi)); }
+
+// A fragment of a 16x16 tile whose element (r, c) is p[r * sr + c * sc].
+DI void frag_a(const u16* p, int sr, int sc, int lane, uint32_t a[4]) {
+  int g = lane >> 2, t2 = (lane & 3) * 2;
+  a[0] = pk(p[g * sr + t2 * sc], p[g * sr + (t2 + 1) * sc]);
+  a[1] = pk(p[(g + 8) * sr + t2 * sc], p[(g + 8) * sr + (t2 + 1) * sc]);
+  a[2] = pk(p[g * sr + (t2 + 8) * sc], p[g * sr + (t2 + 9) * sc]);
+  a[3] = pk(p[(g + 8) * sr + (t2 + 8) * sc], p[(g + 8) * sr + (t2 + 9) * sc]);
+}
+// B fragment of a 16x8 (k x n) tile whose element (k, n) is p[k * sr + n * sc].
+DI void frag_b(const u16* p, int sr, int sc, int lane, uint32_t b[2]) {
+  int g = lane >> 2, t2 = (lane & 3) * 2;
+  b[0] = pk(p[t2 * sr + g * sc], p[(t2 + 1) * sr + g * sc]);
+  b[1] = pk(p[(t2 + 8) * sr + g * sc], p[(t2 + 9) * sr + g * sc]);
+}
+DI void mma(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+DI void st2(u16* p, float lo, float hi) { *reinterpret_cast<uint32_t*>(p) = pkf(lo, hi); }
+
+// Hidden layer on the warp's 32 rows: out = bf16(relu(in W + b)), W [K][64] at w (stride LDH).
+template <int KS>
+DI void fwd_hidden(const u16* in, int ldin, const u16* w, const float* b, u16* out, int row0, int lane) {
+  int g = lane >> 2, t2 = (lane & 3) * 2;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      acc[nt][0] = acc[nt][2] = b[nt * 8 + t2];
+      acc[nt][1] = acc[nt][3] = b[nt * 8 + t2 + 1];
+    }
+    const u16* a0 = in + (row0 + mt * 16) * ldin;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      uint32_t a[4];
+      frag_a(a0 + ks * 16, ldin, 1, lane, a);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t bb[2];
+        frag_b(w + ks * 16 * LDH + nt * 8, LDH, 1, lane, bb);
+        mma(acc[nt], a, bb);
+      }
+    }
+    u16* o = out + (row0 + mt * 16) * LDH;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      st2(o + g * LDH + nt * 8 + t2, fmaxf(acc[nt][0], 0.f), fmaxf(acc[nt][1], 0.f));
+      st2(o + (g + 8) * LDH + nt * 8 + t2, fmaxf(acc[nt][2], 0.f), fmaxf(acc[nt][3], 0.f));
+    }
+  }
+}
+
+// Output layer on the warp's 32 rows: Y[s][j] = in[s] . W4[:, j] + b4[j], j < 3.
+DI void fwd_out(const u16* in, const u16* w4, const float* b4, float* Y, int row0, int lane) {
+  int g = lane >> 2, t2 = (lane & 3) * 2;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    float acc[4];
+    acc[0] = acc[2] = t2 < NO ? b4[t2] : 0.f;
+    acc[1] = acc[3] = t2 + 1 < NO ? b4[t2 + 1] : 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      uint32_t a[4], bb[2];
+      frag_a(in + (row0 + mt * 16) * LDH + ks * 16, LDH, 1, lane, a);
+      frag_b(w4 + ks * 16 * LDX, LDX, 1, lane, bb);
+      mma(acc, a, bb);
+    }
+    int r = row0 + mt * 16 + g;
+    if (t2 < 4) {
+      Y[r * 4 + t2] = acc[0];
+      Y[r * 4 + t2 + 1] = acc[1];
+      Y[(r + 8) * 4 + t2] = acc[2];
+      Y[(r + 8) * 4 + t2 + 1] = acc[3];
+    }
+  }
+}
+
+// Activation gradient on the warp's 32 rows:
+//   dz[s][k] = [h[s][k] > 0] sum_j d[s][j] W[k][j]
+// d: [128][K] at (din, ldd); W stored as w[k * ldw + j] (k < 64, j < K);
+// the bf16(dz) goes to out (stride LDH), the FP32 column sums of dz to gb[64].
+template <int KS>
+DI void bwd_act(const u16* din, int ldd, const u16* w, int ldw, const u16* h, u16* out, float* gb, int row0,
+                int lane) {
+  int g = lane >> 2, t2 = (lane & 3) * 2;
+  float cs[8][2];
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) cs[nt][0] = cs[nt][1] = 0.f;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      uint32_t a[4];
+      frag_a(din + (row0 + mt * 16) * ldd + ks * 16, ldd, 1, lane, a);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t bb[2];
+        frag_b(w + nt * 8 * ldw + ks * 16, 1, ldw, lane, bb);  // (k = j, n = unit) -> w[unit][j]
+        mma(acc[nt], a, bb);
+      }
+    }
+    int r0 = row0 + mt * 16 + g, r1 = r0 + 8;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      int c = nt * 8 + t2;
+      float v0 = pos(h[r0 * LDH + c]) ? acc[nt][0] : 0.f;
+      float v1 = pos(h[r0 * LDH + c + 1]) ? acc[nt][1] : 0.f;
+      float v2 = pos(h[r1 * LDH + c]) ? acc[nt][2] : 0.f;
+      float v3 = pos(h[r1 * LDH + c + 1]) ? acc[nt][3] : 0.f;
+      st2(out + r0 * LDH + c, v0, v1);
+      st2(out + r1 * LDH + c, v2, v3);
+      cs[nt][0] += v0 + v2;
+      cs[nt][1] += v1 + v3;
+    }
+  }
+  // Column sums over the warp's rows: reduce over the 8 row groups.
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float v = cs[nt][e];
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      if (g == 0) gb[nt * 8 + t2 + e] = v;
+    }
+}
+
+// Weight gradient rows k0..k0+15 of dW = A^T D over the 128 samples:
+// A: [128][*] at (a, lda) (columns k), D: [128][*] at (d, ldd) (columns j).
+// Writes dW[k][j] = out[k * nj + j] for k < kmax, j < nj, columns nt0..nt0+NT-1 (n8 tiles).
+template <int NT>
+DI void bwd_weight(const u16* a, int lda, const u16* d, int ldd, float* out, int nj, int k0, int kmax, int nt0,
+                   int lane) {
+  int g = lane >> 2, t2 = (lane & 3) * 2;
+  float acc[NT][4];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < TM / 16; ++ks) {
+    uint32_t af[4];
+    frag_a(a + ks * 16 * lda + k0, 1, lda, lane, af);  // (r = k, c = sample)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      uint32_t bb[2];
+      frag_b(d + ks * 16 * ldd + (nt0 + nt) * 8, ldd, 1, lane, bb);
+      mma(acc[nt], af, bb);
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    int j = (nt0 + nt) * 8 + t2;
+    int k = k0 + g;
+    if (k < kmax) {
+      if (j < nj) out[k * nj + j] = acc[nt][0];
+      if (j + 1 < nj) out[k * nj + j + 1] = acc[nt][1];
+    }
+    if (k + 8 < kmax) {
+      if (j < nj) out[(k + 8) * nj + j] = acc[nt][2];
+      if (j + 1 < nj) out[(k + 8) * nj + j + 1] = acc[nt][3];
+    }
+  }
+}
+
+// Loads the weights (BF16) and biases / normalisation (FP32) into shared memory.
+DI void load_params(const float* __restrict__ w, const float* __restrict__ norm, u16* S, float* F) {
+  for (int q = threadIdx.x; q < 16 * LDH; q += blockDim.x) {
+    int k = q / LDH, j = q % LDH;
+    S[S_W1 + q] = (k < NI && j < NH) ? bf(w[OW1 + k * NH + j]) : 0;
+  }
+  for (int q = threadIdx.x; q < 64 * LDH; q += blockDim.x) {
+    int k = q / LDH, j = q % LDH;
+    S[S_W2 + q] = j < NH ? bf(w[OW2 + k * NH + j]) : 0;
+    S[S_W3 + q] = j < NH ? bf(w[OW3 + k * NH + j]) : 0;
+  }
+  for (int q = threadIdx.x; q < 64 * LDX; q += blockDim.x) {
+    int k = q / LDX, j = q % LDX;
+    S[S_W4 + q] = j < NO ? bf(w[OW4 + k * NO + j]) : 0;
+  }
+  for (int q = threadIdx.x; q < NH; q += blockDim.x) {
+    F[F_B + q] = w[OB1 + q];
+    F[F_B + NH + q] = w[OB2 + q];
+    F[F_B + 2 * NH + q] = w[OB3 + q];
+  }
+  if (threadIdx.x < 4) F[F_B + 3 * NH + threadIdx.x] = threadIdx.x < NO ? w[OB4 + threadIdx.x] : 0.f;
+  if (threadIdx.x < NNORM) F[F_NORM + threadIdx.x] = norm[threadIdx.x];
+}
+
+// Features of one flat-metric conserved state (D, DYe, tau, S_i, B^i).  The
+// quantities whose cancellation BF16 inputs could not resolve ((1 + q)^2 - r^2
+// at large Lorentz factors, r and q themselves) are formed in FP64; the
+// logarithms of the formed quantities, whose results are FP32 features, run
+// in FP32.
+DI void features(const double* c, float f[NI]) {
+  double D = c[0], iD = 1.0 / D;
+  double q = c[2] * iD;
+  double S2 = c[3] * c[3] + c[4] * c[4] + c[5] * c[5];
+  double B2 = c[6] * c[6] + c[7] * c[7] + c[8] * c[8];
+  double r = sqrt(S2) * iD, b2 = B2 * iD;
+  double Q = fmax(1.0 + q, 1e-30);
+  double X = fmax((1.0 + q - r) * (1.0 + q + r), 1e-30);
+  float SB = (float)(c[3] * c[6] + c[4] * c[7] + c[5] * c[8]);
+  float den = sqrtf((float)S2) * sqrtf((float)B2);
+  f[0] = log10f((float)D);
+  f[1] = (float)(c[1] * iD);
+  f[2] = logf((float)Q);
+  f[3] = logf((float)X);
+  f[4] = (float)(r / Q);
+  f[5] = log10f(fmaxf((float)b2, 1e-30f));
+  f[6] = den > 0.f ? SB / den : 0.f;
+  f[7] = (float)(b2 / Q);
+}
+
+// (sqrt(1 + r^2), max(1 + q, 1e-30)) of a flat-metric state: the scalings of
+// the mu_+ and mu targets.
+DI void target_scales(const double* c, double* sr, double* Q) {
+  double D = c[0];
+  double r = sqrt(c[3] * c[3] + c[4] * c[4] + c[5] * c[5]) / D;
+  *sr = sqrt(1.0 + r * r);
+  *Q = fmax(1.0 + c[2] / D, 1e-30);
+}
+
+// Writes the standardized, BF16-rounded input row of sample row s.
+DI void put_x(u16* X, int s, const float f[NI], const float* norm, bool valid) {
+#pragma unroll
+  for (int k = 0; k < NI; ++k) X[s * LDX + k] = valid ? bf((f[k] - norm[k]) / norm[NI + k]) : 0;
+#pragma unroll
+  for (int k = NI; k < 16; ++k) X[s * LDX + k] = 0;
+}
+
+// Forward through the three hidden layers and the output (warp-local rows).
+DI void forward_tile(u16* S, float* F, u16* h3_out, int row0, int lane) {
+  fwd_hidden<1>(S + S_X, LDX, S + S_W1, F + F_B, S + S_H1, row0, lane);
+  __syncwarp();
+  fwd_hidden<4>(S + S_H1, LDH, S + S_W2, F + F_B + NH, S + S_H2, row0, lane);
+  __syncwarp();
+  fwd_hidden<4>(S + S_H2, LDH, S + S_W3, F + F_B + 2 * NH, h3_out, row0, lane);
+  __syncwarp();
+  fwd_out(h3_out, S + S_W4, F + F_B + 3 * NH, F + F_Y, row0, lane);
+  __syncwarp();
+}
+
+// MODE 0: inference from conserved states to seeds (double [n][3]).
+// MODE 1: forward from raw features to targets (float [n][3]).
+// Persistent: each CTA converts the weights once and walks over tiles of 128
+// samples with a stride of the grid; every warp touches only its own 32 rows,
+// so tiles follow one another without block barriers.
+template <int MODE>
+__global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restrict__ in, const float* __restrict__ w,
+                                                const float* __restrict__ norm, void* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  u16* S = reinterpret_cast<u16*>(smem);
+  float* F = reinterpret_cast<float*>(smem + (size_t)S_END_INFER * 2);
+  load_params(w, norm, S, F);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * 32, s = threadIdx.x;
+  const float* nm = F + F_NORM + 2 * NI;
+  const long long ntiles = (n + TM - 1) / TM;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    long long q = tile * TM + s;
+    bool valid = q < n;
+    float f[NI];
+    if (valid) {
+      if (MODE == 0) {
+        double c[9];
+        const double* cp = static_cast<const double*>(in) + q * 10;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) c[m] = cp[m];
+        features(c, f);
+      } else {
+        const float* fp = static_cast<const float*>(in) + q * NI;
+#pragma unroll
+        for (int k = 0; k < NI; ++k) f[k] = fp[k];
+      }
+    }
+    put_x(S + S_X, s, f, F + F_NORM, valid);
+    __syncwarp();
+    // Layer 3 writes into H1 (free after layer 2): inference keeps two hidden tiles.
+    fwd_hidden<1>(S + S_X, LDX, S + S_W1, F + F_B, S + S_H1, row0, lane);
+    __syncwarp();
+    fwd_hidden<4>(S + S_H1, LDH, S + S_W2, F + F_B + NH, S + S_H2, row0, lane);
+    __syncwarp();
+    fwd_hidden<4>(S + S_H2, LDH, S + S_W3, F + F_B + 2 * NH, S + S_H1, row0, lane);
+    __syncwarp();
+    fwd_out(S + S_H1, S + S_W4, F + F_B + 3 * NH, F + F_Y, row0, lane);
+    __syncwarp();
+    if (valid) {
+      float t0 = fmaf(F[F_Y + s * 4 + 0], nm[NO + 0], nm[0]);
+      float t1 = fmaf(F[F_Y + s * 4 + 1], nm[NO + 1], nm[1]);
+      float t2 = fmaf(F[F_Y + s * 4 + 2], nm[NO + 2], nm[2]);
+      if (MODE == 0) {
+        // Seeds need no more than FP32 accuracy: the FP64 root finder polishes them.
+        const double* cp = static_cast<const double*>(in) + q * 10;
+        float D = (float)cp[0];
+        float r = sqrtf((float)(cp[3] * cp[3] + cp[4] * cp[4] + cp[5] * cp[5])) / D;
+        float Q = fmaxf(1.f + (float)(cp[2] / cp[0]), 1e-30f);
+        double* o = static_cast<double*>(out) + q * 3;
+        o[0] = (double)(expf(t0) / sqrtf(1.f + r * r));
+        o[1] = (double)(expf(t1) / Q);
+        o[2] = (double)expf(t2);
+      } else {
+        float* o = static_cast<float*>(out) + q * 3;
+        o[0] = t0;
+        o[1] = t1;
+        o[2] = t2;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Forward and backward over one tile of the batch [off, off + nb); writes the
+// tile's partial gradient (gpart[tile][NPAR]) and sum of squared errors (lpart[tile]).
+// off = (step[0] mod nbatch) * nb when step is given, else 0.
+__global__ void __launch_bounds__(TM) k_mlp_train(long long n, const float* __restrict__ X,
+                                                  const float* __restrict__ T, int nb, long long nbatch,
+                                                  const unsigned long long* __restrict__ step,
+                                                  const float* __restrict__ w, const float* __restrict__ norm,
+                                                  float* __restrict__ gpart, double* __restrict__ lpart, float scale) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  u16* S = reinterpret_cast<u16*>(smem);
+  float* F = reinterpret_cast<float*>(smem + (size_t)S_END_TRAIN * 2);
+  load_params(w, norm, S, F);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, row0 = warp * 32, s = threadIdx.x;
+  long long off = step ? (long long)(step[0] % (unsigned long long)nbatch) * nb : 0;
+  long long i = (long long)blockIdx.x * TM + s;  // index within the batch
+  bool valid = i < nb && off + i < n;
+  long long q = off + i;
+  float f[NI];
+  if (valid)
+#pragma unroll
+    for (int k = 0; k < NI; ++k) f[k] = X[q * NI + k];
+  put_x(S + S_X, s, f, F + F_NORM, valid);
+  __syncwarp();
+  forward_tile(S, F, S + S_H3, row0, lane);
+  // Output error: dy = scale (y - t_std); loss partial; bf16(dy) into DY.
+  const float* nm = F + F_NORM + 2 * NI;
+  float dy[NO];
+  double se = 0.0;
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    float e = 0.f;
+    if (valid) {
+      float tj = (T[q * NO + j] - nm[j]) / nm[NO + j];
+      e = F[F_Y + s * 4 + j] - tj;
+    }
+    se += (double)e * (double)e;
+    dy[j] = scale * e;
+  }
+  u16* DY = S + S_DY;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) DY[s * LDX + j] = j < NO ? bf(dy[j]) : 0;
+  // b4 gradient and loss: warp sums, then fixed-order sums over the warps.
+  float* gbw = F + F_GB + warp * (3 * NH + 4);
+#pragma unroll
+  for (int j = 0; j < NO; ++j) {
+    float v = dy[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) gbw[3 * NH + j] = v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+  double* lw = reinterpret_cast<double*>(F + F_LOSS);
+  if (lane == 0) lw[warp] = se;
+  __syncthreads();
+  float* gp = gpart + (size_t)blockIdx.x * NPAR;
+  // dW4 (warp: rows 16w..16w+15) and dZ3 (warp rows) -> DZ.
+  bwd_weight<1>(S + S_H3, LDH, DY, LDX, gp + OW4, NO, warp * 16, NH, 0, lane);
+  bwd_act<1>(DY, LDX, S + S_W4, LDX, S + S_H3, S + S_DZ, gbw + 2 * NH, row0, lane);
+  __syncthreads();
+  // dW3 = H2^T dZ3; dZ2 -> H3 buffer (H3 no longer needed).
+  bwd_weight<8>(S + S_H2, LDH, S + S_DZ, LDH, gp + OW3, NH, warp * 16, NH, 0, lane);
+  bwd_act<4>(S + S_DZ, LDH, S + S_W3, LDH, S + S_H2, S + S_H3, gbw + NH, row0, lane);
+  __syncthreads();
+  // dW2 = H1^T dZ2; dZ1 -> DZ buffer.
+  bwd_weight<8>(S + S_H1, LDH, S + S_H3, LDH, gp + OW2, NH, warp * 16, NH, 0, lane);
+  bwd_act<4>(S + S_H3, LDH, S + S_W2, LDH, S + S_H1, S + S_DZ, gbw, row0, lane);
+  __syncthreads();
+  // dW1 = X^T dZ1 (rows k < 8; warp: column tiles 2w, 2w+1).
+  bwd_weight<2>(S + S_X, LDX, S + S_DZ, LDH, gp + OW1, NH, 0, NI, warp * 2, lane);
+  // Bias gradients and loss: fixed-order sums of the warp partials.
+  for (int c = threadIdx.x; c < 3 * NH + NO; c += blockDim.x) {
+    float v = 0.f;
+#pragma unroll
+    for (int ww = 0; ww < 4; ++ww) v += F[F_GB + ww * (3 * NH + 4) + c];
+    int dst = c < NH ? OB1 + c : c < 2 * NH ? OB2 + (c - NH) : c < 3 * NH ? OB3 + (c - 2 * NH) : OB4 + (c - 3 * NH);
+    gp[dst] = v;
+  }
+  if (threadIdx.x == 0) lpart[blockIdx.x] = ((lw[0] + lw[1]) + lw[2]) + lw[3];
+}
+
+// Sums nparts partial gradients (fixed order) into grad and the loss partials into loss.
+__global__ void k_reduce_grad(const float* __restrict__ gpart, int nparts, const double* __restrict__ lpart,
+                              float* __restrict__ grad, double* __restrict__ loss, double lscale) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < NPAR) {
+    float g = 0.f;
+    for (int p = 0; p < nparts; ++p) g += gpart[(size_t)p * NPAR + q];
+    grad[q] = g;
+  }
+  if (q == 0 && loss) {
+    double l = 0.0;
+    for (int p = 0; p < nparts; ++p) l += lpart[p];
+    *loss = l * lscale;
+  }
+}
+
+// Adam on the FP32 master weights.  The gradient is the fixed-order sum of
+// nparts partials.  With ctr: step s = ctr[0] (then ctr[0] += 1 once every
+// block is done), learning rate on a half cosine from lr0 to lr1 over total
+// steps, and the step's mean loss added to loss_hist[s / spe]; without ctr:
+// step s = fixed_step - 1, learning rate lr0.
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ gpart, int nparts, unsigned long long* ctr, long long fixed_step,
+                       long long total, long long spe, float lr0, float lr1, float b1, float b2, float eps,
+                       const double* __restrict__ lpart, double* __restrict__ loss_hist, double lscale) {
+  long long s = ctr ? (long long)ctr[0] : fixed_step - 1;
+  float lr = lr0;
+  if (ctr && total > 1)
+    lr = lr1 + 0.5f * (lr0 - lr1) * (1.f + cospif((float)((double)s / (double)(total - 1))));
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < NPAR) {
+    float g = 0.f;
+    for (int p = 0; p < nparts; ++p) g += gpart[(size_t)p * NPAR + q];
+    // Bias corrections in FP64: 1 - beta2^t in FP32 loses ~5 digits to cancellation.
+    double t = (double)(s + 1);
+    float c1 = (float)(1.0 - pow((double)b1, t)), c2 = (float)(1.0 - pow((double)b2, t));
+    float mm = b1 * m[q] + (1.f - b1) * g;
+    float vv = b2 * v[q] + (1.f - b2) * g * g;
+    m[q] = mm;
+    v[q] = vv;
+    float mh = mm / c1;
+    float vh = vv / c2;
+    w[q] -= lr * mh / (sqrtf(vh) + eps);
+  }
+  if (ctr) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss_hist) {
+      double l = 0.0;
+      for (int p = 0; p < nparts; ++p) l += lpart[p];
+      loss_hist[s / spe] += l * lscale;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      unsigned long long tk = atomicAdd(&ctr[1], 1ull);
+      if (tk == gridDim.x - 1) {
+        ctr[1] = 0ull;
+        ctr[0] = (unsigned long long)(s + 1);
+        __threadfence();
+      }
+    }
+  }
+}
+
+// Per-channel sums of the 11 channels (8 features, 3 targets): block b writes
+// part[b][22] = (sum x, sum x^2) per channel.
+constexpr int STAT_BLOCKS = 304, STAT_THREADS = 256;
+__global__ void __launch_bounds__(STAT_THREADS) k_stats(long long n, const float* __restrict__ X,
+                                                        const float* __restrict__ T, double* __restrict__ part) {
+  __shared__ double red[STAT_THREADS / 32][2 * (NI + NO)];
+  double acc[2 * (NI + NO)];
+#pragma unroll
+  for (int c = 0; c < 2 * (NI + NO); ++c) acc[c] = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < NI + NO; ++c) {
+      double x = c < NI ? X[q * NI + c] : T[q * NO + (c - NI)];
+      acc[2 * c] += x;
+      acc[2 * c + 1] += x * x;
+    }
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 2 * (NI + NO); ++c) {
+    double x = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][c] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * (NI + NO)) {
+    double x = 0.0;
+    for (int ww = 0; ww < STAT_THREADS / 32; ++ww) x += red[ww][threadIdx.x];
+    part[blockIdx.x * 2 * (NI + NO) + threadIdx.x] = x;
+  }
+}
+
+// Normalisation from the block sums: mean and standard deviation (scale 1
+// for a channel that does not vary).
+__global__ void k_norm(long long n, const double* __restrict__ part, float* __restrict__ norm) {
+  int c = threadIdx.x;
+  if (c >= NI + NO) return;
+  double s1 = 0.0, s2 = 0.0;
+  for (int b = 0; b < STAT_BLOCKS; ++b) {
+    s1 += part[b * 2 * (NI + NO) + 2 * c];
+    s2 += part[b * 2 * (NI + NO) + 2 * c + 1];
+  }
+  double mean = s1 / (double)n;
+  double var = fmax(s2 / (double)n - mean * mean, 0.0);
+  double sdv = sqrt(var);
+  if (!(sdv > 1e-6 * (1.0 + fabs(mean)))) sdv = 1.0;
+  if (c < NI) {
+    norm[c] = (float)mean;
+    norm[NI + c] = (float)sdv;
+  } else {
+    norm[2 * NI + (c - NI)] = (float)mean;
+    norm[2 * NI + NO + (c - NI)] = (float)sdv;
+  }
+}
+
+__global__ void k_features(long long n, const double* __restrict__ cons, float* __restrict__ f) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  double c[9];
+#pragma unroll
+  for (int m = 0; m < 9; ++m) c[m] = cons[q * 10 + m];
+  float o[NI];
+  features(c, o);
+#pragma unroll
+  for (int k = 0; k < NI; ++k) f[q * NI + k] = o[k];
+}
+
+__global__ void k_targets(long long n, const double* __restrict__ cons, const double* __restrict__ roots,
+                          float* __restrict__ t) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  double sr, Q;
+  target_scales(cons + q * 10, &sr, &Q);
+  t[q * 3] = (float)log(roots[q * 3] * sr);
+  t[q * 3 + 1] = (float)log(roots[q * 3 + 1] * Q);
+  t[q * 3 + 2] = (float)log(roots[q * 3 + 2]);
+}
+
+__global__ void __launch_bounds__(128) k_c2p_flat_seeded(grmhd_params P, Eos E, long long n,
+                                                          const double* __restrict__ cons,
+                                                          const double* __restrict__ seeds, double delta,
+                                                          double* __restrict__ prim, int8_t* __restrict__ status,
+                                                          int32_t* __restrict__ iters, double* __restrict__ roots,
+                                                          int8_t* __restrict__ seeded) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double g[6] = {1.0, 0.0, 0.0, 1.0, 0.0, 1.0};
+  double cb[9];
+  for (int m = 0; m < 9; ++m) cb[m] = ld(cons + q * 10 + m);
+  double sq[3];
+  if (seeds)
+    for (int m = 0; m < 3; ++m) sq[m] = ld(seeds + q * 3 + m);
+  C2POut r;
+  c2p_point(P, E, cb, g, g, 1.0, 1.0, r, seeds ? sq : nullptr, delta);
+  for (int m = 0; m < NP; ++m) prim[q * NP + m] = r.prim[m];
+  status[q] = (int8_t)r.status;
+  if (iters) iters[q] = r.iters;
+  if (seeded) seeded[q] = (int8_t)r.seeded;
+  if (roots) {
+    roots[q * 3] = r.mu_plus;
+    roots[q * 3 + 1] = r.mu;
+    roots[q * 3 + 2] = r.W_root;
+  }
+}
+
+// splitmix64 (Steele, Lea and Flood 2014) for the weight initialisation.
+inline uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace sd
+}  // namespace gk
+
+using namespace gk;
+using namespace gk::sd;
+
+struct grmhd_seeder {
+  int dev = 0;
+  float* w = nullptr;  // [NPAR] master weights
+  float* m = nullptr;  // [NPAR] Adam first moment
+  float* v = nullptr;  // [NPAR] Adam second moment
+  float* norm = nullptr;  // [NNORM]
+  unsigned long long* ctr = nullptr;  // [2] step, ticket
+  double* stats = nullptr;            // [STAT_BLOCKS][22]
+  float* gpart = nullptr;             // [MAX_TILES][NPAR]
+  double* lpart = nullptr;            // [MAX_TILES]
+  void* block = nullptr;              // one allocation for all of the above
+  cudaStream_t cap = nullptr;         // stream used for graph capture
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool attr_set = false;
+int set_smem_attrs() {
+  if (attr_set) return GRMHD_OK;
+  if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true)) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
+          cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  attr_set = true;
+  return GRMHD_OK;
+}
+
+unsigned grid_of(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Persistent grid of the forward kernels: resident CTAs per SM x SMs, at most
+// one CTA per tile.
+template <int MODE>
+unsigned fwd_grid(long long n) {
+  static int per_dev[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!per_dev[dev]) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_fwd<MODE>, TM, smem_bytes(false));
+    per_dev[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  }
+  long long tiles = (n + TM - 1) / TM;
+  return (unsigned)(tiles < per_dev[dev] ? tiles : per_dev[dev]);
+}
+
+int last_rc() { return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int grmhd_seeder_create(grmhd_seeder** out, unsigned long long seed) {
+  if (!out) return GRMHD_ERR_ARG;
+  *out = nullptr;
+  if (set_smem_attrs()) return GRMHD_ERR_CUDA;
+  grmhd_seeder* s = new grmhd_seeder();
+  cudaGetDevice(&s->dev);
+  size_t o_w = 0, o_m = align256(o_w + NPAR * 4), o_v = align256(o_m + NPAR * 4), o_n = align256(o_v + NPAR * 4),
+         o_c = align256(o_n + NNORM * 4), o_s = align256(o_c + 16), o_g = align256(o_s + STAT_BLOCKS * 22 * 8),
+         o_l = align256(o_g + (size_t)MAX_TILES * NPAR * 4), total = align256(o_l + MAX_TILES * 8);
+  if (cudaMalloc(&s->block, total) != cudaSuccess) {
+    delete s;
+    return GRMHD_ERR_CUDA;
+  }
+  char* b = static_cast<char*>(s->block);
+  s->w = (float*)(b + o_w);
+  s->m = (float*)(b + o_m);
+  s->v = (float*)(b + o_v);
+  s->norm = (float*)(b + o_n);
+  s->ctr = (unsigned long long*)(b + o_c);
+  s->stats = (double*)(b + o_s);
+  s->gpart = (float*)(b + o_g);
+  s->lpart = (double*)(b + o_l);
+  if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFree(s->block);
+    delete s;
+    return GRMHD_ERR_CUDA;
+  }
+  // He-uniform weights, zero biases.
+  float h[NPAR];
+  uint64_t st = seed;
+  const int offs[4] = {OW1, OW2, OW3, OW4}, fan[4] = {NI, NH, NH, NH}, cnt[4] = {NI * NH, NH * NH, NH * NH, NH * NO};
+  for (int q = 0; q < NPAR; ++q) h[q] = 0.f;
+  for (int l = 0; l < 4; ++l) {
+    float a = sqrtf(6.f / (float)fan[l]);
+    for (int q = 0; q < cnt[l]; ++q) {
+      double u = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+      h[offs[l] + q] = (float)((2.0 * u - 1.0) * a);
+    }
+  }
+  float nm[NNORM];
+  for (int c = 0; c < NNORM; ++c) nm[c] = 0.f;
+  for (int c = 0; c < NI; ++c) nm[NI + c] = 1.f;
+  for (int c = 0; c < NO; ++c) nm[2 * NI + NO + c] = 1.f;
+  int rc = grmhd_seeder_set_params(s, h, nm);
+  if (rc) {
+    grmhd_seeder_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return GRMHD_OK;
+}
+
+int grmhd_seeder_set_params(grmhd_seeder* s, const float* params, const float* norm) {
+  if (!s) return GRMHD_ERR_ARG;
+  if (params && cudaMemcpy(s->w, params, NPAR * 4, cudaMemcpyHostToDevice) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (norm) {
+    for (int c = 0; c < NI; ++c)
+      if (!(norm[NI + c] != 0.f)) return GRMHD_ERR_ARG;
+    for (int c = 0; c < NO; ++c)
+      if (!(norm[2 * NI + NO + c] != 0.f)) return GRMHD_ERR_ARG;
+    if (cudaMemcpy(s->norm, norm, NNORM * 4, cudaMemcpyHostToDevice) != cudaSuccess) return GRMHD_ERR_CUDA;
+  }
+  if (cudaMemset(s->m, 0, NPAR * 4) != cudaSuccess || cudaMemset(s->v, 0, NPAR * 4) != cudaSuccess ||
+      cudaMemset(s->ctr, 0, 16) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  return GRMHD_OK;
+}
+
+int grmhd_seeder_get_params(grmhd_seeder* s, float* params, float* norm) {
+  if (!s) return GRMHD_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (params && cudaMemcpy(params, s->w, NPAR * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (norm && cudaMemcpy(norm, s->norm, NNORM * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return GRMHD_ERR_CUDA;
+  return GRMHD_OK;
+}
+
+int grmhd_seeder_features(long long n, const double* cons, float* f, void* stream) {
+  if (n < 0 || (n > 0 && (!cons || !f))) return GRMHD_ERR_ARG;
+  if (n == 0) return GRMHD_OK;
+  k_features<<<grid_of(n, 256), 256, 0, (cudaStream_t)stream>>>(n, cons, f);
+  return last_rc();
+}
+
+int grmhd_seeder_targets(long long n, const double* cons, const double* roots, float* t, void* stream) {
+  if (n < 0 || (n > 0 && (!cons || !roots || !t))) return GRMHD_ERR_ARG;
+  if (n == 0) return GRMHD_OK;
+  k_targets<<<grid_of(n, 256), 256, 0, (cudaStream_t)stream>>>(n, cons, roots, t);
+  return last_rc();
+}
+
+int grmhd_seeder_forward(grmhd_seeder* s, long long n, const float* f, float* t_out, void* stream) {
+  if (!s || n < 0 || (n > 0 && (!f || !t_out))) return GRMHD_ERR_ARG;
+  if (n == 0) return GRMHD_OK;
+  k_mlp_fwd<1><<<fwd_grid<1>(n), TM, smem_bytes(false), (cudaStream_t)stream>>>(n, f, s->w, s->norm, t_out);
+  return last_rc();
+}
+
+int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double* seeds, void* stream) {
+  if (!s || n < 0 || (n > 0 && (!cons || !seeds))) return GRMHD_ERR_ARG;
+  if (n == 0) return GRMHD_OK;
+  k_mlp_fwd<0><<<fwd_grid<0>(n), TM, smem_bytes(false), (cudaStream_t)stream>>>(n, cons, s->w, s->norm, seeds);
+  return last_rc();
+}
+
+int grmhd_seeder_grad(grmhd_seeder* s, long long n, const float* f, const float* t, float* grad, double* loss,
+                      void* stream) {
+  if (!s || n < 1 || n > MAX_BATCH || !f || !t || !grad) return GRMHD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int tiles = (int)grid_of(n, TM);
+  k_mlp_train<<<tiles, TM, smem_bytes(true), st>>>(n, f, t, (int)n, 1, nullptr, s->w, s->norm, s->gpart, s->lpart,
+                                                   (float)(2.0 / (3.0 * (double)n)));
+  k_reduce_grad<<<grid_of(NPAR, 256), 256, 0, st>>>(s->gpart, tiles, s->lpart, grad, loss, 1.0 / (3.0 * (double)n));
+  return last_rc();
+}
+
+int grmhd_seeder_adam(grmhd_seeder* s, const float* grad, long long step, float lr, float beta1, float beta2,
+                      float eps, void* stream) {
+  if (!s || !grad || step < 1) return GRMHD_ERR_ARG;
+  k_adam<<<grid_of(NPAR, 256), 256, 0, (cudaStream_t)stream>>>(s->w, s->m, s->v, grad, 1, nullptr, step, 0, 1, lr,
+                                                               lr, beta1, beta2, eps, nullptr, nullptr, 0.0);
+  return last_rc();
+}
+
+int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float* t, const grmhd_train_cfg* cfg,
+                       double* loss_hist, void* stream) {
+  if (!s || !cfg || !f || !t) return GRMHD_ERR_ARG;
+  const int bsz = cfg->batch;
+  if (bsz < TM || bsz > MAX_BATCH || bsz % TM || cfg->epochs < 1 || n < bsz) return GRMHD_ERR_ARG;
+  if (!(cfg->lr > 0.f) || !(cfg->lr_final >= 0.f) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+      !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f))
+    return GRMHD_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long nbatch = n / bsz, total = nbatch * cfg->epochs;
+  const int tiles = bsz / TM;
+  if (cfg->fit_norm) {
+    k_stats<<<STAT_BLOCKS, STAT_THREADS, 0, st>>>(n, f, t, s->stats);
+    k_norm<<<1, 32, 0, st>>>(n, s->stats, s->norm);
+  }
+  if (cudaMemsetAsync(s->m, 0, NPAR * 4, st) != cudaSuccess || cudaMemsetAsync(s->v, 0, NPAR * 4, st) != cudaSuccess ||
+      cudaMemsetAsync(s->ctr, 0, 16, st) != cudaSuccess ||
+      (loss_hist && cudaMemsetAsync(loss_hist, 0, sizeof(double) * cfg->epochs, st) != cudaSuccess))
+    return GRMHD_ERR_CUDA;
+  // One epoch as a graph: nbatch x (forward/backward, Adam).
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GRMHD_ERR_CUDA;
+  const float scale = (float)(2.0 / (3.0 * (double)bsz));
+  const double lscale = 1.0 / (3.0 * (double)bsz * (double)nbatch);
+  for (long long b = 0; b < nbatch; ++b) {
+    k_mlp_train<<<tiles, TM, smem_bytes(true), s->cap>>>(n, f, t, bsz, nbatch, s->ctr, s->w, s->norm, s->gpart,
+                                                         s->lpart, scale);
+    k_adam<<<grid_of(NPAR, 256), 256, 0, s->cap>>>(s->w, s->m, s->v, s->gpart, tiles, s->ctr, 0, total, nbatch,
+                                                    cfg->lr, cfg->lr_final, cfg->beta1, cfg->beta2, cfg->eps, s->lpart,
+                                                    loss_hist, lscale);
+  }
+  cudaError_t e1 = cudaStreamEndCapture(s->cap, &g);
+  if (e1 != cudaSuccess || !g) return GRMHD_ERR_CUDA;
+  cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) return GRMHD_ERR_CUDA;
+  int rc = GRMHD_OK;
+  for (int e = 0; e < cfg->epochs && rc == GRMHD_OK; ++e)
+    if (cudaGraphLaunch(ge, st) != cudaSuccess) rc = GRMHD_ERR_CUDA;
+  // The executable graph may be destroyed while its launches are pending.
+  cudaGraphExecDestroy(ge);
+  return rc;
+}
+
+void grmhd_seeder_destroy(grmhd_seeder* s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  if (s->cap) cudaStreamDestroy(s->cap);
+  if (s->block) cudaFree(s->block);
+  delete s;
+}
+
+int grmhd_c2p_flat_seeded(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
+                          const double* seeds, double delta, double* prim, int8_t* status, int32_t* iters,
+                          double* roots, int8_t* seeded, void* stream) {
+  if (!p || n < 0 || (n > 0 && (!cons || !prim || !status))) return GRMHD_ERR_ARG;
+  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2)) return GRMHD_ERR_ARG;
+  if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
+  if (seeds && !(delta > 0.0 && delta < 1.0)) return GRMHD_ERR_ARG;
+  if (n == 0) return GRMHD_OK;
+  k_c2p_flat_seeded<<<grid_of(n, 128), 128, 0, (cudaStream_t)stream>>>(*p, make_eos(*p, eos), n, cons, seeds, delta,
+                                                                       prim, status, iters, roots, seeded);
+  return last_rc();
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""The learned con2prim seeder on the GPU, through the C ABI, against the oracle.
+
+- Features and targets against the oracle's plain definitions (FP32 rounding).
+- Network forward and gradient against the oracle's FP64 network evaluated on
+  BF16-rounded operands: relative L2 error <= 1e-3 per parameter tensor; the
+  gradient also against the unrounded FP64 gradient (which the CPU tests pin to
+  central differences): no further from it than the BF16 oracle is, + 2e-3.
+- Adam against the textbook update (oracle, FP64).
+- Seeded con2prim with the same seeds on both sides: same statuses, primitives
+  within the con2prim tolerances, same use of the seed brackets; unusable seeds
+  (non-finite network) fall back to the plain brackets with identical results.
+- A trained network: fewer function evaluations than the plain brackets, same
+  results as the oracle's plain con2prim.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._checks import prim_check
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2510_13965_gb300 as g  # noqa: E402
+
+NPAR = oracle.MLP_NPARAMS
+NP = 10
+# Parameter tensors: name, offset, size.
+TENSORS = [("W1", 0, 512), ("b1", 512, 64), ("W2", 576, 4096), ("b2", 4672, 64), ("W3", 4736, 4096),
+           ("b3", 8832, 64), ("W4", 8896, 192), ("b4", 9088, 3)]
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _he_params(seed):
+    rng = np.random.default_rng(seed)
+    p = np.zeros(NPAR, dtype=np.float32)
+    for name, off, n in TENSORS:
+        fan = 8 if name == "W1" else 64
+        if name.startswith("W"):
+            p[off:off + n] = rng.uniform(-1, 1, n) * np.sqrt(6.0 / fan)
+        else:
+            p[off:off + n] = 0.1 * rng.normal(size=n)
+    return p
+
+
+def _identity_norm():
+    m = np.zeros(22, dtype=np.float32)
+    m[8:16] = 1.0
+    m[19:22] = 1.0
+    return m
+
+
+def _table_states(n, seed, table, O):
+    s = synth.c2p_states(n, seed=seed)
+    cons = np.zeros((n, 10))
+    for q in range(n):
+        pr = np.zeros(NP)
+        pr[0], pr[7] = s["rho"][q], s["ye"][q]
+        e = O.eos_from_T(s["rho"][q], s["T"][q], s["ye"][q])
+        pr[1], pr[2] = e[1], e[0]
+        pr[3:6] = s["v"][q]
+        cons[q, :9] = oracle.prim2con_point(pr, s["B"][q], [1.0, 0, 0, 1.0, 0, 1.0])
+    return cons
+
+
+@pytest.fixture(scope="module")
+def table_setup():
+    table = synth.make_table(nr=64, nt=48, ny=16)
+    P = synth.table_params(table)
+    O = oracle.Oracle(P, table)
+    return table, P, O, g.Table(table)
+
+
+def test_features_and_targets_match_oracle(table_setup):
+    table, P, O, T = table_setup
+    cons = _table_states(700, 11, table, O)
+    f_g = g.seeder_features(torch.as_tensor(cons, device="cuda")).cpu().numpy()
+    f_o = oracle.seeder_features(cons)
+    # FP32 logarithms of FP64-formed quantities: a few float ulps.
+    assert np.allclose(f_g, f_o, rtol=1e-6, atol=1e-6)
+    _, st, _, roots, _ = O.c2p_flat_ext(cons)
+    assert np.all(st >= 0)
+    t_g = g.seeder_targets(torch.as_tensor(cons, device="cuda"), torch.as_tensor(roots, device="cuda")).cpu().numpy()
+    t_o = oracle.seeder_targets(cons, roots)
+    assert np.allclose(t_g, t_o, rtol=2e-7, atol=2e-7)
+
+
+@pytest.mark.parametrize("n", [1000, 128, 77])
+def test_forward_matches_oracle_bf16(n):
+    p = _he_params(1)
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(n, 8)).astype(np.float32)
+    S = g.Seeder()
+    S.set_params(p, _identity_norm())
+    y_g = S.forward(torch.as_tensor(x, device="cuda")).cpu().numpy().astype(np.float64)
+    y_o = oracle.mlp_forward(p, x, bf16=True)
+    assert _rel_l2(y_g, y_o) <= 1e-3
+
+
+@pytest.mark.parametrize("n", [1000, 4096])
+def test_gradient_matches_oracle(n):
+    p = _he_params(3)
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(n, 8)).astype(np.float32)
+    t = rng.normal(size=(n, 3)).astype(np.float32)
+    S = g.Seeder()
+    S.set_params(p, _identity_norm())
+    loss_g, g_g = S.grad(torch.as_tensor(x, device="cuda"), torch.as_tensor(t, device="cuda"))
+    loss_g = float(loss_g.cpu().numpy()[0])
+    g_g = g_g.cpu().numpy().astype(np.float64)
+    loss_b, g_b = oracle.mlp_grad(p, x, t, bf16=True)
+    _, g_64 = oracle.mlp_grad(p, x, t, bf16=False)
+    assert abs(loss_g - loss_b) <= 1e-5 * loss_b
+    for name, off, k in TENSORS:
+        e_b = _rel_l2(g_g[off:off + k], g_b[off:off + k])
+        e_64 = _rel_l2(g_g[off:off + k], g_64[off:off + k])
+        # BF16 operands alone move the gradient 1-2.5 % from the FP64 one (the
+        # oracle with and without rounding); the kernel may add no more than 2e-3.
+        e_round = _rel_l2(g_b[off:off + k], g_64[off:off + k])
+        assert e_b <= 1e-3, (name, e_b)
+        assert e_64 <= e_round + 2e-3, (name, e_64, e_round)
+
+
+def test_adam_matches_oracle():
+    p = _he_params(5)
+    rng = np.random.default_rng(6)
+    S = g.Seeder()
+    S.set_params(p, _identity_norm())
+    w, m, v = p.astype(np.float64), np.zeros(NPAR), np.zeros(NPAR)
+    for step in (1, 2, 3):
+        gr = (1e-2 * rng.normal(size=NPAR)).astype(np.float32)
+        S.adam(torch.as_tensor(gr, device="cuda"), step, 1e-3, 0.9, 0.999, 1e-8)
+        w, m, v = oracle.adam(w, m, v, gr.astype(np.float64), 1e-3, 0.9, 0.999, 1e-8, step)
+    wg, _ = S.get_params()
+    # FP32 master weights: up to ~1.5 ulp of rounding over the three updates.
+    assert np.all(np.abs(wg - w) <= 4e-7 * np.abs(w) + 2e-9)
+
+
+def test_seeded_con2prim_matches_oracle_with_same_seeds(table_setup):
+    table, P, O, T = table_setup
+    n = 1500
+    cons = _table_states(n, 12, table, O)
+    p0, s0, it0, roots, _ = O.c2p_flat_ext(cons)
+    rng = np.random.default_rng(7)
+    seeds = roots * (1.0 + 3e-3 * rng.uniform(-1, 1, size=roots.shape))
+    seeds[::50] = np.nan  # a few unusable seeds
+    seeds[1::50] *= 1.5   # and a few that do not bracket
+    delta = 1e-2
+    p1, s1, it1, r1, sd1 = O.c2p_flat_ext(cons, seeds, delta=delta)
+    cg = torch.as_tensor(cons, device="cuda")
+    pg, sg, itg, rg, sdg = (a.cpu().numpy() for a in
+                           g.c2p_flat_seeded(P, cg, torch.as_tensor(seeds, device="cuda"), delta, table=T))
+    prim_check(pg.T, p1.T, sg, s1, cons[:, :3].T)
+    prim_check(pg.T, p0.T, sg, s0, cons[:, :3].T)  # and the plain oracle
+    assert np.mean(sdg == sd1) >= 0.99
+    ok = s1 >= 0
+    assert np.all(np.abs(rg[ok, 1] - r1[ok, 1]) <= 1e-12 * r1[ok, 1])
+    both = ok & (rg[:, 0] > 0) & (r1[:, 0] > 0)
+    assert np.all(np.abs(rg[both, 0] - r1[both, 0]) <= 1e-12 * r1[both, 0])
+    # Evaluation counts are not unique: Brent's last steps to the 4-ulp stop
+    # turn on rounding-level comparisons, which FMA contraction changes.  Their
+    # means agree, and so does the saving from the seeds.
+    _, sp, itp, _, sdp = (a.cpu().numpy() for a in g.c2p_flat_seeded(P, cg, None, table=T))
+    assert np.all(sdp == 0) and np.array_equal(sp, s0)
+    m = dict(gpu_seeded=itg.mean(), oracle_seeded=it1.mean(), gpu_plain=itp.mean(), oracle_plain=it0.mean())
+    assert abs(m["gpu_seeded"] - m["oracle_seeded"]) <= 0.05 * m["oracle_seeded"], m
+    assert abs(m["gpu_plain"] - m["oracle_plain"]) <= 0.05 * m["oracle_plain"], m
+    saving_g, saving_o = m["gpu_plain"] - m["gpu_seeded"], m["oracle_plain"] - m["oracle_seeded"]
+    assert abs(saving_g - saving_o) <= 0.5, m
+
+
+def test_non_finite_network_falls_back_to_plain(table_setup):
+    table, P, O, T = table_setup
+    cons = _table_states(600, 13, table, O)
+    S = g.Seeder()
+    p = _he_params(8)
+    p[-3:] = np.nan
+    S.set_params(p, _identity_norm())
+    cg = torch.as_tensor(cons, device="cuda")
+    seeds = S.infer(cg)
+    assert not torch.isfinite(seeds[:, :2]).any()
+    a = [x.cpu().numpy() for x in g.c2p_flat_seeded(P, cg, seeds, 1e-2, table=T)]
+    b = [x.cpu().numpy() for x in g.c2p_flat_seeded(P, cg, None, table=T)]
+    assert np.all(a[4] == 0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def _gpu_pairs(P, T, n, seed):
+    """Training pairs made on the GPU: prim2con of seeded primitives, then the plain con2prim's roots."""
+    table_s = synth.c2p_states(n, seed=seed)
+    prim = np.zeros((n, NP))
+    prim[:, 0], prim[:, 7], prim[:, 8] = table_s["rho"], table_s["ye"], table_s["T"]
+    prim[:, 3:6] = table_s["v"]
+    cons = g.prim2con_flat(P, torch.as_tensor(prim, device="cuda"), torch.as_tensor(table_s["B"], device="cuda"),
+                           table=T)
+    _, st, _, roots, _ = g.c2p_flat_seeded(P, cons, None, table=T)
+    keep = st >= 0
+    f = g.seeder_features(cons)[keep].contiguous()
+    t = g.seeder_targets(cons, roots)[keep].contiguous()
+    return f, t
+
+
+def test_trained_seeder(table_setup):
+    """Trained on the GPU: the loss falls tenfold and the mu seeds land within
+    a few per cent of the oracle's roots (untrained ones are far off), seeded
+    solves give the oracle's plain results, and the evaluation count stays
+    within 10 % of the plain one.  Brent converges superlinearly from any
+    bracket and ends with steps of a few ulps, so per-cent seeds save few
+    evaluations; near-exact seeds (the oracle's roots) save at least 20 %,
+    which shows the saving is bounded by the seeds' accuracy."""
+    table, P, O, T = table_setup
+    f, t = _gpu_pairs(P, T, 1 << 16, 13)
+    S = g.Seeder(seed=1)
+    n = 2000
+    cons = _table_states(n, 3, table, O)
+    cg = torch.as_tensor(cons, device="cuda")
+    po, so, ito, ro, _ = O.c2p_flat_ext(cons)
+    ok = so >= 0
+    rel_untrained = np.abs(S.infer(cg).cpu().numpy()[ok, 1] / ro[ok, 1] - 1.0)
+    hist = S.train(f, t, batch=1024, epochs=25, lr=3e-3, lr_final=3e-5).cpu().numpy()
+    assert np.all(np.isfinite(hist)) and hist[-1] < 0.1 * hist[0], hist
+    seeds = S.infer(cg).cpu().numpy()
+    rel = np.abs(seeds[ok, 1] / ro[ok, 1] - 1.0)
+    assert np.median(rel) < 2e-2, np.percentile(rel, [50, 90, 99])
+    assert np.median(rel) < 0.1 * np.median(rel_untrained)
+    res = {}
+    sg_t = torch.as_tensor(seeds, device="cuda")
+    for delta in (1e-2, 3e-2):
+        pg, sg, itg, _, sdg = (a.cpu().numpy() for a in g.c2p_flat_seeded(P, cg, sg_t, delta, table=T))
+        prim_check(pg.T, po.T, sg, so, cons[:, :3].T)
+        res[delta] = (itg.mean(), np.mean((sdg & 2) > 0))
+    best = min(v[0] for v in res.values())
+    assert best <= 1.10 * ito.mean(), (res, ito.mean())
+    assert max(v[1] for v in res.values()) > 0.5, res
+    exact = torch.as_tensor(ro * (1.0 + 3e-7), device="cuda")
+    pg, sg, itx, _, _ = (a.cpu().numpy() for a in g.c2p_flat_seeded(P, cg, exact, 1e-6, table=T))
+    prim_check(pg.T, po.T, sg, so, cons[:, :3].T)
+    assert itx[ok].mean() <= 0.8 * ito[ok].mean(), (itx[ok].mean(), ito[ok].mean())

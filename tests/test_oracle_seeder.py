@@ -90,7 +90,7 @@ def test_seeded_con2prim_same_root_and_fallback():
     seeds = roots * (1.0 + 2e-4)
     p1, s1, it1, r1, sd = O.c2p_flat_ext(cons, seeds, delta=1e-3)
     assert np.array_equal(s0, s1)
-    assert np.mean(sd[ok] == 3) > 0.9
+    assert np.mean((sd[ok] & 2) > 0) > 0.9
     assert np.all(np.abs(p1[ok, 0] - p0[ok, 0]) <= 1e-13 * p0[ok, 0])
     assert np.all(np.abs(r1[ok, 1] - roots[ok, 1]) <= 1e-13 * roots[ok, 1])
     assert it1[ok].mean() < it0[ok].mean()
@@ -100,3 +100,44 @@ def test_seeded_con2prim_same_root_and_fallback():
     p2, s2, it2, r2, sd2 = O.c2p_flat_ext(cons, bad, delta=1e-3)
     assert np.all(sd2 == 0)
     assert np.array_equal(s2, s0) and np.array_equal(p2, p0)
+
+
+def test_seeder_features_and_targets_closed_forms():
+    # D = 1e-3, Ye = 0.1, q = 0.2, S = (1e-4, 0, 0) -> r = 0.1, B = (1e-3, 0, 0) -> b2 = 1e-3, S parallel to B.
+    c = np.zeros((3, 10))
+    c[:, 0], c[:, 1], c[:, 2] = 1e-3, 1e-4, 2e-4
+    c[0, 3], c[0, 6] = 1e-4, 1e-3
+    c[1, 3], c[1, 7] = 1e-4, 1e-3          # S perpendicular to B
+    c[2, 3] = -1e-4                        # no field
+    f = oracle.seeder_features(c)
+    want = [-3.0, 0.1, np.log(1.2), np.log(1.1 * 1.3), 0.1 / 1.2, -3.0, 1.0, 1e-3 / 1.2]
+    assert np.allclose(f[0], want, rtol=1e-14, atol=1e-15)
+    assert abs(f[1, 6]) < 1e-15 and f[2, 5] == -30.0 and f[2, 6] == 0.0 and f[2, 7] == 0.0
+    t = oracle.seeder_targets(c[:1], np.array([[0.5, 0.25, 3.0]]))
+    assert np.allclose(t[0], [np.log(0.5 * np.sqrt(1.01)), np.log(0.25 * 1.2), np.log(3.0)], rtol=0, atol=1e-15)
+
+
+def test_seeder_targets_vanish_for_the_unmagnetised_closed_forms():
+    # B = 0 and h0 = 1: mu_+ = 1 / sqrt(1 + r^2) exactly, and mu (1 + q) = 1 - p / (rho h W^2).
+    P = synth.ideal_params()
+    assert P["h0"] == 1.0
+    O = oracle.Oracle(P)
+    rows, pr_list = [], []
+    for rho, eps, v in [(1e-3, 0.1, 0.3), (1e-5, 2.0, 0.9), (0.1, 1e-4, 0.0), (1e-7, 5e-3, 0.99)]:
+        pr = np.zeros(oracle.NP)
+        pr[0], pr[1], pr[2], pr[3], pr[7] = rho, eps, rho * eps, v, 0.1
+        c = np.zeros(10)
+        c[:9] = oracle.prim2con_point(pr, [0, 0, 0], [1.0, 0, 0, 1.0, 0, 1.0])
+        rows.append(c)
+        pr_list.append(pr)
+    cons = np.array(rows)
+    p, st, _, roots, _ = O.c2p_flat_ext(cons)
+    assert np.all(st == 0)
+    t = oracle.seeder_targets(cons, roots)
+    assert np.all(np.abs(t[:, 0]) <= 2e-15)
+    for k, pr in enumerate(pr_list):
+        rho, eps, prs, v = pr[0], pr[1], pr[2], pr[3]
+        W = 1.0 / np.sqrt(1.0 - v * v)
+        h = 1.0 + eps + prs / rho
+        assert abs(t[k, 1] - np.log(1.0 - prs / (rho * h * W * W))) <= 1e-12
+        assert abs(t[k, 2] - np.log(W)) <= 1e-12
