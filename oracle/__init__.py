@@ -82,6 +82,9 @@ def lib(flops=False):
             "oracle_mlp_grad": (d, [vp, l, vp, vp, vp, i]),
             "oracle_adam": (i, [vp, vp, vp, vp, l, d, d, d, d, i]),
             "oracle_seeder_features": (i, [l, vp, vp]),
+            "oracle_hier_ghost_fill": (i, [vp, i, vp, vp, vp]),
+            "oracle_hier_restrict": (i, [i, vp, vp, vp]),
+            "oracle_hier_rk4_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
             "oracle_seeder_targets": (i, [l, vp, vp, vp]),
             "oracle_prim2con_point": (i, [vp, vp, vp, vp]),
             "oracle_eos_from_eps": (i, [vp, vp, d, d, d, vp]),
@@ -339,3 +342,44 @@ def mp5(f5):
 
 def minmod4(a, b, c, d):
     return lib().oracle_minmod4(a, b, c, d)
+
+
+class Hierarchy:
+    """A fixed mesh-refinement hierarchy of patches held by the oracle.
+
+    specs: list of dicts with n (3 ints), level, o (3 ints: origin index on the
+    level's grid, which starts at the level-0 origin) and dx.  Arrays per patch
+    and register: float64 (NF, n2+6, n1+6, px) with px = n0 + 6.
+    """
+
+    def __init__(self, oracle, specs):
+        self.O = oracle
+        self.specs = specs
+        np_ = len(specs)
+        self.meta = np.zeros((np_, 8), dtype=np.int32)
+        for q, s in enumerate(specs):
+            n = s["n"]
+            self.meta[q] = [n[0], n[1], n[2], n[0] + 6, s["level"], s["o"][0], s["o"][1], s["o"][2]]
+        self.dx = np.array([s["dx"] for s in specs], dtype=np.float64)
+        self.U = [[np.zeros((NF, s["n"][2] + 6, s["n"][1] + 6, s["n"][0] + 6)) for s in specs] for _ in range(4)]
+        self.prim = [np.zeros((NP,) + self.U[0][q].shape[1:]) for q in range(np_)]
+        self.status = [np.zeros(self.U[0][q].shape[1:], dtype=np.int8) for q in range(np_)]
+
+    def _ptrs(self, arrs):
+        return (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+
+    def init_state(self, q, ID):
+        self.U[0][q][...] = self.O.init_state(np.ascontiguousarray(ID), self.specs[q]["n"], self.specs[q]["dx"])
+
+    def ghost_fill(self, reg=0):
+        return self.O.L.oracle_hier_ghost_fill(_ref(self.O.P), len(self.specs), _p(self.meta), _p(self.dx),
+                                              self._ptrs(self.U[reg]))
+
+    def restrict(self, reg=0):
+        return self.O.L.oracle_hier_restrict(len(self.specs), _p(self.meta), _p(self.dx), self._ptrs(self.U[reg]))
+
+    def rk4_step(self, dt):
+        return self.O.L.oracle_hier_rk4_step(_ref(self.O.P), self.O.Tp, len(self.specs), _p(self.meta), _p(self.dx),
+                                            dt, self._ptrs(self.U[0]), self._ptrs(self.U[1]),
+                                            self._ptrs(self.U[2]), self._ptrs(self.U[3]), self._ptrs(self.prim),
+                                            self._ptrs(self.status))

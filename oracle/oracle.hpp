@@ -95,6 +95,19 @@ struct grid {
 };
 static const int NG = 3;
 
+// ---- patch-level steps (patch.cpp) ------------------------------------------
+grid make_grid(const int n[3], int px, double dx);
+// bc 0 periodic, 1 linear extrapolation; bc 2 (frozen) and 3 (mesh-refinement
+// hierarchy, filled by amr.cpp) leave the ghosts to the caller.
+void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf);
+void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* ID, double* U);
+int c2p_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, double* U, double* prim,
+              int8_t* status, long* iters_total);
+void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs,
+               long long* counts);
+int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, int stage, double dt, double* Un,
+            double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs, long long* counts);
+
 // ---- EOS (eos.cpp) --------------------------------------------------------
 struct eos_state {
   real p, eps, T, cs2;

@@ -27,10 +27,12 @@ grid make_grid(const int n[3], int px, double dx) {
 // extrapolation of Sec. IV B, taken at first order).
 // bc 2: frozen ghosts (the initial data's ghost values, kept by every
 // register; see substep) -- nothing to fill here.
+// bc 3: ghosts of a mesh-refinement hierarchy, filled by amr.cpp before each
+// substep -- nothing to fill here.
 static void ghost_fill_bc(int bc, const grid& G, double* U, int nf);
 
 void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf) {
-  if (P->bc == 2) return;
+  if (P->bc == 2 || P->bc == 3) return;
   ghost_fill_bc(P->bc, G, U, nf);
 }
 
@@ -143,8 +145,8 @@ void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G
       }
   if (P->bc == 2)  // frozen ghosts keep the initial data; Gammahat is extrapolated into them
     ghost_fill_bc(1, G, U + (long)F_GH * G.sf, 3);
-  else
-    ghost_fill(P, G, U, NF);
+  else  // a hierarchy's patch (bc 3) is extrapolated like an outer boundary until its first ghost fill
+    ghost_fill_bc(P->bc == 3 ? 1 : P->bc, G, U, NF);
 }
 
 // con2prim at every point of the patch, ghosts included; corrected conserved

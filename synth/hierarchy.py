@@ -1,0 +1,53 @@
+"""Patch layouts of fixed mesh-refinement hierarchies (geometry only).
+
+A hierarchy is a list of patch specs: n (interior points per axis), level,
+o (origin index on the level's grid, which starts at the level-0 origin X0
+with spacing dx0 / 2^level), and the derived dx and x0 = X0 + o dx.  Level 0
+is a single patch.
+"""
+import numpy as np
+
+
+def spec(n, level, o, dx0, X0):
+    dx = dx0 / 2 ** level
+    return dict(n=tuple(int(v) for v in n), level=int(level), o=tuple(int(v) for v in o), dx=dx,
+                x0=tuple(float(X0[a]) + o[a] * dx for a in range(3)))
+
+
+def small_hierarchy(dx0=1.0, X0=(-12.0, -12.0, -12.0), n0=24):
+    """Three levels, five patches of uneven shapes: a 24^3 level-0 patch, two
+    level-1 patches that share a face, and two level-2 patches, one of which
+    straddles the two level-1 patches."""
+    return [
+        spec((n0, n0, n0), 0, (0, 0, 0), dx0, X0),
+        spec((12, 12, 12), 1, (12, 12, 12), dx0, X0),
+        spec((10, 12, 12), 1, (24, 12, 12), dx0, X0),
+        spec((16, 12, 12), 2, (30, 28, 28), dx0, X0),
+        spec((8, 8, 10), 2, (50, 28, 30), dx0, X0),
+    ]
+
+
+def nested_cubes(n0, dx0, X0, fine, edges=(16, 24, 32, 48, 64), seed=4):
+    """Level 0: one n0^3 patch at X0.  fine: list of (level, start, size) with
+    start and size in points of that level's grid (same on every axis); each
+    such cube is split into blocks whose edges are drawn per axis from edges
+    (seeded), the last block of a row taking what remains."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    out = [spec((n0,) * 3, 0, (0, 0, 0), dx0, X0)]
+    for level, start, size in fine:
+        cuts = []
+        for _ in range(3):
+            c, pos = [], 0
+            while pos < size:
+                e = int(rng.choice(edges))
+                e = min(e, size - pos)
+                if size - pos - e and size - pos - e < 8:  # no sliver blocks
+                    e = size - pos
+                c.append((pos, e))
+                pos += e
+            cuts.append(c)
+        for (oz, ez) in cuts[2]:
+            for (oy, ey) in cuts[1]:
+                for (ox, ex) in cuts[0]:
+                    out.append(spec((ex, ey, ez), level, (start + ox, start + oy, start + oz), dx0, X0))
+    return out
