@@ -97,7 +97,8 @@ typedef struct grmhd_params {
   double c2p_xtol;                  /* absolute part of the Brent stop rule             */
   int eos_kind;                     /* 0 ideal gas, 1 table                             */
   int bc;                           /* ghosts: 0 periodic, 1 linear extrapolation,
-                                       2 frozen (the initial data's ghost values)       */
+                                       2 frozen (the initial data's ghost values),
+                                       3 mesh-refinement hierarchy (see below)          */
   int max_iter;                     /* Brent iteration cap per root find                */
   int reserved;
 } grmhd_params;
@@ -115,7 +116,23 @@ typedef struct grmhd_eos_table {
 } grmhd_eos_table;
 
 /* One patch.  U[0] holds U^n; U[1], U[2] hold RK stage values; U[3] holds the
- * RK4 accumulator.  All arrays are device pointers with the layout above. */
+ * RK4 accumulator.  All arrays are device pointers with the layout above.
+ *
+ * Mesh-refinement hierarchy (bc = 3; Sec. III D, prolongation and
+ * restriction, for a fixed hierarchy advanced without sub-cycling):
+ *   - exactly one patch has level 0; its outer ghosts are extrapolated as for
+ *     bc = 1;
+ *   - a level-l patch has dx = dx_0 / 2^l and x0 on the level-l grid that
+ *     starts at the level-0 x0 (x0 = x0_0 + o dx, o integer); patches of one
+ *     level do not overlap; level-l point g coincides with level-(l-1) point
+ *     g/2 when g is even and is the midpoint of (g-1)/2 and (g+1)/2 when odd;
+ *   - a ghost point of a level-l patch (l >= 1) is copied from the interior of
+ *     another level-l patch that holds it, else prolongated from the level-
+ *     (l-1) patch whose interior holds floor(g/2): the paper's six-point
+ *     Lagrange midpoint formula along every axis where g is odd (x, then y,
+ *     then z), the coarse value along the others.  Levels are filled in order;
+ *   - grmhd_init_patches returns GRMHD_ERR_ARG (with a message on stderr) when
+ *     the layout breaks these rules or a fine ghost point is not covered. */
 typedef struct grmhd_patch_desc {
   int n[3];
   int px;
@@ -185,8 +202,16 @@ int grmhd_rk_update(grmhd_ctx* ctx, int stage, double dt, double* const* rhs);
  * stage combination of grmhd_rk_update, without storing k. */
 int grmhd_rhs_substep(grmhd_ctx* ctx, int stage, double dt);
 
-/* One full RK4 step (four fused substeps). */
+/* One full RK4 step (four fused substeps); with bc = 3, followed by
+ * grmhd_restrict(ctx, 0). */
 int grmhd_step(grmhd_ctx* ctx, double dt);
+
+/* Restriction of a hierarchy (bc = 3; a no-op otherwise): every interior
+ * point of a level-l patch at even level-l coordinates g overwrites, for all
+ * fields of register reg, the interior point g/2 of the level-(l-1) patch that
+ * holds it (direct copy, the paper's restriction operator); finest level
+ * first. */
+int grmhd_restrict(grmhd_ctx* ctx, int reg);
 
 /* Captures nsteps RK4 steps into a CUDA graph owned by the context
  * (replacing a previous one); grmhd_graph_launch replays it on the stream. */

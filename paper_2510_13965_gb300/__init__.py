@@ -70,6 +70,7 @@ _SIGS = {
     "grmhd_rk_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     "grmhd_rhs_substep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "grmhd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "grmhd_restrict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "grmhd_capture_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "grmhd_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
     "grmhd_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
@@ -237,6 +238,9 @@ class Patches:
         self._enter()
         assert id_tensor.dtype == self.torch.float64 and id_tensor.is_contiguous()
         assert tuple(id_tensor.shape) == (NID,) + self.specs[patch]["shape"]
+        # The library reads id_tensor on its own stream: keep the caching
+        # allocator from handing its memory to another tensor before that.
+        id_tensor.record_stream(self.stream)
         _check(self.L.grmhd_init_state(self.ctx, patch, ctypes.c_void_p(id_tensor.data_ptr())), self.ctx,
                "grmhd_init_state")
 
@@ -255,18 +259,26 @@ class Patches:
         torch = self.torch
         if out is None:
             out = [torch.zeros((NF,) + sp["shape"], dtype=torch.float64, device=self.device) for sp in self.specs]
+        for t in out:
+            t.record_stream(self.stream)
         arr = (ctypes.c_void_p * len(out))(*[t.data_ptr() for t in out])
         _check(self.L.grmhd_rhs_eval(self.ctx, reg, arr), self.ctx, "grmhd_rhs_eval")
         return out
 
     def rk_update(self, stage, dt, rhs):
         self._enter()
+        for t in rhs:
+            t.record_stream(self.stream)
         arr = (ctypes.c_void_p * len(rhs))(*[t.data_ptr() for t in rhs])
         _check(self.L.grmhd_rk_update(self.ctx, stage, float(dt), arr), self.ctx, "grmhd_rk_update")
 
     def rhs_substep(self, stage, dt):
         self._enter()
         _check(self.L.grmhd_rhs_substep(self.ctx, stage, float(dt)), self.ctx, "grmhd_rhs_substep")
+
+    def restrict(self, reg=0):
+        self._enter()
+        _check(self.L.grmhd_restrict(self.ctx, reg), self.ctx, "grmhd_restrict")
 
     def step(self, dt):
         self._enter()

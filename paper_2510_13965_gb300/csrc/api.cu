@@ -25,6 +25,11 @@ struct grmhd_ctx {
   double** rhs_ptrs = nullptr;  // device array of npatch pointers
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  // mesh-refinement hierarchy (bc 3): ghost tasks per level 1..L, then
+  // restriction tasks per level L..1, in one device array
+  AmrTask* amr = nullptr;
+  int amr_level0 = -1, amr_nlev = 0;
+  std::vector<long long> amr_gofs, amr_gcnt, amr_rofs, amr_rcnt;
   long long launches = 0;
   long long graph_kernels = 0;
   std::string err;
@@ -115,6 +120,7 @@ void grmhd_destroy(grmhd_ctx* c) {
   cudaFree(c->flags);
   cudaFree(c->stats);
   cudaFree(c->rhs_ptrs);
+  cudaFree(c->amr);
   delete c;
 }
 
@@ -126,7 +132,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   if (p->eos_kind != 0 && p->eos_kind != 1) return GRMHD_ERR_ARG;
   if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2 || eos->nr < 2 || eos->nt < 2 || eos->ny < 2))
     return GRMHD_ERR_ARG;
-  if (p->bc < 0 || p->bc > 2) return GRMHD_ERR_ARG;
+  if (p->bc < 0 || p->bc > 3) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   for (int i = 0; i < npatch; ++i) {
     const grmhd_patch_desc& q = d[i];
@@ -199,6 +205,44 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     grmhd_destroy(c);
     return rc == GRMHD_ERR_CUDA ? GRMHD_ERR_NOMEM : rc;
   }
+  if (p->bc == 3) {
+    std::vector<Geo> geo(npatch);
+    for (int i = 0; i < npatch; ++i) geo[i] = c->pd_host[i].G;
+    AmrPlan plan;
+    if (amr_plan(d, geo, npatch, plan) != GRMHD_OK) {
+      std::fprintf(stderr, "grmhd_init_patches: %s\n", plan.err.c_str());
+      grmhd_destroy(c);
+      return GRMHD_ERR_ARG;
+    }
+    c->amr_level0 = plan.level0;
+    c->amr_nlev = plan.nlev;
+    std::vector<AmrTask> all;
+    c->amr_gofs.assign(plan.nlev, 0);
+    c->amr_gcnt.assign(plan.nlev, 0);
+    c->amr_rofs.assign(plan.nlev, 0);
+    c->amr_rcnt.assign(plan.nlev, 0);
+    for (int l = 1; l < plan.nlev; ++l) {
+      c->amr_gofs[l] = (long long)all.size();
+      c->amr_gcnt[l] = (long long)plan.ghost[l].size();
+      all.insert(all.end(), plan.ghost[l].begin(), plan.ghost[l].end());
+    }
+    for (int l = plan.nlev - 1; l >= 1; --l) {
+      c->amr_rofs[l] = (long long)all.size();
+      c->amr_rcnt[l] = (long long)plan.restr[l].size();
+      all.insert(all.end(), plan.restr[l].begin(), plan.restr[l].end());
+    }
+    if (!all.empty()) {
+      if ((rc = cuda_ok(c, cudaMalloc(&c->amr, all.size() * sizeof(AmrTask)), "cudaMalloc amr tasks"))) {
+        grmhd_destroy(c);
+        return GRMHD_ERR_NOMEM;
+      }
+      if ((rc = cuda_ok(c, cudaMemcpy(c->amr, all.data(), all.size() * sizeof(AmrTask), cudaMemcpyHostToDevice),
+                        "copy amr tasks"))) {
+        grmhd_destroy(c);
+        return rc;
+      }
+    }
+  }
   if ((rc = cuda_ok(c, cudaMemcpyAsync(c->work, wl.data(), wl.size() * sizeof(Work), cudaMemcpyHostToDevice, c->st),
                     "copy work")) ||
       (rc = cuda_ok(c, cudaMemcpyAsync(c->pd, c->pd_host.data(), npatch * sizeof(PatchDev), cudaMemcpyHostToDevice,
@@ -218,6 +262,15 @@ static int nblk(grmhd_ctx* c, int dom, int bs = 128) {
 }
 static const Work* wl(grmhd_ctx* c, int dom, int bs = 128) { return c->work + c->wofs[bs_index(bs)][dom]; }
 
+// The contiguous slice of a ghost-line work list (block size 128) that belongs
+// to one patch: work items are grouped by patch in increasing order.
+static void patch_range(grmhd_ctx* c, int dom, int patch, int* first, int* cnt) {
+  long long before = 0;
+  for (int i = 0; i < patch; ++i) before += (dom_count(dom, c->pd_host[i].G) + BS_ALL - 1) / BS_ALL;
+  *first = (int)before;
+  *cnt = (int)((dom_count(dom, c->pd_host[patch].G) + BS_ALL - 1) / BS_ALL);
+}
+
 int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
   if (!c) return GRMHD_ERR_ARG;
   if (patch < 0 || patch >= c->np || !id) return fail(c, GRMHD_ERR_ARG, "init_state: bad patch or id");
@@ -236,13 +289,7 @@ int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
     int n = nblk(c, dom);
     // find the contiguous range of this patch
     int first = -1, cnt = 0;
-    {
-      // work items are grouped by patch in increasing order
-      long long before = 0;
-      for (int i = 0; i < patch; ++i) before += (dom_count(dom, c->pd_host[i].G) + BS_ALL - 1) / BS_ALL;
-      first = (int)before;
-      cnt = (int)((dom_count(dom, q.G) + BS_ALL - 1) / BS_ALL);
-    }
+    patch_range(c, dom, patch, &first, &cnt);
     if (first + cnt > n) return fail(c, GRMHD_ERR_ARG, "init_state: work list");
     if (c->P.bc == 2)  // frozen ghosts keep the initial data; only Gammahat is extrapolated
       launch_ghost(c->pd, w + first, cnt, 0, ax, 1, c->st, GH, GH + 3);
@@ -256,6 +303,23 @@ int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
 int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
   if (!c) return GRMHD_ERR_ARG;
   if (reg < 0 || reg > 3) return fail(c, GRMHD_ERR_ARG, "ghost_fill: reg");
+  if (c->P.bc == 3) {
+    // Level 0: outer boundary extrapolation of its single patch; then each
+    // finer level from its own interiors and the next coarser level.
+    for (int ax = 0; ax < 3; ++ax) {
+      int first, cnt;
+      patch_range(c, DOM_GX + ax, c->amr_level0, &first, &cnt);
+      ProfScope ps(c, K_GHOST);
+      launch_ghost(c->pd, wl(c, DOM_GX + ax) + first, cnt, reg, ax, 1, c->st);
+      c->launches += 1;
+    }
+    for (int l = 1; l < c->amr_nlev; ++l) {
+      ProfScope ps(c, K_GHOST);
+      launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st);
+      c->launches += 1;
+    }
+    return check_launch(c, "ghost hierarchy");
+  }
   if (c->P.bc == 2) {
     if (reg != 0) {
       ProfScope ps(c, K_GHOST);
@@ -363,13 +427,25 @@ int grmhd_rhs_substep(grmhd_ctx* c, int stage, double dt) {
   return check_launch(c, "rhs fused");
 }
 
+int grmhd_restrict(grmhd_ctx* c, int reg) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (reg < 0 || reg > 3) return fail(c, GRMHD_ERR_ARG, "restrict: reg");
+  if (c->P.bc != 3) return GRMHD_OK;
+  for (int l = c->amr_nlev - 1; l >= 1; --l) {
+    ProfScope ps(c, K_GHOST);
+    launch_amr(c->pd, c->amr + c->amr_rofs[l], c->amr_rcnt[l], reg, c->st);
+    c->launches += 1;
+  }
+  return check_launch(c, "restrict");
+}
+
 int grmhd_step(grmhd_ctx* c, double dt) {
   if (!c) return GRMHD_ERR_ARG;
   for (int s = 0; s < 4; ++s) {
     int rc = grmhd_rhs_substep(c, s, dt);
     if (rc) return rc;
   }
-  return GRMHD_OK;
+  return grmhd_restrict(c, 0);
 }
 
 int grmhd_capture_graph(grmhd_ctx* c, int nsteps, double dt) {

@@ -2,6 +2,9 @@
 // kernel translation units and the host API.
 #pragma once
 #include <cuda_runtime.h>
+#include <array>
+#include <string>
+#include <vector>
 #include "c2p.cuh"
 
 namespace gk {
@@ -105,6 +108,21 @@ void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, cons
 constexpr int BS_ALL = 128;
 constexpr int BS_INT = 128;
 constexpr int BS_IF = 128;
+// Mesh-refinement hierarchy (amr.cu).  One task moves one point for all
+// fields: a copy (odd == 0) or a prolongation from the coarse base point sofs
+// of patch src (bit a of odd: midpoint along axis a).
+struct AmrTask {
+  int dst, dofs, src, sofs, odd;
+};
+struct AmrPlan {
+  int level0 = -1, nlev = 0;
+  std::vector<std::vector<AmrTask>> ghost;  // per level (0 unused): ghost tasks
+  std::vector<std::vector<AmrTask>> restr;  // per level (0 unused): restriction into level - 1
+  std::string err;
+};
+int amr_plan(const grmhd_patch_desc* d, const std::vector<Geo>& geo, int np, AmrPlan& P);
+void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, cudaStream_t st);
+
 // Block sizes the autotuner chooses from.
 constexpr int NBS = 3;
 constexpr int BS_CAND[NBS] = {64, 128, 256};

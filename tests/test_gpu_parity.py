@@ -11,6 +11,7 @@ import pytest
 import oracle
 import synth
 from tests._checks import prim_check as _prim_check
+from tests._checks import interior as _interior, field_err as _field_err, init_ok as _init_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -24,17 +25,6 @@ NF, NP = 32, 10
 INT = (slice(None), slice(3, -3), slice(3, -3), slice(3, -3))
 
 
-def _interior(a, n):
-    return a[:, 3:3 + n[2], 3:3 + n[1], 3:3 + n[0]]
-
-
-def _field_err(got, want):
-    gg = got.reshape(got.shape[0], -1)
-    ww = want.reshape(want.shape[0], -1)
-    scale = np.maximum(np.abs(ww).max(axis=1), 1e-30)
-    return np.abs(gg - ww).max(axis=1) / scale
-
-
 def _setup(P, n, dx, ID, table=None):
     T = g.Table(table) if table is not None else None
     pt = g.Patches(P, [dict(n=n, dx=dx)], table=T)
@@ -45,22 +35,6 @@ def _setup(P, n, dx, ID, table=None):
 
 
 NOISE = 1e-12  # RHS components below this norm vanish analytically (rounding noise only)
-
-
-def _init_ok(Ug, U, dx=None):
-    """Initial-data conversion: 1e-13 per field.  Gammahat (fields 15-17) is a
-    centred derivative of gt_ij = O(1): its rounding is absolute, ~eps / dx
-    (times the extrapolation factor in the ghosts), so it is held to 1e-13 / dx
-    absolute (or 1e-10 relative when dx is not given)."""
-    e = _field_err(Ug, U)
-    tol = np.full(NF, 1e-13)
-    tol[15:18] = 1e-10
-    d = np.abs(Ug - U).reshape(NF, -1).max(axis=1)
-    small = np.abs(U).reshape(NF, -1).max(axis=1) < 1e-12
-    ok = (e < tol) | (small & (d < 1e-13))
-    if dx is not None:
-        ok[15:18] |= d[15:18] < 1e-13 / dx
-    return bool(np.all(ok)), {f: e[f] for f in range(NF) if not ok[f]}
 
 
 def _rhs_ok(got, want, tol=1e-11, U=None, dx=None):
