@@ -59,12 +59,15 @@ def _args():
     a.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
     a.add_argument("--no-cpu-baseline", action="store_true")
     a.add_argument("--e2e-steps", type=int, default=3)
-    a.add_argument("--workload", default="tov", choices=["tov", "batched", "c2p"],
+    a.add_argument("--workload", default="tov", choices=["tov", "batched", "c2p", "amr"],
                    help="tov: the 128^3 TOV star (default); batched: 256 uneven patches over 5 levels; "
-                        "c2p: con2prim of 2^24 tabulated-EOS states, plain vs NN-seeded")
+                        "c2p: con2prim of 2^24 tabulated-EOS states, plain vs NN-seeded; "
+                        "amr: tabulated-EOS magnetised star on a 5-level, 366-patch hierarchy")
     a.add_argument("--c2p-states", type=int, default=1 << 24)
     a.add_argument("--train-pairs", type=int, default=1 << 20)
     a.add_argument("--train-epochs", type=int, default=40)
+    a.add_argument("--amr-scale", type=float, default=1.0,
+                   help="point counts of the hierarchy workload relative to the 366-patch layout")
     a.add_argument("--edge", type=int, default=N_EDGE,
                    help="interior points per axis (the same [-20,20]^3 star; 128 is the benchmark workload)")
     return a.parse_args()
@@ -543,6 +546,87 @@ def run_c2p(args):
     return 0
 
 
+def run_amr(args):
+    """The magnetised TOV star with the synthetic tabulated EOS on a fixed
+    5-level hierarchy (level 0 one 128^3 patch, levels 1-3 160^3 cubes in
+    uneven blocks, level 4 a 256^3 cube of 64^3 blocks; 366 patches, ~69 GB of
+    device state), advanced without sub-cycling: every substep fills the
+    hierarchy's ghosts level by level, then runs con2prim, fluxes and the
+    right-hand side over all patches in one launch per kernel; each step ends
+    with the restriction.  One bench step = one RK4 step of every level."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_13965_gb300 as g
+    import synth
+
+    table = synth.make_table()
+    P = synth.table_params(table, bc=3)
+    T = g.Table(table)
+    specs = synth.amr_tov_layout(scale=args.amr_scale)
+    prof = synth.tov_profile()
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    pt = g.Patches(P, specs, table=T, stream=stream)
+    for q, s_ in enumerate(specs):
+        ID = synth.tov_id(n=s_["n"], x0=s_["x0"], dx=s_["dx"], seed=4000 + q, table=table,
+                          rho_atmo=P["rho_atmo"], profile=prof)
+        pt.init_state(q, torch.as_tensor(ID, device="cuda"))
+        pt.synchronize()
+    pt.restrict(0)
+    pt.synchronize()
+    setup_s = time.perf_counter() - t0
+    zones = int(sum(np.prod(s_["n"]) for s_ in specs))
+    dt = 0.25 * min(s_["dx"] for s_ in specs)
+    for _ in range(max(args.warmup, 3)):
+        pt.step(dt)
+    pt.synchronize()
+    rc = pt.sync_status()
+    if rc != 0:
+        raise SystemExit("warm-up failed: status %d" % rc)
+    pt.capture_graph(1, dt)
+    launches0 = pt.launch_count()
+    clocks = Clocks(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        pt.graph_launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = pt.launch_count() - launches0
+    clk = clocks.stop()
+    rc = pt.sync_status()
+    # One eager, profiled step for the per-kernel split.
+    pt.profile(True)
+    pt.step(dt)
+    pt.synchronize()
+    prof_k = pt.profile_read()
+    pt.profile(False)
+    tot = sum(v[0] for v in prof_k.values()) or 1.0
+    levels = {}
+    for s_ in specs:
+        levels.setdefault(s_["level"], [0, 0])
+        levels[s_["level"]][0] += 1
+        levels[s_["level"]][1] += int(np.prod(s_["n"]))
+    line = {"metric": METRIC, "value": zones / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tov_table_eos_5_level_hierarchy_%d_patches_rk4_step" % len(specs),
+                       "scale": args.amr_scale,
+                       "patches": len(specs), "interior_points": zones,
+                       "levels": {str(k): {"patches": v[0], "points": v[1]} for k, v in sorted(levels.items())},
+                       "finest_dx": min(s_["dx"] for s_ in specs), "dt": dt, "subcycling": "none",
+                       "eos": "synthetic table 256x128x64", "l2": "inputs larger than L2"},
+            "kernel_ms_per_step": {k: v[0] for k, v in prof_k.items() if v[1]},
+            "kernel_share": {k: v[0] / tot for k, v in prof_k.items() if v[1]},
+            "gpu_launches": int(launches), "status": rc, "clocks": clk, "setup_s": setup_s}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -551,6 +635,8 @@ def main():
         return run_batched(args)
     if args.workload == "c2p":
         return run_c2p(args)
+    if args.workload == "amr":
+        return run_amr(args)
     return run_grmhd(args)
 
 

@@ -13,6 +13,8 @@ low-density atmosphere of 1e-10, optional 1 % random pressure perturbation
 and a poloidal field from A_phi = A_b max(p - 0.04 p_max, 0).
 """
 import numpy as np
+
+from .eos_table import M_B, model, radiation_constant
 from scipy.integrate import solve_ivp
 from scipy.interpolate import CubicSpline
 
@@ -209,9 +211,33 @@ def tov_profile(K=100.0, Gamma=2.0, rho_c=1.28e-3):
                 alpha=mk(alpha), K=K, Gamma=Gamma)
 
 
+def _table_temperature(rho, p, ye, table, iters=48):
+    """T [MeV] at which the synthetic table model gives pressure p at (rho, ye):
+    bisection in log T over the table's range (clamped to its ends)."""
+    a_r = radiation_constant()
+
+    def pres(T):  # the model's pressure alone
+        return rho * (T / M_B) * (1.0 + ye) + a_r * T ** 4 / 3.0
+
+    lo = np.full(rho.shape, table["lt0"])
+    hi = np.full(rho.shape, table["lt0"] + table["dlt"] * (table["nt"] - 1))
+    p_lo = pres(10.0 ** lo)
+    p_hi = pres(10.0 ** hi)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        pm = pres(10.0 ** mid)
+        up = pm < p
+        lo = np.where(up, mid, lo)
+        hi = np.where(up, hi, mid)
+    lt = np.where(p <= p_lo, table["lt0"], np.where(p >= p_hi, hi, 0.5 * (lo + hi)))
+    return 10.0 ** lt
+
+
 def tov_id(n=(128, 128, 128), x0=(-20.0, -20.0, -20.0), dx=0.3125, seed=1, perturb=True, bfield=True,
-           pad=1, rho_atmo=1e-10, profile=None, ye=0.1):
-    """Static TOV star on a vertex-centred patch (ghosts included)."""
+           pad=1, rho_atmo=1e-10, profile=None, ye=0.1, table=None):
+    """Static TOV star on a vertex-centred patch (ghosts included).  With a
+    synthetic table, the temperature (field 25) is set so the table model's
+    pressure equals the polytropic one (eps then follows from the table)."""
     n = tuple(int(v) for v in n)
     prof = profile if profile is not None else tov_profile()
     K, Gamma, M, Rb = prof["K"], prof["Gamma"], prof["M"], prof["Rb"]
@@ -235,6 +261,9 @@ def tov_id(n=(128, 128, 128), x0=(-20.0, -20.0, -20.0), dx=0.3125, seed=1, pertu
         p = np.where(rho > 100.0 * rho_atmo, p * (1.0 + 0.01 * xi), p)
     eps = p / ((Gamma - 1.0) * rho)
     ID = np.zeros((NID,) + shp)
+    if table is not None:
+        ID[25] = _table_temperature(rho, p, ye, table)
+        eps = model(rho, ID[25], ye)[1]
     psi4 = psi ** 4
     ID[0] = psi4
     ID[3] = psi4

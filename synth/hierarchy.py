@@ -28,18 +28,20 @@ def small_hierarchy(dx0=1.0, X0=(-12.0, -12.0, -12.0), n0=24):
 
 
 def nested_cubes(n0, dx0, X0, fine, edges=(16, 24, 32, 48, 64), seed=4):
-    """Level 0: one n0^3 patch at X0.  fine: list of (level, start, size) with
-    start and size in points of that level's grid (same on every axis); each
-    such cube is split into blocks whose edges are drawn per axis from edges
-    (seeded), the last block of a row taking what remains."""
+    """Level 0: one n0^3 patch at X0.  fine: list of (level, start, size[,
+    edges]) with start and size in points of that level's grid (same on every
+    axis); each such cube is split into blocks whose edges are drawn per axis
+    from edges (seeded), the last block of a row taking what remains."""
     rng = np.random.default_rng(np.random.PCG64(seed))
     out = [spec((n0,) * 3, 0, (0, 0, 0), dx0, X0)]
-    for level, start, size in fine:
+    for entry in fine:
+        level, start, size = entry[:3]
+        lev_edges = entry[3] if len(entry) > 3 else edges
         cuts = []
         for _ in range(3):
             c, pos = [], 0
             while pos < size:
-                e = int(rng.choice(edges))
+                e = int(rng.choice(lev_edges))
                 e = min(e, size - pos)
                 if size - pos - e and size - pos - e < 8:  # no sliver blocks
                     e = size - pos
@@ -51,3 +53,25 @@ def nested_cubes(n0, dx0, X0, fine, edges=(16, 24, 32, 48, 64), seed=4):
                 for (ox, ex) in cuts[0]:
                     out.append(spec((ex, ey, ez), level, (start + ox, start + oy, start + oz), dx0, X0))
     return out
+
+
+def amr_tov_layout(scale=1.0, levels=5, seed=4):
+    """The magnetised-star hierarchy.  At scale 1: level 0 one 128^3 patch on
+    [-80, 80)^3 (dx0 = 1.25), levels 1..levels-2 cubes of 160 points centred
+    on the origin and split into blocks with edges from {24, 32, 48}, and the
+    finest level a cube of 256 points in 64^3 blocks (dx0 / 16 = 0.078 on
+    [-10, 10)).  A smaller scale shrinks every point count by it and widens
+    dx0 by 1/scale, so the finest level still spans [-10, 10)."""
+    n0 = int(round(128 * scale))
+    fine_size = 8 * int(round(20 * scale))
+    finest = 8 * int(round(32 * scale))
+    dx0 = 1.25 / scale
+    half = n0 * dx0 / 2.0
+    X0 = (-half,) * 3
+    fine = []
+    for l in range(1, levels):
+        size = finest if l == levels - 1 else fine_size
+        centre = int(round(half / (dx0 / 2 ** l)))
+        start = centre - size // 2
+        fine.append((l, start, size, (64,) if l == levels - 1 else (24, 32, 48)))
+    return nested_cubes(n0, dx0, X0, fine, seed=seed)
