@@ -242,7 +242,8 @@ int grmhd_autotune(grmhd_ctx* ctx, double dt, int reps, int* chosen);
  * grmhd_profile_read synchronises the stream, writes the summed milliseconds
  * and launch counts per kernel kind (0 ghost fill, 1 con2prim + pointwise
  * fluxes, 2 interface fluxes, 3 right-hand side + RK epilogue, 4 unfused RK
- * update, 5 initial data) into ms[0..nkinds) and count[0..nkinds), and
+ * update, 5 initial data, 6 seeder inference) into ms[0..nkinds) and
+ * count[0..nkinds), and
  * discards the records. */
 int grmhd_profile(grmhd_ctx* ctx, int on);
 int grmhd_profile_read(grmhd_ctx* ctx, double* ms, long long* count, int nkinds);
@@ -403,6 +404,19 @@ int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float
 int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double* seeds, void* stream);
 
 void grmhd_seeder_destroy(grmhd_seeder* s);
+
+/* Seeded con2prim in the substep of a patch context: with a seeder set,
+ * every con2prim pass (grmhd_con2prim, grmhd_rhs_substep, grmhd_step and the
+ * captured graphs recorded afterwards) first runs the network on every point
+ * (features from the conserved variables and the metric: the network's
+ * inputs are functions of Kastaun's invariants q, r^2 = S_i S^i / D^2,
+ * B_i B^i / D and S_i B^i, so the flat-metric training applies) and then
+ * con2prim from those seeds with bracket half-width delta, as in
+ * grmhd_c2p_flat_seeded.  Atmosphere and non-finite points get no seed.  The
+ * first call allocates the seed buffer (3 floats per ghosted point) and
+ * synchronises; s = NULL returns to the plain brackets.  The seeder must
+ * outlive its use by the context. */
+int grmhd_set_seeder(grmhd_ctx* ctx, const grmhd_seeder* s, double delta);
 
 /* grmhd_c2p_flat with optional seeds (device double [n][3] or NULL).  The
  * mu seed s gives the bracket [s (1 - delta), min(s (1 + delta), 1 / h0)]:

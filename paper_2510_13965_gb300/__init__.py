@@ -71,6 +71,7 @@ _SIGS = {
     "grmhd_rhs_substep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "grmhd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "grmhd_restrict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_set_seeder": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "grmhd_capture_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "grmhd_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
     "grmhd_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
@@ -276,6 +277,12 @@ class Patches:
         self._enter()
         _check(self.L.grmhd_rhs_substep(self.ctx, stage, float(dt)), self.ctx, "grmhd_rhs_substep")
 
+    def set_seeder(self, seeder, delta=1e-2):
+        """Seed every con2prim of this context with the network (None: plain brackets)."""
+        self._seeder = seeder  # keep it alive while the context uses it
+        rc = self.L.grmhd_set_seeder(self.ctx, seeder.h if seeder is not None else None, float(delta))
+        _check(rc, self.ctx, "grmhd_set_seeder")
+
     def restrict(self, reg=0):
         self._enter()
         _check(self.L.grmhd_restrict(self.ctx, reg), self.ctx, "grmhd_restrict")
@@ -295,7 +302,7 @@ class Patches:
     def sync_status(self):
         return self.L.grmhd_sync_status(self.ctx)
 
-    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init")
+    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init", "seed")
 
     def set_block_sizes(self, bs_c2p, bs_iflux, bs_rhs):
         _check(self.L.grmhd_set_block_sizes(self.ctx, bs_c2p, bs_iflux, bs_rhs), self.ctx, "grmhd_set_block_sizes")

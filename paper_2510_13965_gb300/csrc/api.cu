@@ -28,6 +28,10 @@ struct grmhd_ctx {
   // mesh-refinement hierarchy (bc 3): ghost tasks per level 1..L, then
   // restriction tasks per level L..1, in one device array
   AmrTask* amr = nullptr;
+  // learned con2prim seeder (grmhd_set_seeder): seeds [3][sf] per patch
+  const grmhd_seeder* seeder = nullptr;
+  double seed_delta = 0.0;
+  float* seed_buf = nullptr;
   int amr_level0 = -1, amr_nlev = 0;
   std::vector<long long> amr_gofs, amr_gcnt, amr_rofs, amr_rcnt;
   long long launches = 0;
@@ -43,7 +47,7 @@ struct grmhd_ctx {
   std::vector<cudaEvent_t> pool;
 };
 
-enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, NKIND = 6 };
+enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, K_SEED = 6, NKIND = 7 };
 
 static cudaEvent_t ev_get(grmhd_ctx* c) {
   if (!c->pool.empty()) {
@@ -121,6 +125,7 @@ void grmhd_destroy(grmhd_ctx* c) {
   cudaFree(c->stats);
   cudaFree(c->rhs_ptrs);
   cudaFree(c->amr);
+  cudaFree(c->seed_buf);
   delete c;
 }
 
@@ -182,6 +187,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     q.Fp = c->scratch + ofs[i];
     q.lam = q.Fp + 30 * q.G.sf;
     q.Fh = q.lam + 3 * q.G.sf;
+    q.seed = nullptr;
   }
   // work lists: for each block size and domain, the blocks of patch 0, then patch 1, ...
   std::vector<Work> wl;
@@ -337,11 +343,44 @@ int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
 }
 
 static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats) {
+  if (c->seeder) {
+    ProfScope ps(c, K_SEED);
+    int rc = launch_seeder_patches(c->seeder, c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->P.rho_min, c->st);
+    c->launches += 1;
+    if (rc) return fail(c, rc, "seeder launch");
+  }
   ProfScope ps(c, K_C2P);
   launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p), nblk(c, DOM_ALL, c->bs_c2p), reg, c->P, c->E, c->flags,
-             stats ? c->stats : nullptr, c->st, c->bs_c2p);
+             stats ? c->stats : nullptr, c->st, c->bs_c2p, c->seeder != nullptr, c->seed_delta);
   c->launches += 1;
   return check_launch(c, "con2prim");
+}
+
+int grmhd_set_seeder(grmhd_ctx* c, const grmhd_seeder* s, double delta) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (!s) {
+    c->seeder = nullptr;
+    return GRMHD_OK;
+  }
+  if (!(delta > 0.0 && delta < 1.0)) return fail(c, GRMHD_ERR_ARG, "set_seeder: delta in (0, 1)");
+  int rc;
+  if (!c->seed_buf) {
+    size_t total = 0;
+    for (int i = 0; i < c->np; ++i) total += 3 * (size_t)c->pd_host[i].G.sf;
+    if ((rc = cuda_ok(c, cudaMalloc(&c->seed_buf, total * sizeof(float)), "cudaMalloc seeds"))) return GRMHD_ERR_NOMEM;
+    size_t o = 0;
+    for (int i = 0; i < c->np; ++i) {
+      c->pd_host[i].seed = c->seed_buf + o;
+      o += 3 * (size_t)c->pd_host[i].G.sf;
+    }
+    if ((rc = cuda_ok(c, cudaMemcpyAsync(c->pd, c->pd_host.data(), c->np * sizeof(PatchDev), cudaMemcpyHostToDevice,
+                                         c->st), "copy pd")) ||
+        (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
+      return rc;
+  }
+  c->seeder = s;
+  c->seed_delta = delta;
+  return GRMHD_OK;
 }
 
 static int iflux(grmhd_ctx* c, int reg) {

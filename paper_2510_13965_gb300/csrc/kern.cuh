@@ -17,6 +17,7 @@ struct PatchDev {
   double* Fp;   // pointwise fluxes [3][10][sf]
   double* lam;  // pointwise max |lambda_fast| [3][sf]
   double* Fh;   // interface fluxes [3][10][sf] at the interface between o and o + s_d
+  float* seed;  // learned con2prim seeds [3][sf] (mu_+, mu, W) or null
 };
 
 // Work item of a launch: patch index and block index within that patch's domain.
@@ -92,7 +93,7 @@ void launch_ghost(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int 
 // bs: threads per block of the launch (64, 128 or 256); the work list must
 // have been built for the same block size.
 void launch_c2p(const PatchDev* pd_dev, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs = 128);
+                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs = 128, bool seeded = false, double delta = 0.0);
 void launch_iflux(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs = 128);
 void launch_rhs(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int mode, int stage, double dt,
                 const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs = 128);
@@ -122,6 +123,11 @@ struct AmrPlan {
 };
 int amr_plan(const grmhd_patch_desc* d, const std::vector<Geo>& geo, int np, AmrPlan& P);
 void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, cudaStream_t st);
+
+// Learned seeder over patch points (seeder.cu): seeds of every point of the
+// work list (blocks of 128 points) of register reg into PatchDev::seed.
+int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd_dev, const Work* w, int nblk, int reg,
+                          double rho_min, cudaStream_t st);
 
 // Block sizes the autotuner chooses from.
 constexpr int NBS = 3;

@@ -166,9 +166,10 @@ void launch_ghost(const PatchDev* pd, const Work* w, int nblk, int reg, int axis
 // con2prim at every point, then the point-wise flux vectors F^d (10 fields)
 // and max |lambda^{+-}_fast| along d for the directions whose interface
 // stencils use this point.
-template <bool STATS, int BS>
+template <bool STATS, int BS, bool SEEDED>
 __global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
-                                                 grmhd_params P, Eos E, DevFlags* flags, C2PStats* stats) {
+                                                 grmhd_params P, Eos E, DevFlags* flags, C2PStats* stats,
+                                                 double delta) {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
@@ -195,7 +196,13 @@ __global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, con
     for (int n = 0; n < 9; ++n) cb[n] = U[(DD + n) * sf + o];
     double al = U[ALP * sf + o];
     C2POut r;
-    c2p_point(P, E, cb, gdd, guu, sg, al, r);
+    if (SEEDED) {
+      double sq[3];
+      for (int m = 0; m < 3; ++m) sq[m] = (double)PD.seed[m * sf + o];
+      c2p_point(P, E, cb, gdd, guu, sg, al, r, sq, delta);
+    } else {
+      c2p_point(P, E, cb, gdd, guu, sg, al, r);
+    }
     st_code = r.status;
     iters = r.iters;
     for (int n = 0; n < NP; ++n) PD.prim[n * sf + o] = r.prim[n];
@@ -291,19 +298,25 @@ __global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, con
 
 template <int BS>
 static void launch_c2p_bs(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                          DevFlags* flags, C2PStats* stats, cudaStream_t st) {
-  if (stats)
-    k_c2p<true, BS><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats);
-  else
-    k_c2p<false, BS><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats);
+                          DevFlags* flags, C2PStats* stats, cudaStream_t st, bool seeded, double delta) {
+  if (seeded) {
+    if (stats)
+      k_c2p<true, BS, true><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, delta);
+    else
+      k_c2p<false, BS, true><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, delta);
+  } else if (stats) {
+    k_c2p<true, BS, false><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, 0.0);
+  } else {
+    k_c2p<false, BS, false><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, 0.0);
+  }
 }
 
 void launch_c2p(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs) {
+                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs, bool seeded, double delta) {
   if (nblk <= 0) return;
-  if (bs == 64) launch_c2p_bs<64>(pd, w, nblk, reg, P, E, flags, stats, st);
-  else if (bs == 256) launch_c2p_bs<256>(pd, w, nblk, reg, P, E, flags, stats, st);
-  else launch_c2p_bs<128>(pd, w, nblk, reg, P, E, flags, stats, st);
+  if (bs == 64) launch_c2p_bs<64>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  else if (bs == 256) launch_c2p_bs<256>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  else launch_c2p_bs<128>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
 }
 
 // ---------------------------------------------------------------------------

@@ -97,6 +97,7 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   pd.Fp = (double*)area;
   pd.lam = pd.Fp + 30 * G.sf;
   pd.Fh = pd.lam + 3 * G.sf;
+  pd.seed = nullptr;
 
   Work wl[kMaxWork];
   int wofs[NDOM + 1];

@@ -259,29 +259,38 @@ DI void load_params(const float* __restrict__ w, const float* __restrict__ norm,
   if (threadIdx.x < NNORM) F[F_NORM + threadIdx.x] = norm[threadIdx.x];
 }
 
-// Features of one flat-metric conserved state (D, DYe, tau, S_i, B^i).  The
-// quantities whose cancellation BF16 inputs could not resolve ((1 + q)^2 - r^2
-// at large Lorentz factors, r and q themselves) are formed in FP64; the
-// logarithms of the formed quantities, whose results are FP32 features, run
-// in FP32.
-DI void features(const double* c, float f[NI]) {
-  double D = c[0], iD = 1.0 / D;
-  double q = c[2] * iD;
-  double S2 = c[3] * c[3] + c[4] * c[4] + c[5] * c[5];
-  double B2 = c[6] * c[6] + c[7] * c[7] + c[8] * c[8];
+// Features of one conserved state from its undensitized D, DYe, tau and the
+// invariants S2 = S_i S^i, B2 = B_i B^i, SB = S_i B^i (Kastaun's scalars: the
+// features do not depend on the metric otherwise).  The quantities whose
+// cancellation BF16 inputs could not resolve ((1 + q)^2 - r^2 at large
+// Lorentz factors, r and q themselves) are formed in FP64; the logarithms of
+// the formed quantities, whose results are FP32 features, run in FP32.
+// Returns sqrt(1 + r^2) and max(1 + q, 1e-30) for the seed map.
+DI void features_sc(double D, double DYe, double tau, double S2, double B2, double SB, float f[NI], double* sr,
+                    double* Qo) {
+  double iD = 1.0 / D;
+  double q = tau * iD;
   double r = sqrt(S2) * iD, b2 = B2 * iD;
   double Q = fmax(1.0 + q, 1e-30);
   double X = fmax((1.0 + q - r) * (1.0 + q + r), 1e-30);
-  float SB = (float)(c[3] * c[6] + c[4] * c[7] + c[5] * c[8]);
   float den = sqrtf((float)S2) * sqrtf((float)B2);
   f[0] = log10f((float)D);
-  f[1] = (float)(c[1] * iD);
+  f[1] = (float)(DYe * iD);
   f[2] = logf((float)Q);
   f[3] = logf((float)X);
   f[4] = (float)(r / Q);
   f[5] = log10f(fmaxf((float)b2, 1e-30f));
-  f[6] = den > 0.f ? SB / den : 0.f;
+  f[6] = den > 0.f ? (float)SB / den : 0.f;
   f[7] = (float)(b2 / Q);
+  *sr = sqrt(1.0 + r * r);
+  *Qo = Q;
+}
+
+// Flat-metric state (D, DYe, tau, S_i, B^i).
+DI void features(const double* c, float f[NI]) {
+  double sr, Q;
+  features_sc(c[0], c[1], c[2], c[3] * c[3] + c[4] * c[4] + c[5] * c[5], c[6] * c[6] + c[7] * c[7] + c[8] * c[8],
+              c[3] * c[6] + c[4] * c[7] + c[5] * c[8], f, &sr, &Q);
 }
 
 // (sqrt(1 + r^2), max(1 + q, 1e-30)) of a flat-metric state: the scalings of
@@ -376,6 +385,91 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
         o[0] = t0;
         o[1] = t1;
         o[2] = t2;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Seeds for the points of patch work items (blocks of 128 points, DOM_ALL):
+// features from the conserved variables of register reg and the metric
+// (gamma_ij = gt_ij / chi, gamma^ij = chi gt^ij, sqrt(gamma) = sqrt(det gt)
+// chi^(-3/2)), network, seeds (float) into PatchDev::seed.  Atmosphere points
+// (D < rho_min, which con2prim resets without solving) and non-finite states
+// get NaN seeds.  Persistent over the work list.
+__global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
+                                                  int nblk, int reg, double rho_min, const float* __restrict__ wts,
+                                                  const float* __restrict__ norm) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  u16* S = reinterpret_cast<u16*>(smem);
+  float* F = reinterpret_cast<float*>(smem + (size_t)S_END_INFER * 2);
+  load_params(wts, norm, S, F);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * 32, s = threadIdx.x;
+  const float* nm = F + F_NORM + 2 * NI;
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const Work wk = w[b];
+    const PatchDev& PD = pd[wk.patch];
+    const Geo G = PD.G;
+    long long q = (long long)wk.block * TM + s;
+    bool valid = q < dom_count(DOM_ALL, G);
+    bool solve = false;
+    long long o = 0;
+    float f[NI];
+    double sr = 1.0, Q = 1.0;
+    if (valid) {
+      int i, j, k;
+      dom_decode(DOM_ALL, G, q, i, j, k);
+      o = at(G, i, j, k);
+      const long long sf = G.sf;
+      const double* U = PD.U[reg];
+      double gt[6];
+      for (int n = 0; n < 6; ++n) gt[n] = U[(GT + n) * sf + o];
+      double chi = U[CHI * sf + o];
+      double det = det3(gt);
+      double ichi = 1.0 / chi;
+      double isg = 1.0 / (sqrt(det) * ichi * sqrt(ichi));
+      double D = U[DD * sf + o] * isg;
+      if (D >= rho_min && isfinite(D)) {
+        double gtu[6];
+        inv3(gt, 1.0 / det, gtu);
+        double Sd[3], Bu[3];
+        for (int a = 0; a < 3; ++a) {
+          Sd[a] = U[(DD + 3 + a) * sf + o] * isg;
+          Bu[a] = U[(DD + 6 + a) * sf + o] * isg;
+        }
+        double Su[3], Bd[3];
+        lower3(gtu, Sd, Su);  // gt^ij S_j; times chi below
+        lower3(gt, Bu, Bd);   // gt_ij B^j; times 1/chi below
+        double S2 = chi * (Sd[0] * Su[0] + Sd[1] * Su[1] + Sd[2] * Su[2]);
+        double B2 = ichi * (Bu[0] * Bd[0] + Bu[1] * Bd[1] + Bu[2] * Bd[2]);
+        double SB = Sd[0] * Bu[0] + Sd[1] * Bu[1] + Sd[2] * Bu[2];
+        features_sc(D, U[(DD + 1) * sf + o] * isg, U[(DD + 2) * sf + o] * isg, S2, B2, SB, f, &sr, &Q);
+        solve = true;
+      }
+    }
+    put_x(S + S_X, s, f, F + F_NORM, solve);
+    __syncwarp();
+    fwd_hidden<1>(S + S_X, LDX, S + S_W1, F + F_B, S + S_H1, row0, lane);
+    __syncwarp();
+    fwd_hidden<4>(S + S_H1, LDH, S + S_W2, F + F_B + NH, S + S_H2, row0, lane);
+    __syncwarp();
+    fwd_hidden<4>(S + S_H2, LDH, S + S_W3, F + F_B + 2 * NH, S + S_H1, row0, lane);
+    __syncwarp();
+    fwd_out(S + S_H1, S + S_W4, F + F_B + 3 * NH, F + F_Y, row0, lane);
+    __syncwarp();
+    if (valid) {
+      float* sd = PD.seed + o;
+      const long long sf = G.sf;
+      if (solve) {
+        float t0 = fmaf(F[F_Y + s * 4 + 0], nm[NO + 0], nm[0]);
+        float t1 = fmaf(F[F_Y + s * 4 + 1], nm[NO + 1], nm[1]);
+        float t2 = fmaf(F[F_Y + s * 4 + 2], nm[NO + 2], nm[2]);
+        sd[0] = expf(t0) / (float)sr;
+        sd[sf] = expf(t1) / (float)Q;
+        sd[2 * sf] = expf(t2);
+      } else {
+        sd[0] = sd[sf] = sd[2 * sf] = __int_as_float(0x7fc00000);
       }
     }
     __syncwarp();
@@ -673,6 +767,8 @@ int set_smem_attrs() {
       cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
           cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_patch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
           cudaSuccess)
     return GRMHD_ERR_CUDA;
   attr_set = true;
@@ -702,6 +798,26 @@ unsigned fwd_grid(long long n) {
 int last_rc() { return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA; }
 
 }  // namespace
+
+namespace gk {
+int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd, const Work* w, int nblk, int reg, double rho_min,
+                          cudaStream_t st) {
+  if (!s || nblk <= 0) return nblk <= 0 ? GRMHD_OK : GRMHD_ERR_ARG;
+  static int per_dev[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!per_dev[dev]) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_patch, TM, smem_bytes(false));
+    per_dev[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  }
+  int grid = nblk < per_dev[dev] ? nblk : per_dev[dev];
+  k_mlp_patch<<<grid, TM, smem_bytes(false), st>>>(pd, w, nblk, reg, rho_min, s->w, s->norm);
+  return last_rc();
+}
+}  // namespace gk
 
 extern "C" {
 

@@ -244,3 +244,36 @@ def test_trained_seeder(table_setup):
     pg, sg, itx, _, _ = (a.cpu().numpy() for a in g.c2p_flat_seeded(P, cg, exact, 1e-6, table=T))
     prim_check(pg.T, po.T, sg, so, cons[:, :3].T)
     assert itx[ok].mean() <= 0.8 * ito[ok].mean(), (itx[ok].mean(), ito[ok].mean())
+
+
+def test_seeded_patch_con2prim_matches_oracle(table_setup):
+    """Seeds inside the patch substep (features from the conserved variables
+    and the metric): the tabulated-EOS star's primitives equal the oracle's
+    plain con2prim; the seeds change the evaluation count."""
+    table, P0, O0, T = table_setup
+    P = synth.table_params(table, bc=1)
+    n, dx = (24, 24, 24), 1.0
+    ID = synth.tov_id(n=n, x0=(-12.0,) * 3, dx=dx, seed=3, table=table, rho_atmo=P["rho_atmo"])
+    O = oracle.Oracle(P, table)
+    U = O.init_state(ID, n, dx)
+    f, t = _gpu_pairs(P, T, 1 << 15, 13)
+    S = g.Seeder(seed=2)
+    S.train(f, t, batch=1024, epochs=10, lr=3e-3, lr_final=3e-5)
+    res = {}
+    for seeded in (False, True):
+        pt = g.Patches(P, [dict(n=n, dx=dx, x0=(-12.0,) * 3)], table=T)
+        pt.U[0][0].copy_(torch.as_tensor(U, device="cuda"))
+        torch.cuda.synchronize()
+        if seeded:
+            pt.set_seeder(S, 3e-2)
+        st = pt.con2prim(0, stats=True)
+        pt.synchronize()
+        res[seeded] = (pt.prim[0].cpu().numpy(), pt.status[0].cpu().numpy(), st)
+    Uo = U.copy()
+    po, so, worst, _ = O.con2prim_patch(Uo, n)
+    cons = Uo[22:25]
+    for seeded in (False, True):
+        pg, sg, st = res[seeded]
+        prim_check(pg.reshape(NP, -1), po.reshape(NP, -1), sg.reshape(-1), so.reshape(-1), cons.reshape(3, -1))
+        assert st["failed"] == 0
+    assert res[True][2]["iterations"] != res[False][2]["iterations"]
