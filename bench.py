@@ -68,6 +68,9 @@ def _args():
     a.add_argument("--train-epochs", type=int, default=40)
     a.add_argument("--amr-scale", type=float, default=1.0,
                    help="point counts of the hierarchy workload relative to the 366-patch layout")
+    a.add_argument("--amr-seeded", action="store_true",
+                   help="also time the hierarchy with NN-seeded con2prim")
+    a.add_argument("--amr-delta", type=float, default=3e-2)
     a.add_argument("--edge", type=int, default=N_EDGE,
                    help="interior points per axis (the same [-20,20]^3 star; 128 is the benchmark workload)")
     return a.parse_args()
@@ -606,6 +609,38 @@ def run_amr(args):
     prof_k = pt.profile_read()
     pt.profile(False)
     tot = sum(v[0] for v in prof_k.values()) or 1.0
+    seeded = None
+    if args.amr_seeded:
+        # The same steps with NN-seeded con2prim: network trained on 2^20
+        # flat-metric pairs (seed 13) made on the GPU, as in the c2p workload.
+        cons = _c2p_cons(g, P, T, args.train_pairs, seed=13)
+        _, st_, _, roots, _ = g.c2p_flat_seeded(P, cons, None, table=T)
+        keep = st_ >= 0
+        f = g.seeder_features(cons)[keep].contiguous()
+        t = g.seeder_targets(cons, roots)[keep].contiguous()
+        del cons, roots
+        S = g.Seeder(seed=1)
+        S.train(f, t, batch=4096, epochs=args.train_epochs, lr=3e-3, lr_final=3e-5)
+        del f, t
+        pt.set_seeder(S, args.amr_delta)
+        for _ in range(2):
+            pt.step(dt)
+        pt.capture_graph(1, dt)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            pt.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / args.steps
+        pt.profile(True)
+        pt.step(dt)
+        pt.synchronize()
+        prof_s = pt.profile_read()
+        pt.profile(False)
+        seeded = {"value": zones / (ms_s / 1e3), "ms_per_step": ms_s, "delta": args.amr_delta,
+                  "kernel_ms_per_step": {k: v[0] for k, v in prof_s.items() if v[1]},
+                  "status": pt.sync_status(), "speedup_vs_plain": ms / ms_s}
     levels = {}
     for s_ in specs:
         levels.setdefault(s_["level"], [0, 0])
@@ -623,6 +658,8 @@ def run_amr(args):
             "kernel_ms_per_step": {k: v[0] for k, v in prof_k.items() if v[1]},
             "kernel_share": {k: v[0] / tot for k, v in prof_k.items() if v[1]},
             "gpu_launches": int(launches), "status": rc, "clocks": clk, "setup_s": setup_s}
+    if seeded is not None:
+        line["nn_seeded"] = seeded
     print(json.dumps(line), flush=True)
     return 0
 
