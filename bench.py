@@ -174,6 +174,52 @@ def cpu_baseline(n=48, budget_s=12.0):
                       "oracle, %.1f s" % (steps, n, el)}
 
 
+def cpu_baseline_c2p(n=1 << 19):
+    """The oracle's flat-metric con2prim (plain brackets), serial, on n states
+    of the isolated-con2prim workload made by the oracle's own prim2con."""
+    import oracle
+    import synth
+    table = synth.make_table()
+    O = oracle.Oracle(synth.table_params(table), table)
+    st = synth.c2p_states(n, seed=3)
+    cons = np.zeros((n, 10))
+    for q in range(n):
+        pr = np.zeros(oracle.NP)
+        pr[0], pr[7] = st["rho"][q], st["ye"][q]
+        e = O.eos_from_T(st["rho"][q], st["T"][q], st["ye"][q])
+        pr[1], pr[2] = e[1], e[0]
+        pr[3:6] = st["v"][q]
+        cons[q, :9] = oracle.prim2con_point(pr, st["B"][q], [1.0, 0, 0, 1.0, 0, 1.0])
+    t0 = time.perf_counter()
+    O.c2p_flat_ext(cons)
+    el = time.perf_counter() - t0
+    return {"value": n / el, "unit": "con2prim solves/s", "cores": 1, "kind": "oracle",
+            "sample": "%d states (seed 3) of the workload, plain brackets, serial C++ oracle, %.1f s" % (n, el)}
+
+
+def cpu_baseline_amr(scale=0.25):
+    """One RK4 step of the hierarchy workload at a reduced scale on the oracle
+    (serial; every level at the finest time step, restriction at the end)."""
+    import oracle
+    import synth
+    table = synth.make_table()
+    P = synth.table_params(table, bc=3)
+    specs = synth.amr_tov_layout(scale=scale)
+    prof = synth.tov_profile()
+    H = oracle.Hierarchy(oracle.Oracle(P, table), specs)
+    for q, s_ in enumerate(specs):
+        H.init_state(q, synth.tov_id(n=s_["n"], x0=s_["x0"], dx=s_["dx"], seed=4000 + q, table=table,
+                                     rho_atmo=P["rho_atmo"], profile=prof))
+    H.restrict(0)
+    zones = int(sum(np.prod(s_["n"]) for s_ in specs))
+    t0 = time.perf_counter()
+    H.rk4_step(0.25 * min(s_["dx"] for s_ in specs))
+    el = time.perf_counter() - t0
+    return {"value": zones / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one RK4 step of the %d-patch hierarchy at scale %g (%d interior points), serial C++ "
+                      "oracle, %.1f s" % (len(specs), scale, zones, el)}
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -545,6 +591,8 @@ def run_c2p(args):
                          "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1])},
             "seeded_vs_plain": {"same_status": same_status, "max_rel_rho_diff": rel_rho},
             "gpu_launches": 4 * K, "clocks": clk, "setup_s": gen_s}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_c2p()
     print(json.dumps(line), flush=True)
     return 0
 
@@ -660,6 +708,8 @@ def run_amr(args):
             "gpu_launches": int(launches), "status": rc, "clocks": clk, "setup_s": setup_s}
     if seeded is not None:
         line["nn_seeded"] = seeded
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_amr()
     print(json.dumps(line), flush=True)
     return 0
 
