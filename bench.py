@@ -145,9 +145,15 @@ def _max_over_ranks(ws, x):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _whole_job_rate(ws, steps, units_per_rank_step, ms_max):
+    """Units all ranks processed per second, timed by the slowest rank."""
+    return ws * steps * units_per_rank_step / (ms_max / 1e3)
 
 
 def cpu_baseline(n=48, budget_s=12.0):
@@ -308,7 +314,7 @@ def run_grmhd(args):
     if rc != 0:
         raise SystemExit("timed steps failed: status %d" % rc)
     zones = edge ** 3
-    value = ws * args.steps * zones / (ms_max / 1e3)
+    value = _whole_job_rate(ws, args.steps, zones, ms_max)
 
     # ---- end to end: state from pinned host memory, step, state back --------
     host_in = pt.U[0][0].detach().to("cpu").pin_memory()

@@ -1,0 +1,52 @@
+"""Static magnetised TOV star, 128^3 (the benchmark workload), 100 RK4 steps
+on the GPU: the star stays static to the accuracy the discretisation gives.
+
+- central density: |rho_c(t) / rho_c(0) - 1| <= 1e-3 without, <= 2e-2 with
+  the 1 % pressure perturbation;
+- velocity inside the star (rho > rho_c(0) / 10; the outer layers carry the
+  surface's interaction with the atmosphere): max |v| <= 1e-3;
+- total rest mass, the sum of Dbar dV over the interior: relative drift
+  <= 1e-6 (the atmosphere and the outer boundary may exchange a little).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2510_13965_gb300 as g  # noqa: E402
+
+
+@pytest.mark.parametrize("perturb,rho_tol", [(False, 1e-3), (True, 2e-2)])
+def test_static_star_stays_static(perturb, rho_tol):
+    edge = 128
+    dx = 40.0 / edge
+    P = synth.ideal_params(bc=1)
+    ID = synth.tov_id(n=(edge,) * 3, x0=(-20.0,) * 3, dx=dx, seed=1, perturb=perturb, bfield=True)
+    pt = g.Patches(P, [dict(n=(edge,) * 3, dx=dx, x0=(-20.0,) * 3)])
+    pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    c = edge // 2 + 3
+
+    def observe():
+        pt.con2prim(0)
+        pt.synchronize()
+        prim = pt.prim[0]
+        rho = prim[0, 3:-3, 3:-3, 3:-3]
+        v = torch.sqrt(prim[3] ** 2 + prim[4] ** 2 + prim[5] ** 2)[3:-3, 3:-3, 3:-3]
+        return float(prim[0, c, c, c]), v, rho, float(pt.U[0][0][22, 3:-3, 3:-3, 3:-3].sum()) * dx ** 3
+
+    rho_c0, _, _, mass0 = observe()
+    dt = 0.4 * dx
+    for step in range(1, 101):
+        pt.step(dt)
+        if step % 25 == 0:
+            rho_c, v, rho, mass = observe()
+            assert pt.sync_status() == 0
+            assert abs(rho_c / rho_c0 - 1.0) <= rho_tol, (step, rho_c / rho_c0 - 1.0)
+            assert float(v[rho > 0.1 * rho_c0].max()) <= 1e-3, step
+            assert abs(mass / mass0 - 1.0) <= 1e-6, (step, mass / mass0 - 1.0)
