@@ -400,8 +400,16 @@ int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float
                        double* loss_hist, void* stream);
 
 /* Seeds (device double [n][3]: mu_+, mu, W) for the conserved states cons
- * (device double [n][10]): features, network and the seed map in one kernel. */
+ * (device double [n][10]): features, network and the seed map in one kernel.
+ * The network runs on the tcgen05 tensor cores: 128-sample tiles, BF16
+ * operands in shared memory, FP32 accumulators in tensor memory. */
 int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double* seeds, void* stream);
+
+/* Synchronises the device and returns GRMHD_ERR_TIMEOUT when an inference
+ * kernel of this seeder gave up waiting for its tensor-core products (each
+ * wait is bounded; the kernel then frees its tensor memory and stops), else
+ * GRMHD_OK; clears the condition. */
+int grmhd_seeder_status(grmhd_seeder* s);
 
 void grmhd_seeder_destroy(grmhd_seeder* s);
 

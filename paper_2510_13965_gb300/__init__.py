@@ -105,6 +105,7 @@ _SIGS = {
     "grmhd_seeder_infer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
     "grmhd_seeder_destroy": (None, [ctypes.c_void_p]),
+    "grmhd_seeder_status": (ctypes.c_int, [ctypes.c_void_p]),
     "grmhd_c2p_flat_seeded": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -455,6 +456,11 @@ class Seeder:
                                        _stream(torch, stream))
         _check(rc, None, "grmhd_seeder_train")
         return hist
+
+    def status(self):
+        """0, or raises when an inference kernel timed out waiting for its tensor-core products."""
+        _check(load().grmhd_seeder_status(self.h), None, "grmhd_seeder_status")
+        return 0
 
     def infer(self, cons, stream=None):
         """Seeds (n, 3) = (mu_+, mu, W) for flat-metric conserved states (n, 10)."""

@@ -345,7 +345,8 @@ int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
 static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats) {
   if (c->seeder) {
     ProfScope ps(c, K_SEED);
-    int rc = launch_seeder_patches(c->seeder, c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->P.rho_min, c->st);
+    int rc = launch_seeder_patches(c->seeder, c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->P.rho_min,
+                                   &c->flags->flags, c->st);
     c->launches += 1;
     if (rc) return fail(c, rc, "seeder launch");
   }
@@ -612,6 +613,7 @@ int grmhd_sync_status(grmhd_ctx* c) {
       (rc = cuda_ok(c, cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->st), "flags clear")) ||
       (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
     return rc;
+  if (h.flags & 4) return fail(c, GRMHD_ERR_TIMEOUT, "seeder tensor-core wait timed out");
   if (h.flags & 2) return fail(c, GRMHD_ERR_NONFINITE, "non-finite state reached con2prim");
   if (h.flags & 1) return fail(c, GRMHD_ERR_C2P_FATAL, "fatal con2prim point");
   return GRMHD_OK;

@@ -127,7 +127,7 @@ void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, 
 // Learned seeder over patch points (seeder.cu): seeds of every point of the
 // work list (blocks of 128 points) of register reg into PatchDev::seed.
 int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd_dev, const Work* w, int nblk, int reg,
-                          double rho_min, cudaStream_t st);
+                          double rho_min, int* err, cudaStream_t st);
 
 // Block sizes the autotuner chooses from.
 constexpr int NBS = 3;

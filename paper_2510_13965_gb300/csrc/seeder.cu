@@ -273,16 +273,18 @@ DI void features_sc(double D, double DYe, double tau, double S2, double B2, doub
   double r = sqrt(S2) * iD, b2 = B2 * iD;
   double Q = fmax(1.0 + q, 1e-30);
   double X = fmax((1.0 + q - r) * (1.0 + q + r), 1e-30);
+  // Past the cancellation, FP32 is enough for what becomes an FP32 feature.
+  const float rf = (float)r, Qf = (float)Q, b2f = (float)b2;
   float den = sqrtf((float)S2) * sqrtf((float)B2);
   f[0] = log10f((float)D);
   f[1] = (float)(DYe * iD);
-  f[2] = logf((float)Q);
+  f[2] = logf(Qf);
   f[3] = logf((float)X);
-  f[4] = (float)(r / Q);
-  f[5] = log10f(fmaxf((float)b2, 1e-30f));
+  f[4] = rf / Qf;
+  f[5] = log10f(fmaxf(b2f, 1e-30f));
   f[6] = den > 0.f ? (float)SB / den : 0.f;
-  f[7] = (float)(b2 / Q);
-  *sr = sqrt(1.0 + r * r);
+  f[7] = b2f / Qf;
+  *sr = (double)sqrtf(fmaf(rf, rf, 1.f));
   *Qo = Q;
 }
 
@@ -322,21 +324,236 @@ DI void forward_tile(u16* S, float* F, u16* h3_out, int row0, int lane) {
   __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the 5th-generation tensor cores (tcgen05).  One CTA of 128
+// threads owns a tile of 128 samples: thread r writes row r of the input and
+// of each hidden activation into shared memory, one elected thread issues the
+// layer's tcgen05.mma (M = 128 samples, N = 64 units or 16 for the 3 outputs,
+// K in steps of 16; BF16 operands from shared memory, FP32 accumulator in 64
+// TMEM columns), commits it to an mbarrier, and every warp reads its 32 rows
+// of the accumulator back with tcgen05.ld for the bias + ReLU + BF16 epilogue.
+// Operands use the no-swizzle K-major core-matrix layout: 8 rows x 16 bytes
+// per core matrix, slabs of K = 16; within a slab the core matrix of row group
+// g and K half h sits at g * 256 + h * 128 bytes, so a matrix descriptor has
+// leading (K) byte offset 128 and stride (row group) byte offset 256.
+// Persistent: the weights are converted once per CTA.
+namespace tc {
+constexpr int W1_B = 0;                      // B operand of layer 1: 64 units x K 16 (inputs 8..15 zero)
+constexpr int W2_B = W1_B + 64 * 16 * 2;     // 64 x 64
+constexpr int W3_B = W2_B + 64 * 64 * 2;     // 64 x 64
+constexpr int W4_B = W3_B + 64 * 64 * 2;     // 16 x 64 (outputs 3..15 zero)
+constexpr int X_B = W4_B + 16 * 64 * 2;      // A operand of layer 1: 128 x 16
+constexpr int H_B = X_B + 128 * 16 * 2;      // A operand of layers 2-4: 128 x 64 (reused)
+constexpr int FL_B = H_B + 128 * 64 * 2;     // floats: biases (3 x 64 + 4), normalisation (22 + 2)
+constexpr int MBAR_B = FL_B + (3 * NH + 4 + NNORM + 2) * 4;
+constexpr int TADDR_B = MBAR_B + 8;
+constexpr int SMEM = TADDR_B + 8;
+static_assert(MBAR_B % 8 == 0, "mbarrier alignment");
+constexpr uint32_t TMEM_COLS = 64;
+constexpr uint32_t IDESC_BASE = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 4) << 24);  // f32 <- bf16 x bf16, M 128
+constexpr uint32_t IDESC_N64 = IDESC_BASE | ((uint32_t)(64 >> 3) << 17);
+constexpr uint32_t IDESC_N16 = IDESC_BASE | ((uint32_t)(16 >> 3) << 17);
+constexpr long WAIT_LIMIT = 20000000;
+
+// Byte offset of element (r, k) in an operand of `rows` rows (K-major core layout).
+__host__ __device__ inline int core_off(int r, int k, int rows) {
+  int kk = k & 15;
+  return (k >> 4) * (rows * 32) + (r >> 3) * 256 + (kk >> 3) * 128 + (r & 7) * 16 + (kk & 7) * 2;
+}
+DI uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+DI uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) | (1ull << 46);
+}
+DI void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+DI void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+// Bounded wait for the mbarrier phase with the given parity; false on timeout.
+DI bool wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done = 0;
+  for (long it = 0; it < WAIT_LIMIT && !done; ++it)
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+DI void ld64(uint32_t ta, float* f) {
+  uint32_t v[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+      "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+        "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]),
+        "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]),
+        "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]),
+        "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 64; ++c) f[c] = __uint_as_float(v[c]);
+}
+DI void ld16(uint32_t ta, float* f) {
+  uint32_t v[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(ta));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 16; ++c) f[c] = __uint_as_float(v[c]);
+}
+
+// Weights (BF16, core layout), biases and normalisation into shared memory.
+DI void load(const float* __restrict__ w, const float* __restrict__ norm, unsigned char* sm) {
+  for (int q = threadIdx.x; q < 64 * 16; q += blockDim.x) {
+    int n = q >> 4, k = q & 15;
+    *reinterpret_cast<u16*>(sm + W1_B + core_off(n, k, 64)) = k < NI ? bf(w[OW1 + k * NH + n]) : 0;
+  }
+  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+    int n = q >> 6, k = q & 63;
+    *reinterpret_cast<u16*>(sm + W2_B + core_off(n, k, 64)) = bf(w[OW2 + k * NH + n]);
+    *reinterpret_cast<u16*>(sm + W3_B + core_off(n, k, 64)) = bf(w[OW3 + k * NH + n]);
+  }
+  for (int q = threadIdx.x; q < 16 * 64; q += blockDim.x) {
+    int n = q >> 6, k = q & 63;
+    *reinterpret_cast<u16*>(sm + W4_B + core_off(n, k, 16)) = n < NO ? bf(w[OW4 + k * NO + n]) : 0;
+  }
+  float* F = reinterpret_cast<float*>(sm + FL_B);
+  for (int q = threadIdx.x; q < NH; q += blockDim.x) {
+    F[q] = w[OB1 + q];
+    F[NH + q] = w[OB2 + q];
+    F[2 * NH + q] = w[OB3 + q];
+  }
+  if (threadIdx.x < 4) F[3 * NH + threadIdx.x] = threadIdx.x < NO ? w[OB4 + threadIdx.x] : 0.f;
+  if (threadIdx.x < NNORM) F[3 * NH + 4 + threadIdx.x] = norm[threadIdx.x];
+}
+
+// Row r of the input operand: standardized features as BF16, zeros beyond 8.
+DI void put_x(unsigned char* sm, int r, const float f[NI], const float* nrm, bool valid) {
+  uint32_t p[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    p[c] = valid ? pk(bf((f[2 * c] - nrm[2 * c]) / nrm[NI + 2 * c]), bf((f[2 * c + 1] - nrm[2 * c + 1]) / nrm[NI + 2 * c + 1]))
+                 : 0u;
+  *reinterpret_cast<uint4*>(sm + X_B + core_off(r, 0, 128)) = make_uint4(p[0], p[1], p[2], p[3]);
+  *reinterpret_cast<uint4*>(sm + X_B + core_off(r, 8, 128)) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Epilogue of a hidden layer: row r = bf16(relu(acc + bias)) into the activation operand.
+DI void put_h(unsigned char* sm, int r, const float* acc, const float* bias) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint32_t p[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int k = 8 * c + 2 * e;
+      p[e] = pkf(fmaxf(acc[k] + bias[k], 0.f), fmaxf(acc[k + 1] + bias[k + 1], 0.f));
+    }
+    *reinterpret_cast<uint4*>(sm + H_B + core_off(r, 8 * c, 128)) = make_uint4(p[0], p[1], p[2], p[3]);
+  }
+}
+
+// The four layers of one tile whose inputs are in place; y = network outputs
+// of this thread's row.  Returns false (in every thread) when a wait timed out.
+DI bool forward(unsigned char* sm, uint32_t tmem, uint32_t& phase, float y[NO]) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t mbar = su32(sm + MBAR_B);
+  const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+  const float* F = reinterpret_cast<const float*>(sm + FL_B);
+  bool ok = true;
+  float acc[64];
+#pragma unroll 1
+  for (int layer = 0; layer < 4; ++layer) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (layer == 0) {
+        mma(tmem, sdesc(su32(sm + X_B)), sdesc(su32(sm + W1_B)), IDESC_N64, 0u);
+      } else {
+        const int wb = layer == 1 ? W2_B : layer == 2 ? W3_B : W4_B, nrows = layer == 3 ? 16 : 64;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          mma(tmem, sdesc(su32(sm + H_B + ks * 128 * 32)), sdesc(su32(sm + wb + ks * nrows * 32)),
+              layer == 3 ? IDESC_N16 : IDESC_N64, ks > 0 ? 1u : 0u);
+      }
+      commit(mbar);
+    }
+    bool done = wait(mbar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!done)) {
+      // Timed out: let the MMA finish (bounded) before the caller frees TMEM.
+      wait(mbar, phase ^ 1u);
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (layer < 3) {
+      ld64(ta, acc);
+      put_h(sm, tid, acc, F + layer * NH);
+    } else {
+      ld16(ta, acc);
+#pragma unroll
+      for (int j = 0; j < NO; ++j) y[j] = acc[j] + F[3 * NH + j];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  return ok;
+}
+
+// TMEM and mbarrier set-up / tear-down of a CTA.
+DI uint32_t begin(unsigned char* sm) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(sm + MBAR_B)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(sm + TADDR_B)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *reinterpret_cast<volatile uint32_t*>(sm + TADDR_B);
+}
+DI void end(uint32_t tmem) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+}  // namespace tc
+
 // MODE 0: inference from conserved states to seeds (double [n][3]).
 // MODE 1: forward from raw features to targets (float [n][3]).
-// Persistent: each CTA converts the weights once and walks over tiles of 128
-// samples with a stride of the grid; every warp touches only its own 32 rows,
-// so tiles follow one another without block barriers.
 template <int MODE>
 __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restrict__ in, const float* __restrict__ w,
-                                                const float* __restrict__ norm, void* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  u16* S = reinterpret_cast<u16*>(smem);
-  float* F = reinterpret_cast<float*>(smem + (size_t)S_END_INFER * 2);
-  load_params(w, norm, S, F);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * 32, s = threadIdx.x;
-  const float* nm = F + F_NORM + 2 * NI;
+                                                const float* __restrict__ norm, void* __restrict__ out,
+                                                int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  tc::load(w, norm, smem);
+  const uint32_t tmem = tc::begin(smem);
+  const float* F = reinterpret_cast<const float*>(smem + tc::FL_B);
+  const float* nm = F + 3 * NH + 4;  // features mean/scale, then targets
+  const float* tn = nm + 2 * NI;
+  const int s = threadIdx.x;
+  uint32_t phase = 0;
   const long long ntiles = (n + TM - 1) / TM;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     long long q = tile * TM + s;
@@ -355,40 +572,34 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
         for (int k = 0; k < NI; ++k) f[k] = fp[k];
       }
     }
-    put_x(S + S_X, s, f, F + F_NORM, valid);
-    __syncwarp();
-    // Layer 3 writes into H1 (free after layer 2): inference keeps two hidden tiles.
-    fwd_hidden<1>(S + S_X, LDX, S + S_W1, F + F_B, S + S_H1, row0, lane);
-    __syncwarp();
-    fwd_hidden<4>(S + S_H1, LDH, S + S_W2, F + F_B + NH, S + S_H2, row0, lane);
-    __syncwarp();
-    fwd_hidden<4>(S + S_H2, LDH, S + S_W3, F + F_B + 2 * NH, S + S_H1, row0, lane);
-    __syncwarp();
-    fwd_out(S + S_H1, S + S_W4, F + F_B + 3 * NH, F + F_Y, row0, lane);
-    __syncwarp();
-    if (valid) {
-      float t0 = fmaf(F[F_Y + s * 4 + 0], nm[NO + 0], nm[0]);
-      float t1 = fmaf(F[F_Y + s * 4 + 1], nm[NO + 1], nm[1]);
-      float t2 = fmaf(F[F_Y + s * 4 + 2], nm[NO + 2], nm[2]);
-      if (MODE == 0) {
-        // Seeds need no more than FP32 accuracy: the FP64 root finder polishes them.
-        const double* cp = static_cast<const double*>(in) + q * 10;
-        float D = (float)cp[0];
-        float r = sqrtf((float)(cp[3] * cp[3] + cp[4] * cp[4] + cp[5] * cp[5])) / D;
-        float Q = fmaxf(1.f + (float)(cp[2] / cp[0]), 1e-30f);
-        double* o = static_cast<double*>(out) + q * 3;
-        o[0] = (double)(expf(t0) / sqrtf(1.f + r * r));
-        o[1] = (double)(expf(t1) / Q);
-        o[2] = (double)expf(t2);
-      } else {
-        float* o = static_cast<float*>(out) + q * 3;
-        o[0] = t0;
-        o[1] = t1;
-        o[2] = t2;
-      }
+    tc::put_x(smem, s, f, nm, valid);
+    float y[NO];
+    if (!tc::forward(smem, tmem, phase, y)) {
+      if (s == 0) atomicOr(err, 1);
+      break;
     }
-    __syncwarp();
+    if (!valid) continue;
+    float t0 = fmaf(y[0], tn[NO + 0], tn[0]);
+    float t1 = fmaf(y[1], tn[NO + 1], tn[1]);
+    float t2 = fmaf(y[2], tn[NO + 2], tn[2]);
+    if (MODE == 0) {
+      // Seeds need no more than FP32 accuracy: the FP64 root finder polishes them.
+      const double* cp = static_cast<const double*>(in) + q * 10;
+      float D = (float)cp[0];
+      float r = sqrtf((float)(cp[3] * cp[3] + cp[4] * cp[4] + cp[5] * cp[5])) / D;
+      float Q = fmaxf(1.f + (float)(cp[2] / cp[0]), 1e-30f);
+      double* o = static_cast<double*>(out) + q * 3;
+      o[0] = (double)(expf(t0) / sqrtf(1.f + r * r));
+      o[1] = (double)(expf(t1) / Q);
+      o[2] = (double)expf(t2);
+    } else {
+      float* o = static_cast<float*>(out) + q * 3;
+      o[0] = t0;
+      o[1] = t1;
+      o[2] = t2;
+    }
   }
+  tc::end(tmem);
 }
 
 // Seeds for the points of patch work items (blocks of 128 points, DOM_ALL):
@@ -399,14 +610,15 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
 // get NaN seeds.  Persistent over the work list.
 __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
                                                   int nblk, int reg, double rho_min, const float* __restrict__ wts,
-                                                  const float* __restrict__ norm) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  u16* S = reinterpret_cast<u16*>(smem);
-  float* F = reinterpret_cast<float*>(smem + (size_t)S_END_INFER * 2);
-  load_params(wts, norm, S, F);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, row0 = (threadIdx.x >> 5) * 32, s = threadIdx.x;
-  const float* nm = F + F_NORM + 2 * NI;
+                                                  const float* __restrict__ norm, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  tc::load(wts, norm, smem);
+  const uint32_t tmem = tc::begin(smem);
+  const float* F = reinterpret_cast<const float*>(smem + tc::FL_B);
+  const float* nm = F + 3 * NH + 4;
+  const float* tn = nm + 2 * NI;
+  const int s = threadIdx.x;
+  uint32_t phase = 0;
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     const Work wk = w[b];
     const PatchDev& PD = pd[wk.patch];
@@ -424,7 +636,7 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
       const long long sf = G.sf;
       const double* U = PD.U[reg];
       double gt[6];
-      for (int n = 0; n < 6; ++n) gt[n] = U[(GT + n) * sf + o];
+      for (int m = 0; m < 6; ++m) gt[m] = U[(GT + m) * sf + o];
       double chi = U[CHI * sf + o];
       double det = det3(gt);
       double ichi = 1.0 / chi;
@@ -448,32 +660,25 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
         solve = true;
       }
     }
-    put_x(S + S_X, s, f, F + F_NORM, solve);
-    __syncwarp();
-    fwd_hidden<1>(S + S_X, LDX, S + S_W1, F + F_B, S + S_H1, row0, lane);
-    __syncwarp();
-    fwd_hidden<4>(S + S_H1, LDH, S + S_W2, F + F_B + NH, S + S_H2, row0, lane);
-    __syncwarp();
-    fwd_hidden<4>(S + S_H2, LDH, S + S_W3, F + F_B + 2 * NH, S + S_H1, row0, lane);
-    __syncwarp();
-    fwd_out(S + S_H1, S + S_W4, F + F_B + 3 * NH, F + F_Y, row0, lane);
-    __syncwarp();
+    tc::put_x(smem, s, f, nm, solve);
+    float y[NO];
+    if (!tc::forward(smem, tmem, phase, y)) {
+      if (s == 0) atomicOr(err, 4);
+      break;
+    }
     if (valid) {
       float* sd = PD.seed + o;
       const long long sf = G.sf;
       if (solve) {
-        float t0 = fmaf(F[F_Y + s * 4 + 0], nm[NO + 0], nm[0]);
-        float t1 = fmaf(F[F_Y + s * 4 + 1], nm[NO + 1], nm[1]);
-        float t2 = fmaf(F[F_Y + s * 4 + 2], nm[NO + 2], nm[2]);
-        sd[0] = expf(t0) / (float)sr;
-        sd[sf] = expf(t1) / (float)Q;
-        sd[2 * sf] = expf(t2);
+        sd[0] = expf(fmaf(y[0], tn[NO + 0], tn[0])) / (float)sr;
+        sd[sf] = expf(fmaf(y[1], tn[NO + 1], tn[1])) / (float)Q;
+        sd[2 * sf] = expf(fmaf(y[2], tn[NO + 2], tn[2]));
       } else {
         sd[0] = sd[sf] = sd[2 * sf] = __int_as_float(0x7fc00000);
       }
     }
-    __syncwarp();
   }
+  tc::end(tmem);
 }
 
 // Forward and backward over one tile of the batch [off, off + nb); writes the
@@ -748,6 +953,7 @@ struct grmhd_seeder {
   float* v = nullptr;  // [NPAR] Adam second moment
   float* norm = nullptr;  // [NNORM]
   unsigned long long* ctr = nullptr;  // [2] step, ticket
+  int* err = nullptr;                 // tensor-core wait timed out (inference kernels)
   double* stats = nullptr;            // [STAT_BLOCKS][22]
   float* gpart = nullptr;             // [MAX_TILES][NPAR]
   double* lpart = nullptr;            // [MAX_TILES]
@@ -764,18 +970,30 @@ int set_smem_attrs() {
   if (attr_set) return GRMHD_OK;
   if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true)) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_mlp_patch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(false)) !=
-          cudaSuccess)
+      cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess ||
+      cudaFuncSetAttribute(k_mlp_patch, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
     return GRMHD_ERR_CUDA;
   attr_set = true;
   return GRMHD_OK;
 }
 
 unsigned grid_of(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Resident CTAs per SM of a tensor-core inference kernel, from its registers
+// and shared memory, at most 4 (each CTA holds 64 of the SM's 512 TMEM
+// columns; 4 leaves room for other work).
+int tc_ctas_per_sm(const void* fn, int dev) {
+  cudaFuncAttributes fa;
+  int smem_sm = 0;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+    return 1;
+  int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * TM) : 4;
+  int by_smem = smem_sm / (tc::SMEM + 1024);
+  int n = by_regs < by_smem ? by_regs : by_smem;
+  return n < 1 ? 1 : (n > 4 ? 4 : n);
+}
 
 // Persistent grid of the forward kernels: resident CTAs per SM x SMs, at most
 // one CTA per tile.
@@ -786,10 +1004,9 @@ unsigned fwd_grid(long long n) {
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (!per_dev[dev]) {
-    int sms = 0, per_sm = 0;
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_fwd<MODE>, TM, smem_bytes(false));
-    per_dev[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    per_dev[dev] = (sms > 0 ? sms : 1) * tc_ctas_per_sm((const void*)k_mlp_fwd<MODE>, dev);
   }
   long long tiles = (n + TM - 1) / TM;
   return (unsigned)(tiles < per_dev[dev] ? tiles : per_dev[dev]);
@@ -801,20 +1018,19 @@ int last_rc() { return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_
 
 namespace gk {
 int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd, const Work* w, int nblk, int reg, double rho_min,
-                          cudaStream_t st) {
+                          int* err, cudaStream_t st) {
   if (!s || nblk <= 0) return nblk <= 0 ? GRMHD_OK : GRMHD_ERR_ARG;
   static int per_dev[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (!per_dev[dev]) {
-    int sms = 0, per_sm = 0;
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_patch, TM, smem_bytes(false));
-    per_dev[dev] = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    per_dev[dev] = (sms > 0 ? sms : 1) * tc_ctas_per_sm((const void*)k_mlp_patch, dev);
   }
   int grid = nblk < per_dev[dev] ? nblk : per_dev[dev];
-  k_mlp_patch<<<grid, TM, smem_bytes(false), st>>>(pd, w, nblk, reg, rho_min, s->w, s->norm);
+  k_mlp_patch<<<grid, TM, tc::SMEM, st>>>(pd, w, nblk, reg, rho_min, s->w, s->norm, err);
   return last_rc();
 }
 }  // namespace gk
@@ -828,7 +1044,7 @@ int grmhd_seeder_create(grmhd_seeder** out, unsigned long long seed) {
   grmhd_seeder* s = new grmhd_seeder();
   cudaGetDevice(&s->dev);
   size_t o_w = 0, o_m = align256(o_w + NPAR * 4), o_v = align256(o_m + NPAR * 4), o_n = align256(o_v + NPAR * 4),
-         o_c = align256(o_n + NNORM * 4), o_s = align256(o_c + 16), o_g = align256(o_s + STAT_BLOCKS * 22 * 8),
+         o_c = align256(o_n + NNORM * 4), o_s = align256(o_c + 32), o_g = align256(o_s + STAT_BLOCKS * 22 * 8),
          o_l = align256(o_g + (size_t)MAX_TILES * NPAR * 4), total = align256(o_l + MAX_TILES * 8);
   if (cudaMalloc(&s->block, total) != cudaSuccess) {
     delete s;
@@ -840,6 +1056,7 @@ int grmhd_seeder_create(grmhd_seeder** out, unsigned long long seed) {
   s->v = (float*)(b + o_v);
   s->norm = (float*)(b + o_n);
   s->ctr = (unsigned long long*)(b + o_c);
+  s->err = (int*)(b + o_c + 16);
   s->stats = (double*)(b + o_s);
   s->gpart = (float*)(b + o_g);
   s->lpart = (double*)(b + o_l);
@@ -865,6 +1082,8 @@ int grmhd_seeder_create(grmhd_seeder** out, unsigned long long seed) {
   for (int c = 0; c < NI; ++c) nm[NI + c] = 1.f;
   for (int c = 0; c < NO; ++c) nm[2 * NI + NO + c] = 1.f;
   int rc = grmhd_seeder_set_params(s, h, nm);
+  if (!rc && (cudaMemset(s->err, 0, sizeof(int)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess))
+    rc = GRMHD_ERR_CUDA;
   if (rc) {
     grmhd_seeder_destroy(s);
     return rc;
@@ -914,14 +1133,14 @@ int grmhd_seeder_targets(long long n, const double* cons, const double* roots, f
 int grmhd_seeder_forward(grmhd_seeder* s, long long n, const float* f, float* t_out, void* stream) {
   if (!s || n < 0 || (n > 0 && (!f || !t_out))) return GRMHD_ERR_ARG;
   if (n == 0) return GRMHD_OK;
-  k_mlp_fwd<1><<<fwd_grid<1>(n), TM, smem_bytes(false), (cudaStream_t)stream>>>(n, f, s->w, s->norm, t_out);
+  k_mlp_fwd<1><<<fwd_grid<1>(n), TM, tc::SMEM, (cudaStream_t)stream>>>(n, f, s->w, s->norm, t_out, s->err);
   return last_rc();
 }
 
 int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double* seeds, void* stream) {
   if (!s || n < 0 || (n > 0 && (!cons || !seeds))) return GRMHD_ERR_ARG;
   if (n == 0) return GRMHD_OK;
-  k_mlp_fwd<0><<<fwd_grid<0>(n), TM, smem_bytes(false), (cudaStream_t)stream>>>(n, cons, s->w, s->norm, seeds);
+  k_mlp_fwd<0><<<fwd_grid<0>(n), TM, tc::SMEM, (cudaStream_t)stream>>>(n, cons, s->w, s->norm, seeds, s->err);
   return last_rc();
 }
 
@@ -987,6 +1206,15 @@ int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float
   // The executable graph may be destroyed while its launches are pending.
   cudaGraphExecDestroy(ge);
   return rc;
+}
+
+int grmhd_seeder_status(grmhd_seeder* s) {
+  if (!s) return GRMHD_ERR_ARG;
+  int e = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(s->err, 0, sizeof(int)) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  return e ? GRMHD_ERR_TIMEOUT : GRMHD_OK;
 }
 
 void grmhd_seeder_destroy(grmhd_seeder* s) {
