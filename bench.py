@@ -58,6 +58,8 @@ def _args():
     a.add_argument("--warmup", type=int, default=3)
     a.add_argument("--impl", default="grmhd", choices=["grmhd", "reference"])
     a.add_argument("--no-cpu-baseline", action="store_true")
+    a.add_argument("--no-c2p", action="store_true",
+                   help="skip the con2prim plain-vs-NN-seeded section of the default line")
     a.add_argument("--e2e-steps", type=int, default=3)
     a.add_argument("--workload", default="tov", choices=["tov", "batched", "c2p", "amr"],
                    help="tov: the 128^3 TOV star (default); batched: 256 uneven patches over 5 levels; "
@@ -356,6 +358,22 @@ def run_grmhd(args):
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "kernel_share": {k: v[0] / tot for k, v in prof.items() if v[1]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    if ws == 1 and not args.no_c2p:
+        # The metric's second half: con2prim solves/s, plain vs NN-seeded, on
+        # the isolated workload (2^24 states, tabulated EOS), same GPU.
+        del pt, host_in, host_out
+        torch.cuda.empty_cache()
+        c = _c2p_measure(args, min(args.steps, 5))
+        line["con2prim"] = {
+            "workload": c["config"]["workload"], "unit": "con2prim solves/s",
+            "plain": c["plain"]["solves_per_s"], "nn_seeded": c["seeded"]["solves_per_s"],
+            "speedup_nn_seeded_vs_plain": c["speedup_seeded_vs_plain"], "delta": c["seeded"]["delta"],
+            "evaluations_per_state": {"plain": c["plain"]["evaluations_per_state"],
+                                      "nn_seeded": c["seeded"]["evaluations_per_state"]},
+            "inference_ms": c["seeded"]["inference_ms"], "training_ms": c["training"]["ms"],
+            "same_status": c["seeded_vs_plain"]["same_status"],
+            "max_rel_rho_diff": c["seeded_vs_plain"]["max_rel_rho_diff"], "clocks": c["clocks"]}
+        line["gpu_launches_con2prim"] = c["gpu_launches"]
     if ws == 1 and not args.no_cpu_baseline and edge == N_EDGE:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -466,6 +484,14 @@ def run_c2p(args):
     """con2prim in isolation: 2^24 states, synthetic 256 x 128 x 64 table; the
     seeder trained on 2^20 pairs (seed 13) made on the GPU; plain brackets
     against network seeds (inference included in the seeded time)."""
+    line = _c2p_measure(args, args.steps)
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_c2p()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _c2p_measure(args, K):
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
@@ -564,7 +590,6 @@ def run_c2p(args):
     for _ in range(max(args.warmup, 3)):
         plain()
         seeded()
-    K = args.steps
     clocks = Clocks(0)
     ms_plain = timed(plain, K)
     ms_seeded = timed(seeded, K)
@@ -597,10 +622,7 @@ def run_c2p(args):
                          "loss_first_epoch": float(hist[0]), "loss_last_epoch": float(hist[-1])},
             "seeded_vs_plain": {"same_status": same_status, "max_rel_rho_diff": rel_rho},
             "gpu_launches": 4 * K, "clocks": clk, "setup_s": gen_s}
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_c2p()
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_amr(args):
