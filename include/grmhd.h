@@ -100,7 +100,8 @@ typedef struct grmhd_params {
                                        2 frozen (the initial data's ghost values),
                                        3 mesh-refinement hierarchy (see below)          */
   int max_iter;                     /* Brent iteration cap per root find                */
-  int reserved;
+  int rk;                           /* time integrator (Sec. III A): 0 RK4 (Table RK4),
+                                       1 SSP-RK3 (Table RK3SSP), explicit parts          */
 } grmhd_params;
 
 /* Tabulated EOS: p, eps, c_s^2 on the nodes of a uniform (log10 rho,
@@ -190,20 +191,28 @@ int grmhd_con2prim(grmhd_ctx* ctx, int reg, grmhd_c2p_stats* stats);
  * the patch layout (32 fields); ghost entries are not written. */
 int grmhd_rhs_eval(grmhd_ctx* ctx, int reg, double* const* rhs);
 
-/* RK4 stage combination (unfused), interior points, with k = rhs[p]:
+/* Stage combination (unfused), interior points, with k = rhs[p].  RK4:
  *   stage 0: U[1] = U[0] + dt/2 k, U[3] = U[0] + dt/6 k
  *   stage 1: U[2] = U[0] + dt/2 k, U[3] += dt/3 k
  *   stage 2: U[1] = U[0] + dt k,   U[3] += dt/3 k
- *   stage 3: U[0] = U[3] + dt/6 k */
+ *   stage 3: U[0] = U[3] + dt/6 k
+ * SSP-RK3 (rk = 1):
+ *   stage 0: U[1] = U[0] + dt k, U[2] = U[0] + dt/4 k, U[3] = U[0] + dt/6 k
+ *   stage 1: U[2] += dt/4 k, U[3] += dt/6 k
+ *   stage 2: U[0] = U[3] + 2 dt/3 k */
 int grmhd_rk_update(grmhd_ctx* ctx, int stage, double dt, double* const* rhs);
 
-/* One fused substep `stage` (0..3) of RK4: ghost fill of the stage input
- * (U[0], U[1], U[2], U[1] for stages 0..3), con2prim, right-hand side and the
- * stage combination of grmhd_rk_update, without storing k. */
+/* One fused substep `stage` of the time integrator: ghost fill of the stage
+ * input, con2prim, right-hand side and the stage combination of
+ * grmhd_rk_update, without storing k.  RK4 (rk = 0): stages 0..3, inputs U[0],
+ * U[1], U[2], U[1].  SSP-RK3 (rk = 1): stages 0..2, inputs U[0] (Y1), U[1]
+ * (Y2 = U^n + dt k1), U[2] (Y3 = U^n + dt/4 k1 + dt/4 k2); U[3] accumulates
+ * U^n + dt/6 (k1 + k2) and the last stage writes U^{n+1} = U[3] + 2 dt/3 k3
+ * into U[0]. */
 int grmhd_rhs_substep(grmhd_ctx* ctx, int stage, double dt);
 
-/* One full RK4 step (four fused substeps); with bc = 3, followed by
- * grmhd_restrict(ctx, 0). */
+/* One full step of the time integrator (four fused substeps for RK4, three
+ * for SSP-RK3); with bc = 3, followed by grmhd_restrict(ctx, 0). */
 int grmhd_step(grmhd_ctx* ctx, double dt);
 
 /* Restriction of a hierarchy (bc = 3; a no-op otherwise): every interior

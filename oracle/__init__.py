@@ -18,7 +18,7 @@ NID = 26
 _P_DOUBLES = ["kappa_z", "kappa_c", "kappa_2", "eta", "sigma_ko", "c_b", "kappa_b", "gamma_th", "K_atmo",
               "rho_atmo", "rho_min", "rho_low", "rho_max", "alpha_bh", "W_max", "eps_max", "ye_min", "ye_max",
               "ye_atmo", "T_atmo", "h0", "c2p_xtol"]
-_P_INTS = ["eos_kind", "bc", "max_iter", "pad_"]
+_P_INTS = ["eos_kind", "bc", "max_iter", "rk"]
 
 
 class Params(ctypes.Structure):

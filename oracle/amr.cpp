@@ -179,7 +179,8 @@ int oracle_hier_restrict(int np, const int* meta, const double* dx, double* cons
   return restrict_hier(H, U);
 }
 
-// One RK4 step of the whole hierarchy with time step dt on every level: per
+// One Runge-Kutta step (RK4, or SSP-RK3 when P->rk = 1) of the whole
+// hierarchy with time step dt on every level: per
 // substep the hierarchy ghost fill of the stage's input register, then each
 // patch's con2prim, right-hand side and stage update; finally the restriction
 // of U^{n+1}.  P->bc must be 3 (ghosts are filled here, not per patch).
@@ -189,7 +190,8 @@ int oracle_hier_rk4_step(const oracle_params* P, const oracle_eos_table* E, int 
   if (P->bc != 3) return -3;
   std::vector<hpatch> H = parse(np, meta, dx);
   int worst = 0;
-  for (int s = 0; s < 4; ++s) {
+  const int nsub = P->rk == 1 ? 3 : 4;
+  for (int s = 0; s < nsub; ++s) {
     double* const* in = s == 0 ? U0 : s == 1 ? U1 : s == 2 ? U2 : U1;
     int rc = ghost_fill_hier(P, H, in);
     if (rc) return rc;

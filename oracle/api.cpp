@@ -96,7 +96,8 @@ int oracle_rk4_step(const oracle_params* P, const oracle_eos_table* E, const int
   grid G = make_grid(n, px, dx);
   std::vector<double> k((size_t)NF * G.sf, 0.0);
   int worst = 0;
-  for (int s = 0; s < 4; ++s) {
+  const int nsub = P->rk == 1 ? 3 : 4;
+  for (int s = 0; s < nsub; ++s) {
     int w = substep(P, E, G, s, dt, Un, Ua, Ub, acc, prim, status, k.data(), nullptr);
     if (w < worst) worst = w;
   }

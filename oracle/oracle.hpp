@@ -26,9 +26,9 @@ struct oracle_params {
   double h0;                                        // specific-enthalpy lower bound of the EOS
   double c2p_xtol;                                  // absolute part of the Brent stop rule
   int eos_kind;                                     // 0 ideal gas, 1 table
-  int bc;                                           // 0 periodic, 1 linear extrapolation, 2 frozen
+  int bc;                                           // 0 periodic, 1 linear extrapolation, 2 frozen, 3 hierarchy
   int max_iter;                                     // Brent iteration cap
-  int pad_;
+  int rk;                                           // 0 RK4 (Table RK4), 1 SSP-RK3 (Table RK3SSP)
 };
 
 // Tabulated EOS on nodes of (log10 rho, log10 T[MeV], Ye); rho varies fastest:

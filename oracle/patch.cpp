@@ -267,8 +267,16 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
 // Each stage first fills ghosts and runs con2prim on its input register.
 // counts (optional, counting build): [con2prim, pointwise fluxes, interface
 // fluxes, local right-hand side, RK combination].
+// One Runge-Kutta substep (Sec. III A).  RK4 (Table RK4, explicit part):
+// stage inputs U^n, Ua, Ub, Ua; the stages' outputs U^n + dt/2 k1, U^n + dt/2 k2,
+// U^n + dt k3 and the accumulator acc = U^n + dt (k1/6 + k2/3 + k3/3), then
+// U^{n+1} = acc + dt k4/6.  SSP-RK3 (Table RK3SSP, explicit part; rk = 1):
+// stage inputs Y1 = U^n, Y2 = Ua, Y3 = Ub with Y2 = U^n + dt k1,
+// Y3 = U^n + dt/4 k1 + dt/4 k2, U^{n+1} = U^n + dt (k1/6 + k2/6 + 2 k3/3)
+// (acc collects the first two terms).
 int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, int stage, double dt, double* Un,
             double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs, long long* counts) {
+  const bool rk3 = P->rk == 1;
   double* in = stage == 0 ? Un : stage == 1 ? Ua : stage == 2 ? Ub : Ua;
   double* out = stage == 0 ? Ua : stage == 1 ? Ub : stage == 2 ? Ua : Un;
   ghost_fill(P, G, in, NF);
@@ -294,7 +302,18 @@ int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, in
         for (int i = 0; i < G.n[0]; ++i) {
           long o = (long)f * G.sf + G.at(i, j, k);
           real kk = krhs[o];
-          if (stage == 0) {
+          if (rk3) {
+            if (stage == 0) {
+              Ua[o] = dbl(real(Un[o]) + dt * kk);
+              Ub[o] = dbl(real(Un[o]) + (0.25 * dt) * kk);
+              acc[o] = dbl(real(Un[o]) + sdt * kk);
+            } else if (stage == 1) {
+              Ub[o] = dbl(real(Ub[o]) + (0.25 * dt) * kk);
+              acc[o] = dbl(real(acc[o]) + sdt * kk);
+            } else {
+              Un[o] = dbl(real(acc[o]) + (2.0 * dt / 3.0) * kk);
+            }
+          } else if (stage == 0) {
             out[o] = dbl(real(Un[o]) + hdt * kk);
             acc[o] = dbl(real(Un[o]) + sdt * kk);
           } else if (stage == 1) {

@@ -22,7 +22,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_C2P_FATAL", -4: "ERR_
 _P_DOUBLES = ["kappa_z", "kappa_c", "kappa_2", "eta", "sigma_ko", "c_b", "kappa_b", "gamma_th", "K_atmo",
               "rho_atmo", "rho_min", "rho_low", "rho_max", "alpha_bh", "W_max", "eps_max", "ye_min", "ye_max",
               "ye_atmo", "T_atmo", "h0", "c2p_xtol"]
-_P_INTS = ["eos_kind", "bc", "max_iter", "reserved"]
+_P_INTS = ["eos_kind", "bc", "max_iter", "rk"]
 
 
 class Params(ctypes.Structure):

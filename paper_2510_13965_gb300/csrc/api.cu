@@ -139,6 +139,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     return GRMHD_ERR_ARG;
   if (p->bc < 0 || p->bc > 3) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
+  if (p->rk != 0 && p->rk != 1) return GRMHD_ERR_ARG;
   for (int i = 0; i < npatch; ++i) {
     const grmhd_patch_desc& q = d[i];
     if (q.n[0] < 4 || q.n[1] < 4 || q.n[2] < 4 || q.px < q.n[0] + 6 || !(q.dx > 0.0)) return GRMHD_ERR_ARG;
@@ -434,7 +435,7 @@ int grmhd_rhs_eval(grmhd_ctx* c, int reg, double* const* rhs) {
 
 int grmhd_rk_update(grmhd_ctx* c, int stage, double dt, double* const* rhs) {
   if (!c) return GRMHD_ERR_ARG;
-  if (stage < 0 || stage > 3 || !rhs) return fail(c, GRMHD_ERR_ARG, "rk_update: args");
+  if (stage < 0 || stage > (c->P.rk == 1 ? 2 : 3) || !rhs) return fail(c, GRMHD_ERR_ARG, "rk_update: args");
   int rc;
   if ((rc = cuda_ok(c, cudaMemcpyAsync(c->rhs_ptrs, rhs, c->np * sizeof(double*), cudaMemcpyHostToDevice, c->st),
                     "rhs ptrs")) ||
@@ -442,18 +443,20 @@ int grmhd_rk_update(grmhd_ctx* c, int stage, double dt, double* const* rhs) {
     return rc;
   {
     ProfScope ps(c, K_RK);
-    launch_rk(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), stage, dt, c->rhs_ptrs, c->st);
+    launch_rk(c->pd, wl(c, DOM_INT), nblk(c, DOM_INT), stage, dt, c->rhs_ptrs, c->st, c->P.rk);
   }
   c->launches += 1;
   return check_launch(c, "rk");
 }
 
-static const int kStageIn[4] = {0, 1, 2, 1};
+static const int kStageIn[4] = {0, 1, 2, 1};    // RK4
+static const int kStageInRk3[3] = {0, 1, 2};    // SSP-RK3
 
 int grmhd_rhs_substep(grmhd_ctx* c, int stage, double dt) {
   if (!c) return GRMHD_ERR_ARG;
-  if (stage < 0 || stage > 3) return fail(c, GRMHD_ERR_ARG, "rhs_substep: stage");
-  int reg = kStageIn[stage];
+  const bool rk3 = c->P.rk == 1;
+  if (stage < 0 || stage > (rk3 ? 2 : 3)) return fail(c, GRMHD_ERR_ARG, "rhs_substep: stage");
+  int reg = rk3 ? kStageInRk3[stage] : kStageIn[stage];
   int rc;
   if ((rc = grmhd_ghost_fill(c, reg))) return rc;
   if ((rc = c2p_and_fluxes(c, reg, false))) return rc;
@@ -481,7 +484,8 @@ int grmhd_restrict(grmhd_ctx* c, int reg) {
 
 int grmhd_step(grmhd_ctx* c, double dt) {
   if (!c) return GRMHD_ERR_ARG;
-  for (int s = 0; s < 4; ++s) {
+  const int nsub = c->P.rk == 1 ? 3 : 4;
+  for (int s = 0; s < nsub; ++s) {
     int rc = grmhd_rhs_substep(c, s, dt);
     if (rc) return rc;
   }

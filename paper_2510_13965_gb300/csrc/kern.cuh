@@ -99,7 +99,7 @@ void launch_rhs(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int mo
                 const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs = 128);
 void launch_ghost_copy(const PatchDev* pd_dev, const Work* w, int nblk, int reg, cudaStream_t st);
 void launch_rk(const PatchDev* pd_dev, const Work* w, int nblk, int stage, double dt, double* const* rhs_dev,
-               cudaStream_t st);
+               cudaStream_t st, int rk = 0);
 void launch_c2p_flat(const grmhd_params& P, const Eos& E, long long n, const double* cons, double* prim,
                      int8_t* status, int32_t* iters, cudaStream_t st);
 void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, const double* prim, const double* B,

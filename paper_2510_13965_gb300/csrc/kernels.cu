@@ -394,7 +394,7 @@ void launch_ghost_copy(const PatchDev* pd, const Work* w, int nblk, int reg, cud
 // ---------------------------------------------------------------------------
 // Unfused RK4 stage combination at interior points.
 __global__ void k_rk(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int stage, double dt,
-                     double* const* __restrict__ rhs) {
+                     double* const* __restrict__ rhs, int rk) {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
@@ -405,6 +405,24 @@ __global__ void k_rk(const PatchDev* __restrict__ pd, const Work* __restrict__ w
   const long long o = at(G, i, j, k), sf = G.sf;
   const double* K = rhs[wk.patch];
   double *Un = PD.U[0], *Ua = PD.U[1], *Ub = PD.U[2], *acc = PD.U[3];
+  if (rk == 1) {  // SSP-RK3
+    for (int f = 0; f < NF; ++f) {
+      long long x = f * sf + o;
+      double kk = K[x];
+      if (stage == 0) {
+        double u = Un[x];
+        Ua[x] = fma(dt, kk, u);
+        Ub[x] = fma(0.25 * dt, kk, u);
+        acc[x] = fma(dt / 6.0, kk, u);
+      } else if (stage == 1) {
+        Ub[x] = fma(0.25 * dt, kk, Ub[x]);
+        acc[x] = fma(dt / 6.0, kk, acc[x]);
+      } else {
+        Un[x] = fma(2.0 * dt / 3.0, kk, acc[x]);
+      }
+    }
+    return;
+  }
   for (int f = 0; f < NF; ++f) {
     long long x = f * sf + o;
     double kk = K[x];
@@ -424,9 +442,10 @@ __global__ void k_rk(const PatchDev* __restrict__ pd, const Work* __restrict__ w
   }
 }
 
-void launch_rk(const PatchDev* pd, const Work* w, int nblk, int stage, double dt, double* const* rhs, cudaStream_t st) {
+void launch_rk(const PatchDev* pd, const Work* w, int nblk, int stage, double dt, double* const* rhs, cudaStream_t st,
+               int rk) {
   if (nblk <= 0) return;
-  k_rk<<<nblk, BS_INT, 0, st>>>(pd, w, stage, dt, rhs);
+  k_rk<<<nblk, BS_INT, 0, st>>>(pd, w, stage, dt, rhs, rk);
 }
 
 // ---------------------------------------------------------------------------

@@ -402,6 +402,29 @@ __global__ void __launch_bounds__(BS) k_rhs(const PatchDev* __restrict__ pd, con
     double* out = rhs_out[wk.patch] + o;
 #pragma unroll
     for (int f = 0; f < NF; ++f) out[f * sf] = r[f];
+  } else if (P.rk == 1) {
+    // SSP-RK3 (Table RK3SSP): Y2 = U^n + dt k1 into U[1], Y3 = U^n + dt/4 k1 +
+    // dt/4 k2 built in U[2], U[3] = U^n + dt/6 (k1 + k2), U^{n+1} = U[3] + 2 dt/3 k3.
+    double* Un = PD.U[0] + o;
+    double* Y2 = PD.U[1] + o;
+    double* Y3 = PD.U[2] + o;
+    double* acc = PD.U[3] + o;
+    const double q = 0.25 * dt, s6 = dt / 6.0, t23 = 2.0 * dt / 3.0;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      long long x = f * sf;
+      if (stage == 0) {
+        double u = Un[x];
+        Y2[x] = fma(dt, r[f], u);
+        Y3[x] = fma(q, r[f], u);
+        acc[x] = fma(s6, r[f], u);
+      } else if (stage == 1) {
+        Y3[x] = fma(q, r[f], Y3[x]);
+        acc[x] = fma(s6, r[f], acc[x]);
+      } else {
+        Un[x] = fma(t23, r[f], acc[x]);
+      }
+    }
   } else {
     double* Un = PD.U[0] + o;
     double* acc = PD.U[3] + o;

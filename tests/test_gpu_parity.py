@@ -384,3 +384,42 @@ def test_autotune_keeps_results_bitwise():
     b.synchronize()
     for p_ in range(len(specs)):
         assert torch.equal(a.U[p_][0], b.U[p_][0])
+
+
+def test_ssp_rk3_steps_parity_fourier():
+    """SSP-RK3 (Table RK3SSP) through the fused substeps: three steps against the oracle."""
+    n, dx = (16, 16, 16), 1 / 16
+    P = synth.ideal_params(bc=0, rk=1)
+    ID = synth.config0_id(n=n, seed=2)
+    pt, O, U = _setup(P, n, dx, ID)
+    _upload(pt, U)
+    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    prim = np.zeros((NP,) + U.shape[1:])
+    st = np.zeros(U.shape[1:], dtype=np.int8)
+    dt = 0.3 * dx
+    for _ in range(3):
+        pt.step(dt)
+        O.rk4_step(regs, prim, st, n, dx, dt)
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    err = _field_err(_interior(pt.U[0][0].cpu().numpy(), n), _interior(regs[0], n))
+    assert np.all(err < 1e-10), err
+
+
+def test_ssp_rk3_unfused_matches_fused():
+    P, n, dx = synth.ideal_params(bc=0, rk=1), (12, 12, 12), 1 / 12
+    ID = synth.config0_id(n=n, seed=4)
+    a = g.Patches(P, [dict(n=n, dx=dx)])
+    b = g.Patches(P, [dict(n=n, dx=dx)])
+    for pt in (a, b):
+        pt.init_state(0, torch.as_tensor(ID, device="cuda"))
+    dt = 0.3 * dx
+    a.step(dt)
+    for s, reg in enumerate((0, 1, 2)):
+        b.ghost_fill(reg)
+        b.con2prim(reg)
+        k = b.rhs_eval(reg)
+        b.rk_update(s, dt, k)
+    a.synchronize()
+    b.synchronize()
+    assert np.array_equal(_interior(a.U[0][0].cpu().numpy(), n), _interior(b.U[0][0].cpu().numpy(), n))

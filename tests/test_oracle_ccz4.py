@@ -224,3 +224,29 @@ def test_rk4_step_is_fourth_order_taylor_polynomial():
     got = U[19:22, 3:-3, 3:-3, 3:-3]
     want = np.array([0.1, -0.2, 0.3])[:, None, None, None] * fac
     assert np.allclose(got, want, rtol=2e-15, atol=0)
+
+
+def test_ssp_rk3_step_is_third_order_taylor_polynomial():
+    # Same linear decay d_t beta = -eta beta: one SSP-RK3 step (Table RK3SSP)
+    # multiplies beta by 1 - z + z^2/2 - z^3/6, z = eta dt.
+    P = synth.ideal_params(bc=0, eta=1.4, rk=1)
+    O = oracle.Oracle(P)
+    n = (6, 6, 6)
+    shp = synth.patch_shape(n)
+    ID = np.zeros((26,) + shp)
+    ID[0] = ID[3] = ID[5] = 1.0
+    ID[12] = 1.0
+    ID[13], ID[14], ID[15] = 0.1, -0.2, 0.3
+    ID[16] = 1e-12
+    ID[24] = 0.1
+    U = O.init_state(ID, n, 0.1)
+    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+    prim = np.zeros((NP,) + shp)
+    st = np.zeros(shp, dtype=np.int8)
+    dt = 0.05
+    O.rk4_step(regs, prim, st, n, 0.1, dt)
+    zz = P["eta"] * dt
+    fac = 1 - zz + zz ** 2 / 2 - zz ** 3 / 6
+    got = U[19:22, 3:-3, 3:-3, 3:-3]
+    want = np.array([0.1, -0.2, 0.3])[:, None, None, None] * fac
+    assert np.allclose(got, want, rtol=2e-15, atol=0)
