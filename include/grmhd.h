@@ -95,13 +95,28 @@ typedef struct grmhd_params {
   double T_atmo;                    /* tabulated EOS: atmosphere temperature [MeV]      */
   double h0;                        /* lower bound of the specific enthalpy of the EOS  */
   double c2p_xtol;                  /* absolute part of the Brent stop rule             */
-  int eos_kind;                     /* 0 ideal gas, 1 table                             */
+  int eos_kind;                     /* 0 ideal gas, 1 table, 2 hybrid (below)           */
   int bc;                           /* ghosts: 0 periodic, 1 linear extrapolation,
                                        2 frozen (the initial data's ghost values),
                                        3 mesh-refinement hierarchy (see below)          */
   int max_iter;                     /* Brent iteration cap per root find                */
   int rk;                           /* time integrator (Sec. III A): 0 RK4 (Table RK4),
                                        1 SSP-RK3 (Table RK3SSP), explicit parts          */
+  /* Hybrid EOS (eos_kind 2; Sec. II B, piecewise-polytropic cold part plus a
+   * thermal ideal gas):
+   *   p = p_cold(rho) + (gamma_th - 1) rho (eps - eps_cold(rho)),
+   *   p_cold = K_i rho^Gamma_i,  eps_cold = a_i + K_i rho^(Gamma_i - 1) / (Gamma_i - 1)
+   * on piece i (rho_poly[i-1] < rho <= rho_poly[i]), K_0 = K_poly, a_0 = 0,
+   * K_i and a_i fixed by continuity of p_cold and eps_cold at rho_poly.
+   * eps is clamped to [eps_cold(rho), eps_max]; T is reported as 0; initial
+   * data give eps (as for the ideal gas).  Requires 1 <= npoly <= 4,
+   * gamma_poly[i] > 1, K_poly > 0, rho_poly[0..npoly-2] > 0 increasing;
+   * unused entries are ignored. */
+  int npoly;
+  int reserved2;
+  double K_poly;
+  double rho_poly[3];
+  double gamma_poly[4];
 } grmhd_params;
 
 /* Tabulated EOS: p, eps, c_s^2 on the nodes of a uniform (log10 rho,

@@ -22,7 +22,9 @@ _P_INTS = ["eos_kind", "bc", "max_iter", "rk"]
 
 
 class Params(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS]
+    _fields_ = ([(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS] +
+                [("npoly", ctypes.c_int), ("pad2_", ctypes.c_int), ("K_poly", ctypes.c_double),
+                 ("rho_poly", ctypes.c_double * 3), ("gamma_poly", ctypes.c_double * 4)])
 
 
 class EosTable(ctypes.Structure):
@@ -38,6 +40,12 @@ def make_params(d):
         setattr(p, n, float(d.get(n, 0.0)))
     for n in _P_INTS:
         setattr(p, n, int(d.get(n, 0)))
+    p.npoly = int(d.get("npoly", 0))
+    p.K_poly = float(d.get("K_poly", 0.0))
+    for i, v in enumerate(d.get("rho_poly", ())):
+        p.rho_poly[i] = float(v)
+    for i, v in enumerate(d.get("gamma_poly", ())):
+        p.gamma_poly[i] = float(v)
     return p
 
 

@@ -5,6 +5,13 @@
 // (the ideal-EOS sound speed quoted with the fast magnetosonic bound,
 // Appendix "Characteristic speeds").
 //
+// Hybrid (eos_kind 2, Sec. II B): p = p_cold(rho) + p_th, eps = eps_cold(rho) +
+// eps_th, p_th = (Gamma_th - 1) rho eps_th; the cold part a piecewise
+// polytrope p_cold = K_i rho^Gamma_i, eps_cold = a_i + K_i rho^(Gamma_i - 1) /
+// (Gamma_i - 1) on rho_{i-1} <= rho <= rho_i, with K_0 given, a_0 = 0 and the
+// other K_i, a_i from continuity of p_cold and eps_cold (eq.
+// piecewise_p_eps_cold).  eps >= eps_cold(rho) (no negative thermal energy).
+//
 // Table: p, eps, c_s^2 given at the nodes of a (log10 rho, log10 T, Ye) grid
 // and interpolated trilinearly (the tabulated finite-temperature EOS of
 // Sec. II B).  T(rho, eps, Ye) is inverted exactly: at fixed (rho, Ye) the
@@ -50,14 +57,53 @@ static tab_loc tab_locate(const oracle_eos_table* E, real rho, real ye) {
   return L;
 }
 
+// Piecewise-polytrope constants K_i, a_i from continuity at the dividing
+// densities, and the cold part at rho.
+struct cold_state {
+  real p, eps, gamma;
+};
+static cold_state hybrid_cold(const oracle_params* P, real rho) {
+  double K[4], a[4];
+  K[0] = P->K_poly;
+  a[0] = 0.0;
+  for (int i = 1; i < P->npoly; ++i) {
+    double rb = P->rho_poly[i - 1], g0 = P->gamma_poly[i - 1], g1 = P->gamma_poly[i];
+    K[i] = K[i - 1] * std::pow(rb, g0 - g1);
+    a[i] = a[i - 1] + K[i - 1] / (g0 - 1.0) * std::pow(rb, g0 - 1.0) - K[i] / (g1 - 1.0) * std::pow(rb, g1 - 1.0);
+  }
+  int i = 0;
+  while (i < P->npoly - 1 && rho > P->rho_poly[i]) ++i;
+  double g = P->gamma_poly[i];
+  cold_state c;
+  c.gamma = g;
+  c.p = K[i] * pow(rho, g);
+  c.eps = a[i] + K[i] / (g - 1.0) * pow(rho, g - 1.0);
+  return c;
+}
+
+static eos_state hybrid_from_eps(const oracle_params* P, real rho, real eps) {
+  cold_state c = hybrid_cold(P, rho);
+  real gth = P->gamma_th - 1.0;
+  eos_state s;
+  s.eps = eps;
+  s.p = c.p + gth * rho * (eps - c.eps);
+  s.T = 0.0;
+  // c_s^2 h = dp/drho|_eps + p / rho^2 dp/deps|_rho, with d eps_cold / d rho = p_cold / rho^2.
+  real dpdrho = c.gamma * c.p / rho + gth * (eps - c.eps) - gth * c.p / rho;
+  real h = 1.0 + eps + s.p / rho;
+  s.cs2 = (dpdrho + gth * s.p / rho) / h;
+  return s;
+}
+
 real eos_eps_min(const oracle_params* P, const oracle_eos_table* E, real rho, real ye) {
   if (P->eos_kind == 0) return 0.0;
+  if (P->eos_kind == 2) return hybrid_cold(P, rho).eps;
   tab_loc L = tab_locate(E, rho, ye);
   return bilin(E, E->eps, L.ir, L.wr, 0, L.iy, L.wy);
 }
 
 real eos_eps_max(const oracle_params* P, const oracle_eos_table* E, real rho, real ye) {
-  if (P->eos_kind == 0) return P->eps_max;
+  if (P->eos_kind == 0 || P->eos_kind == 2) return P->eps_max;
   tab_loc L = tab_locate(E, rho, ye);
   return bilin(E, E->eps, L.ir, L.wr, E->nt - 1, L.iy, L.wy);
 }
@@ -73,6 +119,7 @@ static eos_state ideal_from_eps(const oracle_params* P, real rho, real eps) {
 
 eos_state eos_from_eps(const oracle_params* P, const oracle_eos_table* E, real rho, real eps, real ye) {
   if (P->eos_kind == 0) return ideal_from_eps(P, rho, eps);
+  if (P->eos_kind == 2) return hybrid_from_eps(P, rho, eps);
   tab_loc L = tab_locate(E, rho, ye);
   // Binary search for the T interval whose node values bracket eps.
   int lo = 0, hi = E->nt - 1;
@@ -118,6 +165,7 @@ eos_state eos_from_T(const oracle_params* P, const oracle_eos_table* E, real rho
     real p = P->K_atmo * pow(rho, P->gamma_th);
     return ideal_from_eps(P, rho, p / ((P->gamma_th - 1.0) * rho));
   }
+  if (P->eos_kind == 2) return hybrid_from_eps(P, rho, hybrid_cold(P, rho).eps);  // cold: no temperature
   tab_loc L = tab_locate(E, rho, ye);
   int it;
   real wt;

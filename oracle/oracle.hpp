@@ -29,6 +29,14 @@ struct oracle_params {
   int bc;                                           // 0 periodic, 1 linear extrapolation, 2 frozen, 3 hierarchy
   int max_iter;                                     // Brent iteration cap
   int rk;                                           // 0 RK4 (Table RK4), 1 SSP-RK3 (Table RK3SSP)
+  // Hybrid EOS (eos_kind 2, Sec. II B): piecewise-polytropic cold part with
+  // npoly pieces, K_0 = K_poly, exponents gamma_poly[i], dividing densities
+  // rho_poly[i] between pieces i and i + 1; thermal part (gamma_th - 1) rho eps_th.
+  int npoly;
+  int pad2_;
+  double K_poly;
+  double rho_poly[3];
+  double gamma_poly[4];
 };
 
 // Tabulated EOS on nodes of (log10 rho, log10 T[MeV], Ye); rho varies fastest:

@@ -105,6 +105,8 @@ void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G
         if (P->eos_kind == 0) {
           s.eps = id(I_EPS);
           s.p = (P->gamma_th - 1.0) * rho * s.eps;
+        } else if (P->eos_kind == 2) {
+          s = eos_from_eps(P, E, rho, id(I_EPS), ye);
         } else {
           s = eos_from_T(P, E, rho, id(I_T), ye);
         }

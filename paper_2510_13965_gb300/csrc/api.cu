@@ -134,9 +134,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   if (!out) return GRMHD_ERR_ARG;
   *out = nullptr;
   if (!p || !d || npatch <= 0) return GRMHD_ERR_ARG;
-  if (p->eos_kind != 0 && p->eos_kind != 1) return GRMHD_ERR_ARG;
-  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2 || eos->nr < 2 || eos->nt < 2 || eos->ny < 2))
-    return GRMHD_ERR_ARG;
+  if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
   if (p->bc < 0 || p->bc > 3) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (p->rk != 0 && p->rk != 1) return GRMHD_ERR_ARG;
@@ -626,7 +624,7 @@ int grmhd_sync_status(grmhd_ctx* c) {
 int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* prim,
                         const double* B, double* cons, void* stream) {
   if (!p || n < 0 || (n > 0 && (!prim || !B || !cons))) return GRMHD_ERR_ARG;
-  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2)) return GRMHD_ERR_ARG;
+  if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
   launch_prim2con_flat(*p, make_eos(*p, eos), n, prim, B, cons, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }
@@ -634,7 +632,7 @@ int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long 
 int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons, double* prim,
                    int8_t* status, int32_t* iters, void* stream) {
   if (!p || n < 0 || (n > 0 && (!cons || !prim || !status))) return GRMHD_ERR_ARG;
-  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2)) return GRMHD_ERR_ARG;
+  if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   launch_c2p_flat(*p, make_eos(*p, eos), n, cons, prim, status, iters, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;

@@ -14,6 +14,9 @@ namespace gk {
 struct Eos {
   int kind;
   double gam, K, eps_max;
+  // hybrid: cold pieces (K_i, a_i, Gamma_i), dividing densities
+  int npoly;
+  double hK[4], ha[4], hg[4], hr[3];
   // table
   int nr, nt, ny;
   double lr0, idlr, lt0, dlt, idlt, ye0, idye;
@@ -61,12 +64,39 @@ DI double tab_bl(const TabPos& t, const double* A, int it) {
   return fma(t.wy, hi - lo, lo);
 }
 
+// Hybrid EOS cold part on the piece holding rho: p_cold, eps_cold, Gamma_i.
+struct HybCold {
+  double p, eps, g;
+};
+DI HybCold hyb_cold(const Eos& E, double rho) {
+  int i = 0;
+  while (i < E.npoly - 1 && rho > E.hr[i]) ++i;
+  HybCold c;
+  c.g = E.hg[i];
+  const double rg1 = pow(rho, c.g - 1.0);
+  c.p = E.hK[i] * rg1 * rho;
+  c.eps = fma(E.hK[i] / (c.g - 1.0), rg1, E.ha[i]);
+  return c;
+}
+// Hybrid (p, cs2) at eps: p = p_c + (Gamma_th - 1) rho (eps - eps_c);
+// c_s^2 h = dp/drho|_eps + p / rho^2 dp/deps|_rho with deps_c/drho = p_c / rho^2.
+DI void hyb_eps(const Eos& E, const HybCold& c, double rho, double eps, double* p, double* cs2) {
+  const double gth = E.gam - 1.0, de = eps - c.eps;
+  *p = fma(gth * rho, de, c.p);
+  if (cs2) {
+    const double ir = 1.0 / rho;
+    const double dpdr = fma(gth, de, (c.g - gth) * c.p * ir);
+    *cs2 = fma(gth * ir, *p, dpdr) / (1.0 + eps + *p * ir);
+  }
+}
+
 DI double eos_emin(const Eos& E, double rho, double ye) {
   if (E.kind == 0) return 0.0;
+  if (E.kind == 2) return hyb_cold(E, rho).eps;
   return tab_bl(tab_pos(E, rho, ye), E.e, 0);
 }
 DI double eos_emax(const Eos& E, double rho, double ye) {
-  if (E.kind == 0) return E.eps_max;
+  if (E.kind != 1) return E.eps_max;
   return tab_bl(tab_pos(E, rho, ye), E.e, E.nt - 1);
 }
 
@@ -78,6 +108,11 @@ DI EosOut eos_eps(const Eos& E, double rho, double eps, double ye) {
     o.p = (E.gam - 1.0) * rho * eps;
     o.T = 0.0;
     o.cs2 = E.gam * o.p / fma(rho, 1.0 + eps, o.p);
+    return o;
+  }
+  if (E.kind == 2) {
+    hyb_eps(E, hyb_cold(E, rho), rho, eps, &o.p, &o.cs2);
+    o.T = 0.0;
     return o;
   }
   TabPos t = tab_pos(E, rho, ye);
@@ -130,6 +165,16 @@ DI EosClamp eos_clamped(const Eos& E, double rho, double eps_raw, double ye, int
     o.p = (E.gam - 1.0) * rho * o.eps;
     o.T = 0.0;
     o.cs2 = FULL ? E.gam * o.p / fma(rho, 1.0 + o.eps, o.p) : 0.0;
+    return o;
+  }
+  if (E.kind == 2) {
+    const HybCold c = hyb_cold(E, rho);
+    o.emin = c.eps;
+    o.emax = E.eps_max;
+    o.eps = fmax(fmin(o.emax, eps_raw), o.emin);
+    o.T = 0.0;
+    o.cs2 = 0.0;
+    hyb_eps(E, c, rho, o.eps, &o.p, FULL ? &o.cs2 : nullptr);
     return o;
   }
   TabPos t = tab_pos(E, rho, ye);
@@ -186,9 +231,17 @@ DI EosClamp eos_clamped(const Eos& E, double rho, double eps_raw, double ye, int
   return o;
 }
 
-// (p, eps, cs2) from (rho, T, ye) (table), or the cold polytrope (ideal gas).
+// (p, eps, cs2) from (rho, T, ye) (table), the cold polytrope (ideal gas), or
+// the cold part (hybrid).
 DI EosOut eos_T(const Eos& E, double rho, double T, double ye) {
   EosOut o;
+  if (E.kind == 2) {
+    const HybCold c = hyb_cold(E, rho);
+    o.eps = c.eps;
+    o.T = 0.0;
+    hyb_eps(E, c, rho, c.eps, &o.p, &o.cs2);
+    return o;
+  }
   if (E.kind == 0) {
     o.p = E.K * pow(rho, E.gam);
     o.eps = o.p / ((E.gam - 1.0) * rho);

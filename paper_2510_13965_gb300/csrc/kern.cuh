@@ -84,6 +84,9 @@ struct DevFlags {
 };
 
 Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T);
+// GRMHD_OK when the EOS kind and its parameters (table pointers and sizes,
+// hybrid pieces) are usable, else GRMHD_ERR_ARG.
+int eos_check(const grmhd_params& P, const grmhd_eos_table* T);
 
 // Launchers (host functions in the .cu files; all enqueue on `st`).
 void launch_init(const PatchDev* pd, int p, const Geo& G, const grmhd_params& P, const Eos& E, const double* id,

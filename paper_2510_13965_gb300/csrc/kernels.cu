@@ -2,6 +2,7 @@
 // ghost fill, con2prim with the point-wise MHD fluxes and speeds, interface
 // fluxes (Lax-Friedrichs split + MP5), the unfused RK4 stage combination and
 // the flat-metric con2prim of independent states.
+#include <cmath>
 #include "kern.cuh"
 
 namespace gk {
@@ -15,6 +16,24 @@ Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T) {
   E.nr = E.nt = E.ny = 0;
   E.lr0 = E.idlr = E.lt0 = E.dlt = E.idlt = E.ye0 = E.idye = 0.0;
   E.p = E.e = E.c = nullptr;
+  E.npoly = 0;
+  for (int i = 0; i < 4; ++i) E.hK[i] = E.ha[i] = E.hg[i] = 0.0;
+  for (int i = 0; i < 3; ++i) E.hr[i] = 0.0;
+  if (P.eos_kind == 2) {
+    // Piece constants of the hybrid EOS's cold part (Sec. II B): K_0 given,
+    // a_0 = 0; p_cold and eps_cold continuous at each dividing density.
+    E.npoly = P.npoly;
+    E.hK[0] = P.K_poly;
+    E.hg[0] = P.gamma_poly[0];
+    for (int i = 1; i < P.npoly; ++i) {
+      const double rb = P.rho_poly[i - 1], g0 = P.gamma_poly[i - 1], g1 = P.gamma_poly[i];
+      E.hg[i] = g1;
+      E.hK[i] = E.hK[i - 1] * std::pow(rb, g0 - g1);
+      E.ha[i] = E.ha[i - 1] + E.hK[i - 1] / (g0 - 1.0) * std::pow(rb, g0 - 1.0) -
+                E.hK[i] / (g1 - 1.0) * std::pow(rb, g1 - 1.0);
+      E.hr[i - 1] = rb;
+    }
+  }
   if (T && P.eos_kind == 1) {
     E.nr = T->nr;
     E.nt = T->nt;
@@ -31,6 +50,18 @@ Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T) {
     E.c = T->cs2;
   }
   return E;
+}
+
+int eos_check(const grmhd_params& P, const grmhd_eos_table* T) {
+  if (P.eos_kind == 0) return GRMHD_OK;
+  if (P.eos_kind == 1)
+    return (T && T->p && T->eps && T->cs2 && T->nr >= 2 && T->nt >= 2 && T->ny >= 2) ? GRMHD_OK : GRMHD_ERR_ARG;
+  if (P.eos_kind != 2 || P.npoly < 1 || P.npoly > 4 || !(P.K_poly > 0.0)) return GRMHD_ERR_ARG;
+  for (int i = 0; i < P.npoly; ++i)
+    if (!(P.gamma_poly[i] > 1.0)) return GRMHD_ERR_ARG;
+  for (int i = 0; i + 1 < P.npoly; ++i)
+    if (!(P.rho_poly[i] > 0.0) || (i > 0 && !(P.rho_poly[i] > P.rho_poly[i - 1]))) return GRMHD_ERR_ARG;
+  return GRMHD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -65,6 +96,9 @@ __global__ void k_init(Geo G, grmhd_params P, Eos E, const double* __restrict__ 
   if (P.eos_kind == 0) {
     eps = id[IEPS * sf + o];
     p = (P.gamma_th - 1.0) * rho * eps;
+  } else if (P.eos_kind == 2) {
+    eps = id[IEPS * sf + o];
+    p = eos_eps(E, rho, eps, ye).p;
   } else {
     EosOut eo = eos_T(E, rho, id[IT * sf + o], ye);
     eps = eo.eps;
@@ -476,6 +510,9 @@ __global__ void k_prim2con_flat(grmhd_params P, Eos E, long long n, const double
     EosOut eo = eos_T(E, rho, pr[TT], ye);
     eps = eo.eps;
     p = eo.p;
+  } else if (P.eos_kind == 2) {
+    eps = pr[EPS];
+    p = eos_eps(E, rho, eps, ye).p;
   } else {
     eps = pr[EPS];
     p = (P.gamma_th - 1.0) * rho * eps;

@@ -60,9 +60,7 @@ using namespace gk;
 extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_desc* d, const grmhd_eos_table* eos,
                                      int reg, double* rhs, void* stream) {
   if (!p || !d || !rhs || reg < 0 || reg > 3) return GRMHD_ERR_ARG;
-  if (p->eos_kind != 0 && p->eos_kind != 1) return GRMHD_ERR_ARG;
-  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2 || eos->nr < 2 || eos->nt < 2 || eos->ny < 2))
-    return GRMHD_ERR_ARG;
+  if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
   if (p->bc != 0 && p->bc != 1) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (d->n[0] < 4 || d->n[1] < 4 || d->n[2] < 4 || d->px < d->n[0] + 6 || !(d->dx > 0.0)) return GRMHD_ERR_ARG;

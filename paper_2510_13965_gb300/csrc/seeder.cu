@@ -1229,7 +1229,7 @@ int grmhd_c2p_flat_seeded(const grmhd_params* p, const grmhd_eos_table* eos, lon
                           const double* seeds, double delta, double* prim, int8_t* status, int32_t* iters,
                           double* roots, int8_t* seeded, void* stream) {
   if (!p || n < 0 || (n > 0 && (!cons || !prim || !status))) return GRMHD_ERR_ARG;
-  if (p->eos_kind == 1 && (!eos || !eos->p || !eos->eps || !eos->cs2)) return GRMHD_ERR_ARG;
+  if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (seeds && !(delta > 0.0 && delta < 1.0)) return GRMHD_ERR_ARG;
   if (n == 0) return GRMHD_OK;

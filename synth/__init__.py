@@ -16,7 +16,7 @@ holding, at every point including the three ghost layers per side:
 """
 import numpy as np
 
-from .configs import (NID, NG, ideal_params, table_params, grid_coords, patch_shape)  # noqa: F401
+from .configs import (NID, NG, ideal_params, table_params, hybrid_params, grid_coords, patch_shape)  # noqa: F401
 from .fields import config0_id, tov_id, tov_profile, batched_specs, batched_id, EDGES  # noqa: F401
 from .eos_table import make_table  # noqa: F401
 from .states import c2p_states  # noqa: F401

@@ -71,3 +71,16 @@ def grid_coords(n, x0, dx, pad=1):
     y = ax[1][None, :, None]
     z = ax[2][:, None, None]
     return z, y, x
+
+
+def hybrid_params(bc=0, **over):
+    """Hybrid-EOS parameters (eos_kind 2): a synthetic three-piece cold
+    polytrope (K_0 = 100, Gamma = 2, 2.3, 2.6 with pieces divided at rho =
+    5e-4 and 1.1e-3, so a 1.28e-3 star centre lies in the stiffest piece) plus a
+    Gamma_th = 1.8 thermal part; causal (c_s^2 < 1) up to rho ~ 4e-3 at
+    eps = 1.5 eps_cold.  Not a fit to any nuclear EOS."""
+    p = ideal_params(bc=bc)
+    p.update(eos_kind=2, gamma_th=1.8, npoly=3, K_poly=100.0, rho_poly=(5e-4, 1.1e-3, 0.0),
+             gamma_poly=(2.0, 2.3, 2.6, 0.0), eps_max=1e6, h0=1.0)
+    p.update(over)
+    return p

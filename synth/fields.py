@@ -234,10 +234,13 @@ def _table_temperature(rho, p, ye, table, iters=48):
 
 
 def tov_id(n=(128, 128, 128), x0=(-20.0, -20.0, -20.0), dx=0.3125, seed=1, perturb=True, bfield=True,
-           pad=1, rho_atmo=1e-10, profile=None, ye=0.1, table=None):
+           pad=1, rho_atmo=1e-10, profile=None, ye=0.1, table=None, heat=1.0):
     """Static TOV star on a vertex-centred patch (ghosts included).  With a
     synthetic table, the temperature (field 25) is set so the table model's
-    pressure equals the polytropic one (eps then follows from the table)."""
+    pressure equals the polytropic one (eps then follows from the table).
+    heat > 1 scales the specific internal energy of the polytrope (a heated
+    star: for EOS models whose cold part is stiffer than the polytrope's the
+    data then stay above their cold energy)."""
     n = tuple(int(v) for v in n)
     prof = profile if profile is not None else tov_profile()
     K, Gamma, M, Rb = prof["K"], prof["Gamma"], prof["M"], prof["Rb"]
@@ -259,7 +262,7 @@ def tov_id(n=(128, 128, 128), x0=(-20.0, -20.0, -20.0), dx=0.3125, seed=1, pertu
         rng = np.random.default_rng(np.random.PCG64(seed))
         xi = rng.uniform(-1.0, 1.0, size=shp)
         p = np.where(rho > 100.0 * rho_atmo, p * (1.0 + 0.01 * xi), p)
-    eps = p / ((Gamma - 1.0) * rho)
+    eps = heat * p / ((Gamma - 1.0) * rho)
     ID = np.zeros((NID,) + shp)
     if table is not None:
         ID[25] = _table_temperature(rho, p, ye, table)

@@ -69,6 +69,9 @@ CASES = {
                                        synth.config0_id(n=(20, 12, 17), seed=5)),
     "tov_40": lambda: (synth.ideal_params(bc=1), (40, 40, 40), 0.5,
                        synth.tov_id(n=(40, 40, 40), x0=(-10, -10, -10), dx=0.5, seed=1)),
+    # Hybrid EOS (three cold pieces, all crossed by the star's density range).
+    "tov_40_hybrid": lambda: (synth.hybrid_params(bc=1), (40, 40, 40), 0.5,
+                              synth.tov_id(n=(40, 40, 40), x0=(-10, -10, -10), dx=0.5, seed=1, heat=1.5)),
 }
 
 
@@ -179,10 +182,10 @@ def test_graph_replay_equals_eager_and_is_deterministic():
     assert np.array_equal(ua, uc)
 
 
-def _tov_runs(perturb, bfield, nsteps, checkpoints, oracle_twin=False):
+def _tov_runs(perturb, bfield, nsteps, checkpoints, oracle_twin=False, P=None, heat=1.0):
     n, dx = (24, 24, 24), 0.8
-    P = synth.ideal_params(bc=1)
-    ID = synth.tov_id(n=n, x0=(-9.6, -9.6, -9.6), dx=dx, seed=1, perturb=perturb, bfield=bfield)
+    P = synth.ideal_params(bc=1) if P is None else P
+    ID = synth.tov_id(n=n, x0=(-9.6, -9.6, -9.6), dx=dx, seed=1, perturb=perturb, bfield=bfield, heat=heat)
     pt, O, U = _setup(P, n, dx, ID)
     _upload(pt, U)
     runs = [U.copy()]
@@ -215,6 +218,12 @@ def test_tov_100_steps_parity(perturb):
     """Coarse 24^3 TOV star without field, 100 RK4 steps through a CUDA graph: <= 1e-9 per field."""
     out = _tov_runs(perturb, False, 100, (100,))
     assert out[100][0] < 1e-9, out
+
+
+def test_tov_hybrid_eos_steps_parity():
+    """Heated 24^3 TOV star with the three-piece hybrid EOS, 50 RK4 steps: <= 1e-9 per field."""
+    out = _tov_runs(True, False, 50, (50,), P=synth.hybrid_params(bc=1), heat=1.5)
+    assert out[50][0] < 1e-9, out
 
 
 @pytest.mark.parametrize("perturb", [False, True])
@@ -261,10 +270,20 @@ def test_full_size_tov_sampled_points():
     assert ok, bad
 
 
-@pytest.mark.parametrize("kind", ["ideal", "table"])
+@pytest.mark.parametrize("kind", ["ideal", "table", "hybrid"])
 def test_c2p_flat_parity(kind):
     N = 1 << 14
-    if kind == "ideal":
+    if kind == "hybrid":
+        table = None
+        P = synth.hybrid_params()
+        s = synth.c2p_states(N, seed=4, rho=(1e-10, 2e-3))
+        prim = np.zeros((N, NP))
+        prim[:, 0], prim[:, 7] = s["rho"], s["ye"]
+        prim[:, 3:6] = s["v"]
+        # Thermal part from the sample's temperature: eps = eps_cold (1 + T / 10).
+        prim[:, 1] = 1.0 + s["T"] / 10.0
+        B = s["B"]
+    elif kind == "ideal":
         table = None
         P = synth.ideal_params()
         rng = np.random.default_rng(9)
@@ -292,6 +311,9 @@ def test_c2p_flat_parity(kind):
         if kind == "table":
             e = O.eos_from_T(pr[0], pr[8], pr[7])
             pr[1], pr[2] = e[1], e[0]
+        elif kind == "hybrid":
+            pr[1] *= O.eos_from_T(pr[0], 0.0, pr[7])[1]
+            pr[2] = O.eos_from_eps(pr[0], pr[1], pr[7])[0]
         else:
             pr[2] = pr[0] * pr[1]
         cons[q, :9] = oracle.prim2con_point(pr, B[q], [1.0, 0, 0, 1.0, 0, 1.0])
