@@ -93,6 +93,10 @@ def lib(flops=False):
             "oracle_hier_ghost_fill": (i, [vp, i, vp, vp, vp]),
             "oracle_hier_restrict": (i, [i, vp, vp, vp]),
             "oracle_hier_rk4_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
+            "oracle_hier_rk4_step_mask": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp, i]),
+            "oracle_hier_subcycle_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
+            "oracle_dense_derivs": (None, [i, vp, vp]),
+            "oracle_bor_coeffs": (None, [i, i, i, i, vp]),
             "oracle_seeder_targets": (i, [l, vp, vp, vp]),
             "oracle_prim2con_point": (i, [vp, vp, vp, vp]),
             "oracle_eos_from_eps": (i, [vp, vp, d, d, d, vp]),
@@ -343,6 +347,23 @@ def seeder_targets(cons, roots):
     return t
 
 
+def dense_derivs(rk, k):
+    """(D_1, D_2, D_3, J): D_m = dt^m d^m U/dt^m at t^n from one step's k_j = dt f
+    (dense output, Sec. III A), J = 4 (k3 - k2) ~ dt^3 f_U U'' (RK4; 0 for SSP-RK3)."""
+    kk = np.zeros(4)
+    kk[:len(k)] = k
+    D = np.zeros(4)
+    lib().oracle_dense_derivs(int(rk), _p(kk), _p(D))
+    return D
+
+
+def bor_coeffs(rk, msub, R, s):
+    """Coefficients of (U^n, D_1, D_2, D_3, J) in the BOR stage value of stage s of fine step msub of R."""
+    c = np.zeros(5)
+    lib().oracle_bor_coeffs(int(rk), int(msub), int(R), int(s), _p(c))
+    return c
+
+
 def mp5(f5):
     f = np.ascontiguousarray(f5, dtype=np.float64)
     return lib().oracle_mp5(_p(f))
@@ -386,8 +407,17 @@ class Hierarchy:
     def restrict(self, reg=0):
         return self.O.L.oracle_hier_restrict(len(self.specs), _p(self.meta), _p(self.dx), self._ptrs(self.U[reg]))
 
-    def rk4_step(self, dt):
-        return self.O.L.oracle_hier_rk4_step(_ref(self.O.P), self.O.Tp, len(self.specs), _p(self.meta), _p(self.dx),
-                                            dt, self._ptrs(self.U[0]), self._ptrs(self.U[1]),
-                                            self._ptrs(self.U[2]), self._ptrs(self.U[3]), self._ptrs(self.prim),
-                                            self._ptrs(self.status))
+    def subcycle_step(self, dt0):
+        """One level-0 step of dt0 with sub-cycling (level l: 2^l steps of dt0 / 2^l)."""
+        return self.O.L.oracle_hier_subcycle_step(_ref(self.O.P), self.O.Tp, len(self.specs), _p(self.meta),
+                                                 _p(self.dx), dt0, self._ptrs(self.U[0]), self._ptrs(self.U[1]),
+                                                 self._ptrs(self.U[2]), self._ptrs(self.U[3]),
+                                                 self._ptrs(self.prim), self._ptrs(self.status))
+
+    def rk4_step(self, dt, rmask=-1):
+        """One step of dt on every level; afterwards level l >= 1 is restricted
+        into l - 1 when bit l of rmask is set (default: all levels)."""
+        return self.O.L.oracle_hier_rk4_step_mask(_ref(self.O.P), self.O.Tp, len(self.specs), _p(self.meta),
+                                                 _p(self.dx), dt, self._ptrs(self.U[0]), self._ptrs(self.U[1]),
+                                                 self._ptrs(self.U[2]), self._ptrs(self.U[3]), self._ptrs(self.prim),
+                                                 self._ptrs(self.status), int(rmask))

@@ -20,4 +20,4 @@ from .configs import (NID, NG, ideal_params, table_params, hybrid_params, grid_c
 from .fields import config0_id, tov_id, tov_profile, batched_specs, batched_id, EDGES  # noqa: F401
 from .eos_table import make_table  # noqa: F401
 from .states import c2p_states  # noqa: F401
-from .hierarchy import small_hierarchy, nested_cubes, amr_tov_layout  # noqa: F401
+from .hierarchy import small_hierarchy, nested_cubes, amr_tov_layout, subcycle_hierarchy  # noqa: F401

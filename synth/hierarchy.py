@@ -75,3 +75,18 @@ def amr_tov_layout(scale=1.0, levels=5, seed=4):
         start = centre - size // 2
         fine.append((l, start, size, (64,) if l == levels - 1 else (24, 32, 48)))
     return nested_cubes(n0, dx0, X0, fine, seed=seed)
+
+
+def subcycle_hierarchy(dx0=1.0 / 24, X0=(0.0, 0.0, 0.0), n0=24):
+    """Three properly nested levels for sub-cycling: a 24^3 level-0 patch,
+    level 1 a 24^3 cube (level-1 points 12..35) in four uneven patches, level 2
+    a 16^3 cube (level-2 points 32..47) in two patches.  Every fine ghost
+    point's prolongation stencil lies inside the interiors of the next coarser
+    level (or the level-0 patch's ghosts)."""
+    out = [spec((n0, n0, n0), 0, (0, 0, 0), dx0, X0)]
+    for (ox, ex) in ((0, 16), (16, 8)):
+        for (oy, ey) in ((0, 8), (8, 16)):
+            out.append(spec((ex, ey, 24), 1, (12 + ox, 12 + oy, 12), dx0, X0))
+    for (ox, ex) in ((0, 8), (8, 8)):
+        out.append(spec((ex, 16, 16), 2, (32 + ox, 32, 32), dx0, X0))
+    return out
