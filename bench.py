@@ -73,6 +73,8 @@ def _args():
     a.add_argument("--amr-seeded", action="store_true",
                    help="also time the hierarchy with NN-seeded con2prim")
     a.add_argument("--amr-delta", type=float, default=3e-2)
+    a.add_argument("--amr-subcycle", action="store_true",
+                   help="amr workload: also time sub-cycled steps (BOR) over the same physical time")
     a.add_argument("--edge", type=int, default=N_EDGE,
                    help="interior points per axis (the same [-20,20]^3 star; 128 is the benchmark workload)")
     return a.parse_args()
@@ -722,6 +724,43 @@ def run_amr(args):
         levels.setdefault(s_["level"], [0, 0])
         levels[s_["level"]][0] += 1
         levels[s_["level"]][1] += int(np.prod(s_["n"]))
+    subcycled = None
+    if args.amr_subcycle:
+        # Sub-cycling (Sec. III D, BOR): level l steps dt0 / 2^l with
+        # dt0 = 2^L dt, so every level keeps the synchronous run's Courant
+        # factor on its own grid; one bench step = one level-0 step, the same
+        # physical time as 2^L synchronous steps.
+        if seeded is not None:
+            pt.set_seeder(None)  # the plain con2prim of the synchronous timing
+        nlev = max(levels) + 1
+        dt0 = dt * 2 ** (nlev - 1)
+        pt.set_subcycling(True)
+        pt.step(dt0)
+        pt.capture_graph(1, dt0)
+        l0 = pt.launch_count()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            pt.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1) / args.steps
+        lc = pt.launch_count() - l0
+        pt.profile(True)
+        pt.step(dt0)
+        pt.synchronize()
+        prof_c = pt.profile_read()
+        pt.profile(False)
+        updates = sum(v[1] * 2 ** k for k, v in levels.items())
+        sync_time_rate = dt / (ms / 1e3)
+        subcycled = {"unit": "simulated time per second (code units)",
+                     "value": dt0 / (ms_c / 1e3), "synchronous": sync_time_rate,
+                     "speedup_vs_synchronous": (dt0 / (ms_c / 1e3)) / sync_time_rate,
+                     "ms_per_level0_step": ms_c, "dt0": dt0,
+                     "zone_updates_per_s": updates / (ms_c / 1e3), "zone_updates_per_level0_step": updates,
+                     "kernel_ms_per_step": {k: v[0] for k, v in prof_c.items() if v[1]},
+                     "gpu_launches": int(lc), "status": pt.sync_status()}
+        pt.set_subcycling(False)
     line = {"metric": METRIC, "value": zones / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -736,6 +775,8 @@ def run_amr(args):
             "gpu_launches": int(launches), "status": rc, "clocks": clk, "setup_s": setup_s}
     if seeded is not None:
         line["nn_seeded"] = seeded
+    if subcycled is not None:
+        line["subcycled"] = subcycled
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_amr()
     print(json.dumps(line), flush=True)

@@ -227,8 +227,32 @@ int grmhd_rk_update(grmhd_ctx* ctx, int stage, double dt, double* const* rhs);
 int grmhd_rhs_substep(grmhd_ctx* ctx, int stage, double dt);
 
 /* One full step of the time integrator (four fused substeps for RK4, three
- * for SSP-RK3); with bc = 3, followed by grmhd_restrict(ctx, 0). */
+ * for SSP-RK3); with bc = 3, followed by grmhd_restrict(ctx, 0).  With
+ * sub-cycling on (grmhd_set_subcycling), dt is the level-0 step and one call
+ * advances level l by 2^l steps of dt / 2^l (see below). */
 int grmhd_step(grmhd_ctx* ctx, double dt);
+
+/* Sub-cycling in time on a hierarchy (bc = 3; Sec. III D, "Sub-cycling in
+ * time", the BOR scheme, with the dense output of Sec. III A).  With on != 0,
+ * grmhd_step(ctx, dt0) advances level l recursively: one step of
+ * dt_l = dt0 / 2^l of level l, then two steps of level l + 1 and the
+ * restriction of level l + 1 into level l.  During a step of level l >= 1 its
+ * ghost points are copied from same-level interiors of the same stage, or
+ * prolongated (six-point Lagrange, as for bc = 3) from the parent's stage value
+ *   Y = c_0 U^n + c_1 D_1 + c_2 D_2 + c_3 D_3 + c_4 J
+ * formed at each coarse stencil point: D_m = dt^m d^m U/dt^m at the parent's
+ * t^n from the derivatives of the dense output b_j(theta) (RK4: third-order
+ * interpolator; SSP-RK3: second-order), J = 4 (k3 - k2) = dt^3 f_U U'' +
+ * O(dt^4) (RK4 only), and c the fine RK stages expanded in the Taylor data of
+ * the interpolant at the start of the fine step, keeping RK4's third-order
+ * f_U U'' terms.  The first call allocates five (RK4) or three (SSP-RK3)
+ * dense registers per patch on the levels that have a finer level and
+ * synchronises.  Returns GRMHD_ERR_ARG (message in grmhd_last_error) when
+ * bc != 3 or when a prolongation stencil of a level >= 2 leaves the interiors
+ * of the next coarser level (the dense output exists only there); on = 0
+ * returns to synchronous steps.  A graph captured while on replays sub-cycled
+ * steps. */
+int grmhd_set_subcycling(grmhd_ctx* ctx, int on);
 
 /* Restriction of a hierarchy (bc = 3; a no-op otherwise): every interior
  * point of a level-l patch at even level-l coordinates g overwrites, for all
@@ -237,7 +261,7 @@ int grmhd_step(grmhd_ctx* ctx, double dt);
  * first. */
 int grmhd_restrict(grmhd_ctx* ctx, int reg);
 
-/* Captures nsteps RK4 steps into a CUDA graph owned by the context
+/* Captures nsteps grmhd_step calls into a CUDA graph owned by the context
  * (replacing a previous one); grmhd_graph_launch replays it on the stream. */
 int grmhd_capture_graph(grmhd_ctx* ctx, int nsteps, double dt);
 int grmhd_graph_launch(grmhd_ctx* ctx);
@@ -266,7 +290,8 @@ int grmhd_autotune(grmhd_ctx* ctx, double dt, int reps, int* chosen);
  * grmhd_profile_read synchronises the stream, writes the summed milliseconds
  * and launch counts per kernel kind (0 ghost fill, 1 con2prim + pointwise
  * fluxes, 2 interface fluxes, 3 right-hand side + RK epilogue, 4 unfused RK
- * update, 5 initial data, 6 seeder inference) into ms[0..nkinds) and
+ * update, 5 initial data, 6 seeder inference, 7 sub-cycling dense-output
+ * record and its ghosts) into ms[0..nkinds) and
  * count[0..nkinds), and
  * discards the records. */
 int grmhd_profile(grmhd_ctx* ctx, int on);

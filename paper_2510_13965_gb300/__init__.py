@@ -73,6 +73,7 @@ _SIGS = {
     "grmhd_rhs_substep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "grmhd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
     "grmhd_restrict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_set_subcycling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "grmhd_set_seeder": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     "grmhd_capture_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "grmhd_graph_launch": (ctypes.c_int, [ctypes.c_void_p]),
@@ -298,6 +299,12 @@ class Patches:
         self._enter()
         _check(self.L.grmhd_restrict(self.ctx, reg), self.ctx, "grmhd_restrict")
 
+    def set_subcycling(self, on=True):
+        """Sub-cycling in time on a hierarchy (bc 3): step(dt0) then advances
+        level l by 2^l steps of dt0 / 2^l (BOR ghosts from the dense output)."""
+        self._enter()
+        _check(self.L.grmhd_set_subcycling(self.ctx, 1 if on else 0), self.ctx, "grmhd_set_subcycling")
+
     def step(self, dt):
         self._enter()
         _check(self.L.grmhd_step(self.ctx, float(dt)), self.ctx, "grmhd_step")
@@ -313,7 +320,7 @@ class Patches:
     def sync_status(self):
         return self.L.grmhd_sync_status(self.ctx)
 
-    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init", "seed")
+    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init", "seed", "dense")
 
     def set_block_sizes(self, bs_c2p, bs_iflux, bs_rhs):
         _check(self.L.grmhd_set_block_sizes(self.ctx, bs_c2p, bs_iflux, bs_rhs), self.ctx, "grmhd_set_block_sizes")

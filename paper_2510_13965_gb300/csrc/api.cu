@@ -15,9 +15,10 @@ struct grmhd_ctx {
   std::vector<grmhd_patch_desc> desc;
   std::vector<PatchDev> pd_host;
   PatchDev* pd = nullptr;
-  // work lists per block size and domain, concatenated
+  // work lists per group, block size and domain, concatenated; group 0 holds
+  // every patch, group 1 + l the level-l patches of a hierarchy (bc 3)
   Work* work = nullptr;
-  int wofs[NBS][NDOM + 1];
+  std::vector<std::array<std::array<int, NDOM + 1>, NBS>> wofs;
   int bs_c2p = 128, bs_if = 128, bs_rhs = 128;  // chosen block sizes
   double* scratch = nullptr;
   DevFlags* flags = nullptr;
@@ -33,7 +34,14 @@ struct grmhd_ctx {
   double seed_delta = 0.0;
   float* seed_buf = nullptr;
   int amr_level0 = -1, amr_nlev = 0;
-  std::vector<long long> amr_gofs, amr_gcnt, amr_rofs, amr_rcnt;
+  std::vector<long long> amr_gofs, amr_gcnt, amr_rofs, amr_rcnt, amr_gsame;
+  // per level: coarse points its prolongation stencils read (sub-cycling)
+  AmrPoint* amr_tp = nullptr;
+  std::vector<long long> amr_tofs, amr_tcnt;
+  std::string amr_sub_err;
+  // sub-cycling in time (grmhd_set_subcycling): dense-output registers
+  bool subcycle = false;
+  double* dense_buf = nullptr;
   long long launches = 0;
   long long graph_kernels = 0;
   std::string err;
@@ -47,7 +55,7 @@ struct grmhd_ctx {
   std::vector<cudaEvent_t> pool;
 };
 
-enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, K_SEED = 6, NKIND = 7 };
+enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, K_SEED = 6, K_DENSE = 7, NKIND = 8 };
 
 static cudaEvent_t ev_get(grmhd_ctx* c) {
   if (!c->pool.empty()) {
@@ -120,6 +128,8 @@ void grmhd_destroy(grmhd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   cudaFree(c->pd);
   cudaFree(c->work);
+  cudaFree(c->dense_buf);
+  cudaFree(c->amr_tp);
   cudaFree(c->scratch);
   cudaFree(c->flags);
   cudaFree(c->stats);
@@ -188,20 +198,34 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     q.Fh = q.lam + 3 * q.G.sf;
     q.seed = nullptr;
   }
-  // work lists: for each block size and domain, the blocks of patch 0, then patch 1, ...
-  std::vector<Work> wl;
-  for (int b = 0; b < NBS; ++b) {
-    int bs = BS_CAND[b];
-    for (int dom = 0; dom < NDOM; ++dom) {
-      c->wofs[b][dom] = (int)wl.size();
-      for (int i = 0; i < npatch; ++i) {
-        long long n = dom_count(dom, c->pd_host[i].G);
-        long long nb = (n + bs - 1) / bs;
-        for (long long k = 0; k < nb; ++k) wl.push_back(Work{i, (int)k});
-      }
+  // work lists: for each group, block size and domain, the blocks of patch
+  // 0, then patch 1, ... (group 0: every patch; group 1 + l: level l)
+  int ngrp = 1;
+  if (p->bc == 3) {
+    int maxl = 0;
+    bool ok = true;
+    for (int i = 0; i < npatch; ++i) {
+      ok = ok && d[i].level >= 0 && d[i].level <= 20;
+      if (d[i].level > maxl) maxl = d[i].level;
     }
-    c->wofs[b][NDOM] = (int)wl.size();
+    if (ok) ngrp = 2 + maxl;  // otherwise the hierarchy plan below rejects the layout
   }
+  c->wofs.assign(ngrp, {});
+  std::vector<Work> wl;
+  for (int g = 0; g < ngrp; ++g)
+    for (int b = 0; b < NBS; ++b) {
+      int bs = BS_CAND[b];
+      for (int dom = 0; dom < NDOM; ++dom) {
+        c->wofs[g][b][dom] = (int)wl.size();
+        for (int i = 0; i < npatch; ++i) {
+          if (g > 0 && d[i].level != g - 1) continue;
+          long long n = dom_count(dom, c->pd_host[i].G);
+          long long nb = (n + bs - 1) / bs;
+          for (long long k = 0; k < nb; ++k) wl.push_back(Work{i, (int)k});
+        }
+      }
+      c->wofs[g][b][NDOM] = (int)wl.size();
+    }
   if ((rc = cuda_ok(c, cudaMalloc(&c->work, wl.size() * sizeof(Work)), "cudaMalloc work")) ||
       (rc = cuda_ok(c, cudaMalloc(&c->pd, npatch * sizeof(PatchDev)), "cudaMalloc pd")) ||
       (rc = cuda_ok(c, cudaMalloc(&c->flags, sizeof(DevFlags)), "cudaMalloc flags")) ||
@@ -221,6 +245,8 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     }
     c->amr_level0 = plan.level0;
     c->amr_nlev = plan.nlev;
+    c->amr_gsame = plan.nsame;
+    c->amr_sub_err = plan.sub_err;
     std::vector<AmrTask> all;
     c->amr_gofs.assign(plan.nlev, 0);
     c->amr_gcnt.assign(plan.nlev, 0);
@@ -235,6 +261,25 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
       c->amr_rofs[l] = (long long)all.size();
       c->amr_rcnt[l] = (long long)plan.restr[l].size();
       all.insert(all.end(), plan.restr[l].begin(), plan.restr[l].end());
+    }
+    std::vector<AmrPoint> tp;
+    c->amr_tofs.assign(plan.nlev, 0);
+    c->amr_tcnt.assign(plan.nlev, 0);
+    for (int l = 1; l < plan.nlev; ++l) {
+      c->amr_tofs[l] = (long long)tp.size();
+      c->amr_tcnt[l] = (long long)plan.tpts[l].size();
+      tp.insert(tp.end(), plan.tpts[l].begin(), plan.tpts[l].end());
+    }
+    if (!tp.empty()) {
+      if ((rc = cuda_ok(c, cudaMalloc(&c->amr_tp, tp.size() * sizeof(AmrPoint)), "cudaMalloc amr points"))) {
+        grmhd_destroy(c);
+        return GRMHD_ERR_NOMEM;
+      }
+      if ((rc = cuda_ok(c, cudaMemcpy(c->amr_tp, tp.data(), tp.size() * sizeof(AmrPoint), cudaMemcpyHostToDevice),
+                        "copy amr points"))) {
+        grmhd_destroy(c);
+        return rc;
+      }
     }
     if (!all.empty()) {
       if ((rc = cuda_ok(c, cudaMalloc(&c->amr, all.size() * sizeof(AmrTask)), "cudaMalloc amr tasks"))) {
@@ -261,11 +306,13 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   return GRMHD_OK;
 }
 
-static int nblk(grmhd_ctx* c, int dom, int bs = 128) {
+static int nblk(grmhd_ctx* c, int dom, int bs = 128, int grp = 0) {
   int b = bs_index(bs);
-  return c->wofs[b][dom + 1] - c->wofs[b][dom];
+  return c->wofs[grp][b][dom + 1] - c->wofs[grp][b][dom];
 }
-static const Work* wl(grmhd_ctx* c, int dom, int bs = 128) { return c->work + c->wofs[bs_index(bs)][dom]; }
+static const Work* wl(grmhd_ctx* c, int dom, int bs = 128, int grp = 0) {
+  return c->work + c->wofs[grp][bs_index(bs)][dom];
+}
 
 // The contiguous slice of a ghost-line work list (block size 128) that belongs
 // to one patch: work items are grouped by patch in increasing order.
@@ -341,16 +388,16 @@ int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
   return check_launch(c, "ghost");
 }
 
-static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats) {
+static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats, int grp = 0) {
   if (c->seeder) {
     ProfScope ps(c, K_SEED);
-    int rc = launch_seeder_patches(c->seeder, c->pd, wl(c, DOM_ALL), nblk(c, DOM_ALL), reg, c->P.rho_min,
-                                   &c->flags->flags, c->st);
+    int rc = launch_seeder_patches(c->seeder, c->pd, wl(c, DOM_ALL, 128, grp), nblk(c, DOM_ALL, 128, grp), reg,
+                                   c->P.rho_min, &c->flags->flags, c->st);
     c->launches += 1;
     if (rc) return fail(c, rc, "seeder launch");
   }
   ProfScope ps(c, K_C2P);
-  launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p), nblk(c, DOM_ALL, c->bs_c2p), reg, c->P, c->E, c->flags,
+  launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p, grp), nblk(c, DOM_ALL, c->bs_c2p, grp), reg, c->P, c->E, c->flags,
              stats ? c->stats : nullptr, c->st, c->bs_c2p, c->seeder != nullptr, c->seed_delta);
   c->launches += 1;
   return check_launch(c, "con2prim");
@@ -383,10 +430,11 @@ int grmhd_set_seeder(grmhd_ctx* c, const grmhd_seeder* s, double delta) {
   return GRMHD_OK;
 }
 
-static int iflux(grmhd_ctx* c, int reg) {
+static int iflux(grmhd_ctx* c, int reg, int grp = 0) {
   for (int d = 0; d < 3; ++d) {
     ProfScope ps(c, K_IFLUX);
-    launch_iflux(c->pd, wl(c, DOM_IFX + d, c->bs_if), nblk(c, DOM_IFX + d, c->bs_if), reg, d, c->st, c->bs_if);
+    launch_iflux(c->pd, wl(c, DOM_IFX + d, c->bs_if, grp), nblk(c, DOM_IFX + d, c->bs_if, grp), reg, d, c->st,
+                 c->bs_if);
     c->launches += 1;
   }
   return check_launch(c, "iflux");
@@ -480,8 +528,148 @@ int grmhd_restrict(grmhd_ctx* c, int reg) {
   return check_launch(c, "restrict");
 }
 
+// Coefficients of (U^n, D_1, D_2, D_3, J) in the BOR stage value (Sec. III D,
+// sub-cycling; Sec. III A, dense output) of stage s of fine step msub (0, 1)
+// of a coarse step, refinement ratio 2.  With the Taylor data of the
+// dense-output cubic at t0 = t^n + msub dt/2 and h = dt/2,
+//   P_0 = sum_m th^m/m! D_m, P_1 = (D_1 + th D_2 + th^2/2 D_3)/2,
+//   P_2 = (D_2 + th D_3)/4, P_3 = D_3/8, P_J = J/8  (th = msub/2),
+// the fine stages are Y = sum_i w_i P_i + w_J P_J with, for RK4,
+//   w = (1), (1, 1/2), (1, 1/2, 1/4, 1/16; w_J -1/16), (1, 1, 1/2, 1/8; w_J 1/8),
+// and for SSP-RK3 (1), (1, 1), (1, 1/2, 1/4).
+static void bor_coef(int rk, int msub, int s, double c[NDENSE]) {
+  const double th = 0.5 * msub;
+  const double P[4][4] = {{1.0, th, 0.5 * th * th, th * th * th / 6.0},
+                          {0.0, 0.5, 0.5 * th, 0.25 * th * th},
+                          {0.0, 0.0, 0.25, 0.25 * th},
+                          {0.0, 0.0, 0.0, 0.125}};
+  double w[4] = {1.0, 0.0, 0.0, 0.0}, wj = 0.0;
+  if (rk == 1) {
+    if (s == 1) w[1] = 1.0;
+    if (s == 2) w[1] = 0.5, w[2] = 0.25;
+  } else if (s == 1) {
+    w[1] = 0.5;
+  } else if (s == 2) {
+    w[1] = 0.5, w[2] = 0.25, w[3] = 1.0 / 16.0, wj = -1.0 / 16.0;
+  } else if (s == 3) {
+    w[1] = 1.0, w[2] = 0.5, w[3] = 0.125, wj = 0.125;
+  }
+  for (int m = 0; m < 4; ++m) {
+    double v = 0.0;
+    for (int i = 0; i < 4; ++i) v += w[i] * P[i][m];
+    c[m] = v;
+  }
+  c[4] = wj * 0.125;
+}
+
+// Outer-boundary extrapolation of register reg of the level-0 patch.
+static void ghost_level0(grmhd_ctx* c, int reg) {
+  for (int ax = 0; ax < 3; ++ax) {
+    int first, cnt;
+    patch_range(c, DOM_GX + ax, c->amr_level0, &first, &cnt);
+    launch_ghost(c->pd, wl(c, DOM_GX + ax) + first, cnt, reg, ax, 1, c->st);
+    c->launches += 1;
+  }
+}
+
+// One step of dt of level l (fine step msub of its parent's step), then two
+// steps of level l + 1 and its restriction into level l (Sec. III D, BOR).
+static int sub_advance(grmhd_ctx* c, int l, int msub, double dt) {
+  const bool rk3 = c->P.rk == 1;
+  const int ns = rk3 ? 3 : 4, nd = rk3 ? 3 : NDENSE, grp = 1 + l;
+  const bool parent = l + 1 < c->amr_nlev;
+  int rc;
+  for (int s = 0; s < ns; ++s) {
+    const int reg = rk3 ? kStageInRk3[s] : kStageIn[s];
+    {
+      ProfScope ps(c, K_GHOST);
+      if (l == 0) {
+        ghost_level0(c, reg);
+      } else {
+        // The parent's stage value at the coarse points the stencils read,
+        // into the parent's accumulator register (free between its steps),
+        // then the ghost fill from it.
+        double cf[NDENSE];
+        bor_coef(c->P.rk, msub, s, cf);
+        launch_amr_time(c->pd, c->amr_tp + c->amr_tofs[l], c->amr_tcnt[l], cf, nd, 3, c->st);
+        launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st, 3);
+        c->launches += 2;
+      }
+    }
+    if ((rc = check_launch(c, "sub-cycled ghost fill"))) return rc;
+    if ((rc = c2p_and_fluxes(c, reg, false, grp))) return rc;
+    if ((rc = iflux(c, reg, grp))) return rc;
+    {
+      ProfScope ps(c, K_RHS);
+      launch_rhs(c->pd, wl(c, DOM_INT, c->bs_rhs, grp), nblk(c, DOM_INT, c->bs_rhs, grp), reg, 1, s, dt, c->P,
+                 nullptr, c->st, c->bs_rhs);
+      c->launches += 1;
+    }
+    if (parent) {
+      ProfScope ps(c, K_DENSE);
+      launch_dense_rec(c->pd, wl(c, DOM_INT, 128, grp), nblk(c, DOM_INT, 128, grp), s, c->P.rk, c->st);
+      c->launches += 1;
+    }
+    if ((rc = check_launch(c, "sub-cycled substep"))) return rc;
+  }
+  if (!parent) return GRMHD_OK;
+  // Ghosts of the dense registers: extrapolated on level 0, same-level
+  // copies on finer levels (the prolongation stencils need no others).
+  for (int e = 0; e < nd; ++e) {
+    ProfScope ps(c, K_DENSE);
+    if (l == 0) {
+      ghost_level0(c, REG_DENSE + e);
+    } else {
+      launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gsame[l], REG_DENSE + e, c->st);
+      c->launches += 1;
+    }
+  }
+  for (int m = 0; m < 2; ++m)
+    if ((rc = sub_advance(c, l + 1, m, 0.5 * dt))) return rc;
+  {
+    ProfScope ps(c, K_GHOST);
+    launch_amr(c->pd, c->amr + c->amr_rofs[l + 1], c->amr_rcnt[l + 1], 0, c->st);
+    c->launches += 1;
+  }
+  return check_launch(c, "restrict");
+}
+
+int grmhd_set_subcycling(grmhd_ctx* c, int on) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (!on) {
+    c->subcycle = false;
+    return GRMHD_OK;
+  }
+  if (c->P.bc != 3) return fail(c, GRMHD_ERR_ARG, "set_subcycling: needs a mesh-refinement hierarchy (bc 3)");
+  if (!c->amr_sub_err.empty()) return fail(c, GRMHD_ERR_ARG, "set_subcycling: " + c->amr_sub_err);
+  if (!c->dense_buf && c->amr_nlev > 1) {
+    const int nd = c->P.rk == 1 ? 3 : NDENSE;
+    size_t total = 0;
+    for (int i = 0; i < c->np; ++i)
+      if (c->desc[i].level + 1 < c->amr_nlev) total += (size_t)nd * NF * c->pd_host[i].G.sf;
+    int rc;
+    if ((rc = cuda_ok(c, cudaMalloc(&c->dense_buf, total * sizeof(double)), "cudaMalloc dense registers")))
+      return GRMHD_ERR_NOMEM;
+    size_t o = 0;
+    for (int i = 0; i < c->np; ++i) {
+      if (c->desc[i].level + 1 >= c->amr_nlev) continue;
+      for (int e = 0; e < nd; ++e) {
+        c->pd_host[i].U[REG_DENSE + e] = c->dense_buf + o;
+        o += (size_t)NF * c->pd_host[i].G.sf;
+      }
+    }
+    if ((rc = cuda_ok(c, cudaMemcpyAsync(c->pd, c->pd_host.data(), c->np * sizeof(PatchDev), cudaMemcpyHostToDevice,
+                                         c->st), "copy pd")) ||
+        (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")))
+      return rc;
+  }
+  c->subcycle = true;
+  return GRMHD_OK;
+}
+
 int grmhd_step(grmhd_ctx* c, double dt) {
   if (!c) return GRMHD_ERR_ARG;
+  if (c->subcycle) return sub_advance(c, 0, 0, dt);
   const int nsub = c->P.rk == 1 ? 3 : 4;
   for (int s = 0; s < nsub; ++s) {
     int rc = grmhd_rhs_substep(c, s, dt);

@@ -9,9 +9,14 @@
 
 namespace gk {
 
+// Registers 0..3: RK registers (U^n, two stage values, accumulator).
+// Registers 4..8 (levels with a finer level, under sub-cycling): the dense
+// output of the level's last step, U^n, D_1, D_2, D_3, J; otherwise null.
+constexpr int REG_DENSE = 4;
+constexpr int NDENSE = 5;
 struct PatchDev {
   Geo G;
-  double* U[4];
+  double* U[REG_DENSE + NDENSE];
   double* prim;
   int8_t* status;
   double* Fp;   // pointwise fluxes [3][10][sf]
@@ -113,19 +118,40 @@ constexpr int BS_ALL = 128;
 constexpr int BS_INT = 128;
 constexpr int BS_IF = 128;
 // Mesh-refinement hierarchy (amr.cu).  One task moves one point for all
-// fields: a copy (odd == 0) or a prolongation from the coarse base point sofs
-// of patch src (bit a of odd: midpoint along axis a).
+// fields: a copy (odd & 7 == 0) or a prolongation from the coarse base point
+// sofs of patch src (bit a of odd: midpoint along axis a); bit 3 of odd marks
+// a source on the coarser level (else a same-level copy).
+constexpr int AMR_COARSE = 8;
 struct AmrTask {
   int dst, dofs, src, sofs, odd;
+};
+// One coarse point (patch, offset in its ghosted layout) that a level's
+// prolongation stencils read.
+struct AmrPoint {
+  int patch, ofs;
 };
 struct AmrPlan {
   int level0 = -1, nlev = 0;
   std::vector<std::vector<AmrTask>> ghost;  // per level (0 unused): ghost tasks
   std::vector<std::vector<AmrTask>> restr;  // per level (0 unused): restriction into level - 1
+  std::vector<long long> nsame;             // per level: leading same-level copies among its ghost tasks
+  std::vector<std::vector<AmrPoint>> tpts;  // per level (0 unused): coarse points its stencils read, unique
   std::string err;
+  // Empty when every prolongation stencil point lies in an interior of the
+  // coarser level (or in the level-0 patch's ghosts), which sub-cycling needs.
+  std::string sub_err;
 };
 int amr_plan(const grmhd_patch_desc* d, const std::vector<Geo>& geo, int np, AmrPlan& P);
-void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, cudaStream_t st);
+// Ghost fill or restriction tasks on register reg; coarse-source tasks read
+// register reg_coarse of their source (reg_coarse < 0: reg).
+void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, cudaStream_t st, int reg_coarse = -1);
+// Sub-cycling: register reg_t of each listed coarse point receives the
+// stage value sum_d coef[d] U[REG_DENSE + d] (nd terms).
+void launch_amr_time(const PatchDev* pd_dev, const AmrPoint* pts, long long n, const double coef[NDENSE], int nd,
+                     int reg_t, cudaStream_t st);
+// Dense-output record after substep `stage` of a step (rk 0 RK4, 1 SSP-RK3)
+// at the interior points of the work list (block size 128).
+void launch_dense_rec(const PatchDev* pd_dev, const Work* w, int nblk, int stage, int rk, cudaStream_t st);
 
 // Learned seeder over patch points (seeder.cu): seeds of every point of the
 // work list (blocks of 128 points) of register reg into PatchDev::seed.

@@ -90,6 +90,7 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   PatchDev pd;
   pd.G = G;
   for (int r = 0; r < 4; ++r) pd.U[r] = d->U[r] ? d->U[r] : d->U[reg];
+  for (int r = 4; r < REG_DENSE + NDENSE; ++r) pd.U[r] = nullptr;
   pd.prim = d->prim;
   pd.status = d->status;
   pd.Fp = (double*)area;

@@ -49,6 +49,7 @@ def test_abi_version_and_argument_checks(lib):
     assert lib.grmhd_init_state(None, 0, None) == -1
     assert lib.grmhd_rhs_substep(None, 0, 0.1) == -1
     assert lib.grmhd_c2p_flat(None, None, 1, None, None, None, None, None) == -1
+    assert lib.grmhd_set_subcycling(None, 1) == -1
 
 
 def test_hybrid_eos_parameters_rejected_on_the_host(lib):
