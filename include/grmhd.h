@@ -117,6 +117,13 @@ typedef struct grmhd_params {
   double K_poly;
   double rho_poly[3];
   double gamma_poly[4];
+  /* LES gradient sub-grid-scale model (Sec. II B; Appendix "Large Eddy
+   * Simulation techniques"): coefficients C_N, C_Y, C_T, C_M of the SGS terms
+   * of D, DYe, S_i and B^i (the paper's default: C_M = 8, the others 0); all
+   * zero: no LES terms.  With any nonzero, every pointwise MHD flux along d
+   * gains alpha C xi sqrt(gamma) H^d (xi = gamma^{1/3} dx^2 / 24) before the
+   * reconstruction; see grmhd_init_patches for the requirements. */
+  double les_c[4];
 } grmhd_params;
 
 /* Tabulated EOS: p, eps, c_s^2 on the nodes of a uniform (log10 rho,

@@ -24,7 +24,8 @@ _P_INTS = ["eos_kind", "bc", "max_iter", "rk"]
 class Params(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS] +
                 [("npoly", ctypes.c_int), ("pad2_", ctypes.c_int), ("K_poly", ctypes.c_double),
-                 ("rho_poly", ctypes.c_double * 3), ("gamma_poly", ctypes.c_double * 4)])
+                 ("rho_poly", ctypes.c_double * 3), ("gamma_poly", ctypes.c_double * 4),
+                 ("les_c", ctypes.c_double * 4)])
 
 
 class EosTable(ctypes.Structure):
@@ -46,6 +47,8 @@ def make_params(d):
         p.rho_poly[i] = float(v)
     for i, v in enumerate(d.get("gamma_poly", ())):
         p.gamma_poly[i] = float(v)
+    for i, v in enumerate(d.get("les_c", ())):
+        p.les_c[i] = float(v)
     return p
 
 
@@ -93,6 +96,7 @@ def lib(flops=False):
             "oracle_hier_ghost_fill": (i, [vp, i, vp, vp, vp]),
             "oracle_hier_restrict": (i, [i, vp, vp, vp]),
             "oracle_hier_rk4_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
+            "oracle_les_flux_points": (i, [vp, vp, i, d, vp, vp, i, vp, i, vp]),
             "oracle_hier_rk4_step_mask": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp, i]),
             "oracle_hier_subcycle_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
             "oracle_dense_derivs": (None, [i, vp, vp]),
@@ -238,6 +242,19 @@ class Oracle:
         self.L.oracle_c2p_flat_ext(_ref(self.P), self.Tp, n, _p(cons), _p(prim), _p(status), _p(iters), _p(sd),
                                    float(delta), _p(roots), _p(seeded))
         return prim, status, iters, roots, seeded
+
+    def les_flux_points(self, U, prim, n, dx, ijk, d):
+        """LES SGS flux vectors along d at points ijk ([m][3] ints): [m][10]."""
+        n3 = _n3(n)
+        U = _chk(U)
+        prim = _chk(prim)
+        pts = np.ascontiguousarray(ijk, dtype=np.int32)
+        out = np.zeros((pts.shape[0], 10))
+        rc = self.L.oracle_les_flux_points(_ref(self.P), n3, U.shape[-1], dx, _p(U), _p(prim), pts.shape[0],
+                                           _p(pts), int(d), _p(out))
+        if rc:
+            raise ValueError("LES terms need an EOS with pressure derivatives (ideal gas or hybrid)")
+        return out
 
     def eos_from_eps(self, rho, eps, ye):
         out = np.zeros(4)

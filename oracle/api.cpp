@@ -48,10 +48,31 @@ int oracle_rhs_patch(const oracle_params* P, const int* n, int px, double dx, co
 int oracle_rhs_points(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
                       int npts, const int* ijk, double* out) {
   grid G = make_grid(n, px, dx);
+  std::vector<double> aux;
+  if (les_on(P)) {
+    aux.assign((size_t)les_naux() * G.sf, 0.0);
+    if (les_aux_patch(P, G, U, prim, aux.data())) return -1;
+  }
   for (int q = 0; q < npts; ++q) {
     real r[NF];
-    rhs_point(P, G, U, prim, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r);
+    rhs_point(P, G, U, prim, ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], r, aux.empty() ? nullptr : aux.data());
     for (int f = 0; f < NF; ++f) out[(long)q * NF + f] = dbl(r[f]);
+  }
+  return 0;
+}
+
+// LES SGS flux vectors along d (added to the MHD fluxes) at a list of points
+// (interior, or ghost points along d); out is [npts][10].  Returns -1 when the
+// EOS provides no pressure derivatives.
+int oracle_les_flux_points(const oracle_params* P, const int* n, int px, double dx, const double* U,
+                           const double* prim, int npts, const int* ijk, int d, double* out) {
+  grid G = make_grid(n, px, dx);
+  std::vector<double> aux((size_t)les_naux() * G.sf, 0.0);
+  if (les_aux_patch(P, G, U, prim, aux.data())) return -1;
+  for (int q = 0; q < npts; ++q) {
+    real F[10];
+    les_flux_point(P, G, U, aux.data(), ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], d, F);
+    for (int m = 0; m < 10; ++m) out[(long)q * 10 + m] = dbl(F[m]);
   }
   return 0;
 }

@@ -12,7 +12,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["eos.cpp", "c2p.cpp", "fd.cpp", "ccz4.cpp", "mhd.cpp", "patch.cpp", "api.cpp", "mlp.cpp", "amr.cpp"]
+SOURCES = ["eos.cpp", "c2p.cpp", "fd.cpp", "ccz4.cpp", "mhd.cpp", "patch.cpp", "api.cpp", "mlp.cpp", "amr.cpp", "les.cpp"]
 HEADERS = ["oracle.hpp", "real.hpp"]
 FLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall"]
 

@@ -95,6 +95,25 @@ static eos_state hybrid_from_eps(const oracle_params* P, real rho, real eps) {
   return s;
 }
 
+int eos_derivs(const oracle_params* P, real rho, real eps, real* dpdrho, real* dpdeps, real* dpdye) {
+  // Partial derivatives of p(rho, eps, Ye) (needed by the LES terms).
+  *dpdye = 0.0;
+  if (P->eos_kind == 0) {
+    *dpdrho = (P->gamma_th - 1.0) * eps;
+    *dpdeps = (P->gamma_th - 1.0) * rho;
+    return 0;
+  }
+  if (P->eos_kind == 2) {
+    // d/drho of p_c + (Gamma_th - 1) rho (eps - eps_c) with deps_c/drho = p_c / rho^2.
+    cold_state c = hybrid_cold(P, rho);
+    real gth = P->gamma_th - 1.0;
+    *dpdrho = c.gamma * c.p / rho + gth * (eps - c.eps) - gth * c.p / rho;
+    *dpdeps = gth * rho;
+    return 0;
+  }
+  return -1;  // tabulated EOS: not provided
+}
+
 real eos_eps_min(const oracle_params* P, const oracle_eos_table* E, real rho, real ye) {
   if (P->eos_kind == 0) return 0.0;
   if (P->eos_kind == 2) return hybrid_cold(P, rho).eps;

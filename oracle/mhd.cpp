@@ -178,7 +178,7 @@ void mhd_source_point(const oracle_params* P, const geom& Gm, const double* Up, 
 // Full right-hand side at one interior point with interface fluxes computed
 // from scratch (used for sampled points; the patch driver precomputes them).
 void rhs_point(const oracle_params* P, const grid& G, const double* U, const double* prim, int i, int j, int k,
-               real rhs[NF]) {
+               real rhs[NF], const double* aux) {
   geom Gm;
   ccz4_rhs_point(P, G, U, prim, i, j, k, rhs, &Gm);
   const long o = G.at(i, j, k);
@@ -193,6 +193,13 @@ void rhs_point(const oracle_params* P, const grid& G, const double* U, const dou
     for (int m = 0; m < 7; ++m) {
       long q = o + (m - 3) * st[d];
       mhd_flux_point(P, U + q, G.sf, prim + q, G.sf, d, Fm[m], &lam[m]);
+      if (aux) {
+        int ijk[3] = {i, j, k};
+        ijk[d] += m - 3;
+        real Fs[10];
+        les_flux_point(P, G, U, aux, ijk[0], ijk[1], ijk[2], d, Fs);
+        for (int n = 0; n < 10; ++n) Fm[m][n] = Fm[m][n] + Fs[n];
+      }
       for (int n = 0; n < 10; ++n) Um[m][n] = U[(NST + n) * G.sf + q];
     }
     real Fhm[10], Fhp[10];

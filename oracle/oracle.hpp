@@ -37,6 +37,10 @@ struct oracle_params {
   double K_poly;
   double rho_poly[3];
   double gamma_poly[4];
+  // LES gradient sub-grid-scale model (Sec. II B, Appendix on LES): the
+  // coefficients C_N, C_Y, C_T, C_M of the D, DYe, S_i and B^i terms; all
+  // zero: no LES terms.
+  double les_c[4];
 };
 
 // Tabulated EOS on nodes of (log10 rho, log10 T[MeV], Ye); rho varies fastest:
@@ -127,6 +131,9 @@ eos_state eos_from_eps(const oracle_params* P, const oracle_eos_table* E, real r
 // p, eps, cs2 from (rho, T, ye) (table) or the cold/atmosphere branch for the ideal gas.
 eos_state eos_from_T(const oracle_params* P, const oracle_eos_table* E, real rho, real T, real ye);
 eos_state eos_atmosphere(const oracle_params* P, const oracle_eos_table* E);
+// dp/drho|eps, dp/deps|rho, dp/dYe for the ideal gas and the hybrid EOS;
+// returns -1 for the tabulated EOS.
+int eos_derivs(const oracle_params* P, real rho, real eps, real* dpdrho, real* dpdeps, real* dpdye);
 
 // ---- metric helpers -------------------------------------------------------
 real det_sym(const real g[6]);
@@ -180,6 +187,14 @@ void mhd_source_point(const oracle_params* P, const geom& Gm, const double* Up, 
 // Matter projections: E, S_i, S_ij (lower indices, physical metric) at a point.
 void matter_point(const double* Up, long sf, const double* prp, long spf, real* E, real Si[3],
                   real Sij[6], real gdd[6], real guu[6], real* sqrtg);
-// Full 32-field right-hand side at one interior point, fluxes computed on the fly.
+// Full 32-field right-hand side at one interior point, fluxes computed on the
+// fly; aux: the LES point values of the patch (les_aux_patch) or null when
+// the LES terms are off.
 void rhs_point(const oracle_params* P, const grid& G, const double* U, const double* prim, int i,
-               int j, int k, real rhs[NF]);
+               int j, int k, real rhs[NF], const double* aux);
+// ---- LES gradient SGS model (les.cpp) ------------------------------------
+bool les_on(const oracle_params* P);
+long les_naux();
+int les_aux_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* aux);
+void les_flux_point(const oracle_params* P, const grid& G, const double* U, const double* aux, int i, int j, int k,
+                    int d, real F[10]);

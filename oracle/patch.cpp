@@ -196,6 +196,12 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
   // Fhat[d][n][o]: flux at the interface between point o and o + st[d].
   std::vector<double> Fhat((size_t)3 * 10 * npts, 0.0);
   std::vector<double> Fp((size_t)10 * npts), Lp((size_t)npts);
+  // LES gradient SGS model: point values whose gradients the SGS fluxes use.
+  std::vector<double> aux;
+  if (les_on(P)) {
+    aux.assign((size_t)les_naux() * npts, 0.0);
+    les_aux_patch(P, G, U, prim, aux.data());
+  }
   for (int d = 0; d < 3; ++d) {
     int lo[3] = {0, 0, 0}, hi[3] = {G.n[0], G.n[1], G.n[2]};
     lo[d] = -NG;
@@ -206,6 +212,11 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
           long o = G.at(i, j, k);
           real Fv[10], lam;
           mhd_flux_point(P, U + o, G.sf, prim + o, G.sf, d, Fv, &lam);
+          if (!aux.empty()) {
+            real Fs[10];
+            les_flux_point(P, G, U, aux.data(), i, j, k, d, Fs);
+            for (int n = 0; n < 10; ++n) Fv[n] = Fv[n] + Fs[n];
+          }
           for (int n = 0; n < 10; ++n) Fp[(size_t)n * npts + o] = dbl(Fv[n]);
           Lp[o] = dbl(lam);
         }

@@ -40,6 +40,7 @@ inline counted sqrt(counted a) { ++oracle_flops; return counted(std::sqrt(a.v));
 inline counted log(counted a) { ++oracle_flops; return counted(std::log(a.v)); }
 inline counted log10(counted a) { ++oracle_flops; return counted(std::log10(a.v)); }
 inline counted exp(counted a) { ++oracle_flops; return counted(std::exp(a.v)); }
+inline counted cbrt(counted a) { ++oracle_flops; return counted(std::cbrt(a.v)); }
 inline counted pow(counted a, counted b) { ++oracle_flops; return counted(std::pow(a.v, b.v)); }
 inline counted fabs(counted a) { return counted(std::fabs(a.v)); }
 inline counted fmin(counted a, counted b) { return counted(std::fmin(a.v, b.v)); }

@@ -28,7 +28,8 @@ _P_INTS = ["eos_kind", "bc", "max_iter", "rk"]
 class Params(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS] +
                 [("npoly", ctypes.c_int), ("reserved2", ctypes.c_int), ("K_poly", ctypes.c_double),
-                 ("rho_poly", ctypes.c_double * 3), ("gamma_poly", ctypes.c_double * 4)])
+                 ("rho_poly", ctypes.c_double * 3), ("gamma_poly", ctypes.c_double * 4),
+                 ("les_c", ctypes.c_double * 4)])
 
 
 class EosTable(ctypes.Structure):
@@ -142,7 +143,7 @@ def make_params(d):
         setattr(p, n, int(d.get(n, 0)))
     p.npoly = int(d.get("npoly", 0))
     p.K_poly = float(d.get("K_poly", 0.0))
-    for name, n in (("rho_poly", 3), ("gamma_poly", 4)):
+    for name, n in (("rho_poly", 3), ("gamma_poly", 4), ("les_c", 4)):
         vals = tuple(d.get(name, ()))
         if len(vals) > n:
             raise ValueError(f"{name} holds at most {n} values")
