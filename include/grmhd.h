@@ -122,7 +122,11 @@ typedef struct grmhd_params {
    * of D, DYe, S_i and B^i (the paper's default: C_M = 8, the others 0); all
    * zero: no LES terms.  With any nonzero, every pointwise MHD flux along d
    * gains alpha C xi sqrt(gamma) H^d (xi = gamma^{1/3} dx^2 / 24) before the
-   * reconstruction; see grmhd_init_patches for the requirements. */
+   * reconstruction.  The ideal gas and the hybrid EOS only (the table's
+   * pressure derivatives are not provided): grmhd_init_patches returns
+   * GRMHD_ERR_ARG for eos_kind 1 with LES, and so does grmhd_rhs_eval_static
+   * for any LES coefficient (its point values need scratch memory); a patch
+   * context allocates LES_NAUX = 32 doubles per ghosted point for them. */
   double les_c[4];
 } grmhd_params;
 
@@ -298,7 +302,7 @@ int grmhd_autotune(grmhd_ctx* ctx, double dt, int reps, int* chosen);
  * and launch counts per kernel kind (0 ghost fill, 1 con2prim + pointwise
  * fluxes, 2 interface fluxes, 3 right-hand side + RK epilogue, 4 unfused RK
  * update, 5 initial data, 6 seeder inference, 7 sub-cycling dense-output
- * record and its ghosts) into ms[0..nkinds) and
+ * record and its ghosts, 8 LES SGS fluxes) into ms[0..nkinds) and
  * count[0..nkinds), and
  * discards the records. */
 int grmhd_profile(grmhd_ctx* ctx, int on);

@@ -321,7 +321,7 @@ class Patches:
     def sync_status(self):
         return self.L.grmhd_sync_status(self.ctx)
 
-    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init", "seed", "dense")
+    KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init", "seed", "dense", "les")
 
     def set_block_sizes(self, bs_c2p, bs_iflux, bs_rhs):
         _check(self.L.grmhd_set_block_sizes(self.ctx, bs_c2p, bs_iflux, bs_rhs), self.ctx, "grmhd_set_block_sizes")

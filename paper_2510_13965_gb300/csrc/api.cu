@@ -42,6 +42,7 @@ struct grmhd_ctx {
   // sub-cycling in time (grmhd_set_subcycling): dense-output registers
   bool subcycle = false;
   double* dense_buf = nullptr;
+  double* les_buf = nullptr;  // LES point values of every patch
   long long launches = 0;
   long long graph_kernels = 0;
   std::string err;
@@ -55,7 +56,7 @@ struct grmhd_ctx {
   std::vector<cudaEvent_t> pool;
 };
 
-enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, K_SEED = 6, K_DENSE = 7, NKIND = 8 };
+enum { K_GHOST = 0, K_C2P = 1, K_IFLUX = 2, K_RHS = 3, K_RK = 4, K_INIT = 5, K_SEED = 6, K_DENSE = 7, K_LES = 8, NKIND = 9 };
 
 static cudaEvent_t ev_get(grmhd_ctx* c) {
   if (!c->pool.empty()) {
@@ -129,6 +130,7 @@ void grmhd_destroy(grmhd_ctx* c) {
   cudaFree(c->pd);
   cudaFree(c->work);
   cudaFree(c->dense_buf);
+  cudaFree(c->les_buf);
   cudaFree(c->amr_tp);
   cudaFree(c->scratch);
   cudaFree(c->flags);
@@ -145,6 +147,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   *out = nullptr;
   if (!p || !d || npatch <= 0) return GRMHD_ERR_ARG;
   if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
+  if (les_on(*p) && p->eos_kind == 1) return GRMHD_ERR_ARG;  // no pressure derivatives of the table
   if (p->bc < 0 || p->bc > 3) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (p->rk != 0 && p->rk != 1) return GRMHD_ERR_ARG;
@@ -197,6 +200,20 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     q.lam = q.Fp + 30 * q.G.sf;
     q.Fh = q.lam + 3 * q.G.sf;
     q.seed = nullptr;
+    q.les = nullptr;
+  }
+  if (les_on(*p)) {
+    size_t ltot = 0;
+    for (int i = 0; i < npatch; ++i) ltot += (size_t)LES_NAUX * c->pd_host[i].G.sf;
+    if ((rc = cuda_ok(c, cudaMalloc(&c->les_buf, ltot * sizeof(double)), "cudaMalloc LES values")) != GRMHD_OK) {
+      grmhd_destroy(c);
+      return GRMHD_ERR_NOMEM;
+    }
+    size_t lo = 0;
+    for (int i = 0; i < npatch; ++i) {
+      c->pd_host[i].les = c->les_buf + lo;
+      lo += (size_t)LES_NAUX * c->pd_host[i].G.sf;
+    }
   }
   // work lists: for each group, block size and domain, the blocks of patch
   // 0, then patch 1, ... (group 0: every patch; group 1 + l: level l)
@@ -396,10 +413,17 @@ static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats, int grp = 0) {
     c->launches += 1;
     if (rc) return fail(c, rc, "seeder launch");
   }
-  ProfScope ps(c, K_C2P);
-  launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p, grp), nblk(c, DOM_ALL, c->bs_c2p, grp), reg, c->P, c->E, c->flags,
-             stats ? c->stats : nullptr, c->st, c->bs_c2p, c->seeder != nullptr, c->seed_delta);
-  c->launches += 1;
+  {
+    ProfScope ps(c, K_C2P);
+    launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p, grp), nblk(c, DOM_ALL, c->bs_c2p, grp), reg, c->P, c->E, c->flags,
+               stats ? c->stats : nullptr, c->st, c->bs_c2p, c->seeder != nullptr, c->seed_delta);
+    c->launches += 1;
+  }
+  if (c->les_buf) {
+    ProfScope ps(c, K_LES);
+    launch_les(c->pd, wl(c, DOM_ALL, 128, grp), nblk(c, DOM_ALL, 128, grp), reg, c->P, c->E, c->st);
+    c->launches += 2;
+  }
   return check_launch(c, "con2prim");
 }
 

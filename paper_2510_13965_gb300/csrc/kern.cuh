@@ -13,6 +13,7 @@ namespace gk {
 // Registers 4..8 (levels with a finer level, under sub-cycling): the dense
 // output of the level's last step, U^n, D_1, D_2, D_3, J; otherwise null.
 constexpr int REG_DENSE = 4;
+constexpr int LES_NAUX = 32;  // point values whose gradients the LES closed forms use
 constexpr int NDENSE = 5;
 struct PatchDev {
   Geo G;
@@ -23,6 +24,7 @@ struct PatchDev {
   double* lam;  // pointwise max |lambda_fast| [3][sf]
   double* Fh;   // interface fluxes [3][10][sf] at the interface between o and o + s_d
   float* seed;  // learned con2prim seeds [3][sf] (mu_+, mu, W) or null
+  double* les;  // LES point values [LES_NAUX][sf] (LES terms on) or null
 };
 
 // Work item of a launch: patch index and block index within that patch's domain.
@@ -112,6 +114,13 @@ void launch_c2p_flat(const grmhd_params& P, const Eos& E, long long n, const dou
                      int8_t* status, int32_t* iters, cudaStream_t st);
 void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, const double* prim, const double* B,
                           double* cons, cudaStream_t st);
+
+// LES gradient SGS model (les.cu): true when any coefficient is nonzero;
+// launch_les adds the SGS fluxes to PatchDev::Fp after con2prim of register
+// reg over the DOM_ALL work list (block size 128).
+bool les_on(const grmhd_params& P);
+void launch_les(const PatchDev* pd_dev, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
+                cudaStream_t st);
 
 // Block sizes of the launches (threads per block).
 constexpr int BS_ALL = 128;

@@ -61,6 +61,7 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
                                      int reg, double* rhs, void* stream) {
   if (!p || !d || !rhs || reg < 0 || reg > 3) return GRMHD_ERR_ARG;
   if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
+  if (les_on(*p)) return GRMHD_ERR_ARG;  // the LES point values need scratch memory
   if (p->bc != 0 && p->bc != 1) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (d->n[0] < 4 || d->n[1] < 4 || d->n[2] < 4 || d->px < d->n[0] + 6 || !(d->dx > 0.0)) return GRMHD_ERR_ARG;
@@ -91,6 +92,7 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   pd.G = G;
   for (int r = 0; r < 4; ++r) pd.U[r] = d->U[r] ? d->U[r] : d->U[reg];
   for (int r = 4; r < REG_DENSE + NDENSE; ++r) pd.U[r] = nullptr;
+  pd.les = nullptr;
   pd.prim = d->prim;
   pd.status = d->status;
   pd.Fp = (double*)area;

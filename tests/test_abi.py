@@ -87,3 +87,13 @@ def test_struct_layouts_match_header(tmp_path):
     assert out[-1] == ctypes.sizeof(g.Params)
     assert ctypes.sizeof(g.PatchDesc) == 6 * 4 + 4 * 8 + 6 * 8
     assert ctypes.sizeof(g.EosTable) == 4 * 4 + 6 * 8 + 3 * 8
+
+
+def test_les_rejected_by_the_allocation_free_entry(lib):
+    """grmhd_rhs_eval_static has no scratch for the LES point values: any LES
+    coefficient is refused before a pointer is touched."""
+    import paper_2510_13965_gb300 as g
+    import synth
+    p = g.make_params({**synth.ideal_params(bc=1), "les_c": (0.0, 0.0, 0.0, 8.0)})
+    d = g.PatchDesc()
+    assert lib.grmhd_rhs_eval_static(ctypes.byref(p), ctypes.byref(d), None, 0, ctypes.c_void_p(8), None) == -1
