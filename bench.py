@@ -73,6 +73,8 @@ def _args():
     a.add_argument("--amr-seeded", action="store_true",
                    help="also time the hierarchy with NN-seeded con2prim")
     a.add_argument("--amr-delta", type=float, default=3e-2)
+    a.add_argument("--les-cm", type=float, default=0.0,
+                   help="tov workload: LES gradient SGS model with C_M (the paper's default is 8)")
     a.add_argument("--amr-subcycle", action="store_true",
                    help="amr workload: also time sub-cycled steps (BOR) over the same physical time")
     a.add_argument("--edge", type=int, default=N_EDGE,
@@ -280,6 +282,10 @@ def run_grmhd(args):
     import synth
 
     P = synth.ideal_params(bc=1)
+    if args.les_cm:
+        # SGS fluxes on above the error policy's low-density threshold rho_low.
+        P["les_c"] = (0.0, 0.0, 0.0, args.les_cm)
+        P["les_rho_min"] = P["rho_low"]
     edge = args.edge
     dx = 40.0 / edge
     ID = torch.as_tensor(_workload_id(seed=1 + rank, edge=edge), device="cuda")
@@ -352,7 +358,8 @@ def run_grmhd(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if edge == N_EDGE else "tov_magnetised_%d^3_rk4_step" % edge,
+            "config": {"workload": (WORKLOAD if edge == N_EDGE else "tov_magnetised_%d^3_rk4_step" % edge) +
+                       ("_les_cm%g" % args.les_cm if args.les_cm else ""),
                        "n": [edge] * 3, "dx": dx, "domain": "[-20,20]^3",
                        "step": "one RK4 step (4 fused substeps)", "parallelism": "replicas" if ws > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (616 MB per RK register)"},

@@ -128,6 +128,13 @@ typedef struct grmhd_params {
    * for any LES coefficient (its point values need scratch memory); a patch
    * context allocates LES_NAUX = 32 doubles per ghosted point for them. */
   double les_c[4];
+  /* A flux point whose rest-mass density is below les_rho_min gets no SGS
+   * flux (0: everywhere).  The paper states no rule for low densities; in an
+   * atmosphere the gradient model acts on an almost massless, magnetised
+   * fluid and C_M = 8 drove a static star's atmosphere unstable within nine
+   * steps, so rho_low (the error policy's low-density threshold) is the
+   * natural setting. */
+  double les_rho_min;
 } grmhd_params;
 
 /* Tabulated EOS: p, eps, c_s^2 on the nodes of a uniform (log10 rho,

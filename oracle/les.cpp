@@ -19,7 +19,10 @@
 // paper lists no tau term).  The derivative d_a of a point value is the
 // fourth-order centred difference where its stencil fits in the ghosted
 // patch, else the second-order centred one, else the second-order one-sided
-// one (the patch's outermost ghost layer).
+// one (the patch's outermost ghost layer).  A flux point whose rest-mass
+// density is below les_rho_min gets no SGS flux (the paper states no rule for
+// low densities; there the gradient model acts on an almost massless,
+// magnetised fluid).
 #include <cmath>
 #include <vector>
 
@@ -128,6 +131,8 @@ int les_aux_patch(const oracle_params* P, const grid& G, const double* U, const 
 void les_flux_point(const oracle_params* P, const grid& G, const double* U, const double* aux, int i, int j, int k,
                     int d, real F[10]) {
   const long o = G.at(i, j, k);
+  for (int n = 0; n < 10; ++n) F[n] = 0.0;
+  if (aux[(long)A_RHO * G.sf + o] < P->les_rho_min) return;
   const long st[3] = {1, G.sy, G.sz};
   const int idx[3] = {i, j, k};
   real gr[3][NAUX];

@@ -41,6 +41,8 @@ struct oracle_params {
   // coefficients C_N, C_Y, C_T, C_M of the D, DYe, S_i and B^i terms; all
   // zero: no LES terms.
   double les_c[4];
+  // No SGS flux at a flux point whose rest-mass density is below this.
+  double les_rho_min;
 };
 
 // Tabulated EOS on nodes of (log10 rho, log10 T[MeV], Ye); rho varies fastest:

@@ -29,7 +29,7 @@ class Params(ctypes.Structure):
     _fields_ = ([(n, ctypes.c_double) for n in _P_DOUBLES] + [(n, ctypes.c_int) for n in _P_INTS] +
                 [("npoly", ctypes.c_int), ("reserved2", ctypes.c_int), ("K_poly", ctypes.c_double),
                  ("rho_poly", ctypes.c_double * 3), ("gamma_poly", ctypes.c_double * 4),
-                 ("les_c", ctypes.c_double * 4)])
+                 ("les_c", ctypes.c_double * 4), ("les_rho_min", ctypes.c_double)])
 
 
 class EosTable(ctypes.Structure):
@@ -149,6 +149,7 @@ def make_params(d):
             raise ValueError(f"{name} holds at most {n} values")
         for i, v in enumerate(vals):
             getattr(p, name)[i] = float(v)
+    p.les_rho_min = float(d.get("les_rho_min", 0.0))
     return p
 
 

@@ -13,6 +13,9 @@
 // H_NY^k (DYe, C_Y), H_T^k_i (S_i, C_T), H_M^{ki} (B^i, C_M).  d_a of a point
 // value: fourth-order centred where the stencil fits in the ghosted patch,
 // else second-order centred, else second-order one-sided (outermost ghosts).
+// A flux point whose rest-mass density is below les_rho_min gets no SGS flux
+// (the paper states no rule for low densities; in an atmosphere the model
+// acts on an almost massless, magnetised fluid).
 //
 // Two passes after con2prim: k_les_aux writes the point values whose
 // gradients are needed ([NAUX][sf] per patch), k_les_flux evaluates the
@@ -124,7 +127,8 @@ DI double dgrad(const double* A, long long s, int c, int n, double dx) {
 }
 
 __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
-                                                  int reg, double cN, double cY, double cT, double cM) {
+                                                  int reg, double cN, double cY, double cT, double cM,
+                                                  double rho_min) {
   const Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
   const long long o = at(G, i, j, k), sf = G.sf;
   const double* U = PD.U[reg];
   const double* A = PD.les + o;
+  if (A[A_RHO * sf] < rho_min) return;
   const long long st[3] = {1, G.sy, G.sz};
   const int idx[3] = {i, j, k}, nn[3] = {G.n0, G.n1, G.n2};
   double gr[3][LES_NAUX];
@@ -255,7 +260,7 @@ void launch_les(const PatchDev* pd, const Work* w, int nblk, int reg, const grmh
                 cudaStream_t st) {
   if (nblk <= 0) return;
   k_les_aux<<<nblk, 128, 0, st>>>(pd, w, E, reg);
-  k_les_flux<<<nblk, 128, 0, st>>>(pd, w, reg, P.les_c[0], P.les_c[1], P.les_c[2], P.les_c[3]);
+  k_les_flux<<<nblk, 128, 0, st>>>(pd, w, reg, P.les_c[0], P.les_c[1], P.les_c[2], P.les_c[3], P.les_rho_min);
 }
 
 }  // namespace gk

@@ -69,7 +69,7 @@ def test_struct_layouts_match_header(tmp_path):
     import shutil
     import subprocess
     import paper_2510_13965_gb300 as g
-    assert ctypes.sizeof(g.Params) == 22 * 8 + 4 * 4 + 2 * 4 + 8 + 3 * 8 + 4 * 8 + 4 * 8
+    assert ctypes.sizeof(g.Params) == 22 * 8 + 4 * 4 + 2 * 4 + 8 + 3 * 8 + 4 * 8 + 4 * 8 + 8
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")

@@ -40,6 +40,7 @@ def _fourier(les):
 def _hybrid_star(les):
     P = synth.hybrid_params(bc=1)
     P["les_c"] = les
+    P["les_rho_min"] = 1e-6  # the switch is exercised: the atmosphere gets no SGS flux
     n, x0, dx = (28, 28, 28), (-9.45, -9.45, -9.45), 0.7
     ID = synth.tov_id(n=n, x0=x0, dx=dx, seed=1, heat=1.5)
     # A smooth flow through the magnetised star: the induction SGS term needs

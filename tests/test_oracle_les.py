@@ -173,3 +173,21 @@ def test_tabulated_eos_is_refused():
     U = np.zeros((32, 10, 10, 10))
     with pytest.raises(ValueError):
         O.les_flux_points(U, np.zeros((NP, 10, 10, 10)), (4, 4, 4), 0.1, [[0, 0, 0]], 0)
+
+
+def test_density_switch():
+    """Flux points below les_rho_min get no SGS flux; the others are unchanged."""
+    P, rho0, eps_of = _case("ideal")
+    P["les_c"] = (1.0, 1.0, 1.0, 8.0)
+    ID = synth.config0_id(n=(10, 10, 10), seed=3)
+    base = oracle.Oracle(P)
+    U = base.init_state(ID, (10, 10, 10), 0.1)
+    prim, _, _, _ = base.con2prim_patch(U, (10, 10, 10))
+    pts = [[i, 4, 5] for i in range(10)]
+    F0 = base.les_flux_points(U, prim, (10, 10, 10), 0.1, pts, 0)
+    rho = np.array([prim[0][5 + 3, 4 + 3, i + 3] for i in range(10)])
+    thr = np.median(rho)
+    F1 = oracle.Oracle(dict(P, les_rho_min=thr)).les_flux_points(U, prim, (10, 10, 10), 0.1, pts, 0)
+    assert np.all(F1[rho < thr] == 0.0)
+    assert np.array_equal(F1[rho >= thr], F0[rho >= thr])
+    assert np.any(F0[rho < thr] != 0.0)
