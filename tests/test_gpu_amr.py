@@ -9,6 +9,8 @@
   state: interiors within 1e-11 per field (the right-hand side tolerance).
 - CUDA-graph replay of hierarchy steps equals eager steps bit for bit.
 - A layout whose fine ghosts leave the coarser level is rejected.
+- Full size (the 366-patch star hierarchy, synthetic table): 12 sampled
+  patches of the GPU's ghost fill + con2prim + RHS against the oracle.
 """
 import numpy as np
 import pytest
@@ -137,3 +139,58 @@ def test_uncovered_fine_ghosts_are_rejected():
     specs[1] = synth.hierarchy.spec((12, 12, 12), 1, (1, 12, 12), 1.0, (-12.0,) * 3)
     with pytest.raises(g.GrmhdError):
         g.Patches(synth.ideal_params(bc=3), specs)
+
+
+def test_full_size_hierarchy_sampled_patches():
+    """The star hierarchy at full size (366 patches, 31.2 M interior points,
+    synthetic table): after the GPU's hierarchy ghost fill, con2prim and
+    right-hand side of the whole layout in the batched launches the bench
+    times, 12 seeded-random patches are redone by the oracle from the GPU's
+    own ghost-filled state: statuses bit-exact, primitives to 1e-10, the
+    right-hand side to 1e-11 per field."""
+    from tests._checks import prim_check
+    table = synth.make_table()
+    P = synth.table_params(table, bc=3)
+    T = g.Table(table)
+    specs = synth.amr_tov_layout(scale=1.0)
+    prof = synth.tov_profile()
+    pt = g.Patches(P, specs, table=T)
+    for q, s in enumerate(specs):
+        ID = synth.tov_id(n=s["n"], x0=s["x0"], dx=s["dx"], seed=4000 + q, table=table, rho_atmo=P["rho_atmo"],
+                          profile=prof)
+        pt.init_state(q, torch.as_tensor(ID, device="cuda"))
+        pt.synchronize()
+    pt.restrict(0)
+    pt.ghost_fill(0)
+    pt.synchronize()
+    rng = np.random.default_rng(11)
+    sample = sorted(int(x) for x in rng.choice(len(specs), 12, replace=False))
+    U0 = {q: pt.U[q][0].cpu().numpy().copy() for q in sample}
+    pt.con2prim(0)
+    rhs = pt.rhs_eval(0)
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    O = oracle.Oracle(P, table)
+    # One field spans the whole hierarchy: the right-hand side is held to 1e-11
+    # of the field's largest value over the sampled patches (for the MHD fields
+    # also of |U| / dx, the size of the cancelling flux terms), not of each
+    # patch's own: far from the star the spacetime right-hand sides are
+    # cancellations of the star's tidal terms (A~_ij: ~1e-12 out of ~1e-5).
+    scale = np.zeros(NF)
+    diff = np.zeros(NF)
+    for q in sample:
+        s = specs[q]
+        Uo = U0[q].copy()
+        prim_o, st_o, _, _ = O.con2prim_patch(Uo, s["n"])
+        assert np.array_equal(pt.status[q].cpu().numpy(), st_o), q
+        prim_check(pt.prim[q].cpu().numpy(), prim_o, pt.status[q].cpu().numpy(), st_o, Uo[22:25])
+        want = interior(O.rhs_patch(Uo, prim_o, s["n"], s["dx"]), s["n"]).reshape(NF, -1)
+        got = interior(rhs[q].cpu().numpy(), s["n"]).reshape(NF, -1)
+        un = np.abs(interior(Uo, s["n"])).reshape(NF, -1).max(axis=1)
+        un[28:32] = un[28:32].max()
+        sc = np.abs(want).max(axis=1)
+        sc[22:] = np.maximum(sc[22:], un[22:] / s["dx"])
+        scale = np.maximum(scale, sc)
+        diff = np.maximum(diff, np.abs(got - want).max(axis=1))
+    e = diff / np.maximum(scale, 1e-30)
+    assert np.all((e < 1e-11) | (diff < 1e-14)), {f: (e[f], diff[f]) for f in range(NF) if not e[f] < 1e-11}
