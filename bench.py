@@ -73,6 +73,8 @@ def _args():
     a.add_argument("--amr-seeded", action="store_true",
                    help="also time the hierarchy with NN-seeded con2prim")
     a.add_argument("--amr-delta", type=float, default=3e-2)
+    a.add_argument("--no-autotune", action="store_true",
+                   help="tov workload: keep 128-thread blocks instead of the library's timed choice")
     a.add_argument("--les-cm", type=float, default=0.0,
                    help="tov workload: LES gradient SGS model with C_M (the paper's default is 8)")
     a.add_argument("--amr-subcycle", action="store_true",
@@ -293,6 +295,9 @@ def run_grmhd(args):
     pt.init_state(0, ID)
     del ID
     dt = 0.4 * dx
+    # Block size per kernel kind from the library's timed candidates (64, 128,
+    # 256); it leaves U^n as it is apart from con2prim corrections.
+    chosen = (128, 128, 128) if args.no_autotune else pt.autotune(dt, reps=2)
     for _ in range(max(args.warmup, 3)):
         pt.step(dt)
     pt.synchronize()
@@ -362,6 +367,7 @@ def run_grmhd(args):
                        ("_les_cm%g" % args.les_cm if args.les_cm else ""),
                        "n": [edge] * 3, "dx": dx, "domain": "[-20,20]^3",
                        "step": "one RK4 step (4 fused substeps)", "parallelism": "replicas" if ws > 1 else "1 GPU",
+                       "block_sizes": {"c2p": chosen[0], "iflux": chosen[1], "rhs": chosen[2]},
                        "l2": "inputs larger than L2 (616 MB per RK register)"},
             "substeps_per_s": 4 * args.steps * ws / (ms_max / 1e3),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
