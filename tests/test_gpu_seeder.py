@@ -277,3 +277,57 @@ def test_seeded_patch_con2prim_matches_oracle(table_setup):
         prim_check(pg.reshape(NP, -1), po.reshape(NP, -1), sg.reshape(-1), so.reshape(-1), cons.reshape(3, -1))
         assert st["failed"] == 0
     assert res[True][2]["iterations"] != res[False][2]["iterations"]
+
+
+def _flat_cons_numpy(n, seed):
+    """Conserved states of the isolated con2prim workload built on the host
+    (the oracle's inputs never come from the CUDA path): seeded primitives,
+    p and eps from the synthetic table's analytic model, and the flat-metric
+    conserved variables from their textbook definitions."""
+    s = synth.c2p_states(n, seed=seed)
+    rho, ye, v, B = s["rho"], s["ye"], s["v"], s["B"]
+    p, eps, _ = synth.eos_table.model(rho, s["T"], ye)
+    v2 = np.einsum("ij,ij->i", v, v)
+    W2 = 1.0 / (1.0 - v2)
+    h = rho * (1.0 + eps) + p
+    B2 = np.einsum("ij,ij->i", B, B)
+    vB = np.einsum("ij,ij->i", v, B)
+    cons = np.zeros((n, 10))
+    cons[:, 0] = rho * np.sqrt(W2)
+    cons[:, 1] = cons[:, 0] * ye
+    cons[:, 2] = h * W2 - p + B2 - 0.5 * (B2 / W2 + vB * vB) - cons[:, 0]
+    cons[:, 3:6] = (h * W2 + B2)[:, None] * v - vB[:, None] * B
+    cons[:, 6:9] = B
+    return cons
+
+
+def test_full_size_con2prim_sampled():
+    """The isolated con2prim workload at full size: 2^24 states, the
+    256 x 128 x 64 table, plain and NN-seeded (the bench's recipe: 2^20 GPU-made
+    training pairs, delta = 0.03) in single launches; 4096 seeded-random states
+    redone by the oracle: statuses bit-exact, primitives within the con2prim
+    bounds."""
+    table = synth.make_table()
+    P = synth.table_params(table)
+    T = g.Table(table)
+    O = oracle.Oracle(P, table)
+    n = 1 << 24
+    cons = _flat_cons_numpy(n, seed=3)
+    cg = torch.as_tensor(cons, device="cuda")
+    pg, sg = (a.cpu().numpy() for a in g.c2p_flat(P, cg, table=T))
+    # Seeder trained as in the bench (training pairs may come from the GPU).
+    st_ = synth.c2p_states(1 << 20, seed=13)
+    prim = torch.zeros((1 << 20, 10), dtype=torch.float64)
+    prim[:, 0], prim[:, 7], prim[:, 8] = (torch.from_numpy(st_[k]) for k in ("rho", "ye", "T"))
+    prim[:, 3:6] = torch.from_numpy(st_["v"])
+    ctr = g.prim2con_flat(P, prim.cuda(), torch.from_numpy(st_["B"]).cuda(), table=T)
+    _, s0, _, roots, _ = g.c2p_flat_seeded(P, ctr, None, table=T)
+    keep = s0 >= 0
+    S = g.Seeder(seed=1)
+    S.train(g.seeder_features(ctr)[keep].contiguous(), g.seeder_targets(ctr, roots)[keep].contiguous(),
+            batch=4096, epochs=40, lr=3e-3, lr_final=3e-5)
+    ps, ss, _, _, _ = (a.cpu().numpy() for a in g.c2p_flat_seeded(P, cg, S.infer(cg), 0.03, table=T))
+    idx = np.sort(np.random.default_rng(5).choice(n, 4096, replace=False))
+    po, so, _ = O.c2p_flat(cons[idx])
+    for p_, s_ in ((pg, sg), (ps, ss)):
+        prim_check(p_[idx].T, po.T, s_[idx], so, cons[idx, :3].T)
