@@ -210,7 +210,11 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
 int grmhd_init_state(grmhd_ctx* ctx, int patch, const double* id);
 
 /* Fills the 3-deep ghost zones of register `reg` (0..3) of every patch
- * (periodic copy or linear extrapolation, axis by axis). */
+ * (periodic copy or linear extrapolation, axis by axis; for bc = 3 the
+ * hierarchy fill described at grmhd_patch_desc).  The hierarchy fill computes
+ * the coarse x-midpoints once per coarse row in the library's pointwise-flux
+ * scratch of the coarser patches, so it invalidates the fluxes of an earlier
+ * grmhd_con2prim: call grmhd_con2prim after it, as the substep does. */
 int grmhd_ghost_fill(grmhd_ctx* ctx, int reg);
 
 /* con2prim at every point (ghosts included) of register `reg` of every patch:
@@ -220,7 +224,7 @@ int grmhd_ghost_fill(grmhd_ctx* ctx, int reg);
 int grmhd_con2prim(grmhd_ctx* ctx, int reg, grmhd_c2p_stats* stats);
 
 /* Right-hand side L(U) of register `reg` at interior points, from the
- * primitives of the last grmhd_con2prim call.  rhs[p] is a device array with
+ * primitives and pointwise fluxes of the last grmhd_con2prim call.  rhs[p] is a device array with
  * the patch layout (32 fields); ghost entries are not written. */
 int grmhd_rhs_eval(grmhd_ctx* ctx, int reg, double* const* rhs);
 

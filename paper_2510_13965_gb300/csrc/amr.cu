@@ -34,21 +34,26 @@ DI double mid6(const double* u) {
 // along each axis with its bit set in odd, the midpoint formula over offsets
 // -2..3; x first, then y, then z.  rd(off) reads the coarse value at offset
 // off (in points of the coarse patch's layout) from the base point.
-template <class Rd>
-DI double prolong(Rd rd, long long sy, long long sz, int odd) {
+template <bool XPRE, class Rd, class RdX>
+DI double prolong(Rd rd, RdX rdx, long long sy, long long sz, int odd) {
   const bool ox = odd & 1, oy = odd & 2, oz = odd & 4;
   double zl[6];
   const int nz = oz ? 6 : 1, ny = oy ? 6 : 1;
+#pragma unroll 1
   for (int c2 = 0; c2 < nz; ++c2) {
     const long long pz = oz ? (c2 - 2) * sz : 0;
     double yl[6];
     for (int c1 = 0; c1 < ny; ++c1) {
       const long long py = pz + (oy ? (c1 - 2) * sy : 0);
       if (ox) {
-        double xl[6];
+        if (XPRE) {
+          yl[c1] = rdx(py);  // the x-midpoint of this row, computed by k_amr_xmid
+        } else {
+          double xl[6];
 #pragma unroll
-        for (int c0 = 0; c0 < 6; ++c0) xl[c0] = rd(py + c0 - 2);
-        yl[c1] = mid6(xl);
+          for (int c0 = 0; c0 < 6; ++c0) xl[c0] = rd(py + c0 - 2);
+          yl[c1] = mid6(xl);
+        }
       } else {
         yl[c1] = rd(py);
       }
@@ -58,6 +63,32 @@ DI double prolong(Rd rd, long long sy, long long sz, int odd) {
   return oz ? mid6(zl) : zl[0];
 }
 
+// x-midpoints of a coarse level, once per coarse row that the finer level's
+// stencils read: X(c) = mid6(U(c-2 .. c+3)) along x, into the patch's
+// pointwise-flux scratch (free during a ghost fill; 33 doubles per point).
+__global__ void __launch_bounds__(256) k_amr_xmid(const PatchDev* __restrict__ pd, const AmrPoint* __restrict__ p,
+                                                   long long n, int reg) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const AmrPoint P = p[q];
+  const PatchDev& S = pd[P.patch];
+  const double* u = S.U[reg] + P.ofs;
+  double* x = S.Fp + P.ofs;
+  for (int f = 0; f < NF; ++f) {
+    const double* uf = u + f * S.G.sf;
+    double xl[6];
+#pragma unroll
+    for (int c0 = 0; c0 < 6; ++c0) xl[c0] = uf[c0 - 2];
+    x[f * S.G.sf] = mid6(xl);
+  }
+}
+
+void launch_amr_xmid(const PatchDev* pd, const AmrPoint* pts, long long n, int reg, cudaStream_t st) {
+  if (n <= 0) return;
+  k_amr_xmid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pd, pts, n, reg);
+}
+
+template <bool XPRE>
 __global__ void __launch_bounds__(256) k_amr(const PatchDev* __restrict__ pd, const AmrTask* __restrict__ t,
                                               long long n, int reg, int reg_coarse) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -71,16 +102,24 @@ __global__ void __launch_bounds__(256) k_amr(const PatchDev* __restrict__ pd, co
   if (odd == 0) {
     for (int f = 0; f < NF; ++f) d[f * D.G.sf] = s[f * S.G.sf];
   } else {
+    const double* xs = S.Fp + T.sofs;
     for (int f = 0; f < NF; ++f) {
       const double* sf = s + f * S.G.sf;
-      d[f * D.G.sf] = prolong([sf](long long off) { return sf[off]; }, S.G.sy, S.G.sz, odd);
+      const double* xf = xs + f * S.G.sf;
+      d[f * D.G.sf] = prolong<XPRE>([sf](long long off) { return sf[off]; }, [xf](long long off) { return xf[off]; },
+                                    S.G.sy, S.G.sz, odd);
     }
   }
 }
 
-void launch_amr(const PatchDev* pd, const AmrTask* t, long long n, int reg, cudaStream_t st, int reg_coarse) {
+void launch_amr(const PatchDev* pd, const AmrTask* t, long long n, int reg, cudaStream_t st, int reg_coarse,
+                bool xpre) {
   if (n <= 0) return;
-  k_amr<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pd, t, n, reg, reg_coarse < 0 ? reg : reg_coarse);
+  const int rc = reg_coarse < 0 ? reg : reg_coarse;
+  if (xpre)
+    k_amr<true><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pd, t, n, reg, rc);
+  else
+    k_amr<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pd, t, n, reg, rc);
 }
 
 // Sub-cycled ghost fill (Sec. III D, BOR), first pass: at every coarse point
@@ -405,6 +444,27 @@ int amr_plan(const grmhd_patch_desc* d, const std::vector<Geo>& geo, int np, Amr
         if (m.empty()) continue;
         for (size_t o = 0; o < m.size(); ++o)
           if (m[o]) P.tpts[l].push_back(AmrPoint{r, (int)o});
+        m.clear();
+      }
+    }
+    // Coarse rows whose x-midpoint the level's x-odd tasks read: base points
+    // (c_x, c_y + dy, c_z + dz) over the task's y and z stencil offsets.
+    P.xpts.assign(P.nlev, {});
+    for (int l = 1; l < P.nlev; ++l) {
+      for (const auto& t : P.ghost[l]) {
+        if (!(t.odd & AMR_COARSE) || !(t.odd & 1)) continue;
+        const Geo& G = geo[t.src];
+        auto& m = mark[t.src];
+        if (m.empty()) m.assign((size_t)G.sf, 0);
+        const int oy = (t.odd >> 1) & 1, oz = (t.odd >> 2) & 1;
+        for (int dz = oz ? -2 : 0; dz <= (oz ? 3 : 0); ++dz)
+          for (int dy = oy ? -2 : 0; dy <= (oy ? 3 : 0); ++dy) m[(size_t)(t.sofs + dz * G.sz + dy * G.sy)] = 1;
+      }
+      for (int r = 0; r < np; ++r) {
+        auto& m = mark[r];
+        if (m.empty()) continue;
+        for (size_t o = 0; o < m.size(); ++o)
+          if (m[o]) P.xpts[l].push_back(AmrPoint{r, (int)o});
         m.clear();
       }
     }

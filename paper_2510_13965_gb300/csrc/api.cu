@@ -38,6 +38,8 @@ struct grmhd_ctx {
   // per level: coarse points its prolongation stencils read (sub-cycling)
   AmrPoint* amr_tp = nullptr;
   std::vector<long long> amr_tofs, amr_tcnt;
+  // per level: coarse rows whose x-midpoints its prolongations read (in amr_tp)
+  std::vector<long long> amr_xofs, amr_xcnt;
   std::string amr_sub_err;
   // sub-cycling in time (grmhd_set_subcycling): dense-output registers
   bool subcycle = false;
@@ -287,6 +289,13 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
       c->amr_tcnt[l] = (long long)plan.tpts[l].size();
       tp.insert(tp.end(), plan.tpts[l].begin(), plan.tpts[l].end());
     }
+    c->amr_xofs.assign(plan.nlev, 0);
+    c->amr_xcnt.assign(plan.nlev, 0);
+    for (int l = 1; l < plan.nlev; ++l) {
+      c->amr_xofs[l] = (long long)tp.size();
+      c->amr_xcnt[l] = (long long)plan.xpts[l].size();
+      tp.insert(tp.end(), plan.xpts[l].begin(), plan.xpts[l].end());
+    }
     if (!tp.empty()) {
       if ((rc = cuda_ok(c, cudaMalloc(&c->amr_tp, tp.size() * sizeof(AmrPoint)), "cudaMalloc amr points"))) {
         grmhd_destroy(c);
@@ -383,9 +392,12 @@ int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
       c->launches += 1;
     }
     for (int l = 1; l < c->amr_nlev; ++l) {
+      // The coarser level's x-midpoints once per row, then the fill (uses the
+      // coarser level's pointwise-flux scratch).
       ProfScope ps(c, K_GHOST);
-      launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st);
-      c->launches += 1;
+      launch_amr_xmid(c->pd, c->amr_tp + c->amr_xofs[l], c->amr_xcnt[l], reg, c->st);
+      launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st, -1, true);
+      c->launches += 2;
     }
     return check_launch(c, "ghost hierarchy");
   }
@@ -616,8 +628,9 @@ static int sub_advance(grmhd_ctx* c, int l, int msub, double dt) {
         double cf[NDENSE];
         bor_coef(c->P.rk, msub, s, cf);
         launch_amr_time(c->pd, c->amr_tp + c->amr_tofs[l], c->amr_tcnt[l], cf, nd, 3, c->st);
-        launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st, 3);
-        c->launches += 2;
+        launch_amr_xmid(c->pd, c->amr_tp + c->amr_xofs[l], c->amr_xcnt[l], 3, c->st);
+        launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st, 3, true);
+        c->launches += 3;
       }
     }
     if ((rc = check_launch(c, "sub-cycled ghost fill"))) return rc;

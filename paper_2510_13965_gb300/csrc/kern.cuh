@@ -145,6 +145,7 @@ struct AmrPlan {
   std::vector<std::vector<AmrTask>> restr;  // per level (0 unused): restriction into level - 1
   std::vector<long long> nsame;             // per level: leading same-level copies among its ghost tasks
   std::vector<std::vector<AmrPoint>> tpts;  // per level (0 unused): coarse points its stencils read, unique
+  std::vector<std::vector<AmrPoint>> xpts;  // per level (0 unused): coarse rows whose x-midpoints it reads
   std::string err;
   // Empty when every prolongation stencil point lies in an interior of the
   // coarser level (or in the level-0 patch's ghosts), which sub-cycling needs.
@@ -152,8 +153,13 @@ struct AmrPlan {
 };
 int amr_plan(const grmhd_patch_desc* d, const std::vector<Geo>& geo, int np, AmrPlan& P);
 // Ghost fill or restriction tasks on register reg; coarse-source tasks read
-// register reg_coarse of their source (reg_coarse < 0: reg).
-void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, cudaStream_t st, int reg_coarse = -1);
+// register reg_coarse of their source (reg_coarse < 0: reg).  xpre: the
+// x-midpoints of the coarse rows were computed by launch_amr_xmid into the
+// source patches' Fp scratch (same values, computed once per row).
+void launch_amr(const PatchDev* pd_dev, const AmrTask* t, long long n, int reg, cudaStream_t st, int reg_coarse = -1,
+                bool xpre = false);
+// x-midpoints of register reg at the listed coarse rows into PatchDev::Fp.
+void launch_amr_xmid(const PatchDev* pd_dev, const AmrPoint* pts, long long n, int reg, cudaStream_t st);
 // Sub-cycling: register reg_t of each listed coarse point receives the
 // stage value sum_d coef[d] U[REG_DENSE + d] (nd terms).
 void launch_amr_time(const PatchDev* pd_dev, const AmrPoint* pts, long long n, const double coef[NDENSE], int nd,
