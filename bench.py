@@ -42,10 +42,10 @@ WORKLOAD = "tov_magnetised_128^3_rk4_step"
 RHS_FLOPS_PER_POINT = 6724.0
 RK_FLOPS_PER_POINT = (128.0 * 3 + 64.0) / 4.0
 # DRAM bytes (read + write) per interior point of one k_rhs launch, from the
-# ncu capture in profiles/substep_kernels_tov64_ncu_full.md (64^3 case,
-# 195.1 + 232.1 MB over 262,144 points), scaled to a launch by its points;
+# ncu capture in profiles/launch_list_tov128.md (64^3 case, k_rhs<1, 128>,
+# 192.75 + 208.55 MB over 262,144 points), scaled to a launch by its points;
 # set to None whenever k_rhs changes until it is captured again.
-RHS_TRAFFIC_BYTES_PER_POINT = (195.1e6 + 232.1e6) / 64 ** 3
+RHS_TRAFFIC_BYTES_PER_POINT = (192.75e6 + 208.55e6) / 64 ** 3
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 4 FP64 flops per
 # clock per SM x 2070 MHz (nominal GB300 FP64 1.25 TFLOP/s = 152 x 2.07 GHz x 3.97).
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
