@@ -150,12 +150,18 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
     for (int f = 0; f < LES_NAUX; ++f) gr[a][f] = dgrad(A + f * sf, st[a], idx[a], nn[a], G.dx);
   double gdd[6], guu[6], sg, det;
   metric(U, o, sf, gdd, guu, &sg, &det);
-  auto dot = [&](int f1, int f2) {
-    double s = 0.0;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) s += guu[S6(a, b)] * gr[a][f1] * gr[b][f2];
-    return s;
-  };
+  // gamma^{ab} = L L^T (Cholesky); with each gradient replaced by L^T d f,
+  // grad f . grad g = gamma^{ab} d_a f d_b g is a plain three-term sum.
+  const double L00 = sqrt(guu[0]), L10 = guu[1] / L00, L20 = guu[2] / L00;
+  const double L11 = sqrt(guu[3] - L10 * L10), L21 = (guu[4] - L20 * L10) / L11;
+  const double L22 = sqrt(guu[5] - L20 * L20 - L21 * L21);
+  for (int f = 0; f < LES_NAUX; ++f) {
+    const double d0 = gr[0][f], d1 = gr[1][f], d2 = gr[2][f];
+    gr[0][f] = L00 * d0 + L10 * d1 + L20 * d2;
+    gr[1][f] = L11 * d1 + L21 * d2;
+    gr[2][f] = L22 * d2;
+  }
+  auto dot = [&](int f1, int f2) { return gr[0][f1] * gr[0][f2] + gr[1][f1] * gr[1][f2] + gr[2][f1] * gr[2][f2]; };
   auto val = [&](int f) { return A[f * sf]; };
   const double rho = val(A_RHO), p = val(A_P), D = val(A_D), DY = val(A_DY), cE = val(A_CE), Th = val(A_TH);
   const double vB = val(A_VB), dpdr = val(A_PR), dpde = val(A_PE), dpdy = val(A_PY);
