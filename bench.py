@@ -77,6 +77,9 @@ def _args():
                    help="tov workload: keep 128-thread blocks instead of the library's timed choice")
     a.add_argument("--les-cm", type=float, default=0.0,
                    help="tov workload: LES gradient SGS model with C_M (the paper's default is 8)")
+    a.add_argument("--amr-run", type=int, default=0,
+                   help="amr workload: then advance this many finest-level steps (the configuration's run is 200; "
+                        "with --amr-subcycle as level-0 steps of 2^L of them) and report the central density")
     a.add_argument("--amr-subcycle", action="store_true",
                    help="amr workload: also time sub-cycled steps (BOR) over the same physical time")
     a.add_argument("--edge", type=int, default=N_EDGE,
@@ -774,6 +777,42 @@ def run_amr(args):
                      "kernel_ms_per_step": {k: v[0] for k, v in prof_c.items() if v[1]},
                      "gpu_launches": int(lc), "status": pt.sync_status()}
         pt.set_subcycling(False)
+    run = None
+    if args.amr_run > 0:
+        # The configuration's run length from the state the timing left: the
+        # star's central rest-mass density (the finest level's point at the
+        # origin) before and after, and the device status.
+        nlev = max(levels) + 1
+        pc, ijk = None, None
+        for q, s_ in enumerate(specs):
+            if s_["level"] != nlev - 1:
+                continue
+            idx = [int(round(-s_["x0"][a] / s_["dx"])) for a in range(3)]
+            if all(0 <= idx[a] < s_["n"][a] for a in range(3)):
+                pc, ijk = q, idx
+                break
+        pt.set_seeder(None)
+        pt.con2prim(0)
+        pt.synchronize()
+        rho0 = float(pt.prim[pc][0, ijk[2] + 3, ijk[1] + 3, ijk[0] + 3])
+        sub = bool(args.amr_subcycle)
+        per = 2 ** (nlev - 1) if sub else 1
+        nstep = max(1, args.amr_run // per)
+        pt.set_subcycling(sub)
+        pt.capture_graph(1, dt * per)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(nstep):
+            pt.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        run_s = e0.elapsed_time(e1) / 1e3
+        pt.set_subcycling(False)
+        pt.con2prim(0)
+        pt.synchronize()
+        rho1 = float(pt.prim[pc][0, ijk[2] + 3, ijk[1] + 3, ijk[0] + 3])
+        run = {"finest_steps": nstep * per, "subcycled": sub, "simulated_time": nstep * per * dt, "seconds": run_s,
+               "rho_c": [rho0, rho1], "rho_c_drift": rho1 / rho0 - 1.0, "status": pt.sync_status()}
     line = {"metric": METRIC, "value": zones / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -790,6 +829,8 @@ def run_amr(args):
         line["nn_seeded"] = seeded
     if subcycled is not None:
         line["subcycled"] = subcycled
+    if run is not None:
+        line["run"] = run
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_amr()
     print(json.dumps(line), flush=True)

@@ -122,11 +122,12 @@ typedef struct grmhd_params {
    * of D, DYe, S_i and B^i (the paper's default: C_M = 8, the others 0); all
    * zero: no LES terms.  With any nonzero, every pointwise MHD flux along d
    * gains alpha C xi sqrt(gamma) H^d (xi = gamma^{1/3} dx^2 / 24) before the
-   * reconstruction.  The ideal gas and the hybrid EOS only (the table's
-   * pressure derivatives are not provided): grmhd_init_patches returns
-   * GRMHD_ERR_ARG for eos_kind 1 with LES, and so does grmhd_rhs_eval_static
-   * for any LES coefficient (its point values need scratch memory); a patch
-   * context allocates LES_NAUX = 32 doubles per ghosted point for them. */
+   * reconstruction.  The pressure derivatives are analytic for the ideal gas
+   * and the hybrid EOS and central differences of the table (steps 1e-4 rho,
+   * 1e-4 eps, 1e-4 in Ye) for eos_kind 1.  grmhd_rhs_eval_static returns
+   * GRMHD_ERR_ARG for any LES coefficient (its point values need scratch
+   * memory); a patch context allocates LES_NAUX = 32 doubles per ghosted
+   * point for them. */
   double les_c[4];
   /* A flux point whose rest-mass density is below les_rho_min gets no SGS
    * flux (0: everywhere).  The paper states no rule for low densities; in an

@@ -80,8 +80,8 @@ def lib(flops=False):
             "oracle_ghost_fill": (i, [vp, vp, i, vp, i]),
             "oracle_init_state": (i, [vp, vp, vp, i, d, vp, vp]),
             "oracle_con2prim_patch": (i, [vp, vp, vp, i, vp, vp, vp, vp]),
-            "oracle_rhs_patch": (i, [vp, vp, i, d, vp, vp, vp]),
-            "oracle_rhs_points": (i, [vp, vp, i, d, vp, vp, i, vp, vp]),
+            "oracle_rhs_patch": (i, [vp, vp, vp, i, d, vp, vp, vp]),
+            "oracle_rhs_points": (i, [vp, vp, vp, i, d, vp, vp, i, vp, vp]),
             "oracle_geom_point": (i, [vp, vp, i, d, vp, vp, i, i, i, vp, vp, vp, vp]),
             "oracle_substep": (i, [vp, vp, vp, i, d, i, d, vp, vp, vp, vp, vp, vp]),
             "oracle_rk4_step": (i, [vp, vp, vp, i, d, d, vp, vp, vp, vp, vp, vp]),
@@ -97,7 +97,8 @@ def lib(flops=False):
             "oracle_hier_ghost_fill": (i, [vp, i, vp, vp, vp]),
             "oracle_hier_restrict": (i, [i, vp, vp, vp]),
             "oracle_hier_rk4_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
-            "oracle_les_flux_points": (i, [vp, vp, i, d, vp, vp, i, vp, i, vp]),
+            "oracle_eos_derivs": (i, [vp, vp, d, d, d, vp]),
+            "oracle_les_flux_points": (i, [vp, vp, vp, i, d, vp, vp, i, vp, i, vp]),
             "oracle_hier_rk4_step_mask": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp, i]),
             "oracle_hier_subcycle_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
             "oracle_dense_derivs": (None, [i, vp, vp]),
@@ -173,13 +174,13 @@ class Oracle:
 
     def rhs_patch(self, U, prim, n, dx):
         rhs = np.zeros_like(U)
-        self.L.oracle_rhs_patch(_ref(self.P), _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)), _p(rhs))
+        self.L.oracle_rhs_patch(_ref(self.P), self.Tp, _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)), _p(rhs))
         return rhs
 
     def rhs_points(self, U, prim, n, dx, ijk):
         ijk = np.ascontiguousarray(ijk, dtype=np.int32)
         out = np.zeros((ijk.shape[0], NF))
-        self.L.oracle_rhs_points(_ref(self.P), _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)),
+        self.L.oracle_rhs_points(_ref(self.P), self.Tp, _n3(n), U.shape[-1], dx, _p(_chk(U)), _p(_chk(prim)),
                                  ijk.shape[0], _p(ijk), _p(out))
         return out
 
@@ -244,6 +245,13 @@ class Oracle:
                                    float(delta), _p(roots), _p(seeded))
         return prim, status, iters, roots, seeded
 
+    def eos_derivs(self, rho, eps, ye):
+        """(dp/drho|eps, dp/deps|rho, dp/dYe) of the EOS at one state."""
+        out = np.zeros(3)
+        if self.L.oracle_eos_derivs(_ref(self.P), self.Tp, float(rho), float(eps), float(ye), _p(out)):
+            raise ValueError("no pressure derivatives for this EOS")
+        return out
+
     def les_flux_points(self, U, prim, n, dx, ijk, d):
         """LES SGS flux vectors along d at points ijk ([m][3] ints): [m][10]."""
         n3 = _n3(n)
@@ -251,10 +259,10 @@ class Oracle:
         prim = _chk(prim)
         pts = np.ascontiguousarray(ijk, dtype=np.int32)
         out = np.zeros((pts.shape[0], 10))
-        rc = self.L.oracle_les_flux_points(_ref(self.P), n3, U.shape[-1], dx, _p(U), _p(prim), pts.shape[0],
+        rc = self.L.oracle_les_flux_points(_ref(self.P), self.Tp, n3, U.shape[-1], dx, _p(U), _p(prim), pts.shape[0],
                                            _p(pts), int(d), _p(out))
         if rc:
-            raise ValueError("LES terms need an EOS with pressure derivatives (ideal gas or hybrid)")
+            raise ValueError("LES terms need the EOS's pressure derivatives (a table kind needs its table)")
         return out
 
     def eos_from_eps(self, rho, eps, ye):

@@ -38,20 +38,21 @@ int oracle_con2prim_patch(const oracle_params* P, const oracle_eos_table* E, con
   return c2p_patch(P, E, make_grid(n, px, 1.0), U, prim, status, iters);
 }
 
-int oracle_rhs_patch(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
-                     double* rhs) {
-  rhs_patch(P, make_grid(n, px, dx), U, prim, rhs, nullptr);
+// E: the table (eos_kind 1; its pressure derivatives enter the LES terms) or null.
+int oracle_rhs_patch(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx,
+                     const double* U, const double* prim, double* rhs) {
+  rhs_patch(P, E, make_grid(n, px, dx), U, prim, rhs, nullptr);
   return 0;
 }
 
 // Right-hand side at a list of interior points; out is [npts][32].
-int oracle_rhs_points(const oracle_params* P, const int* n, int px, double dx, const double* U, const double* prim,
-                      int npts, const int* ijk, double* out) {
+int oracle_rhs_points(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx,
+                      const double* U, const double* prim, int npts, const int* ijk, double* out) {
   grid G = make_grid(n, px, dx);
   std::vector<double> aux;
   if (les_on(P)) {
     aux.assign((size_t)les_naux() * G.sf, 0.0);
-    if (les_aux_patch(P, G, U, prim, aux.data())) return -1;
+    if (les_aux_patch(P, E, G, U, prim, aux.data())) return -1;
   }
   for (int q = 0; q < npts; ++q) {
     real r[NF];
@@ -61,14 +62,25 @@ int oracle_rhs_points(const oracle_params* P, const int* n, int px, double dx, c
   return 0;
 }
 
+// dp/drho|eps, dp/deps|rho, dp/dYe at one state (out[3]); -1 when unavailable.
+int oracle_eos_derivs(const oracle_params* P, const oracle_eos_table* E, double rho, double eps, double ye,
+                      double* out) {
+  real a, b, c;
+  if (eos_derivs(P, E, rho, eps, ye, &a, &b, &c)) return -1;
+  out[0] = dbl(a);
+  out[1] = dbl(b);
+  out[2] = dbl(c);
+  return 0;
+}
+
 // LES SGS flux vectors along d (added to the MHD fluxes) at a list of points
 // (interior, or ghost points along d); out is [npts][10].  Returns -1 when the
-// EOS provides no pressure derivatives.
-int oracle_les_flux_points(const oracle_params* P, const int* n, int px, double dx, const double* U,
-                           const double* prim, int npts, const int* ijk, int d, double* out) {
+// EOS derivatives are unavailable (eos_kind 1 without its table).
+int oracle_les_flux_points(const oracle_params* P, const oracle_eos_table* E, const int* n, int px, double dx,
+                           const double* U, const double* prim, int npts, const int* ijk, int d, double* out) {
   grid G = make_grid(n, px, dx);
   std::vector<double> aux((size_t)les_naux() * G.sf, 0.0);
-  if (les_aux_patch(P, G, U, prim, aux.data())) return -1;
+  if (les_aux_patch(P, E, G, U, prim, aux.data())) return -1;
   for (int q = 0; q < npts; ++q) {
     real F[10];
     les_flux_point(P, G, U, aux.data(), ijk[3 * q], ijk[3 * q + 1], ijk[3 * q + 2], d, F);

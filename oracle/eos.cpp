@@ -95,8 +95,20 @@ static eos_state hybrid_from_eps(const oracle_params* P, real rho, real eps) {
   return s;
 }
 
-int eos_derivs(const oracle_params* P, real rho, real eps, real* dpdrho, real* dpdeps, real* dpdye) {
+int eos_derivs(const oracle_params* P, const oracle_eos_table* E, real rho, real eps, real ye, real* dpdrho,
+                real* dpdeps, real* dpdye) {
   // Partial derivatives of p(rho, eps, Ye) (needed by the LES terms).
+  if (P->eos_kind == 1) {
+    // Tabulated EOS: numerical (the paper's remark on the LES terms), central
+    // differences of the table's p(rho, eps, Ye) with steps 1e-4 rho, 1e-4 eps
+    // and 1e-4 in Ye.
+    if (!E) return -1;
+    const real hr = 1e-4 * rho, he = 1e-4 * eps, hy = 1e-4;
+    *dpdrho = (eos_from_eps(P, E, rho + hr, eps, ye).p - eos_from_eps(P, E, rho - hr, eps, ye).p) / (2.0 * hr);
+    *dpdeps = (eos_from_eps(P, E, rho, eps + he, ye).p - eos_from_eps(P, E, rho, eps - he, ye).p) / (2.0 * he);
+    *dpdye = (eos_from_eps(P, E, rho, eps, ye + hy).p - eos_from_eps(P, E, rho, eps, ye - hy).p) / (2.0 * hy);
+    return 0;
+  }
   *dpdye = 0.0;
   if (P->eos_kind == 0) {
     *dpdrho = (P->gamma_th - 1.0) * eps;
@@ -111,7 +123,7 @@ int eos_derivs(const oracle_params* P, real rho, real eps, real* dpdrho, real* d
     *dpdeps = gth * rho;
     return 0;
   }
-  return -1;  // tabulated EOS: not provided
+  return -1;
 }
 
 real eos_eps_min(const oracle_params* P, const oracle_eos_table* E, real rho, real ye) {

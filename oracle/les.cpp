@@ -45,7 +45,8 @@ void metric_at(const double* U, long o, long sf, real gdd[6], real guu[6], real*
 }
 
 // The point values whose gradients the closed forms use.
-int aux_point(const oracle_params* P, const double* U, const double* prim, long o, long sf, double* a, long sa) {
+int aux_point(const oracle_params* P, const oracle_eos_table* E, const double* U, const double* prim, long o, long sf,
+              double* a, long sa) {
   real gdd[6], guu[6], sg, det;
   metric_at(U, o, sf, gdd, guu, &sg, &det);
   real rho = prim[P_RHO * sf + o], eps = prim[P_EPS * sf + o], p = prim[P_P * sf + o];
@@ -68,7 +69,7 @@ int aux_point(const oracle_params* P, const double* U, const double* prim, long 
   real Eu[3];
   for (int i = 0; i < 3; ++i) Eu[i] = guu[sym(i, 0)] * Ed[0] + guu[sym(i, 1)] * Ed[1] + guu[sym(i, 2)] * Ed[2];
   real dpdr, dpde, dpdy;
-  if (eos_derivs(P, rho, eps, &dpdr, &dpde, &dpdy)) return -1;
+  if (eos_derivs(P, E, rho, eps, ye, &dpdr, &dpde, &dpdy)) return -1;
   real D = rho * W;
   real vals[NAUX];
   vals[A_RHO] = rho;
@@ -116,13 +117,15 @@ bool les_on(const oracle_params* P) {
 long les_naux() { return NAUX; }
 
 // Auxiliary point values on every point of the ghosted patch; aux is
-// [NAUX][sf].  Returns -1 when the EOS provides no derivatives (table).
-int les_aux_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* aux) {
+// [NAUX][sf].  Returns -1 when the EOS derivatives are unavailable (a table
+// kind without its table).
+int les_aux_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* U,
+                  const double* prim, double* aux) {
   for (int k = -NG; k < G.n[2] + NG; ++k)
     for (int j = -NG; j < G.n[1] + NG; ++j)
       for (int i = -NG; i < G.n[0] + NG; ++i) {
         long o = G.at(i, j, k);
-        if (aux_point(P, U, prim, o, G.sf, aux + o, G.sf)) return -1;
+        if (aux_point(P, E, U, prim, o, G.sf, aux + o, G.sf)) return -1;
       }
   return 0;
 }
@@ -194,13 +197,16 @@ void les_flux_point(const oracle_params* P, const grid& G, const double* U, cons
   real PsiA = W2 * (p * dpde + rho * rho * dpdr);
   // H_p.
   real giW2 = dot(A_IW2, A_IW2);
-  real brace = rho * (dot(A_PR, A_RHO) + dot(A_PE, A_EPS)) - 2.0 * dpde * dot(A_RHO, A_EPS) -
+  // The Ye terms stand inside the braces with the factor rho, beside the rho
+  // and eps terms (reading of the printed H_p, whose Ye line follows the
+  // closing brace; that placement fails the gradient-model check).
+  real brace = rho * (dot(A_PR, A_RHO) + dot(A_PE, A_EPS)) - 2.0 * dpde * dot(A_RHO, A_EPS) +
+               rho * (dot(A_PY, A_YE) - 2.0 / D * dpdy * dot(A_YE, A_D)) -
                (cE * dpde - PsiA) * (W2 / 4.0 * giW2 + dot(A_IW2, A_RHO) / rho) -
                2.0 / W2 * dpde * (gBgB - W2 * W2 * dot(A_IW2, A_H)) -
                (cE * dpde + PsiA) * (vPsi + gvgv + W2 * giW2) +
                Psi_Th / (cE * Th) * ((cE * dpde + PsiA) * (Th - E2) - PsiA * Th / W2);
-  real Hp = cE * W2 * (Th - E2) / ((rho * cE - PsiA) * (Th - E2) * W2 + PsiA * Th) * brace + dot(A_PY, A_YE) -
-            2.0 / D * dpdy * dot(A_YE, A_D);
+  real Hp = cE * W2 * (Th - E2) / ((rho * cE - PsiA) * (Th - E2) * W2 + PsiA * Th) * brace;
   real HTh = Psi_Th + Th / (Th - E2) * Hp;
   real Hv[3];
   for (int kk = 0; kk < 3; ++kk) Hv[kk] = Psi_v[kk] - (vu[kk] + vB / cE * Bu[kk]) * HTh / Th;

@@ -117,8 +117,8 @@ void ghost_fill(const oracle_params* P, const grid& G, double* U, int nf);
 void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* ID, double* U);
 int c2p_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, double* U, double* prim,
               int8_t* status, long* iters_total);
-void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs,
-               long long* counts);
+void rhs_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* U, const double* prim,
+               double* rhs, long long* counts);
 int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, int stage, double dt, double* Un,
             double* Ua, double* Ub, double* acc, double* prim, int8_t* status, double* krhs, long long* counts);
 
@@ -133,9 +133,10 @@ eos_state eos_from_eps(const oracle_params* P, const oracle_eos_table* E, real r
 // p, eps, cs2 from (rho, T, ye) (table) or the cold/atmosphere branch for the ideal gas.
 eos_state eos_from_T(const oracle_params* P, const oracle_eos_table* E, real rho, real T, real ye);
 eos_state eos_atmosphere(const oracle_params* P, const oracle_eos_table* E);
-// dp/drho|eps, dp/deps|rho, dp/dYe for the ideal gas and the hybrid EOS;
-// returns -1 for the tabulated EOS.
-int eos_derivs(const oracle_params* P, real rho, real eps, real* dpdrho, real* dpdeps, real* dpdye);
+// dp/drho|eps, dp/deps|rho, dp/dYe: analytic for the ideal gas and the
+// hybrid EOS, central differences of the table otherwise (-1 without one).
+int eos_derivs(const oracle_params* P, const oracle_eos_table* E, real rho, real eps, real ye, real* dpdrho,
+               real* dpdeps, real* dpdye);
 
 // ---- metric helpers -------------------------------------------------------
 real det_sym(const real g[6]);
@@ -197,6 +198,7 @@ void rhs_point(const oracle_params* P, const grid& G, const double* U, const dou
 // ---- LES gradient SGS model (les.cpp) ------------------------------------
 bool les_on(const oracle_params* P);
 long les_naux();
-int les_aux_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* aux);
+int les_aux_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* U,
+                  const double* prim, double* aux);
 void les_flux_point(const oracle_params* P, const grid& G, const double* U, const double* aux, int i, int j, int k,
                     int d, real F[10]);

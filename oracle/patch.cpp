@@ -188,8 +188,8 @@ static long long flops_now() { return 0; }
 
 // counts (optional): flops of [pointwise fluxes, interface fluxes, local terms
 // (CCZ4 + sources + flux difference)] in the counting build.
-void rhs_patch(const oracle_params* P, const grid& G, const double* U, const double* prim, double* rhs,
-               long long* counts) {
+void rhs_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* U, const double* prim,
+               double* rhs, long long* counts) {
   long long c0 = flops_now(), c_pt = 0, c_if = 0;
   const long st[3] = {1, G.sy, G.sz};
   const long npts = G.sf;
@@ -200,7 +200,7 @@ void rhs_patch(const oracle_params* P, const grid& G, const double* U, const dou
   std::vector<double> aux;
   if (les_on(P)) {
     aux.assign((size_t)les_naux() * npts, 0.0);
-    les_aux_patch(P, G, U, prim, aux.data());
+    les_aux_patch(P, E, G, U, prim, aux.data());
   }
   for (int d = 0; d < 3; ++d) {
     int lo[3] = {0, 0, 0}, hi[3] = {G.n[0], G.n[1], G.n[2]};
@@ -306,7 +306,7 @@ int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, in
   long long t0 = flops_now();
   int worst = c2p_patch(P, E, G, in, prim, status, nullptr);
   long long t1 = flops_now();
-  rhs_patch(P, G, in, prim, krhs, counts ? counts + 1 : nullptr);
+  rhs_patch(P, E, G, in, prim, krhs, counts ? counts + 1 : nullptr);
   long long t2 = flops_now();
   real hdt = 0.5 * dt, sdt = dt / 6.0, tdt = dt / 3.0;
   for (int f = 0; f < NF; ++f)

@@ -149,7 +149,6 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   *out = nullptr;
   if (!p || !d || npatch <= 0) return GRMHD_ERR_ARG;
   if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
-  if (les_on(*p) && p->eos_kind == 1) return GRMHD_ERR_ARG;  // no pressure derivatives of the table
   if (p->bc < 0 || p->bc > 3) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (p->rk != 0 && p->rk != 1) return GRMHD_ERR_ARG;

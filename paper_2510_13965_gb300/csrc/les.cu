@@ -42,9 +42,18 @@ DI void metric(const double* U, long long o, long long sf, double gdd[6], double
   *sg = sqrt(*det);
 }
 
-// dp/drho|eps and dp/deps|rho of the ideal gas and the hybrid EOS (the
-// hybrid's cold part: deps_c/drho = p_c / rho^2); dp/dYe = 0 for both.
-DI void eos_derivs(const Eos& E, double rho, double eps, double* dpdr, double* dpde) {
+// dp/drho|eps, dp/deps|rho and dp/dYe: analytic for the ideal gas and the
+// hybrid EOS (the hybrid's cold part: deps_c/drho = p_c / rho^2; dp/dYe = 0),
+// numerical for the table (the paper's remark on the LES terms): central
+// differences of its p(rho, eps, Ye) with steps 1e-4 rho, 1e-4 eps, 1e-4.
+DI void eos_derivs(const Eos& E, double rho, double eps, double ye, double* dpdr, double* dpde, double* dpdy) {
+  if (E.kind == 1) {
+    const double hr = 1e-4 * rho, he = 1e-4 * eps, hy = 1e-4;
+    *dpdr = (eos_eps(E, rho + hr, eps, ye).p - eos_eps(E, rho - hr, eps, ye).p) / (2.0 * hr);
+    *dpde = (eos_eps(E, rho, eps + he, ye).p - eos_eps(E, rho, eps - he, ye).p) / (2.0 * he);
+    *dpdy = (eos_eps(E, rho, eps, ye + hy).p - eos_eps(E, rho, eps, ye - hy).p) / (2.0 * hy);
+    return;
+  }
   const double gth = E.gam - 1.0;
   if (E.kind == 2) {
     const HybCold c = hyb_cold(E, rho);
@@ -53,6 +62,7 @@ DI void eos_derivs(const Eos& E, double rho, double eps, double* dpdr, double* d
     *dpdr = gth * eps;
   }
   *dpde = gth * rho;
+  *dpdy = 0.0;
 }
 
 __global__ void __launch_bounds__(128) k_les_aux(const PatchDev* __restrict__ pd, const Work* __restrict__ w, Eos E,
@@ -88,8 +98,8 @@ __global__ void __launch_bounds__(128) k_les_aux(const PatchDev* __restrict__ pd
                         sg * (v[0] * B[1] - v[1] * B[0])};
   double Eu[3];
   lower3(guu, Ed, Eu);
-  double dpdr, dpde;
-  eos_derivs(E, rho, eps, &dpdr, &dpde);
+  double dpdr, dpde, dpdy;
+  eos_derivs(E, rho, eps, ye, &dpdr, &dpde, &dpdy);
   const double D = rho * W;
   double* A = PD.les + o;
   A[A_RHO * sf] = rho;
@@ -104,7 +114,7 @@ __global__ void __launch_bounds__(128) k_les_aux(const PatchDev* __restrict__ pd
   A[A_VB * sf] = vB;
   A[A_PR * sf] = dpdr;
   A[A_PE * sf] = dpde;
-  A[A_PY * sf] = 0.0;
+  A[A_PY * sf] = dpdy;
   A[A_P * sf] = p;
   for (int a = 0; a < 3; ++a) {
     A[(A_VU + a) * sf] = v[a];
@@ -212,13 +222,15 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
   const double Psi_Th = Th / (Th - E2) * (gBgB - gEgE - BvPsi);
   const double PsiA = W2 * (p * dpde + rho * rho * dpdr);
   const double giW2 = dot(A_IW2, A_IW2);
-  const double brace = rho * (dot(A_PR, A_RHO) + dot(A_PE, A_EPS)) - 2.0 * dpde * dot(A_RHO, A_EPS) -
+  // H_p's Ye terms stand inside the braces with the factor rho, beside the
+  // rho and eps terms (where the gradient model puts them).
+  const double brace = rho * (dot(A_PR, A_RHO) + dot(A_PE, A_EPS)) - 2.0 * dpde * dot(A_RHO, A_EPS) +
+                       rho * (dot(A_PY, A_YE) - 2.0 / D * dpdy * dot(A_YE, A_D)) -
                        (cE * dpde - PsiA) * (W2 / 4.0 * giW2 + dot(A_IW2, A_RHO) / rho) -
                        2.0 / W2 * dpde * (gBgB - W2 * W2 * dot(A_IW2, A_H)) -
                        (cE * dpde + PsiA) * (vPsi + gvgv + W2 * giW2) +
                        Psi_Th / (cE * Th) * ((cE * dpde + PsiA) * (Th - E2) - PsiA * Th / W2);
-  const double Hp = cE * W2 * (Th - E2) / ((rho * cE - PsiA) * (Th - E2) * W2 + PsiA * Th) * brace +
-                    dot(A_PY, A_YE) - 2.0 / D * dpdy * dot(A_YE, A_D);
+  const double Hp = cE * W2 * (Th - E2) / ((rho * cE - PsiA) * (Th - E2) * W2 + PsiA * Th) * brace;
   const double HTh = Psi_Th + Th / (Th - E2) * Hp;
   double Hv[3];
   for (int a = 0; a < 3; ++a) Hv[a] = Psi_v[a] - (vu[a] + vB / cE * Bu[a]) * HTh / Th;

@@ -51,12 +51,12 @@ def _case(kind):
     return P, 7e-4, (lambda rho: O.eos_from_T(float(rho), 0.0, 0.1)[1])
 
 
-def _brute(O, g6, x, rho0, eps_of):
+def _brute(O, g6, x, fields):
     g = _mat(g6)
     gu = np.linalg.inv(g)
 
     def prim_vec(xx):
-        rho, eps, v, B, ye = _fields(xx, rho0, eps_of)
+        rho, eps, v, B, ye = fields(xx)
         return np.concatenate([[rho, eps], v, B, [ye]])
 
     def cons(q):
@@ -138,7 +138,7 @@ def test_closed_forms_match_the_gradient_model(kind, metric):
     assert np.all(st == 0)
     c = (4, 4, 4)
     xc = x0 + dx * np.array(c)
-    Hb = _brute(O, g6, xc, rho0, eps_of)
+    Hb = _brute(O, g6, xc, lambda xx: _fields(xx, rho0, eps_of))
     sg = np.sqrt(np.linalg.det(_mat(g6)))
     xi = np.linalg.det(_mat(g6)) ** (1 / 3) * dx * dx / 24
     for d in range(3):
@@ -165,14 +165,86 @@ def test_les_terms_touch_only_the_fluxed_conserved_fields():
         assert not np.array_equal(r0[f], r1[f]), f
 
 
-def test_tabulated_eos_is_refused():
-    table = synth.make_table(nr=16, nt=12, ny=6)
+def _table_case():
+    table = synth.make_table(nr=64, nt=48, ny=16)
     P = synth.table_params(table, bc=1)
-    P["les_c"] = (0.0, 0.0, 0.0, 8.0)
+    # A point in the middle of one table cell of (log10 rho, log10 T, Ye), where
+    # radiation and gas pressure are comparable (rho ~ 1e-7, T ~ 10 MeV): there
+    # dp/dYe at fixed eps is not small (for the gas alone p = 2/3 rho eps).
+    lr = table["lr0"] + table["dlr"] * 36.5
+    lt = table["lt0"] + table["dlt"] * 31.5
+    ye0 = table["ye0"] + table["dye"] * 4.5
+    return table, P, lr, lt, ye0
+
+
+def test_table_pressure_derivatives_against_the_model():
+    table, P, lr, lt, ye0 = _table_case()
     O = oracle.Oracle(P, table)
-    U = np.zeros((32, 10, 10, 10))
-    with pytest.raises(ValueError):
-        O.les_flux_points(U, np.zeros((NP, 10, 10, 10)), (4, 4, 4), 0.1, [[0, 0, 0]], 0)
+    rho, T, ye = 10.0 ** lr, 10.0 ** lt, ye0
+    eps = O.eos_from_T(rho, T, ye)[1]
+    d = O.eos_derivs(rho, eps, ye)
+
+    def p_model(r, e, y):
+        # invert the analytic model for T at (r, y) so that its eps is e
+        lo, hi = -3.0, 3.0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if synth.eos_table.model(r, 10.0 ** mid, y)[1] < e:
+                lo = mid
+            else:
+                hi = mid
+        return synth.eos_table.model(r, 10.0 ** lo, y)[0]
+
+    h = 1e-4
+    want = [(p_model(rho * (1 + h), eps, ye) - p_model(rho * (1 - h), eps, ye)) / (2 * h * rho),
+            (p_model(rho, eps * (1 + h), ye) - p_model(rho, eps * (1 - h), ye)) / (2 * h * eps),
+            (p_model(rho, eps, ye + h) - p_model(rho, eps, ye - h)) / (2 * h)]
+    for a, b in zip(d, want):
+        assert a == pytest.approx(b, rel=0.05), (d, want)
+
+
+def test_closed_forms_match_the_gradient_model_table():
+    table, P, lr, lt, ye0 = _table_case()
+    P["les_c"] = (1.0, 1.0, 1.0, 1.0)
+    O = oracle.Oracle(P, table)
+    g6 = GDD_CURVED
+
+    def fields(x):
+        X, Y, Z = x
+        rho = 10.0 ** lr * (1 + 0.02 * np.sin(2.1 * X + 0.3) * np.cos(1.3 * Y) + 0.01 * Z)
+        T = 10.0 ** lt * (1 + 0.02 * np.cos(1.7 * X - 0.8 * Z) + 0.01 * Y)
+        ye = ye0 + 0.4 * table["dye"] * np.sin(3.0 * X + 2.1 * Y + 1.4 * Z)
+        eps = np.vectorize(lambda r, t, y: O.eos_from_T(r, t, y)[1])(rho, T, ye)
+        v = np.array([0.3 * np.sin(1.1 * Y + 0.5 * Z), 0.2 * np.cos(0.9 * X) + 0.1 * Z, -0.25 * np.sin(1.4 * X + Y)])
+        B = np.array([0.02 * np.cos(1.2 * Z + X), 0.015 * np.sin(0.8 * X - Y) + 0.01, 0.03 * np.cos(Y)]) * 1e-3
+        return rho, eps, v, B, ye, T
+
+    n, dx, x0 = (8, 8, 8), 0.01, np.array([0.09, -0.25, 0.33])
+    shp = (n[2] + 6, n[1] + 6, n[0] + 6)
+    ID = np.zeros((synth.NID,) + shp)
+    ax = [x0[a] + dx * np.arange(-3, n[a] + 3) for a in range(3)]
+    Zg, Yg, Xg = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    rho, eps, v, B, ye, T = fields((Xg, Yg, Zg))
+    for c in range(6):
+        ID[c] = g6[c]
+    ID[12] = 1.0
+    ID[16], ID[17], ID[24], ID[25] = rho, eps, ye, T
+    ID[18:21] = v
+    ID[21:24] = B
+    U = O.init_state(ID, n, dx)
+    prim, st, _, _ = O.con2prim_patch(U, n)
+    assert np.all(st == 0)
+    c = (4, 4, 4)
+    xc = x0 + dx * np.array(c)
+    Hb = _brute(O, g6, xc, lambda xx: fields(xx)[:5])
+    sg = np.sqrt(np.linalg.det(_mat(g6)))
+    xi = np.linalg.det(_mat(g6)) ** (1 / 3) * dx * dx / 24
+    for d in range(3):
+        F = O.les_flux_points(U, prim, n, dx, [c], d)[0]
+        Ho = np.concatenate([F[0:2], F[3:9]]) / (xi * sg)
+        for sl in (slice(0, 1), slice(1, 2), slice(2, 5), slice(5, 8)):
+            scale = np.abs(Hb[:, sl]).max()
+            assert np.abs(Ho[sl] - Hb[d, sl]).max() <= 1e-4 * scale, (d, sl, Ho[sl], Hb[d, sl])
 
 
 def test_density_switch():
