@@ -76,7 +76,7 @@ def _args():
     a.add_argument("--no-autotune", action="store_true",
                    help="tov workload: keep 128-thread blocks instead of the library's timed choice")
     a.add_argument("--les-cm", type=float, default=0.0,
-                   help="tov workload: LES gradient SGS model with C_M (the paper's default is 8)")
+                   help="tov and amr workloads: LES gradient SGS model with C_M (the paper's default is 8)")
     a.add_argument("--amr-run", type=int, default=0,
                    help="amr workload: then advance this many finest-level steps (the configuration's run is 200; "
                         "with --amr-subcycle as level-0 steps of 2^L of them) and report the central density")
@@ -660,6 +660,11 @@ def run_amr(args):
 
     table = synth.make_table()
     P = synth.table_params(table, bc=3)
+    if args.les_cm:
+        # LES gradient SGS model on the table star (numerical pressure
+        # derivatives), SGS flux above the error policy's rho_low.
+        P["les_c"] = (0.0, 0.0, 0.0, args.les_cm)
+        P["les_rho_min"] = P["rho_low"]
     T = g.Table(table)
     specs = synth.amr_tov_layout(scale=args.amr_scale)
     prof = synth.tov_profile()
@@ -816,7 +821,8 @@ def run_amr(args):
     line = {"metric": METRIC, "value": zones / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "tov_table_eos_5_level_hierarchy_%d_patches_rk4_step" % len(specs),
+            "config": {"workload": "tov_table_eos_5_level_hierarchy_%d_patches_rk4_step" % len(specs) +
+                       ("_les_cm%g" % args.les_cm if args.les_cm else ""),
                        "scale": args.amr_scale,
                        "patches": len(specs), "interior_points": zones,
                        "levels": {str(k): {"patches": v[0], "points": v[1]} for k, v in sorted(levels.items())},
