@@ -123,8 +123,8 @@ typedef struct grmhd_params {
    * zero: no LES terms.  With any nonzero, every pointwise MHD flux along d
    * gains alpha C xi sqrt(gamma) H^d (xi = gamma^{1/3} dx^2 / 24) before the
    * reconstruction.  The pressure derivatives are analytic for the ideal gas
-   * and the hybrid EOS and central differences of the table (steps 1e-4 rho,
-   * 1e-4 eps, 1e-4 in Ye) for eos_kind 1.  grmhd_rhs_eval_static returns
+   * and the hybrid EOS, and for eos_kind 1 those of the table's interpolant
+   * (linear in eps between temperature nodes, bilinear in log10 rho and Ye).  grmhd_rhs_eval_static returns
    * GRMHD_ERR_ARG for any LES coefficient (its point values need scratch
    * memory); a patch context allocates LES_NAUX = 32 doubles per ghosted
    * point for them. */

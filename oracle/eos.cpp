@@ -95,18 +95,73 @@ static eos_state hybrid_from_eps(const oracle_params* P, real rho, real eps) {
   return s;
 }
 
+// Derivatives of the table's interpolant p(rho, eps, Ye) (the paper takes the
+// tabulated EOS's derivatives numerically; these are the table's own): in the
+// located cell p = p_lo + w (p_hi - p_lo), w = (eps - e_lo) / (e_hi - e_lo),
+// with p_lo, p_hi, e_lo, e_hi the (log10 rho, Ye)-bilinear values at the T
+// nodes bracketing eps, as in eos_from_eps.  Along a clamped coordinate
+// (outside the table) the interpolant is constant.
+static void table_derivs(const oracle_eos_table* E, real rho, real eps, real ye, real* dpdrho, real* dpdeps,
+                         real* dpdye) {
+  tab_loc L = tab_locate(E, rho, ye);
+  const real fr = (log10(rho) - E->lr0) / E->dlr, fy = (ye - E->ye0) / E->dye;
+  const bool in_r = fr >= 0.0 && fr <= E->nr - 1.0, in_y = fy >= 0.0 && fy <= E->ny - 1.0;
+  int lo = 0, hi = E->nt - 1;
+  real elo = bilin(E, E->eps, L.ir, L.wr, lo, L.iy, L.wy);
+  real ehi = bilin(E, E->eps, L.ir, L.wr, hi, L.iy, L.wy);
+  if (eps <= elo) {
+    hi = 1;
+    ehi = bilin(E, E->eps, L.ir, L.wr, 1, L.iy, L.wy);
+  } else if (eps >= ehi) {
+    lo = E->nt - 2;
+    elo = bilin(E, E->eps, L.ir, L.wr, lo, L.iy, L.wy);
+  } else {
+    while (hi - lo > 1) {
+      int mid = (lo + hi) / 2;
+      real em = bilin(E, E->eps, L.ir, L.wr, mid, L.iy, L.wy);
+      if (em <= eps) {
+        lo = mid;
+        elo = em;
+      } else {
+        hi = mid;
+        ehi = em;
+      }
+    }
+  }
+  real wt = (eps - elo) / (ehi - elo);
+  const bool in_t = wt >= 0.0 && wt <= 1.0;
+  if (wt < 0.0) wt = 0.0;
+  if (wt > 1.0) wt = 1.0;
+  const real plo = bilin(E, E->p, L.ir, L.wr, lo, L.iy, L.wy);
+  const real phi = bilin(E, E->p, L.ir, L.wr, lo + 1, L.iy, L.wy);
+  // d/d(log10 rho) and d/dYe of the bilinear value of A at T node it.
+  auto d_lr = [&](const double* A, int it) {
+    real a = A[node(E, L.ir + 1, it, L.iy)] - A[node(E, L.ir, it, L.iy)];
+    real b = A[node(E, L.ir + 1, it, L.iy + 1)] - A[node(E, L.ir, it, L.iy + 1)];
+    return lerp(a, b, L.wy) / E->dlr;
+  };
+  auto d_ye = [&](const double* A, int it) {
+    real a = A[node(E, L.ir, it, L.iy + 1)] - A[node(E, L.ir, it, L.iy)];
+    real b = A[node(E, L.ir + 1, it, L.iy + 1)] - A[node(E, L.ir + 1, it, L.iy)];
+    return lerp(a, b, L.wr) / E->dye;
+  };
+  auto along = [&](real dplo, real dphi, real delo, real dehi) {
+    real dw = in_t ? -(delo + wt * (dehi - delo)) / (ehi - elo) : real(0.0);
+    return dplo + wt * (dphi - dplo) + dw * (phi - plo);
+  };
+  *dpdeps = in_t ? (phi - plo) / (ehi - elo) : real(0.0);
+  *dpdrho = in_r ? along(d_lr(E->p, lo), d_lr(E->p, lo + 1), d_lr(E->eps, lo), d_lr(E->eps, lo + 1)) /
+                       (rho * std::log(10.0))
+                 : real(0.0);
+  *dpdye = in_y ? along(d_ye(E->p, lo), d_ye(E->p, lo + 1), d_ye(E->eps, lo), d_ye(E->eps, lo + 1)) : real(0.0);
+}
+
 int eos_derivs(const oracle_params* P, const oracle_eos_table* E, real rho, real eps, real ye, real* dpdrho,
-                real* dpdeps, real* dpdye) {
+               real* dpdeps, real* dpdye) {
   // Partial derivatives of p(rho, eps, Ye) (needed by the LES terms).
   if (P->eos_kind == 1) {
-    // Tabulated EOS: numerical (the paper's remark on the LES terms), central
-    // differences of the table's p(rho, eps, Ye) with steps 1e-4 rho, 1e-4 eps
-    // and 1e-4 in Ye.
     if (!E) return -1;
-    const real hr = 1e-4 * rho, he = 1e-4 * eps, hy = 1e-4;
-    *dpdrho = (eos_from_eps(P, E, rho + hr, eps, ye).p - eos_from_eps(P, E, rho - hr, eps, ye).p) / (2.0 * hr);
-    *dpdeps = (eos_from_eps(P, E, rho, eps + he, ye).p - eos_from_eps(P, E, rho, eps - he, ye).p) / (2.0 * he);
-    *dpdye = (eos_from_eps(P, E, rho, eps, ye + hy).p - eos_from_eps(P, E, rho, eps, ye - hy).p) / (2.0 * hy);
+    table_derivs(E, rho, eps, ye, dpdrho, dpdeps, dpdye);
     return 0;
   }
   *dpdye = 0.0;

@@ -134,7 +134,8 @@ eos_state eos_from_eps(const oracle_params* P, const oracle_eos_table* E, real r
 eos_state eos_from_T(const oracle_params* P, const oracle_eos_table* E, real rho, real T, real ye);
 eos_state eos_atmosphere(const oracle_params* P, const oracle_eos_table* E);
 // dp/drho|eps, dp/deps|rho, dp/dYe: analytic for the ideal gas and the
-// hybrid EOS, central differences of the table otherwise (-1 without one).
+// hybrid EOS, the derivatives of the table's interpolant otherwise (-1
+// without a table).
 int eos_derivs(const oracle_params* P, const oracle_eos_table* E, real rho, real eps, real ye, real* dpdrho,
                real* dpdeps, real* dpdye);
 

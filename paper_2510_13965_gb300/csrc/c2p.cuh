@@ -100,22 +100,10 @@ DI double eos_emax(const Eos& E, double rho, double ye) {
   return tab_bl(tab_pos(E, rho, ye), E.e, E.nt - 1);
 }
 
-// (p, T, cs2) from (rho, eps, ye); eps inside [eps_min, eps_max].
-DI EosOut eos_eps(const Eos& E, double rho, double eps, double ye) {
-  EosOut o;
-  o.eps = eps;
-  if (E.kind == 0) {
-    o.p = (E.gam - 1.0) * rho * eps;
-    o.T = 0.0;
-    o.cs2 = E.gam * o.p / fma(rho, 1.0 + eps, o.p);
-    return o;
-  }
-  if (E.kind == 2) {
-    hyb_eps(E, hyb_cold(E, rho), rho, eps, &o.p, &o.cs2);
-    o.T = 0.0;
-    return o;
-  }
-  TabPos t = tab_pos(E, rho, ye);
+// Temperature cell of the table at a (rho, Ye) location: the nodes lo, lo+1
+// whose eps values (elo, ehi) bracket eps by binary search; the first or last
+// cell when eps lies below or above the column.
+DI void tab_tcell(const Eos& E, const TabPos& t, double eps, int* lo_, double* elo_, double* ehi_) {
   int lo = 0, hi = E.nt - 1;
   double elo = tab_bl(t, E.e, lo), ehi = tab_bl(t, E.e, hi);
   if (eps <= elo) {
@@ -137,6 +125,30 @@ DI EosOut eos_eps(const Eos& E, double rho, double eps, double ye) {
       }
     }
   }
+  *lo_ = lo;
+  *elo_ = elo;
+  *ehi_ = ehi;
+}
+
+// (p, T, cs2) from (rho, eps, ye); eps inside [eps_min, eps_max].
+DI EosOut eos_eps(const Eos& E, double rho, double eps, double ye) {
+  EosOut o;
+  o.eps = eps;
+  if (E.kind == 0) {
+    o.p = (E.gam - 1.0) * rho * eps;
+    o.T = 0.0;
+    o.cs2 = E.gam * o.p / fma(rho, 1.0 + eps, o.p);
+    return o;
+  }
+  if (E.kind == 2) {
+    hyb_eps(E, hyb_cold(E, rho), rho, eps, &o.p, &o.cs2);
+    o.T = 0.0;
+    return o;
+  }
+  TabPos t = tab_pos(E, rho, ye);
+  int lo;
+  double elo, ehi;
+  tab_tcell(E, t, eps, &lo, &elo, &ehi);
   double w = fmin(fmax((eps - elo) / (ehi - elo), 0.0), 1.0);
   double p0 = tab_bl(t, E.p, lo), p1 = tab_bl(t, E.p, lo + 1);
   double c0 = tab_bl(t, E.c, lo), c1 = tab_bl(t, E.c, lo + 1);

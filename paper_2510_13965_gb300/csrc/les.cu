@@ -42,16 +42,50 @@ DI void metric(const double* U, long long o, long long sf, double gdd[6], double
   *sg = sqrt(*det);
 }
 
+// Partial derivatives of the table's interpolant p(rho, eps, Ye): p is
+// linear in eps between the two temperature nodes that bracket it, and each
+// node value is bilinear in (log10 rho, Ye); moving rho or Ye at fixed eps
+// also moves the weight along T through the nodes' eps values.  Along a
+// coordinate clamped at the table's edge the interpolant is constant.
+DI void tab_derivs(const Eos& E, double rho, double eps, double ye, double* dpdr, double* dpde, double* dpdy) {
+  const double fr = (log10(rho) - E.lr0) * E.idlr, fy = (ye - E.ye0) * E.idye;
+  const bool in_r = fr >= 0.0 && fr <= E.nr - 1.0, in_y = fy >= 0.0 && fy <= E.ny - 1.0;
+  const TabPos t = tab_pos(E, rho, ye);
+  int lo;
+  double elo, ehi;
+  tab_tcell(E, t, eps, &lo, &elo, &ehi);
+  const double ide = 1.0 / (ehi - elo);
+  double wt = (eps - elo) * ide;
+  const bool in_t = wt >= 0.0 && wt <= 1.0;
+  wt = fmin(fmax(wt, 0.0), 1.0);
+  const double plo = tab_bl(t, E.p, lo), phi = tab_bl(t, E.p, lo + 1);
+  // d/d(log10 rho) and d/dYe of the bilinear node value of A at T node it
+  auto d_lr = [&](const double* A, int it) {
+    const double* q = A + t.b + (long long)it * t.st;
+    const double a = ld(q + 1) - ld(q), b = ld(q + t.sy + 1) - ld(q + t.sy);
+    return fma(t.wy, b - a, a) * E.idlr;
+  };
+  auto d_ye = [&](const double* A, int it) {
+    const double* q = A + t.b + (long long)it * t.st;
+    const double a = ld(q + t.sy) - ld(q), b = ld(q + t.sy + 1) - ld(q + 1);
+    return fma(t.wr, b - a, a) * E.idye;
+  };
+  auto along = [&](double dplo, double dphi, double delo, double dehi) {
+    const double dw = in_t ? -fma(wt, dehi - delo, delo) * ide : 0.0;
+    return fma(dw, phi - plo, fma(wt, dphi - dplo, dplo));
+  };
+  *dpde = in_t ? (phi - plo) * ide : 0.0;
+  *dpdr = in_r ? along(d_lr(E.p, lo), d_lr(E.p, lo + 1), d_lr(E.e, lo), d_lr(E.e, lo + 1)) / (rho * M_LN10) : 0.0;
+  *dpdy = in_y ? along(d_ye(E.p, lo), d_ye(E.p, lo + 1), d_ye(E.e, lo), d_ye(E.e, lo + 1)) : 0.0;
+}
+
 // dp/drho|eps, dp/deps|rho and dp/dYe: analytic for the ideal gas and the
-// hybrid EOS (the hybrid's cold part: deps_c/drho = p_c / rho^2; dp/dYe = 0),
-// numerical for the table (the paper's remark on the LES terms): central
-// differences of its p(rho, eps, Ye) with steps 1e-4 rho, 1e-4 eps, 1e-4.
+// hybrid EOS (the hybrid's cold part: deps_c/drho = p_c / rho^2; dp/dYe = 0);
+// for the table (whose derivatives the paper takes numerically) those of the
+// interpolant that defines its p(rho, eps, Ye).
 DI void eos_derivs(const Eos& E, double rho, double eps, double ye, double* dpdr, double* dpde, double* dpdy) {
   if (E.kind == 1) {
-    const double hr = 1e-4 * rho, he = 1e-4 * eps, hy = 1e-4;
-    *dpdr = (eos_eps(E, rho + hr, eps, ye).p - eos_eps(E, rho - hr, eps, ye).p) / (2.0 * hr);
-    *dpde = (eos_eps(E, rho, eps + he, ye).p - eos_eps(E, rho, eps - he, ye).p) / (2.0 * he);
-    *dpdy = (eos_eps(E, rho, eps, ye + hy).p - eos_eps(E, rho, eps, ye - hy).p) / (2.0 * hy);
+    tab_derivs(E, rho, eps, ye, dpdr, dpde, dpdy);
     return;
   }
   const double gth = E.gam - 1.0;

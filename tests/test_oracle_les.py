@@ -177,6 +177,32 @@ def _table_case():
     return table, P, lr, lt, ye0
 
 
+def test_table_pressure_derivatives_are_the_interpolants():
+    table, P, _, _, _ = _table_case()
+    O = oracle.Oracle(P, table)
+    rng = np.random.default_rng(8)
+    for _ in range(40):
+        # a state well inside one cell of (log10 rho, log10 T, Ye)
+        ir, it, iy = rng.integers(2, 60), rng.integers(2, 44), rng.integers(1, 14)
+        lr = table["lr0"] + table["dlr"] * (ir + rng.uniform(0.2, 0.8))
+        lt = table["lt0"] + table["dlt"] * (it + rng.uniform(0.2, 0.8))
+        ye = table["ye0"] + table["dye"] * (iy + rng.uniform(0.2, 0.8))
+        rho = 10.0 ** lr
+        eps = O.eos_from_T(rho, 10.0 ** lt, ye)[1]
+        d = O.eos_derivs(rho, eps, ye)
+        h = 1e-6
+
+        def p(r, e, y):
+            return O.eos_from_eps(r, e, y)[0]
+
+        fd = [(p(rho * (1 + h), eps, ye) - p(rho * (1 - h), eps, ye)) / (2 * h * rho),
+              (p(rho, eps * (1 + h), ye) - p(rho, eps * (1 - h), ye)) / (2 * h * eps),
+              (p(rho, eps, ye + h) - p(rho, eps, ye - h)) / (2 * h)]
+        pscale = p(rho, eps, ye)
+        for a, b, sc in zip(d, fd, (pscale / rho, pscale / eps, pscale)):
+            assert abs(a - b) <= 1e-6 * max(abs(b), 1e-3 * sc), (d, fd)
+
+
 def test_table_pressure_derivatives_against_the_model():
     table, P, lr, lt, ye0 = _table_case()
     O = oracle.Oracle(P, table)
