@@ -160,14 +160,21 @@ __global__ void __launch_bounds__(128) k_les_aux(const PatchDev* __restrict__ pd
   }
 }
 
-// d_a of the point value at A (stride s) at index c on an axis with n
-// interior points.
-DI double dgrad(const double* A, long long s, int c, int n, double dx) {
-  if (c - 2 >= -3 && c + 2 <= n + 2)
-    return (ld(A - 2 * s) - 8.0 * ld(A - s) + 8.0 * ld(A + s) - ld(A + 2 * s)) / (12.0 * dx);
-  if (c - 1 >= -3 && c + 1 <= n + 2) return (ld(A + s) - ld(A - s)) / (2.0 * dx);
-  if (c == -3) return (-3.0 * ld(A) + 4.0 * ld(A + s) - ld(A + 2 * s)) / (2.0 * dx);
-  return (3.0 * ld(A) - 4.0 * ld(A - s) + ld(A - 2 * s)) / (2.0 * dx);
+// Stencil of d_a at index c on an axis with n interior points: 0 the
+// fourth-order centred difference where it fits in the ghosted patch, else
+// 1 the second-order centred one, else the second-order one-sided one at the
+// low (2) or high (3) end.  dnum gives the stencil's numerator; the factor
+// 1/(12 dx) or 1/(2 dx) is applied with the metric transform.
+DI int dkind(int c, int n) {
+  if (c - 2 >= -3 && c + 2 <= n + 2) return 0;
+  if (c - 1 >= -3 && c + 1 <= n + 2) return 1;
+  return c == -3 ? 2 : 3;
+}
+DI double dnum(const double* A, long long s, int kind) {
+  if (kind == 0) return ld(A - 2 * s) - 8.0 * ld(A - s) + 8.0 * ld(A + s) - ld(A + 2 * s);
+  if (kind == 1) return ld(A + s) - ld(A - s);
+  if (kind == 2) return -3.0 * ld(A) + 4.0 * ld(A + s) - ld(A + 2 * s);
+  return 3.0 * ld(A) - 4.0 * ld(A - s) + ld(A - 2 * s);
 }
 
 __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
@@ -188,22 +195,32 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
   const double* A = PD.les + o;
   if (A[A_RHO * sf] < rho_min) return;
   const long long st[3] = {1, G.sy, G.sz};
-  const int idx[3] = {i, j, k}, nn[3] = {G.n0, G.n1, G.n2};
+  const int ic[3] = {i, j, k}, nn[3] = {G.n0, G.n1, G.n2};
+  int kd[3];
+  double sc[3];
+  const double idx = 1.0 / G.dx;
+  for (int a = 0; a < 3; ++a) {
+    kd[a] = dkind(ic[a], nn[a]);
+    sc[a] = kd[a] == 0 ? (1.0 / 12.0) * idx : 0.5 * idx;
+  }
   double gr[3][LES_NAUX];
   for (int a = 0; a < 3; ++a)
-    for (int f = 0; f < LES_NAUX; ++f) gr[a][f] = dgrad(A + f * sf, st[a], idx[a], nn[a], G.dx);
+    for (int f = 0; f < LES_NAUX; ++f) gr[a][f] = dnum(A + f * sf, st[a], kd[a]);
   double gdd[6], guu[6], sg, det;
   metric(U, o, sf, gdd, guu, &sg, &det);
   // gamma^{ab} = L L^T (Cholesky); with each gradient replaced by L^T d f,
-  // grad f . grad g = gamma^{ab} d_a f d_b g is a plain three-term sum.
+  // grad f . grad g = gamma^{ab} d_a f d_b g is a plain three-term sum.  The
+  // stencils' factors sc_a scale L's rows.
   const double L00 = sqrt(guu[0]), L10 = guu[1] / L00, L20 = guu[2] / L00;
   const double L11 = sqrt(guu[3] - L10 * L10), L21 = (guu[4] - L20 * L10) / L11;
   const double L22 = sqrt(guu[5] - L20 * L20 - L21 * L21);
+  const double M00 = L00 * sc[0], M10 = L10 * sc[1], M20 = L20 * sc[2];
+  const double M11 = L11 * sc[1], M21 = L21 * sc[2], M22 = L22 * sc[2];
   for (int f = 0; f < LES_NAUX; ++f) {
     const double d0 = gr[0][f], d1 = gr[1][f], d2 = gr[2][f];
-    gr[0][f] = L00 * d0 + L10 * d1 + L20 * d2;
-    gr[1][f] = L11 * d1 + L21 * d2;
-    gr[2][f] = L22 * d2;
+    gr[0][f] = M00 * d0 + M10 * d1 + M20 * d2;
+    gr[1][f] = M11 * d1 + M21 * d2;
+    gr[2][f] = M22 * d2;
   }
   auto dot = [&](int f1, int f2) { return gr[0][f1] * gr[0][f2] + gr[1][f1] * gr[1][f2] + gr[2][f1] * gr[2][f2]; };
   auto val = [&](int f) { return A[f * sf]; };
@@ -220,6 +237,7 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
     Ed[a] = val(A_ED + a);
   }
   const double E2 = Ed[0] * Eu[0] + Ed[1] * Eu[1] + Ed[2] * Eu[2];
+  const double iTh = 1.0 / Th, icE = 1.0 / cE;
   double sBv = 0.0, sBvB = 0.0, sBvT = 0.0;
   for (int a = 0; a < 3; ++a) {
     sBv += dot(A_BU + a, A_VD + a);
@@ -228,7 +246,7 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
   }
   double Psi_v[3];
   for (int a = 0; a < 3; ++a)
-    Psi_v[a] = 2.0 / Th * (dot(A_VB, A_BU + a) - dot(A_TH, A_VU + a) + Bu[a] / cE * (Th * sBv + sBvB - sBvT));
+    Psi_v[a] = 2.0 * iTh * (dot(A_VB, A_BU + a) - dot(A_TH, A_VU + a) + Bu[a] * icE * (Th * sBv + sBvB - sBvT));
   // grad B^i . grad v^k (all pairs), grad B^k . grad (v.B), grad v^k . grad Theta.
   double gBv[3][3], gBvB[3], gvT[3];
   for (int a = 0; a < 3; ++a) {
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
       const double t1 = 0.5 * (gBv[ii][kk] - gBv[kk][ii]);
       const double t2 = 0.5 * (Bu[ii] * gBvB[kk] - Bu[kk] * gBvB[ii]);
       const double t3 = 0.5 * (Bu[ii] * gvT[kk] - Bu[kk] * gvT[ii]);
-      const double PsiM = 4.0 / Th * (Th * t1 + t2 - t3);
+      const double PsiM = 4.0 * iTh * (Th * t1 + t2 - t3);
       BvPsi += 0.5 * (Bd[ii] * vd[kk] - Bd[kk] * vd[ii]) * PsiM;
     }
   double gBgB = 0.0, gEgE = 0.0, gvgv = 0.0, vPsi = 0.0;
@@ -263,11 +281,11 @@ __global__ void __launch_bounds__(128) k_les_flux(const PatchDev* __restrict__ p
                        (cE * dpde - PsiA) * (W2 / 4.0 * giW2 + dot(A_IW2, A_RHO) / rho) -
                        2.0 / W2 * dpde * (gBgB - W2 * W2 * dot(A_IW2, A_H)) -
                        (cE * dpde + PsiA) * (vPsi + gvgv + W2 * giW2) +
-                       Psi_Th / (cE * Th) * ((cE * dpde + PsiA) * (Th - E2) - PsiA * Th / W2);
+                       Psi_Th * icE * iTh * ((cE * dpde + PsiA) * (Th - E2) - PsiA * Th / W2);
   const double Hp = cE * W2 * (Th - E2) / ((rho * cE - PsiA) * (Th - E2) * W2 + PsiA * Th) * brace;
   const double HTh = Psi_Th + Th / (Th - E2) * Hp;
   double Hv[3];
-  for (int a = 0; a < 3; ++a) Hv[a] = Psi_v[a] - (vu[a] + vB / cE * Bu[a]) * HTh / Th;
+  for (int a = 0; a < 3; ++a) Hv[a] = Psi_v[a] - (vu[a] + vB * icE * Bu[a]) * HTh * iTh;
   double HM[3][3];
   for (int kk = 0; kk < 3; ++kk)
     for (int ii = 0; ii < 3; ++ii)
