@@ -4,6 +4,9 @@ The oracle is a plain, serial FP64 restatement of the paper's GRMHD substep.
 Only the tests, the smoke check and the benchmark's CPU-baseline leg use it;
 the product (the CUDA library and its binding) never imports this package.
 Arrays are numpy float64, C-contiguous, field-major (nf, n2+6, n1+6, px).
+
+Parity unpinned: the R^chi Z-term factor, kappa_2 and the damping, gauge and
+cleaning constants (see oracle.hpp); no closed form in the paper fixes them.
 """
 import ctypes
 import os
