@@ -72,7 +72,8 @@ def _args():
                    help="point counts of the hierarchy workload relative to the 366-patch layout")
     a.add_argument("--amr-seeded", action="store_true",
                    help="also time the hierarchy with NN-seeded con2prim")
-    a.add_argument("--amr-delta", type=float, default=3e-2)
+    a.add_argument("--amr-delta", type=float, default=3e-2,
+                   help="seed bracket half-width of the NN-seeded hierarchy and batched timings")
     a.add_argument("--no-autotune", action="store_true",
                    help="tov workload: keep 128-thread blocks instead of the library's timed choice")
     a.add_argument("--les-cm", type=float, default=0.0,
@@ -465,6 +466,9 @@ def run_batched(args):
     for p_, q in enumerate(plain):
         q.U[0][0].copy_(init[p_])
     ms_plain = timed(lambda: [q.step(dt) for q in plain], K)
+    del plain
+    torch.cuda.synchronize()
+    seeded = _batched_seeded(args, g, P, batched, reset, timed, dt, K, ms_plain)
     line = {"metric": METRIC, "value": zones / (ms_graph / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -475,8 +479,78 @@ def run_batched(args):
                                      "batched_autotuned": ms_tuned, "batched_autotuned_graph": ms_graph},
             "speedup_batched_graph_vs_plain": ms_plain / ms_graph, "autotuned_block_sizes": list(chosen),
             "gpu_launches": int(launches), "status": rc, "setup_s": gen_s}
+    if seeded is not None:
+        line["variants_ms_per_step"]["batched_autotuned_graph_nn_seeded"] = seeded["ms_per_step"]
+        line["speedup_batched_nn_seeded_graph_vs_plain"] = ms_plain / seeded["ms_per_step"]
+        line["nn_seeded"] = seeded
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _ideal_seeder(g, P, n, epochs, seed=13):
+    """A con2prim seeder for the ideal-gas Fourier workload, trained on the GPU
+    on n flat-metric pairs the method makes itself: primitives spanning the
+    workload's states (rho in [3e-4, 3e-3], W <= 1.03, eps log-uniform in
+    [1e-3, 0.3] taken from the sample's temperature column, b^2/rho in
+    [1e-4, 2]), their conserved states by the library's prim2con and the
+    plain con2prim roots as labels."""
+    import torch
+    import synth
+    st = synth.c2p_states(n, seed=seed, rho=(3e-4, 3e-3), W=(1.0, 1.03), T=(1e-3, 0.3), ye=(0.1, 0.1),
+                          b2rho=(1e-4, 2.0))
+    prim = torch.zeros((n, 10), dtype=torch.float64)
+    prim[:, 0] = torch.from_numpy(st["rho"])
+    prim[:, 1] = torch.from_numpy(st["T"])
+    prim[:, 7] = torch.from_numpy(st["ye"])
+    prim[:, 3:6] = torch.from_numpy(st["v"])
+    cons = g.prim2con_flat(P, prim.cuda(), torch.from_numpy(st["B"]).cuda())
+    _, status, _, roots, _ = g.c2p_flat_seeded(P, cons, None)
+    keep = status >= 0
+    f = g.seeder_features(cons)[keep].contiguous()
+    t = g.seeder_targets(cons, roots)[keep].contiguous()
+    S = g.Seeder(seed=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    hist = S.train(f, t, batch=4096, epochs=epochs, lr=3e-3, lr_final=3e-5)
+    e1.record()
+    torch.cuda.synchronize()
+    return S, e0.elapsed_time(e1), float(hist[-1])
+
+
+def _batched_seeded(args, g, P, batched, reset, timed, dt, K, ms_plain):
+    """The batched, graph-captured step with NN-seeded con2prim against the
+    plain per-patch, bracketed-start form; the primitives of one con2prim of
+    the initial state, seeded and plain, are compared point by point."""
+    import torch
+    S, train_ms, loss = _ideal_seeder(g, P, args.train_pairs, args.train_epochs)
+    reset(batched)
+    batched.set_seeder(None)
+    plain_stats = batched.con2prim(0, stats=True)
+    prim_plain = [p.clone() for p in batched.prim]
+    st_plain = [s.clone() for s in batched.status]
+    reset(batched)
+    batched.set_seeder(S, args.amr_delta)
+    seeded_stats = batched.con2prim(0, stats=True)
+    rel_rho, dv, same = 0.0, 0.0, True
+    for a, b, sa, sb in zip(prim_plain, batched.prim, st_plain, batched.status):
+        rel_rho = max(rel_rho, float(((a[0] - b[0]).abs() / a[0].abs().clamp_min(1e-300)).max()))
+        dv = max(dv, float((a[3:6] * a[6:7] - b[3:6] * b[6:7]).abs().max()))
+        same = same and bool(torch.equal(sa, sb))
+    del prim_plain, st_plain
+    for _ in range(2):
+        batched.step(dt)
+    reset(batched)
+    batched.capture_graph(1, dt)
+    ms = timed(batched.graph_launch, K)
+    rc = batched.sync_status()
+    batched.set_seeder(None)
+    return {"ms_per_step": ms, "delta": args.amr_delta, "status": rc, "training_ms": train_ms,
+            "train_pairs": args.train_pairs, "final_loss": loss,
+            "c2p_iterations_per_point": {"plain": plain_stats["iterations"] / max(plain_stats["points"], 1),
+                                         "nn_seeded": seeded_stats["iterations"] / max(seeded_stats["points"], 1)},
+            "seeded_vs_plain_c2p": {"max_rel_rho_diff": rel_rho, "max_abs_Wv_diff": dv, "same_status": same},
+            "speedup_vs_plain_per_patch": ms_plain / ms}
 
 
 def _c2p_cons(g, P, T, n, seed):
