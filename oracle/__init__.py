@@ -92,6 +92,7 @@ def lib(flops=False):
             "oracle_c2p_point": (i, [vp, vp, vp, vp, d, d, vp, vp, vp]),
             "oracle_c2p_flat": (i, [vp, vp, l, vp, vp, vp, vp]),
             "oracle_c2p_flat_ext": (i, [vp, vp, l, vp, vp, vp, vp, vp, d, vp, vp]),
+            "oracle_c2p_master_scan": (d, [vp, vp, vp, l, vp]),
             "oracle_mlp_nparams": (i, []),
             "oracle_mlp_forward": (i, [vp, l, vp, vp, i]),
             "oracle_mlp_grad": (d, [vp, l, vp, vp, vp, i]),
@@ -247,6 +248,14 @@ class Oracle:
         self.L.oracle_c2p_flat_ext(_ref(self.P), self.Tp, n, _p(cons), _p(prim), _p(status), _p(iters), _p(sd),
                                    float(delta), _p(roots), _p(seeded))
         return prim, status, iters, roots, seeded
+
+    def c2p_master_scan(self, cons, n):
+        """Master function of one flat-metric state (10,) at mu_+ k / n,
+        k = 1..n: returns (mu_+, f (n,)); mu_+ = 0 for a state below rho_min."""
+        cons = np.ascontiguousarray(cons, dtype=np.float64)
+        f = np.zeros(n)
+        mu_plus = self.L.oracle_c2p_master_scan(_ref(self.P), self.Tp, _p(cons), int(n), _p(f))
+        return mu_plus, f
 
     def eos_derivs(self, rho, eps, ye):
         """(dp/drho|eps, dp/deps|rho, dp/dYe) of the EOS at one state."""

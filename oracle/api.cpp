@@ -160,6 +160,13 @@ int oracle_c2p_flat(const oracle_params* P, const oracle_eos_table* E, long n, c
   return worst;
 }
 
+// Master function of flat-metric state cons [10] at mu_+ k / n, k = 1..n,
+// into f [n]; returns mu_+ (0: atmosphere, no solve).
+double oracle_c2p_master_scan(const oracle_params* P, const oracle_eos_table* E, const double* cons, long n,
+                              double* f) {
+  return c2p_master_scan(P, E, cons, n, f);
+}
+
 // Flat-metric con2prim with optional seeds [n][3] (NULL: plain) and bracket
 // half-width delta; roots [n][3] (mu_+, mu, W) and seeded [n] (bit mask of
 // seed brackets used) may be NULL.

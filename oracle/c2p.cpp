@@ -392,3 +392,36 @@ int c2p_point_ext(const oracle_params* P, const oracle_eos_table* E, const doubl
   }
   return status;
 }
+
+// Master function of one flat-metric state sampled on a uniform grid, for the
+// uniqueness pin: Kastaun et al. show that f(mu) changes sign exactly once on
+// (0, mu_+], which makes the bracketed root unique.  Step 1 is redone for
+// gamma_ij = delta_ij (S_i and B^i as given); Step 2 solves mu_+ as
+// c2p_point_ext does without seeds.  Writes f(mu_k) for mu_k = mu_+ k / n,
+// k = 1..n, and returns mu_+ (0 when D < rho_min: no solve).
+double c2p_master_scan(const oracle_params* P, const oracle_eos_table* E, const double cb[10], long n, double* f_out) {
+  real D = cb[0];
+  if (!(D >= P->rho_min)) return 0.0;
+  fixed_q F;
+  F.D = D;
+  F.Ye = cb[1] / D;
+  F.h0 = P->h0;
+  F.q = cb[2] / D;
+  real r[3] = {cb[3] / D, cb[4] / D, cb[5] / D};
+  real sD = sqrt(D);
+  real Bc[3] = {cb[6] / sD, cb[7] / sD, cb[8] / sD};
+  F.r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  F.B2 = Bc[0] * Bc[0] + Bc[1] * Bc[1] + Bc[2] * Bc[2];
+  F.rB = r[0] * Bc[0] + r[1] * Bc[1] + r[2] * Bc[2];
+  F.B2rp2 = F.B2 * F.r2 - F.rB * F.rB;
+  F.v02 = F.r2 / (F.h0 * F.h0 + F.r2);
+  auto fa_fn = [&](real mu) { return f_aux(F, mu); };
+  real up = 1.0 / F.h0;
+  real fa_top = f_aux(F, up);
+  real mu_plus = up;
+  int it = 0;
+  bool ok = true;
+  if (fa_top > 0.0) mu_plus = brent(fa_fn, 0.0, up, -1.0, fa_top, P->max_iter, P->c2p_xtol, &it, &ok);
+  for (long k = 1; k <= n; ++k) f_out[k - 1] = dbl(f_master(P, E, F, mu_plus * (real(k) / real(n))).f);
+  return dbl(mu_plus);
+}

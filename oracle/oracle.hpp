@@ -167,6 +167,10 @@ int c2p_point(const oracle_params* P, const oracle_eos_table* E, const double co
 int c2p_point_ext(const oracle_params* P, const oracle_eos_table* E, const double cons_bar[10],
                   const double gt[6], double chi, double alpha, double prim[NP], double cons_out[10],
                   int* iters, const double* seed3, double delta, double* roots3, int* seeded_ok);
+// Master function f(mu) of a flat-metric state at mu_+ k / n, k = 1..n
+// (uniqueness pin); returns mu_+, or 0 for a state below rho_min.
+double c2p_master_scan(const oracle_params* P, const oracle_eos_table* E, const double cons[10], long n,
+                       double* f_out);
 
 // ---- finite differences and MP5 (fd.cpp) ----------------------------------
 real fd_d1(const double* u, long s, real inv12dx);

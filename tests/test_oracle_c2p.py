@@ -4,7 +4,8 @@ Definitions: Sec. II B, eq. def_con2prim.  Recovery: the appendix
 "Conversion from conserved to primitive fields" (steps 1-4 and the error
 policy).  Pins: closed forms of the conserved variables in special cases, an
 independent textbook recovery for B = 0 (1-D root find on the pressure), the
-prim -> cons -> prim round trip, and one crafted state per policy branch.
+prim -> cons -> prim round trip, the uniqueness of the master function's root
+by brute-force scans, and one crafted state per policy branch.
 """
 import numpy as np
 import pytest
@@ -190,6 +191,62 @@ def test_table_round_trip_kappa_scaled(table):
               and abs(out[1] - pe[1]) <= 1e-10 * kap * abs(pe[1]))
         bad += not ok
     assert bad == 0
+
+
+@pytest.mark.parametrize("kind", ["ideal", "table"])
+@pytest.mark.parametrize("tau_scale", [False, True])
+def test_master_function_root_is_unique(kind, tau_scale, table):
+    """Kastaun et al. prove that the master function changes sign exactly once
+    on (0, mu_+].  Brute force: 1000 states x 1000 values of mu.  Physical
+    states from prim2con, and the same states with tau scaled by U(0, 2)
+    (eps clamps and the velocity bound active).  Where tau is below the
+    kinetic energy the velocity bound v_0 makes f(mu_+) = 0 analytically and
+    rounding may leave it a few ulps negative: no sign change then, and the
+    root is mu_+ itself.  The solver's root lies in the sign-change cell."""
+    n_mu = 1000
+    if kind == "ideal":
+        P = synth.ideal_params()
+        O = oracle.Oracle(P)
+        rng = np.random.default_rng(11)
+        states = []
+        for _ in range(1000):
+            rho, eps = 10 ** rng.uniform(-8, -2), 10 ** rng.uniform(-3, 1)
+            v = rng.normal(size=3)
+            v *= rng.uniform(0, 0.995) / np.linalg.norm(v)
+            B = rng.normal(size=3) * np.sqrt(rho) * 10 ** rng.uniform(-2, 1)
+            states.append(_cons_bar(_prim(rho, eps, rho * eps, v), B, GT_FLAT, 1.0))
+    else:
+        P = synth.table_params(table)
+        O = oracle.Oracle(P, table)
+        st = synth.c2p_states(1000, seed=17)
+        states = []
+        for q in range(1000):
+            pe = O.eos_from_T(st["rho"][q], st["T"][q], st["ye"][q])
+            pr = _prim(st["rho"][q], pe[1], pe[0], st["v"][q], ye=st["ye"][q])
+            states.append(_cons_bar(pr, st["B"][q], GT_FLAT, 1.0))
+    cons = np.array(states)
+    if tau_scale:
+        cons[:, 2] *= np.random.default_rng(5).uniform(0.0, 2.0, len(cons))
+    _, status, _, roots, _ = O.c2p_flat_ext(cons)
+    endpoint = 0
+    for q in range(len(cons)):
+        mu_plus, f = O.c2p_master_scan(cons[q], n_mu)
+        assert mu_plus > 0 and mu_plus == roots[q, 0]
+        assert f[0] < 0
+        up = np.nonzero((f[:-1] < 0) & (f[1:] >= 0))[0]
+        down = np.nonzero((f[:-1] >= 0) & (f[1:] < 0))[0]
+        assert len(down) == 0
+        mu = roots[q, 1]
+        if f[-1] < 0:
+            assert len(up) == 0 and -f[-1] <= 1e-15 * mu_plus and mu == mu_plus
+            endpoint += 1
+            continue
+        assert len(up) <= 1
+        k = up[0] + 1 if len(up) else 0  # first grid index with f >= 0
+        lo, hi = mu_plus * k / n_mu, mu_plus * (k + 1) / n_mu
+        assert lo * (1 - 1e-12) <= mu <= hi * (1 + 1e-12)
+    if not tau_scale:
+        assert endpoint == 0 and np.all(status == 0)
 
 
 # ---- error policy -----------------------------------------------------------
