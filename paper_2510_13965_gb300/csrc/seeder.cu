@@ -660,11 +660,15 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
         solve = true;
       }
     }
-    tc::put_x(smem, s, f, nm, solve);
-    float y[NO];
-    if (!tc::forward(smem, tmem, phase, y)) {
-      if (s == 0) atomicOr(err, 4);
-      break;
+    // A tile without a point to solve (atmosphere, padding) skips the network;
+    // the branch is uniform across the CTA, so the mbarrier phase stays in step.
+    float y[NO] = {0.0f, 0.0f, 0.0f};
+    if (__syncthreads_or(solve)) {
+      tc::put_x(smem, s, f, nm, solve);
+      if (!tc::forward(smem, tmem, phase, y)) {
+        if (s == 0) atomicOr(err, 4);
+        break;
+      }
     }
     if (valid) {
       float* sd = PD.seed + o;
