@@ -870,7 +870,7 @@ def run_amr(args):
         levels[s_["level"]][1] += int(np.prod(s_["n"]))
     subcycled = None
     if args.amr_subcycle:
-        # Sub-cycling (Sec. III D, BOR): level l steps dt0 / 2^l with
+        # Sub-cycling (Sec. IV C, BOR): level l steps dt0 / 2^l with
         # dt0 = 2^L dt, so every level keeps the synchronous run's Courant
         # factor on its own grid; one bench step = one level-0 step, the same
         # physical time as 2^L synchronous steps.

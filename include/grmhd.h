@@ -153,7 +153,7 @@ typedef struct grmhd_eos_table {
 /* One patch.  U[0] holds U^n; U[1], U[2] hold RK stage values; U[3] holds the
  * RK4 accumulator.  All arrays are device pointers with the layout above.
  *
- * Mesh-refinement hierarchy (bc = 3; Sec. III D, prolongation and
+ * Mesh-refinement hierarchy (bc = 3; Sec. IV B, prolongation and
  * restriction, for a fixed hierarchy advanced without sub-cycling):
  *   - exactly one patch has level 0; its outer ghosts are extrapolated as for
  *     bc = 1;
@@ -255,7 +255,7 @@ int grmhd_rhs_substep(grmhd_ctx* ctx, int stage, double dt);
  * advances level l by 2^l steps of dt / 2^l (see below). */
 int grmhd_step(grmhd_ctx* ctx, double dt);
 
-/* Sub-cycling in time on a hierarchy (bc = 3; Sec. III D, "Sub-cycling in
+/* Sub-cycling in time on a hierarchy (bc = 3; Sec. IV C, "Sub-cycling in
  * time", the BOR scheme, with the dense output of Sec. III A).  With on != 0,
  * grmhd_step(ctx, dt0) advances level l recursively: one step of
  * dt_l = dt0 / 2^l of level l, then two steps of level l + 1 and the

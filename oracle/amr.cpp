@@ -1,4 +1,4 @@
-// Oracle of the mesh-refinement ghost fill and restriction (Sec. III D,
+// Oracle of the mesh-refinement ghost fill and restriction (Sec. IV B,
 // "Mesh Refinement: refinement criteria, prolongation and restriction"), for
 // a fixed hierarchy advanced without sub-cycling (every level takes the same
 // time step).  Test infrastructure only: plain loops over points, FP64.
@@ -23,7 +23,7 @@
 // point of a level-l patch at even g overwrites the coarse interior point
 // g / 2 (direct copy, the paper's restriction operator).
 //
-// Sub-cycling in time (Sec. III D, "Sub-cycling in time", BOR scheme): level l
+// Sub-cycling in time (Sec. IV C, "Sub-cycling in time", BOR scheme): level l
 // takes steps of dt_0 / 2^l; after each step of level l, level l+1 takes two
 // steps and is restricted into level l.  The ghost points of level l+1 during
 // its steps come from level l's dense output (Sec. III A, dense output
@@ -433,7 +433,7 @@ void oracle_dense_derivs(int rk, const double* k, double* D) { dense_derivs(rk, 
 void oracle_bor_coeffs(int rk, int msub, int R, int s, double* c) { bor_coeffs(rk, msub, R, s, c); }
 
 // One step of the whole hierarchy with sub-cycling: level 0 advances by dt0,
-// level l by 2^l steps of dt0 / 2^l (Sec. III D, BOR).  P->bc must be 3.
+// level l by 2^l steps of dt0 / 2^l (Sec. IV C, BOR).  P->bc must be 3.
 // Returns the worst con2prim status, or -2 (uncovered ghost point), -3 (bc),
 // -4 (a prolongation stencil reached an undefined dense-output ghost point).
 int oracle_hier_subcycle_step(const oracle_params* P, const oracle_eos_table* E, int np, const int* meta,

@@ -1,5 +1,5 @@
 // Mesh-refinement ghost fill and restriction for a fixed hierarchy advanced
-// without sub-cycling (Sec. III D, prolongation and restriction).
+// without sub-cycling (Sec. IV B, prolongation and restriction).
 //
 // The host turns the patch layout into task lists once, at context creation:
 // every ghost point of a level-l patch (l >= 1) becomes one task, a copy from
@@ -122,7 +122,7 @@ void launch_amr(const PatchDev* pd, const AmrTask* t, long long n, int reg, cuda
     k_amr<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(pd, t, n, reg, rc);
 }
 
-// Sub-cycled ghost fill (Sec. III D, BOR), first pass: at every coarse point
+// Sub-cycled ghost fill (Sec. IV C, BOR), first pass: at every coarse point
 // that the level's prolongation stencils read, the stage value
 // ((((c0 U^n + c1 D_1) + c2 D_2) + c3 D_3) + c4 J) of the coarse level's dense
 // output, rounded operation by operation, into register reg_t (the coarse

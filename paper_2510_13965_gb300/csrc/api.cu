@@ -563,7 +563,7 @@ int grmhd_restrict(grmhd_ctx* c, int reg) {
   return check_launch(c, "restrict");
 }
 
-// Coefficients of (U^n, D_1, D_2, D_3, J) in the BOR stage value (Sec. III D,
+// Coefficients of (U^n, D_1, D_2, D_3, J) in the BOR stage value (Sec. IV C,
 // sub-cycling; Sec. III A, dense output) of stage s of fine step msub (0, 1)
 // of a coarse step, refinement ratio 2.  With the Taylor data of the
 // dense-output cubic at t0 = t^n + msub dt/2 and h = dt/2,
@@ -608,7 +608,7 @@ static void ghost_level0(grmhd_ctx* c, int reg) {
 }
 
 // One step of dt of level l (fine step msub of its parent's step), then two
-// steps of level l + 1 and its restriction into level l (Sec. III D, BOR).
+// steps of level l + 1 and its restriction into level l (Sec. IV C, BOR).
 static int sub_advance(grmhd_ctx* c, int l, int msub, double dt) {
   const bool rk3 = c->P.rk == 1;
   const int ns = rk3 ? 3 : 4, nd = rk3 ? 3 : NDENSE, grp = 1 + l;

@@ -1,4 +1,4 @@
-"""Sub-cycling in time (Sec. III D, BOR) on the GPU, through the C ABI, against the oracle.
+"""Sub-cycling in time (Sec. IV C, BOR) on the GPU, through the C ABI, against the oracle.
 
 - From the identical state, one and three sub-cycled level-0 steps of the
   three-level nested hierarchy (seven level steps, 28 substeps each for RK4)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's mesh-refinement ghost fill and restriction (Sec. III D).
+"""Pins of the oracle's mesh-refinement ghost fill and restriction (Sec. IV B).
 
 - The six-point Lagrange prolongation reproduces polynomials of degree <= 5 in
   each coordinate exactly, on every ghost point that comes from the coarser

@@ -1,4 +1,4 @@
-"""Pins of the oracle's sub-cycling in time (Sec. III D, BOR) and of the dense
+"""Pins of the oracle's sub-cycling in time (Sec. IV C, BOR) and of the dense
 output it rests on (Sec. III A, dense output interpolator).
 
 - The dense output at theta = 1 is the RK step itself (b_j(1) are the
