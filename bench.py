@@ -726,7 +726,8 @@ def _hierarchy_pairs(g, P, T, pt, n, seed):
     density, temperature and composition; W and b^2 move by the conformal
     factor, well inside the spread of the set."""
     import torch
-    gen = torch.Generator(device="cuda")
+    dev = pt.status[0].device
+    gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     counts = [int((st == 0).sum()) for st in pt.status]
     total = sum(counts)
@@ -739,7 +740,7 @@ def _hierarchy_pairs(g, P, T, pt, n, seed):
         if k <= 0:
             continue
         idx = torch.nonzero((pt.status[q] == 0).reshape(-1)).squeeze(1)
-        idx = idx[torch.randint(idx.numel(), (k,), generator=gen, device="cuda")]
+        idx = idx[torch.randint(idx.numel(), (k,), generator=gen, device=dev)]
         pr = pt.prim[q].reshape(g.NP, -1)[:, idx]
         U = pt.U[q][0].reshape(g.NF, -1)[:, idx]
         prims.append(pr.T)
