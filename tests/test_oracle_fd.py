@@ -203,3 +203,22 @@ def test_minmod4_definition():
     assert oracle.minmod4(-1.0, -2.0, -3.0, -0.5) == -0.5
     assert oracle.minmod4(1.0, -2.0, 3.0, 0.5) == 0.0
     assert oracle.minmod4(0.0, 2.0, 3.0, 0.5) == 0.0
+
+
+def test_mp5_accepts_the_unlimited_value_when_the_test_passes():
+    """Suresh & Huynh's acceptance test, the paper's strict form: when
+    (f_ip - f_i)(f_ip - f_MP) < 0 the interface value is the unlimited
+    fifth-order one, f_ip = (2 f_{i-2} - 13 f_{i-1} + 47 f_i + 27 f_{i+1}
+    - 3 f_{i+2}) / 60, with f_MP = f_i + minmod(f_{i+1} - f_i, 4 (f_i - f_{i-1}))."""
+    rng = np.random.default_rng(21)
+    accepted = 0
+    for _ in range(4000):
+        f = np.cumsum(rng.normal(size=5)) if rng.random() < 0.5 else rng.normal(size=5)
+        fip = (2 * f[0] - 13 * f[1] + 47 * f[2] + 27 * f[3] - 3 * f[4]) / 60
+        a, b = f[3] - f[2], 4 * (f[2] - f[1])
+        mm = np.sign(a) * min(abs(a), abs(b)) if np.sign(a) == np.sign(b) else 0.0
+        fmp = f[2] + mm
+        if (fip - f[2]) * (fip - fmp) < -1e-12 * np.max(np.abs(f)) ** 2:
+            accepted += 1
+            assert abs(oracle.mp5(f) - fip) <= 1e-14 * np.max(np.abs(f))
+    assert accepted > 500
