@@ -270,14 +270,19 @@ class Patches:
         return dict(points=s.points, iterations=s.iterations, corrected=s.corrected, failed=s.failed) if stats else None
 
     def rhs_eval(self, reg, out=None):
-        self._enter()
+        """Right-hand side of register reg into per-patch arrays (ghost entries
+        stay zero).  The arrays are zero-filled on the caller's current stream,
+        so the library's stream waits for that stream only after they are
+        allocated; the caller's stream in turn waits for the library's."""
         torch = self.torch
         if out is None:
             out = [torch.zeros((NF,) + sp["shape"], dtype=torch.float64, device=self.device) for sp in self.specs]
+        self._enter()
         for t in out:
             t.record_stream(self.stream)
         arr = (ctypes.c_void_p * len(out))(*[t.data_ptr() for t in out])
         _check(self.L.grmhd_rhs_eval(self.ctx, reg, arr), self.ctx, "grmhd_rhs_eval")
+        torch.cuda.current_stream().wait_stream(self.stream)
         return out
 
     def rk_update(self, stage, dt, rhs):
