@@ -1,5 +1,8 @@
-// Device EOS, prim2con and con2prim (Kastaun's two Brent root finds with the
-// EOS validity clamps and the error policy of the paper's con2prim appendix).
+// Device EOS, prim2con and con2prim: Kastaun's two Brent root finds with the
+// EOS validity clamps and the error policy, following the appendix
+// "Conversion from conserved to primitive fields" (steps 1-4 and the policy
+// list at its end); conserved variables as defined in Sec. II B
+// (eq. def_con2prim); hybrid EOS as in Sec. II B.
 //
 // The master function is evaluated with the identities
 //   eps_hat = W (qbar - mu rbar^2 + 1) - 1      (v^2 W^2 / (1 + W) = W - 1),
@@ -279,7 +282,8 @@ DI EosOut eos_T(const Eos& E, double rho, double T, double ye) {
   return o;
 }
 
-// Undensitized (D, DYe, tau, S_i) from primitives; B^i given; gdd = gamma_ij.
+// Undensitized (D, DYe, tau, S_i) from primitives (Sec. II B, eq.
+// def_con2prim, h = rho (1 + eps) + p); B^i given; gdd = gamma_ij.
 DI void prim2con(const double gdd[6], double rho, double eps, double p, const double v[3], double ye,
                  const double B[3], double out[6]) {
   double vd[3], Bd[3];
@@ -309,18 +313,22 @@ struct C2PEval {
   double f, chi, W, iW, rho, rho_raw, eps, eps_raw, p, T, cs2;
 };
 
+// chi(mu) = 1 / (1 + mu B^2) and rbar^2(mu) of the con2prim appendix.
 DI void c2p_chi_rbar(const C2PFix& F, double mu, double* chi, double* rbar2) {
   double c = 1.0 / fma(mu, F.B2, 1.0);
   *chi = c;
   *rbar2 = fma(F.r2 * c, c, mu * c * (1.0 + c) * F.rB * F.rB);
 }
 
+// Auxiliary function of step 2: f_a(mu) = mu sqrt(h0^2 + rbar^2(mu)) - 1.
 DI double c2p_faux(const C2PFix& F, double mu) {
   double chi, rbar2;
   c2p_chi_rbar(F, mu, &chi, &rbar2);
   return fma(mu, sqrt(fma(F.h0, F.h0, rbar2)), -1.0);
 }
 
+// Master function of step 3, f(mu) = mu - 1 / (nu_hat + mu rbar^2), with
+// the clamps of rho and eps to the EOS validity range.
 template <bool FULL>
 DI C2PEval c2p_master(const grmhd_params& P, const Eos& E, const C2PFix& F, double mu, int* cell) {
   C2PEval m;
@@ -352,7 +360,8 @@ DI C2PEval c2p_master(const grmhd_params& P, const Eos& E, const C2PFix& F, doub
   return m;
 }
 
-// Brent (1973) on [a, b] with f(a) fa, f(b) fb of opposite sign (or zero).
+// Brent (1973) on [a, b] with f(a) fa, f(b) fb of opposite sign (or zero);
+// the root finder the con2prim appendix names for both of its root finds.
 // Stops when |c - b| <= 4 eps_mach |b| + xtol or f(b) = 0.  ok = 0 when the
 // bracket is invalid or the iteration cap is reached.
 template <class Fn>
@@ -428,7 +437,10 @@ struct C2POut {
   double mu_plus, mu, W_root;  // roots and W at mu (0 unless the root finds converged; mu_+ 0 if not solved)
 };
 
-// con2prim at one point.  cb: densitized (D, DYe, tau, S_i, B^i); gdd/guu:
+// con2prim at one point (appendix "Conversion from conserved to primitive
+// fields": step 1 rescaled variables, step 2 mu_+ from f_a, step 3 the master
+// function's root, step 4 primitives, then the error policy).
+// cb: densitized (D, DYe, tau, S_i, B^i); gdd/guu:
 // physical metric and inverse; sg = sqrt(gamma); alpha for the BH test.
 DI void c2p_point(const grmhd_params& P, const Eos& E, const double cb[9], const double gdd[6], const double guu[6],
                   double sg, double alpha, C2POut& o, const double* seed = nullptr, double delta = 0.0) {

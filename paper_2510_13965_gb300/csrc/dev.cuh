@@ -1,4 +1,7 @@
-// Device-side building blocks of the GRMHD substep kernels (sm_103a, FP64).
+// Device-side building blocks of the GRMHD substep kernels (sm_103a, FP64):
+// the fourth-order centred, compact second and mixed differences, the
+// one-sided advection stencils and Kreiss-Oliger dissipation of Sec. III B,
+// and small symmetric-matrix helpers.
 //
 // GB300 executes FP64 at a small fraction of its other pipes, so the kernels
 // count FP64 instructions, not bytes: stencils are written with the fewest

@@ -1,7 +1,11 @@
-// Point-wise and interface kernels of the substep: initial-data conversion,
-// ghost fill, con2prim with the point-wise MHD fluxes and speeds, interface
-// fluxes (Lax-Friedrichs split + MP5), the unfused RK4 stage combination and
-// the flat-metric con2prim of independent states.
+// Point-wise and interface kernels of the substep: initial-data conversion
+// to the CCZ4 variables (Sec. II A), ghost fill (periodic, or the outer
+// boundary's extrapolation of Sec. IV B), con2prim with the point-wise MHD
+// fluxes and characteristic speeds (Sec. II B; appendix on the
+// characteristic structure), interface fluxes (Lax-Friedrichs splitting and
+// MP5 reconstruction, Sec. III C), the unfused RK stage combination
+// (Sec. III A, explicit tableaux) and the flat-metric con2prim of independent
+// states.
 #include <cmath>
 #include "kern.cuh"
 
