@@ -187,3 +187,45 @@ def test_static_tov_interior_rhs_converges_to_zero(tov):
     # Hydrostatic balance: the momentum RHS at dx = 0.1 is tiny against the gravity source.
     grav = (U1[24] + U1[22]) * 0.05  # (taubar + Dbar) |d alpha|, alpha' ~ 0.05 at r ~ 4.4
     assert np.abs(r2[25:28]).max() < 1e-3 * grav
+
+
+def test_divergence_cleaning_terms_closed_form():
+    """Divergence cleaning of the MHD system (Sec. II B, eq. mhd_system, the
+    phibar and Bbar^i equations) on a fluid at rest with uniform B and phibar,
+    flat conformal metric (chi = 1, gt = delta, Gammahat = 0), zero shift,
+    constant Khat and Theta, and a lapse linear in x, alpha = 1 + a x.  The
+    fluxes are then linear in x, which the Lax-Friedrichs split and MP5
+    differentiate exactly, and the equations reduce to
+      d_t phibar = -alpha (c_b^2 phibar (Khat + 2 Theta) + kappa_b phibar)
+        (the flux term -c_b^2 B^x a cancels the source c_b^2 B^k d_k alpha),
+      d_t Bbar^x = -a phibar + phibar a / c_b^2,   d_t Bbar^y = d_t Bbar^z = 0.
+    c_b^2 = 2 and kappa_b = 0.7 keep every term visible."""
+    P = synth.ideal_params(bc=2, c_b=np.sqrt(2.0), kappa_b=0.7)
+    O = oracle.Oracle(P)
+    n, dx, a = (8, 8, 8), 0.05, 0.3
+    shp = synth.patch_shape(n)
+    z, y, x = synth.grid_coords(n, (0.0, 0.0, 0.0), dx)
+    ID = np.zeros((26,) + shp)
+    ID[0] = ID[3] = ID[5] = 1.0
+    Kh = 0.02
+    ID[6] = ID[9] = ID[11] = Kh / 3.0
+    ID[12] = 1.0 + a * x
+    ID[16], ID[17] = 1e-3, 0.1
+    B = np.array([0.011, -0.007, 0.004])
+    ID[21:24] = B[:, None, None, None]
+    ID[24] = 0.1
+    U = O.init_state(ID, n, dx)
+    phi, Th = 3e-3, 0.015
+    U[31] = phi      # phibar (sqrt(gamma) = 1)
+    U[14] = Th       # Theta
+    prim, st, worst, its = O.con2prim_patch(U, n)
+    assert worst >= 0
+    rhs = O.rhs_patch(U, prim, n, dx)
+    inner = (slice(3, -3), slice(3, -3), slice(3, -3))
+    al = (1.0 + a * np.broadcast_to(x, shp))[inner]
+    Khat = U[13][inner]
+    cb2, kb = 2.0, 0.7
+    want_phi = -al * (cb2 * phi * (Khat + 2.0 * Th) + kb * phi)
+    assert np.allclose(rhs[31][inner], want_phi, rtol=1e-12, atol=1e-18)
+    assert np.allclose(rhs[28][inner], -a * phi + phi * a / cb2, rtol=1e-11, atol=1e-17)
+    assert np.all(np.abs(rhs[29][inner]) < 1e-17) and np.all(np.abs(rhs[30][inner]) < 1e-17)
