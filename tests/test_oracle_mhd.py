@@ -229,3 +229,49 @@ def test_divergence_cleaning_terms_closed_form():
     assert np.allclose(rhs[31][inner], want_phi, rtol=1e-12, atol=1e-18)
     assert np.allclose(rhs[28][inner], -a * phi + phi * a / cb2, rtol=1e-11, atol=1e-17)
     assert np.all(np.abs(rhs[29][inner]) < 1e-17) and np.all(np.abs(rhs[30][inner]) < 1e-17)
+
+
+def test_energy_and_momentum_sources_closed_form():
+    """Geometric sources of the taubar and Sbar_i equations (Sec. II B, eq.
+    mhd_system) on a magnetised fluid at rest: flat conformal metric, zero
+    shift, constant extrinsic curvature K_ij (so Atilde_ij = K_ij - delta_ij K/3
+    and Khat = K), Theta = 0, lapse alpha = 1 + a x.  With
+    S_ij = delta_ij (p + B^2/2) - B_i B_j (def_cont at v = 0), tr S = 3p + B^2/2
+    and tau + D = rho (1 + eps) + B^2/2:
+      d_t taubar = alpha (S^ij Atilde_ij + tr S Khat / 3),
+      d_t Sbar_i = -a S^x_i - delta_ix (tau + D) a,
+    the flux of Sbar_i being alpha S^x_i, linear in x."""
+    P = synth.ideal_params(bc=2)
+    O = oracle.Oracle(P)
+    n, dx, a = (8, 8, 8), 0.05, 0.3
+    shp = synth.patch_shape(n)
+    z, y, x = synth.grid_coords(n, (0.0, 0.0, 0.0), dx)
+    K = np.array([[0.02, 0.005, -0.003], [0.005, -0.01, 0.004], [-0.003, 0.004, 0.015]])
+    ID = np.zeros((26,) + shp)
+    ID[0] = ID[3] = ID[5] = 1.0
+    for m, (i, j) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+        ID[6 + m] = K[i, j]
+    ID[12] = 1.0 + a * x
+    rho, eps = 1e-3, 0.1
+    ID[16], ID[17] = rho, eps
+    B = np.array([0.011, -0.007, 0.004])
+    ID[21:24] = B[:, None, None, None]
+    ID[24] = 0.1
+    U = O.init_state(ID, n, dx)
+    prim, st, worst, its = O.con2prim_patch(U, n)
+    assert worst >= 0
+    rhs = O.rhs_patch(U, prim, n, dx)
+    inner = (slice(3, -3), slice(3, -3), slice(3, -3))
+    al = (1.0 + a * np.broadcast_to(x, shp))[inner]
+    p = (P["gamma_th"] - 1.0) * rho * eps
+    B2 = B @ B
+    S = np.eye(3) * (p + 0.5 * B2) - np.outer(B, B)
+    Kh = np.trace(K)
+    At = K - np.eye(3) * Kh / 3.0
+    want_tau = al * (np.sum(S * At) + (3 * p + 0.5 * B2) * Kh / 3.0)
+    assert np.allclose(rhs[24][inner], want_tau, rtol=1e-11, atol=1e-20)
+    tpd = rho * (1 + eps) + 0.5 * B2
+    for i in range(3):
+        want = -a * S[0, i] - (tpd * a if i == 0 else 0.0)
+        assert np.allclose(rhs[25 + i][inner], want, rtol=1e-11, atol=1e-18), i
+    assert np.all(np.abs(rhs[22][inner]) < 1e-18)
