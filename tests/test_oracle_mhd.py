@@ -275,3 +275,37 @@ def test_energy_and_momentum_sources_closed_form():
         want = -a * S[0, i] - (tpd * a if i == 0 else 0.0)
         assert np.allclose(rhs[25 + i][inner], want, rtol=1e-11, atol=1e-18), i
     assert np.all(np.abs(rhs[22][inner]) < 1e-18)
+
+
+def test_shift_advection_terms_closed_form():
+    """Shift terms of the fluxes of eq. mhd_system on a magnetised fluid at
+    rest in flat space with alpha = 1 and a shift linear in x,
+    beta = (b x, c x, 0): every flux -beta^k U and the induction terms
+    Bbar^i (-beta^k) - Bbar^k (-beta^i) are linear in x, so
+      d_t (Dbar, DYebar, taubar) = b (Dbar, DYebar, taubar),  d_t Sbar_i = 0,
+      d_t Bbar = (0, b B^y - c B^x, b B^z),  d_t phibar = 0."""
+    P = synth.ideal_params(bc=2)
+    O = oracle.Oracle(P)
+    n, dx, b, c = (8, 8, 8), 0.05, 0.2, -0.15
+    shp = synth.patch_shape(n)
+    z, y, x = synth.grid_coords(n, (0.0, 0.0, 0.0), dx)
+    ID = np.zeros((26,) + shp)
+    ID[0] = ID[3] = ID[5] = 1.0
+    ID[12] = 1.0
+    ID[13] = b * x
+    ID[14] = c * x
+    ID[16], ID[17] = 1e-3, 0.1
+    B = np.array([0.011, -0.007, 0.004])
+    ID[21:24] = B[:, None, None, None]
+    ID[24] = 0.1
+    U = O.init_state(ID, n, dx)
+    prim, st, worst, its = O.con2prim_patch(U, n)
+    assert worst >= 0
+    rhs = O.rhs_patch(U, prim, n, dx)
+    inner = (slice(3, -3), slice(3, -3), slice(3, -3))
+    for f in (22, 23, 24):
+        assert np.allclose(rhs[f][inner], b * U[f][inner], rtol=1e-11, atol=1e-20), f
+    for f in (25, 26, 27, 28, 31):
+        assert np.all(np.abs(rhs[f][inner]) < 1e-17), f
+    assert np.allclose(rhs[29][inner], b * B[1] - c * B[0], rtol=1e-11, atol=1e-18)
+    assert np.allclose(rhs[30][inner], b * B[2], rtol=1e-11, atol=1e-18)
