@@ -67,6 +67,24 @@ def test_adam_step():
     assert np.allclose(w2, ww, rtol=1e-15, atol=1e-15) and np.allclose(m2, mm) and np.allclose(v2, vv)
 
 
+def test_adam_bias_correction_on_a_constant_gradient():
+    """Kingma & Ba's bias correction makes the moment estimates exact for a
+    constant gradient started from zero moments: m_hat = g, v_hat = g^2 at
+    every step t, so each step moves w by lr g / (|g| + eps) (about lr sign g,
+    the step-size bound of the method)."""
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=40) * 10 ** rng.uniform(-3, 1, 40)
+    w0 = rng.normal(size=40)
+    w, m, v = w0.copy(), np.zeros(40), np.zeros(40)
+    lr, b1, b2, eps = 1e-3, 0.9, 0.999, 1e-8
+    step = lr * g / (np.abs(g) + eps)
+    for t in range(1, 6):
+        w, m, v = oracle.adam(w, m, v, g, lr, b1, b2, eps, t)
+        assert np.allclose(w, w0 - t * step, rtol=0, atol=1e-13 * t)
+        assert np.allclose(m / (1 - b1 ** t), g, rtol=1e-13)
+        assert np.allclose(v / (1 - b2 ** t), g * g, rtol=1e-12)
+
+
 def _cons(O, n, seed):
     s = synth.c2p_states(n, seed=seed)
     cons = np.zeros((n, 10))
