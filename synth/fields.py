@@ -18,7 +18,7 @@ from .eos_table import M_B, model, radiation_constant
 from scipy.integrate import solve_ivp
 from scipy.interpolate import CubicSpline
 
-from .configs import NID, NG, grid_coords, patch_shape
+from .configs import NID, grid_coords, patch_shape
 
 
 def _modes(rng, nmodes=8):

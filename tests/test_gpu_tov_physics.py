@@ -8,7 +8,6 @@ on the GPU: the star stays static to the accuracy the discretisation gives.
 - total rest mass, the sum of Dbar dV over the interior: relative drift
   <= 1e-6 (the atmosphere and the outer boundary may exchange a little).
 """
-import numpy as np
 import pytest
 
 import synth

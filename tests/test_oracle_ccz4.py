@@ -13,7 +13,6 @@ R = -8 psi^-5 lap(psi), and flat space with constant gauge gives exact zeros.
 Errors must fall at 4th order with the grid spacing.
 """
 import numpy as np
-import pytest
 import sympy as sp
 
 import oracle
