@@ -1,9 +1,10 @@
-"""Pins of the oracle's single-patch ghost fill (three ghost layers per side).
+"""Pins of the oracle's single-patch ghost fill (three ghost layers per side)
 
 bc 0: periodic, vertex-centred with period n points (point -m is point n-m);
 bc 1: the outer-boundary extrapolation read as linear, (1 + m) U_0 - m U_1 at
 distance m, exact on data linear in the indices, edges and corners included;
-bc 2: the ghost values are left as they are (frozen)."""
+bc 2: the ghost values are left as they are (frozen).  Also the initial-data
+conversion to the CCZ4 and conserved variables on constant data."""
 import numpy as np
 import pytest
 
@@ -56,3 +57,45 @@ def test_frozen_ghosts_untouched():
     before = U.copy()
     O.ghost_fill(U, n)
     assert np.array_equal(U, before)
+
+
+def test_init_state_conformal_split_of_constant_data():
+    """Initial-data conversion to the CCZ4 variables (Sec. II A definitions):
+    chi = det(gamma)^(-1/3), gt_ij = chi gamma_ij (so det gt = 1),
+    Khat = gamma^ij K_ij, At_ij = chi (K_ij - gamma_ij K / 3) (trace-free with
+    respect to gt), Theta = 0, Gammahat = 0 for a constant metric, and the
+    densitized rest mass Dbar = sqrt(gamma) rho W."""
+    n = (5, 5, 5)
+    O = oracle.Oracle(synth.ideal_params(bc=2))
+    rng = np.random.default_rng(4)
+    M = np.eye(3) + 0.1 * rng.normal(size=(3, 3))
+    g = M @ M.T
+    K = 0.01 * rng.normal(size=(3, 3))
+    K = K + K.T
+    sym = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    ID = np.zeros((26,) + synth.patch_shape(n))
+    for m, (a, b) in enumerate(sym):
+        ID[m] = g[a, b]
+        ID[6 + m] = K[a, b]
+    ID[12] = 1.0
+    rho, eps = 2e-3, 0.2
+    v = np.array([0.1, -0.05, 0.02])
+    ID[16], ID[17] = rho, eps
+    ID[18:21] = v[:, None, None, None]
+    ID[24] = 0.1
+    U = O.init_state(ID, n, 0.1)
+    pt = (slice(None), 4, 4, 4)
+    u = U[pt]
+    chi = np.linalg.det(g) ** (-1.0 / 3.0)
+    gt = np.array([[u[0], u[1], u[2]], [u[1], u[3], u[4]], [u[2], u[4], u[5]]])
+    At = np.array([[u[6], u[7], u[8]], [u[7], u[9], u[10]], [u[8], u[10], u[11]]])
+    assert abs(u[12] - chi) < 1e-15
+    assert np.allclose(gt, chi * g, rtol=1e-14, atol=0)
+    assert abs(np.linalg.det(gt) - 1.0) < 1e-14
+    Kt = np.trace(np.linalg.solve(g, K))
+    assert abs(u[13] - Kt) < 1e-15
+    assert np.allclose(At, chi * (K - g * Kt / 3.0), rtol=1e-13, atol=1e-17)
+    assert abs(np.trace(np.linalg.solve(gt, At))) < 1e-16
+    assert u[14] == 0.0 and np.all(np.abs(u[15:18]) < 1e-15) and u[31] == 0.0
+    W = 1.0 / np.sqrt(1.0 - v @ g @ v)
+    assert abs(u[22] - np.sqrt(np.linalg.det(g)) * rho * W) < 1e-15 * rho
