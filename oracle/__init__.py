@@ -72,14 +72,19 @@ def make_table(t):
 _libs = {}
 
 
-def lib(flops=False):
-    name = "liboracle_flops.so" if flops else "liboracle.so"
+def lib(flops=False, omp=False):
+    """The plain serial build, the flop-counting build (flops) or the OpenMP
+    build of the same sources (omp: point loops on several host threads,
+    bitwise the serial build's results)."""
+    assert not (flops and omp)
+    name = "liboracle_flops.so" if flops else ("liboracle_omp.so" if omp else "liboracle.so")
     if name not in _libs:
         _build.build()
         L = ctypes.CDLL(os.path.join(os.path.dirname(os.path.abspath(__file__)), name))
         d, i, l, vp = ctypes.c_double, ctypes.c_int, ctypes.c_long, ctypes.c_void_p
         sig = {
             "oracle_flop_counter": (ctypes.c_longlong, [i]),
+            "oracle_set_threads": (i, [i]),
             "oracle_ghost_fill": (i, [vp, vp, i, vp, i]),
             "oracle_init_state": (i, [vp, vp, vp, i, d, vp, vp]),
             "oracle_con2prim_patch": (i, [vp, vp, vp, i, vp, vp, vp, vp]),
@@ -150,8 +155,12 @@ def _n3(n):
 class Oracle:
     """Oracle bound to one parameter set (and optional EOS table)."""
 
-    def __init__(self, params, table=None, flops=False):
-        self.L = lib(flops)
+    def __init__(self, params, table=None, flops=False, threads=None):
+        """threads: None for the serial build; n >= 1 for the OpenMP build on
+        n host threads (0: the OpenMP default)."""
+        self.L = lib(flops, omp=threads is not None)
+        if threads is not None:
+            self.threads = self.L.oracle_set_threads(int(threads))
         self.P = make_params(params)
         self.T = make_table(table)
         self.Tp = _ref(self.T.s) if self.T is not None else None

@@ -4,12 +4,27 @@
 #include <cstring>
 #include <vector>
 #include "oracle.hpp"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifdef ORACLE_COUNT_FLOPS
 long long oracle_flops = 0;
 #endif
 
 extern "C" {
+
+// Host threads of the OpenMP build's point loops (n <= 0 keeps the default);
+// returns the count in effect (1 in the serial builds).
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 long long oracle_flop_counter(int reset) {
 #ifdef ORACLE_COUNT_FLOPS

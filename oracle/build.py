@@ -1,10 +1,13 @@
 """Build the CPU oracle shared libraries (test infrastructure only).
 
-Two builds of the same sources:
-  liboracle.so        plain FP64 (`real` = double)
+Three builds of the same sources:
+  liboracle.so        plain FP64 (`real` = double), serial
   liboracle_flops.so  the same code with `real` counting every flop, used to
-                      measure the algorithmic flops per grid point.
-Both are compiled with -O2 -ffp-contract=off so the rounding sequence is the
+                      measure the algorithmic flops per grid point
+  liboracle_omp.so    the plain code with its independent point loops on
+                      several host threads (OpenMP); bitwise the serial results,
+                      for the full-size checks and the timed CPU baseline.
+All are compiled with -O2 -ffp-contract=off so the rounding sequence is the
 one written in the source.  Portable flags only (the GPU hosts are aarch64).
 """
 import os
@@ -29,7 +32,8 @@ def build(verbose=False):
     deps = srcs + [os.path.join(HERE, h) for h in HEADERS] + [os.path.abspath(__file__)]
     outs = []
     jobs = []
-    for name, extra in (("liboracle.so", []), ("liboracle_flops.so", ["-DORACLE_COUNT_FLOPS"])):
+    for name, extra in (("liboracle.so", []), ("liboracle_flops.so", ["-DORACLE_COUNT_FLOPS"]),
+                        ("liboracle_omp.so", ["-fopenmp"])):
         out = os.path.join(HERE, name)
         outs.append(out)
         if _outdated(out, deps):

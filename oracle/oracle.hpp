@@ -117,6 +117,18 @@ struct grid {
 };
 static const int NG = 3;
 
+// Loops over grid points whose iterations are independent (each writes only
+// its own point) may run on several host threads in the OpenMP build of the
+// same sources (liboracle_omp.so).  No point's arithmetic changes, so that
+// build's results are bitwise those of the serial one.
+#ifdef _OPENMP
+#define ORACLE_PAR_FOR _Pragma("omp parallel for collapse(2) schedule(static)")
+#define ORACLE_PAR_FOR_C2P _Pragma("omp parallel for collapse(2) schedule(static) reduction(min : worst) reduction(+ : its)")
+#else
+#define ORACLE_PAR_FOR
+#define ORACLE_PAR_FOR_C2P
+#endif
+
 // ---- patch-level steps (patch.cpp) ------------------------------------------
 grid make_grid(const int n[3], int px, double dx);
 // bc 0 periodic, 1 linear extrapolation; bc 2 (frozen) and 3 (mesh-refinement

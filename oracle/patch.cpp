@@ -73,6 +73,7 @@ static void ghost_fill_bc(int bc, const grid& G, double* U, int nf) {
 // (eq. def_con2prim), phi = 0.  Gammahat^i = Gt^i from the same centred D_i
 // as the right-hand side, so Z^i = 0 on the grid; then all ghosts are refilled.
 void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G, const double* ID, double* U) {
+  ORACLE_PAR_FOR
   for (int k = -NG; k < G.n[2] + NG; ++k)
     for (int j = -NG; j < G.n[1] + NG; ++j)
       for (int i = -NG; i < G.n[0] + NG; ++i) {
@@ -125,6 +126,7 @@ void init_state(const oracle_params* P, const oracle_eos_table* E, const grid& G
   // Gammahat^i = gt^{ij} gt^{kl} d_l gt_jk at interior points.
   const long st[3] = {1, G.sy, G.sz};
   const real inv12dx = 1.0 / (12.0 * G.dx);
+  ORACLE_PAR_FOR
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
@@ -158,6 +160,7 @@ int c2p_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G, 
               int8_t* status, long* iters_total) {
   int worst = 0;
   long its = 0;
+  ORACLE_PAR_FOR_C2P
   for (int k = -NG; k < G.n[2] + NG; ++k)
     for (int j = -NG; j < G.n[1] + NG; ++j)
       for (int i = -NG; i < G.n[0] + NG; ++i) {
@@ -206,6 +209,7 @@ void rhs_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G,
     int lo[3] = {0, 0, 0}, hi[3] = {G.n[0], G.n[1], G.n[2]};
     lo[d] = -NG;
     hi[d] = G.n[d] + NG;
+    ORACLE_PAR_FOR
     for (int k = lo[2]; k < hi[2]; ++k)
       for (int j = lo[1]; j < hi[1]; ++j)
         for (int i = lo[0]; i < hi[0]; ++i) {
@@ -224,6 +228,7 @@ void rhs_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G,
     c_pt += c1 - c0;
     lo[d] = -1;
     hi[d] = G.n[d];
+    ORACLE_PAR_FOR
     for (int k = lo[2]; k < hi[2]; ++k)
       for (int j = lo[1]; j < hi[1]; ++j)
         for (int i = lo[0]; i < hi[0]; ++i) {
@@ -245,6 +250,7 @@ void rhs_patch(const oracle_params* P, const oracle_eos_table* E, const grid& G,
     c_if += c0 - c1;
   }
   real idx = 1.0 / G.dx;
+  ORACLE_PAR_FOR
   for (int k = 0; k < G.n[2]; ++k)
     for (int j = 0; j < G.n[1]; ++j)
       for (int i = 0; i < G.n[0]; ++i) {
@@ -309,6 +315,7 @@ int substep(const oracle_params* P, const oracle_eos_table* E, const grid& G, in
   rhs_patch(P, E, G, in, prim, krhs, counts ? counts + 1 : nullptr);
   long long t2 = flops_now();
   real hdt = 0.5 * dt, sdt = dt / 6.0, tdt = dt / 3.0;
+  ORACLE_PAR_FOR
   for (int f = 0; f < NF; ++f)
     for (int k = 0; k < G.n[2]; ++k)
       for (int j = 0; j < G.n[1]; ++j)
