@@ -48,7 +48,14 @@ RK_FLOPS_PER_POINT = (128.0 * 3 + 64.0) / 4.0
 RHS_TRAFFIC_BYTES_PER_POINT = (192.75e6 + 208.55e6) / 64 ** 3
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 4 FP64 flops per
 # clock per SM x 2070 MHz (nominal GB300 FP64 1.25 TFLOP/s = 152 x 2.07 GHz x 3.97).
+# The line's peak is the measured one (the library's FMA throughput probe,
+# timed before the timed region); this derived figure is reported beside it.
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
+# FP64 flops that k_rhs executes per interior point (ncu: DADD + DMUL + 2 DFMA,
+# thread-level, on the 64^3 case; profiles/substep_kernels_tov64_ncu_full.md):
+# fewer than the algorithmic count, since the kernel shares differences,
+# reciprocals and the Christoffel contraction.
+RHS_EXECUTED_FLOPS_PER_POINT = 5200.0
 
 
 def _args():
@@ -72,6 +79,10 @@ def _args():
                    help="point counts of the hierarchy workload relative to the 366-patch layout")
     a.add_argument("--amr-seeded", action="store_true",
                    help="also time the hierarchy with NN-seeded con2prim")
+    a.add_argument("--amr-per-patch", action="store_true",
+                   help="also time the hierarchy with one launch per patch and kernel kind")
+    a.add_argument("--no-configs", action="store_true",
+                   help="default line: skip the batched (256 patches) and hierarchy (366 patches) sections")
     a.add_argument("--amr-delta", type=float, default=3e-2,
                    help="seed bracket half-width of the NN-seeded hierarchy and batched timings")
     a.add_argument("--no-autotune", action="store_true",
@@ -168,28 +179,35 @@ def _whole_job_rate(ws, steps, units_per_rank_step, ms_max):
     return ws * steps * units_per_rank_step / (ms_max / 1e3)
 
 
-def cpu_baseline(n=48, budget_s=12.0):
-    """The oracle as it stands, serial, on a sub-box of the workload (same dx, star centre)."""
+def cpu_baseline(n=48, budget_s=8.0):
+    """The oracle as it stands on a sub-box of the workload (same dx, star
+    centre): its OpenMP build on all host cores (the line's value), and the
+    serial build on one core beside it."""
     import oracle
     import synth
     P = synth.ideal_params(bc=1)
     nn = (n, n, n)
     ID = synth.tov_id(n=nn, x0=(-(n // 2) * DX,) * 3, dx=DX, seed=1)
-    O = oracle.Oracle(P)
-    U = O.init_state(ID, nn, DX)
-    regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
-    prim = np.zeros((oracle.NP,) + U.shape[1:])
-    st = np.zeros(U.shape[1:], dtype=np.int8)
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        O.rk4_step(regs, prim, st, nn, DX, 0.4 * DX)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or steps >= 50:
-            break
-    return {"value": steps * n ** 3 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d RK4 steps of a %d^3 sub-box of the TOV workload (same dx, star centre), serial C++ "
-                      "oracle, %.1f s" % (steps, n, el)}
+    res = {}
+    for threads in (0, None):
+        O = oracle.Oracle(P, threads=threads)
+        U = O.init_state(ID, nn, DX)
+        regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
+        prim = np.zeros((oracle.NP,) + U.shape[1:])
+        st = np.zeros(U.shape[1:], dtype=np.int8)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            O.rk4_step(regs, prim, st, nn, DX, 0.4 * DX)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > budget_s or steps >= 50:
+                break
+        res[threads] = (steps * n ** 3 / el, steps, el, getattr(O, "threads", 1))
+    v, steps, el, cores = res[0]
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d RK4 steps of a %d^3 sub-box of the TOV workload (same dx, star centre), the C++ "
+                      "oracle's OpenMP build on %d host threads, %.1f s" % (steps, n, cores, el),
+            "serial_1_core": {"value": res[None][0], "steps": res[None][1], "seconds": res[None][2]}}
 
 
 def cpu_baseline_c2p(n=1 << 19):
@@ -239,16 +257,19 @@ def cpu_baseline_amr(scale=0.25):
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, its OpenMP build (the
+    serial code's point loops on all host cores, bitwise the serial results),
+    one RK4 step of a 48^3 sub-box of the TOV workload per bench step."""
     ws, rank, local = _dist()
     if rank != 0:
         return 0
     import oracle
     import synth
-    n = 32
+    n = 48
     P = synth.ideal_params(bc=1)
     nn = (n, n, n)
     ID = synth.tov_id(n=nn, x0=(-(n // 2) * DX,) * 3, dx=DX, seed=1)
-    O = oracle.Oracle(P)
+    O = oracle.Oracle(P, threads=0)
     U = O.init_state(ID, nn, DX)
     regs = [U, np.zeros_like(U), np.zeros_like(U), np.zeros_like(U)]
     prim = np.zeros((oracle.NP,) + U.shape[1:])
@@ -260,12 +281,13 @@ def run_reference(args):
         O.rk4_step(regs, prim, st, nn, DX, 0.4 * DX)
     el = time.perf_counter() - t0
     value = args.steps * n ** 3 / el
-    sample = "one RK4 step of a %d^3 sub-box of the TOV workload per step (same dx, star centre), serial oracle" % n
+    sample = ("one RK4 step of a %d^3 sub-box of the TOV workload per step (same dx, star centre), oracle's "
+              "OpenMP build on %d host threads" % (n, O.threads))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample_edge": n, "dx": DX},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -308,6 +330,8 @@ def run_grmhd(args):
     rc = pt.sync_status()
     if rc != 0:
         raise SystemExit("warm-up failed: status %d" % rc)
+
+    fp64_peak = g.fp64_peak_tflops()
 
     # ---- timed region: K RK4 steps, kernels bracketed by CUDA events ----------
     clocks = Clocks(local) if rank == 0 else None
@@ -360,10 +384,13 @@ def run_grmhd(args):
     achieved = flops / (avg_rhs_ms / 1e3) / 1e12
     tot = sum(v[0] for v in prof.values()) or 1.0
     traffic = RHS_TRAFFIC_BYTES_PER_POINT * zones if RHS_TRAFFIC_BYTES_PER_POINT else None
+    executed = RHS_EXECUTED_FLOPS_PER_POINT * zones / (avg_rhs_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_rhs (CCZ4 + MHD RHS + RK epilogue)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived FP64: 152 SMs x 4 flop/clk x 2070 MHz",
-                "flops_per_point": RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT}
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
+                "peak_source": "measured: FP64 FMA throughput probe (grmhd_dfma_probe), best of 5 launches",
+                "peak_derived": FP64_PEAK_TFLOPS, "flops_per_point": RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT,
+                "executed_flops_per_point": RHS_EXECUTED_FLOPS_PER_POINT, "achieved_executed": executed,
+                "frac_executed": executed / fp64_peak}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -377,11 +404,11 @@ def run_grmhd(args):
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "kernel_share": {k: v[0] / tot for k, v in prof.items() if v[1]},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    del pt, host_in, host_out
+    torch.cuda.empty_cache()
     if ws == 1 and not args.no_c2p:
         # The metric's second half: con2prim solves/s, plain vs NN-seeded, on
         # the isolated workload (2^24 states, tabulated EOS), same GPU.
-        del pt, host_in, host_out
-        torch.cuda.empty_cache()
         c = _c2p_measure(args, min(args.steps, 5))
         line["con2prim"] = {
             "workload": c["config"]["workload"], "unit": "con2prim solves/s",
@@ -393,20 +420,32 @@ def run_grmhd(args):
             "same_status": c["seeded_vs_plain"]["same_status"],
             "max_rel_rho_diff": c["seeded_vs_plain"]["max_rel_rho_diff"], "clocks": c["clocks"]}
         line["gpu_launches_con2prim"] = c["gpu_launches"]
+    if ws == 1 and not args.no_configs and edge == N_EDGE:
+        # The other configurations on the same GPU: 256 uneven patches (plain
+        # per-patch vs batched vs batched NN-seeded) and the 366-patch star
+        # hierarchy (batched vs plain per-patch vs batched NN-seeded), each
+        # variant one RK4 step per bench step replayed from a CUDA graph.
+        torch.cuda.empty_cache()
+        line["batched"] = _batched_measure(args, min(args.steps, 5))
+        torch.cuda.empty_cache()
+        h, st = _amr_measure(args, min(args.steps, 3), seeded=True, per_patch=True)
+        del st
+        line["hierarchy"] = h
+        torch.cuda.empty_cache()
     if ws == 1 and not args.no_cpu_baseline and edge == N_EDGE:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batched(args):
-    """256 uneven patches (edges in {16,24,32,48,64} per axis, 5 levels, frozen
-    ghosts): batched (one launch per kernel over all patches) with and without
-    the autotuner and a CUDA graph, against plain per-patch launches."""
+def _batched_measure(args, K):
+    """Config 2: 256 uneven patches (edges in {16,24,32,48,64} per axis, 5
+    levels, frozen ghosts).  Each variant advances the same initial state by
+    one RK4 step per bench step, replayed from a CUDA graph:
+      plain per-patch: one launch per patch and kernel kind, bracketed con2prim;
+      batched: one launch per kernel kind over all patches (autotuned blocks);
+      batched NN-seeded: the batched form with the learned con2prim seeder."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
     import paper_2510_13965_gb300 as g
     import synth
 
@@ -416,8 +455,8 @@ def run_batched(args):
     zones = int(sum(np.prod(s["n"]) for s in specs))
     dt = 0.4 * min(s["dx"] for s in specs)
     stream = torch.cuda.Stream()
-    batched = g.Patches(P, specs, stream=stream)
     t0 = time.perf_counter()
+    batched = g.Patches(P, specs, stream=stream)
     for p_, s_ in enumerate(specs):
         batched.init_state(p_, torch.as_tensor(synth.batched_id(s_, seed=0, norm=norm), device="cuda"))
     batched.synchronize()
@@ -439,50 +478,55 @@ def run_batched(args):
             pt.U[p_][0].copy_(init[p_])
         torch.cuda.synchronize()
 
-    K = args.steps
     for _ in range(max(args.warmup, 3)):
         batched.step(dt)
     reset(batched)
-    ms_default = timed(lambda: batched.step(dt), K)
-    reset(batched)
     chosen = batched.autotune(dt, reps=2)
-    reset(batched)
-    ms_tuned = timed(lambda: batched.step(dt), K)
-    reset(batched)
-    batched.capture_graph(1, dt)
-    launches0 = batched.launch_count()
-    ms_graph = timed(batched.graph_launch, K)
-    launches = batched.launch_count() - launches0
+    clocks = Clocks(0)
+    ms = {}
+    launches = {}
+    for name, per_patch in (("plain_per_patch_graph", True), ("batched_graph", False)):
+        batched.set_per_patch(per_patch)
+        batched.capture_graph(1, dt)
+        reset(batched)
+        batched.graph_launch()
+        reset(batched)
+        l0 = batched.launch_count()
+        ms[name] = timed(batched.graph_launch, K)
+        launches[name] = (batched.launch_count() - l0) // K
+    batched.set_per_patch(False)
     rc = batched.sync_status()
-    # plain per-patch launches: one context per patch, all on the same stream
-    plain = []
-    for p_, s_ in enumerate(specs):
-        q = g.Patches(P, [s_], stream=stream)
-        q.U[0][0].copy_(init[p_])
-        plain.append(q)
-    torch.cuda.synchronize()
-    for q in plain:
-        q.step(dt)
-    for p_, q in enumerate(plain):
-        q.U[0][0].copy_(init[p_])
-    ms_plain = timed(lambda: [q.step(dt) for q in plain], K)
-    del plain
-    torch.cuda.synchronize()
-    seeded = _batched_seeded(args, g, P, batched, reset, timed, dt, K, ms_plain)
-    line = {"metric": METRIC, "value": zones / (ms_graph / 1e3), "unit": UNIT, "n_gpus": 1, "steps": K,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched_256_uneven_patches_5_levels_rk4_step", "patches": len(specs),
-                       "interior_points": zones, "edges": list(synth.EDGES), "levels": 5, "ghosts": "frozen",
-                       "l2": "inputs larger than L2"},
-            "variants_ms_per_step": {"plain_per_patch": ms_plain, "batched_default_bs128": ms_default,
-                                     "batched_autotuned": ms_tuned, "batched_autotuned_graph": ms_graph},
-            "speedup_batched_graph_vs_plain": ms_plain / ms_graph, "autotuned_block_sizes": list(chosen),
-            "gpu_launches": int(launches), "status": rc, "setup_s": gen_s}
+    seeded = _batched_seeded(args, g, P, batched, reset, timed, dt, K, ms["plain_per_patch_graph"])
     if seeded is not None:
-        line["variants_ms_per_step"]["batched_autotuned_graph_nn_seeded"] = seeded["ms_per_step"]
-        line["speedup_batched_nn_seeded_graph_vs_plain"] = ms_plain / seeded["ms_per_step"]
-        line["nn_seeded"] = seeded
+        ms["batched_graph_nn_seeded"] = seeded["ms_per_step"]
+    clk = clocks.stop()
+    out = {"workload": "batched_256_uneven_patches_5_levels_rk4_step", "unit": UNIT,
+           "patches": len(specs), "interior_points": zones, "edges": list(synth.EDGES), "levels": 5,
+           "ghosts": "frozen", "l2": "inputs larger than L2", "steps": K,
+           "zone_updates_per_s": {k: zones / (v / 1e3) for k, v in ms.items()},
+           "ms_per_step": ms, "launches_per_step": launches,
+           "speedup_batched_vs_plain_per_patch": ms["plain_per_patch_graph"] / ms["batched_graph"],
+           "autotuned_block_sizes": list(chosen), "status": rc, "setup_s": gen_s, "clocks": clk}
+    if seeded is not None:
+        out["speedup_batched_nn_seeded_vs_plain_per_patch"] = ms["plain_per_patch_graph"] / seeded["ms_per_step"]
+        out["nn_seeded"] = seeded
+    return out
+
+
+def run_batched(args):
+    """Config 2 on its own line (see _batched_measure)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    b = _batched_measure(args, args.steps)
+    line = {"metric": METRIC, "value": b["zone_updates_per_s"]["batched_graph"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": b["ms_per_step"]["batched_graph"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": b["workload"], "patches": b["patches"], "interior_points": b["interior_points"],
+                       "l2": b["l2"]},
+            "batched": b, "gpu_launches": int(b["launches_per_step"]["batched_graph"] * args.steps),
+            "clocks": b["clocks"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -750,18 +794,18 @@ def _hierarchy_pairs(g, P, T, pt, n, seed):
     return g.prim2con_flat(P, prim, B, table=T)
 
 
-def run_amr(args):
-    """The magnetised TOV star with the synthetic tabulated EOS on a fixed
-    5-level hierarchy (level 0 one 128^3 patch, levels 1-3 160^3 cubes in
+def _amr_measure(args, K, seeded=False, per_patch=False):
+    """Config 4: the magnetised TOV star with the synthetic tabulated EOS on a
+    fixed 5-level hierarchy (level 0 one 128^3 patch, levels 1-3 160^3 cubes in
     uneven blocks, level 4 a 256^3 cube of 64^3 blocks; 366 patches, ~69 GB of
     device state), advanced without sub-cycling: every substep fills the
     hierarchy's ghosts level by level, then runs con2prim, fluxes and the
-    right-hand side over all patches in one launch per kernel; each step ends
-    with the restriction.  One bench step = one RK4 step of every level."""
+    right-hand side; each step ends with the restriction.  One bench step = one
+    RK4 step of every level, replayed from a CUDA graph.  Variants, each timed
+    from the same state saved after the warm-up: batched (one launch per kernel
+    kind over all patches), plain per-patch (one launch per patch and kernel
+    kind), batched NN-seeded.  Returns (result, state for further runs)."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
     import paper_2510_13965_gb300 as g
     import synth
 
@@ -794,22 +838,30 @@ def run_amr(args):
     rc = pt.sync_status()
     if rc != 0:
         raise SystemExit("warm-up failed: status %d" % rc)
-    pt.capture_graph(1, dt)
-    # The NN-seeded timing restarts from this state, so both forms advance the
-    # same states (the cost of the interface fluxes grows as the atmosphere
-    # picks up motion).
-    snap = [u[0].clone() for u in pt.U] if args.amr_seeded else None
-    launches0 = pt.launch_count()
-    clocks = Clocks(0)
+    # Every variant restarts from this state (the interface fluxes cost more
+    # as the atmosphere picks up motion, so the variants advance the same states).
+    snap = [u[0].clone() for u in pt.U] if (seeded or per_patch) else None
+
+    def restore():
+        for u, u0 in zip(pt.U, snap):
+            u[0].copy_(u0)
+        torch.cuda.synchronize()
+
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        pt.graph_launch()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = pt.launch_count() - launches0
+
+    def timed_graph():
+        l0 = pt.launch_count()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            pt.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K, (pt.launch_count() - l0) // K
+
+    pt.capture_graph(1, dt)
+    clocks = Clocks(0)
+    ms, launches = timed_graph()
     clk = clocks.stop()
     rc = pt.sync_status()
     # One eager, profiled step for the per-kernel split.
@@ -819,8 +871,26 @@ def run_amr(args):
     prof_k = pt.profile_read()
     pt.profile(False)
     tot = sum(v[0] for v in prof_k.values()) or 1.0
-    seeded = None
-    if args.amr_seeded:
+    out = {"workload": "tov_table_eos_5_level_hierarchy_%d_patches_rk4_step" % len(specs) +
+                       ("_les_cm%g" % args.les_cm if args.les_cm else ""),
+           "unit": UNIT, "scale": args.amr_scale, "patches": len(specs), "interior_points": zones,
+           "finest_dx": min(s_["dx"] for s_ in specs), "dt": dt, "subcycling": "none",
+           "eos": "synthetic table 256x128x64", "l2": "inputs larger than L2", "steps": K,
+           "value": zones / (ms / 1e3), "ms_per_step": ms, "launches_per_step": launches,
+           "kernel_ms_per_step": {k: v[0] for k, v in prof_k.items() if v[1]},
+           "kernel_share": {k: v[0] / tot for k, v in prof_k.items() if v[1]},
+           "status": rc, "clocks": clk, "setup_s": setup_s}
+    if per_patch:
+        restore()
+        pt.set_per_patch(True)
+        pt.capture_graph(1, dt)
+        restore()
+        ms_p, launches_p = timed_graph()
+        pt.set_per_patch(False)
+        out["plain_per_patch"] = {"value": zones / (ms_p / 1e3), "ms_per_step": ms_p, "launches_per_step": launches_p,
+                                  "status": pt.sync_status()}
+        out["speedup_batched_vs_plain_per_patch"] = ms_p / ms
+    if seeded:
         # The same steps with NN-seeded con2prim.  The network is trained on
         # the GPU on 2^20 flat-metric pairs the method makes from this star's
         # own solved points (see _hierarchy_pairs); with the network of the
@@ -835,35 +905,47 @@ def run_amr(args):
         S = g.Seeder(seed=1)
         S.train(f, t, batch=4096, epochs=args.train_epochs, lr=3e-3, lr_final=3e-5)
         del f, t
+        restore()
         pt.set_seeder(None)
         it_plain = pt.con2prim(0, stats=True)
         pt.set_seeder(S, args.amr_delta)
         it_seeded = pt.con2prim(0, stats=True)
-        for _ in range(2):
-            pt.step(dt)
         pt.capture_graph(1, dt)
-        torch.cuda.synchronize()
-        for u, u0 in zip(pt.U, snap):
-            u[0].copy_(u0)
-        del snap
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
-            pt.graph_launch()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_s = e0.elapsed_time(e1) / args.steps
+        restore()
+        ms_s, launches_s = timed_graph()
         pt.profile(True)
         pt.step(dt)
         pt.synchronize()
         prof_s = pt.profile_read()
         pt.profile(False)
-        seeded = {"value": zones / (ms_s / 1e3), "ms_per_step": ms_s, "delta": args.amr_delta,
-                  "kernel_ms_per_step": {k: v[0] for k, v in prof_s.items() if v[1]},
-                  "c2p_iterations_per_point": {"plain": it_plain["iterations"] / max(it_plain["points"], 1),
-                                               "nn_seeded": it_seeded["iterations"] / max(it_seeded["points"], 1)},
-                  "train_pairs": "%d flat-metric pairs from the hierarchy's solved points (seed 13)" % args.train_pairs,
-                  "status": pt.sync_status(), "speedup_vs_plain": ms / ms_s}
+        out["nn_seeded"] = {"value": zones / (ms_s / 1e3), "ms_per_step": ms_s, "delta": args.amr_delta,
+                            "launches_per_step": launches_s,
+                            "kernel_ms_per_step": {k: v[0] for k, v in prof_s.items() if v[1]},
+                            "c2p_iterations_per_point": {
+                                "plain": it_plain["iterations"] / max(it_plain["points"], 1),
+                                "nn_seeded": it_seeded["iterations"] / max(it_seeded["points"], 1)},
+                            "train_pairs": "%d flat-metric pairs from the hierarchy's solved points (seed 13)"
+                                           % args.train_pairs,
+                            "status": pt.sync_status(), "speedup_vs_plain": ms / ms_s}
+        if per_patch:
+            out["speedup_batched_nn_seeded_vs_plain_per_patch"] = out["plain_per_patch"]["ms_per_step"] / ms_s
+        pt.set_seeder(None)
+    del snap
+    state = dict(pt=pt, specs=specs, dt=dt, stream=stream, ms=ms, e0=e0, e1=e1)
+    return out, state
+
+
+def run_amr(args):
+    """Config 4 on its own line (see _amr_measure), with optional sub-cycled
+    timing (--amr-subcycle) and a run of the configuration's length (--amr-run)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    out, state = _amr_measure(args, args.steps, seeded=args.amr_seeded, per_patch=args.amr_per_patch)
+    pt, specs, dt, stream, ms = state["pt"], state["specs"], state["dt"], state["stream"], state["ms"]
+    e0, e1 = state["e0"], state["e1"]
+    zones = out["interior_points"]
     levels = {}
     for s_ in specs:
         levels.setdefault(s_["level"], [0, 0])
@@ -875,8 +957,7 @@ def run_amr(args):
         # dt0 = 2^L dt, so every level keeps the synchronous run's Courant
         # factor on its own grid; one bench step = one level-0 step, the same
         # physical time as 2^L synchronous steps.
-        if seeded is not None:
-            pt.set_seeder(None)  # the plain con2prim of the synchronous timing
+        pt.set_seeder(None)  # the plain con2prim of the synchronous timing
         nlev = max(levels) + 1
         dt0 = dt * 2 ** (nlev - 1)
         pt.set_subcycling(True)
@@ -942,21 +1023,16 @@ def run_amr(args):
         rho1 = float(pt.prim[pc][0, ijk[2] + 3, ijk[1] + 3, ijk[0] + 3])
         run = {"finest_steps": nstep * per, "subcycled": sub, "simulated_time": nstep * per * dt, "seconds": run_s,
                "rho_c": [rho0, rho1], "rho_c_drift": rho1 / rho0 - 1.0, "status": pt.sync_status()}
-    line = {"metric": METRIC, "value": zones / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    line = {"metric": METRIC, "value": out["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "tov_table_eos_5_level_hierarchy_%d_patches_rk4_step" % len(specs) +
-                       ("_les_cm%g" % args.les_cm if args.les_cm else ""),
-                       "scale": args.amr_scale,
-                       "patches": len(specs), "interior_points": zones,
+            "config": {"workload": out["workload"], "scale": args.amr_scale, "patches": len(specs),
+                       "interior_points": zones,
                        "levels": {str(k): {"patches": v[0], "points": v[1]} for k, v in sorted(levels.items())},
-                       "finest_dx": min(s_["dx"] for s_ in specs), "dt": dt, "subcycling": "none",
-                       "eos": "synthetic table 256x128x64", "l2": "inputs larger than L2"},
-            "kernel_ms_per_step": {k: v[0] for k, v in prof_k.items() if v[1]},
-            "kernel_share": {k: v[0] / tot for k, v in prof_k.items() if v[1]},
-            "gpu_launches": int(launches), "status": rc, "clocks": clk, "setup_s": setup_s}
-    if seeded is not None:
-        line["nn_seeded"] = seeded
+                       "finest_dx": out["finest_dx"], "dt": dt, "subcycling": "none", "eos": out["eos"],
+                       "l2": out["l2"]},
+            "hierarchy": out, "gpu_launches": int(out["launches_per_step"] * args.steps), "status": out["status"],
+            "clocks": out["clocks"], "setup_s": out["setup_s"]}
     if subcycled is not None:
         line["subcycled"] = subcycled
     if run is not None:

@@ -189,7 +189,8 @@ typedef struct grmhd_c2p_stats {
 
 typedef struct grmhd_ctx grmhd_ctx;
 
-/* Version of this ABI (increases when a signature changes). */
+/* Version of this ABI (increases when a signature changes; 2 since
+ * grmhd_rhs_eval_static gained dev_flags). */
 int grmhd_abi_version(void);
 
 /* Creates a context for npatch patches (init_patches).  Validates the
@@ -218,18 +219,31 @@ int grmhd_init_state(grmhd_ctx* ctx, int patch, const double* id);
  * grmhd_con2prim: call grmhd_con2prim after it, as the substep does. */
 int grmhd_ghost_fill(grmhd_ctx* ctx, int reg);
 
-/* con2prim at every point (ghosts included) of register `reg` of every patch:
- * writes prim and status; where a correction fired, the conserved variables
+/* con2prim at every point (ghosts included) of register `reg` of every patch
+ * (appendix "Conversion from conserved to primitive fields": Kastaun's
+ * bracket mu_+ from eq. f_mu_plus, the master-function root on (0, mu_+],
+ * the EOS validity clamps and the error policy; the conserved definitions
+ * inverted are Sec. II B eq. def_con2prim).  Also forms the pointwise MHD flux
+ * vectors (eq. mhd_system) and fast speeds (appendix "Characteristic
+ * structure", eq. fast_waves) that grmhd_rhs_eval reads.  Writes prim and status; where a correction fired, the conserved variables
  * of `reg` are recomputed from the corrected primitives.  If stats is
  * non-NULL the call synchronises the stream and fills it. */
 int grmhd_con2prim(grmhd_ctx* ctx, int reg, grmhd_c2p_stats* stats);
 
-/* Right-hand side L(U) of register `reg` at interior points, from the
+/* Right-hand side L(U) of register `reg` at interior points (Sec. III,
+ * eq. PDEequation, the semi-discrete operator of the method of lines): the
+ * CCZ4 + gauge right-hand side of Sec. II A (eqs. system1 .. system3) with the
+ * centred, one-sided and Kreiss-Oliger operators of Sec. III B, plus the MHD
+ * flux difference of Sec. III C (eqs. flux_decomposition, LLF2, MP5_unal ..
+ * MP5_dm4) and the geometric sources of eq. mhd_system, from the
  * primitives and pointwise fluxes of the last grmhd_con2prim call.  rhs[p] is a device array with
  * the patch layout (32 fields); ghost entries are not written. */
 int grmhd_rhs_eval(grmhd_ctx* ctx, int reg, double* const* rhs);
 
-/* Stage combination (unfused), interior points, with k = rhs[p].  RK4:
+/* Stage combination (unfused), interior points, with k = rhs[p]: the explicit
+ * half of the IMEX scheme of Sec. III A (eq. eq_IMEX with no stiff part), with
+ * the coefficients of Table RK4 (explicit RK4(4,4)) or Table RK3SSP (explicit
+ * SSP-RK(3,3)).  RK4:
  *   stage 0: U[1] = U[0] + dt/2 k, U[3] = U[0] + dt/6 k
  *   stage 1: U[2] = U[0] + dt/2 k, U[3] += dt/3 k
  *   stage 2: U[1] = U[0] + dt k,   U[3] += dt/3 k
@@ -240,17 +254,20 @@ int grmhd_rhs_eval(grmhd_ctx* ctx, int reg, double* const* rhs);
  *   stage 2: U[0] = U[3] + 2 dt/3 k */
 int grmhd_rk_update(grmhd_ctx* ctx, int stage, double dt, double* const* rhs);
 
-/* One fused substep `stage` of the time integrator: ghost fill of the stage
- * input, con2prim, right-hand side and the stage combination of
- * grmhd_rk_update, without storing k.  RK4 (rk = 0): stages 0..3, inputs U[0],
+/* One fused substep `stage` of the time integrator (Sec. III A, method of
+ * lines with the explicit stages of Table RK4 / Table RK3SSP): ghost fill of
+ * the stage input (Sec. IV B), con2prim (appendix on the conversion from
+ * conserved to primitive fields), right-hand side L(U) (eq. PDEequation) and
+ * the stage combination of grmhd_rk_update, without storing k.  RK4 (rk = 0): stages 0..3, inputs U[0],
  * U[1], U[2], U[1].  SSP-RK3 (rk = 1): stages 0..2, inputs U[0] (Y1), U[1]
  * (Y2 = U^n + dt k1), U[2] (Y3 = U^n + dt/4 k1 + dt/4 k2); U[3] accumulates
  * U^n + dt/6 (k1 + k2) and the last stage writes U^{n+1} = U[3] + 2 dt/3 k3
  * into U[0]. */
 int grmhd_rhs_substep(grmhd_ctx* ctx, int stage, double dt);
 
-/* One full step of the time integrator (four fused substeps for RK4, three
- * for SSP-RK3); with bc = 3, followed by grmhd_restrict(ctx, 0).  With
+/* One full step of the time integrator (Sec. III A: U^{n+1} from the stages
+ * of eq. eq_IMEX with the explicit tableaux of Table RK4 / Table RK3SSP; four
+ * fused substeps for RK4, three for SSP-RK3); with bc = 3, followed by grmhd_restrict(ctx, 0).  With
  * sub-cycling on (grmhd_set_subcycling), dt is the level-0 step and one call
  * advances level l by 2^l steps of dt / 2^l (see below). */
 int grmhd_step(grmhd_ctx* ctx, double dt);
@@ -293,6 +310,14 @@ int grmhd_graph_launch(grmhd_ctx* ctx);
  * the last call (GRMHD_OK, GRMHD_ERR_C2P_FATAL or GRMHD_ERR_NONFINITE), then
  * clears it. */
 int grmhd_sync_status(grmhd_ctx* ctx);
+
+/* Launch granularity.  With on != 0 every seeder, con2prim, LES,
+ * interface-flux and right-hand-side launch covers one patch (one launch per
+ * patch and kernel kind, in patch order, on the same stream): the plain
+ * per-patch form that the batched launches (one per kernel kind over all
+ * patches, the default, on = 0) are measured against.  Results are bitwise
+ * the same in both forms; ghost fills and restrictions stay batched. */
+int grmhd_set_per_patch(grmhd_ctx* ctx, int on);
 
 /* Threads per block of the con2prim, interface-flux and right-hand-side
  * kernels (each 64, 128 or 256; 128 at creation). */
@@ -344,6 +369,18 @@ int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long 
 int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
                    double* prim, int8_t* status, int32_t* iters, void* stream);
 
+/* ---- FP64 peak probe ------------------------------------------------------ */
+
+/* Measurement aid with no counterpart in the paper: one launch of
+ * blocks_per_sm (1..8) blocks of 256 threads per SM, each thread running 8
+ * independent FP64 fused multiply-add chains for iters iterations.  *fmas
+ * receives the thread-level FMAs of the launch (2 FP64 flops each); the caller
+ * times the launch on `stream` with CUDA events to measure the FP64 peak that
+ * the right-hand-side kernels are compared with.  sink: a device array of at
+ * least blocks_per_sm * (SM count) doubles, written only in a case that does
+ * not occur (it keeps the arithmetic from being optimised away). */
+int grmhd_dfma_probe(int blocks_per_sm, long long iters, double* sink, long long* fmas, void* stream);
+
 /* ---- allocation-free right-hand side -------------------------------------- */
 
 /* No counterpart in the paper; this is a service for callers that must not
@@ -359,20 +396,27 @@ int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long 
  * U[reg] must already hold filled ghost zones; only U[reg], prim and status
  * of the descriptor are used.  eos may be NULL for the ideal gas.
  *
+ * dev_flags: NULL, or a device int (4-byte aligned) that receives, in stream
+ * order after the kernels, this call's device error bits: bit 0 a fatal
+ * con2prim point (also in the status array), bit 1 a non-finite conserved
+ * state met by con2prim.  A non-finite right-hand-side value that arises
+ * from finite inputs is not detected.
+ *
  * It calls no cudaMalloc, cudaFree or other allocating routine: its working
  * memory (pointwise and interface fluxes, descriptor, work list, flags) is a
  * file-scope static device array of about 27.7 MB that every GPU which loads
- * the library holds until the process exits.  Patches are limited to
+ * the library holds until the process exits.  The descriptor, rhs and the
+ * work list reach that array through a set-up kernel's arguments, not through
+ * copies from host memory.  Patches are limited to
  * px * (n[1]+6) * (n[2]+6) <= 54872 ghosted points (a 32^3 patch); larger ones
  * return GRMHD_ERR_SIZE before any work is enqueued.  The first call on a device
  * looks up the array's device address with that device current; make that
  * first call before any stream capture.  All calls on a device share the
  * array and it keeps the last call's contents, so calls that may overlap on
  * the GPU (two streams of one device) race and must be serialised by the
- * caller; calls on one stream are ordered.  Work is enqueued on `stream`.
- * Fatal con2prim points are reported only through the status array. */
+ * caller; calls on one stream are ordered.  Work is enqueued on `stream`. */
 int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_desc* d, const grmhd_eos_table* eos, int reg,
-                          double* rhs, void* stream);
+                          double* rhs, int* dev_flags, void* stream);
 
 /* ---- learned con2prim seeder ----------------------------------------------
  *
@@ -482,6 +526,17 @@ int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double*
  * wait is bounded; the kernel then frees its tensor memory and stops), else
  * GRMHD_OK; clears the condition. */
 int grmhd_seeder_status(grmhd_seeder* s);
+
+/* Test hook for the timeout path above (no counterpart in the paper).  With
+ * polls > 0 the inference kernels of this seeder (grmhd_seeder_forward,
+ * grmhd_seeder_infer and the seeds of a context's con2prim) issue no
+ * tensor-core products, so each bounded wait for a product gives up after
+ * `polls` polls with nothing in flight: the kernel records GRMHD_ERR_TIMEOUT
+ * (grmhd_seeder_status, or grmhd_sync_status for a context's seeds), frees its
+ * tensor memory and stops, leaving the outputs it did not reach unwritten.
+ * A seeded con2prim still gives the plain results (every seed is checked
+ * against the bracket).  polls = 0 restores normal operation. */
+int grmhd_seeder_hold_products(grmhd_seeder* s, int polls);
 
 void grmhd_seeder_destroy(grmhd_seeder* s);
 

@@ -91,7 +91,11 @@ _SIGS = {
     "grmhd_c2p_flat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_rhs_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
-                                             ctypes.c_void_p, ctypes.c_void_p]),
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_set_per_patch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_seeder_hold_products": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_dfma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "grmhd_seeder_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong]),
     "grmhd_seeder_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_seeder_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -246,6 +250,11 @@ class Patches:
     def _enter(self):
         self.stream.wait_stream(self.torch.cuda.current_stream())
 
+    def _leave(self):
+        # The caller's stream waits for the work just enqueued, so it may read
+        # the registers, primitives and status arrays without synchronize().
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+
     def synchronize(self):
         self.stream.synchronize()
 
@@ -258,15 +267,18 @@ class Patches:
         id_tensor.record_stream(self.stream)
         _check(self.L.grmhd_init_state(self.ctx, patch, ctypes.c_void_p(id_tensor.data_ptr())), self.ctx,
                "grmhd_init_state")
+        self._leave()
 
     def ghost_fill(self, reg):
         self._enter()
         _check(self.L.grmhd_ghost_fill(self.ctx, reg), self.ctx, "grmhd_ghost_fill")
+        self._leave()
 
     def con2prim(self, reg, stats=False):
         self._enter()
         s = C2PStats()
         _check(self.L.grmhd_con2prim(self.ctx, reg, ctypes.byref(s) if stats else None), self.ctx, "grmhd_con2prim")
+        self._leave()
         return dict(points=s.points, iterations=s.iterations, corrected=s.corrected, failed=s.failed) if stats else None
 
     def rhs_eval(self, reg, out=None):
@@ -291,10 +303,12 @@ class Patches:
             t.record_stream(self.stream)
         arr = (ctypes.c_void_p * len(rhs))(*[t.data_ptr() for t in rhs])
         _check(self.L.grmhd_rk_update(self.ctx, stage, float(dt), arr), self.ctx, "grmhd_rk_update")
+        self._leave()
 
     def rhs_substep(self, stage, dt):
         self._enter()
         _check(self.L.grmhd_rhs_substep(self.ctx, stage, float(dt)), self.ctx, "grmhd_rhs_substep")
+        self._leave()
 
     def set_seeder(self, seeder, delta=1e-2):
         """Seed every con2prim of this context with the network (None: plain brackets)."""
@@ -305,6 +319,7 @@ class Patches:
     def restrict(self, reg=0):
         self._enter()
         _check(self.L.grmhd_restrict(self.ctx, reg), self.ctx, "grmhd_restrict")
+        self._leave()
 
     def set_subcycling(self, on=True):
         """Sub-cycling in time on a hierarchy (bc 3): step(dt0) then advances
@@ -315,6 +330,7 @@ class Patches:
     def step(self, dt):
         self._enter()
         _check(self.L.grmhd_step(self.ctx, float(dt)), self.ctx, "grmhd_step")
+        self._leave()
 
     def capture_graph(self, nsteps, dt):
         self.synchronize()
@@ -323,11 +339,16 @@ class Patches:
     def graph_launch(self):
         self._enter()
         _check(self.L.grmhd_graph_launch(self.ctx), self.ctx, "grmhd_graph_launch")
+        self._leave()
 
     def sync_status(self):
         return self.L.grmhd_sync_status(self.ctx)
 
     KERNEL_KINDS = ("ghost", "c2p", "iflux", "rhs", "rk", "init", "seed", "dense", "les")
+
+    def set_per_patch(self, on=True):
+        """One launch per patch and kernel kind (the plain per-patch form) instead of one per kernel kind."""
+        _check(self.L.grmhd_set_per_patch(self.ctx, 1 if on else 0), self.ctx, "grmhd_set_per_patch")
 
     def set_block_sizes(self, bs_c2p, bs_iflux, bs_rhs):
         _check(self.L.grmhd_set_block_sizes(self.ctx, bs_c2p, bs_iflux, bs_rhs), self.ctx, "grmhd_set_block_sizes")
@@ -367,6 +388,30 @@ def prim2con_flat(params, prim, B, table=None, stream=None):
                                ctypes.c_void_p(cons.data_ptr()), ctypes.c_void_p(s.cuda_stream))
     _check(rc, None, "grmhd_prim2con_flat")
     return cons
+
+
+def fp64_peak_tflops(iters=4000, blocks_per_sm=4, reps=5):
+    """Measured FP64 throughput of this GPU (TFLOP/s, 2 flops per FMA): the
+    best of `reps` launches of the library's FMA probe, each timed with CUDA
+    events on the current stream after one untimed launch."""
+    torch = _torch()
+    L = load()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.zeros(nsm * blocks_per_sm, dtype=torch.float64, device="cuda")
+    fmas = ctypes.c_longlong(0)
+    s = torch.cuda.current_stream()
+    best = 0.0
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        rc = L.grmhd_dfma_probe(int(blocks_per_sm), int(iters), _vp(sink), ctypes.byref(fmas),
+                                ctypes.c_void_p(s.cuda_stream))
+        e1.record(s)
+        _check(rc, None, "grmhd_dfma_probe")
+        torch.cuda.synchronize()
+        if r:
+            best = max(best, 2.0 * fmas.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
 
 
 def c2p_flat(params, cons, table=None, iters=False, stream=None, out=None):
@@ -480,6 +525,11 @@ class Seeder:
                                        _stream(torch, stream))
         _check(rc, None, "grmhd_seeder_train")
         return hist
+
+    def hold_products(self, polls):
+        """Test hook: with polls > 0 the inference kernels issue no tensor-core
+        products and every bounded wait for one gives up after `polls` polls."""
+        _check(load().grmhd_seeder_hold_products(self.h, int(polls)), None, "grmhd_seeder_hold_products")
 
     def status(self):
         """0, or raises when an inference kernel timed out waiting for its tensor-core products."""

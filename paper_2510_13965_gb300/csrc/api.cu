@@ -20,6 +20,11 @@ struct grmhd_ctx {
   Work* work = nullptr;
   std::vector<std::array<std::array<int, NDOM + 1>, NBS>> wofs;
   int bs_c2p = 128, bs_if = 128, bs_rhs = 128;  // chosen block sizes
+  // Per-patch slices of every work list, [group][block size][domain] -> for
+  // each patch of the group in order, (first item, item count) relative to the
+  // list's start; used when per_patch launches are on.
+  std::vector<std::array<std::array<std::vector<std::pair<int, int>>, NDOM>, NBS>> pslice;
+  bool per_patch = false;
   double* scratch = nullptr;
   DevFlags* flags = nullptr;
   C2PStats* stats = nullptr;
@@ -111,9 +116,22 @@ static int check_launch(grmhd_ctx* c, const char* what) {
 
 static int bs_index(int bs) { return bs == 64 ? 0 : (bs == 256 ? 2 : 1); }
 
+// Calls fn(work items, count) once for the whole list of a domain (batched
+// launches) or once per patch of the group (per-patch launches).
+template <class Fn>
+static void for_slices(grmhd_ctx* c, int dom, int bs, int grp, Fn fn) {
+  const int b = bs_index(bs);
+  const Work* w = c->work + c->wofs[grp][b][dom];
+  if (!c->per_patch) {
+    fn(w, c->wofs[grp][b][dom + 1] - c->wofs[grp][b][dom]);
+    return;
+  }
+  for (const auto& sl : c->pslice[grp][b][dom]) fn(w + sl.first, sl.second);
+}
+
 extern "C" {
 
-int grmhd_abi_version(void) { return 1; }
+int grmhd_abi_version(void) { return 2; }
 
 const char* grmhd_last_error(grmhd_ctx* c) { return c ? c->err.c_str() : kNoCtx; }
 
@@ -229,6 +247,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
     if (ok) ngrp = 2 + maxl;  // otherwise the hierarchy plan below rejects the layout
   }
   c->wofs.assign(ngrp, {});
+  c->pslice.assign(ngrp, {});
   std::vector<Work> wl;
   for (int g = 0; g < ngrp; ++g)
     for (int b = 0; b < NBS; ++b) {
@@ -239,6 +258,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
           if (g > 0 && d[i].level != g - 1) continue;
           long long n = dom_count(dom, c->pd_host[i].G);
           long long nb = (n + bs - 1) / bs;
+          c->pslice[g][b][dom].push_back({(int)wl.size() - c->wofs[g][b][dom], (int)nb});
           for (long long k = 0; k < nb; ++k) wl.push_back(Work{i, (int)k});
         }
       }
@@ -419,21 +439,28 @@ int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
 static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats, int grp = 0) {
   if (c->seeder) {
     ProfScope ps(c, K_SEED);
-    int rc = launch_seeder_patches(c->seeder, c->pd, wl(c, DOM_ALL, 128, grp), nblk(c, DOM_ALL, 128, grp), reg,
-                                   c->P.rho_min, &c->flags->flags, c->st);
-    c->launches += 1;
+    int rc = GRMHD_OK;
+    for_slices(c, DOM_ALL, 128, grp, [&](const Work* w, int n) {
+      int r = launch_seeder_patches(c->seeder, c->pd, w, n, reg, c->P.rho_min, &c->flags->flags, c->st);
+      if (r && !rc) rc = r;
+      c->launches += 1;
+    });
     if (rc) return fail(c, rc, "seeder launch");
   }
   {
     ProfScope ps(c, K_C2P);
-    launch_c2p(c->pd, wl(c, DOM_ALL, c->bs_c2p, grp), nblk(c, DOM_ALL, c->bs_c2p, grp), reg, c->P, c->E, c->flags,
-               stats ? c->stats : nullptr, c->st, c->bs_c2p, c->seeder != nullptr, c->seed_delta);
-    c->launches += 1;
+    for_slices(c, DOM_ALL, c->bs_c2p, grp, [&](const Work* w, int n) {
+      launch_c2p(c->pd, w, n, reg, c->P, c->E, c->flags, stats ? c->stats : nullptr, c->st, c->bs_c2p,
+                 c->seeder != nullptr, c->seed_delta);
+      c->launches += 1;
+    });
   }
   if (c->les_buf) {
     ProfScope ps(c, K_LES);
-    launch_les(c->pd, wl(c, DOM_ALL, 128, grp), nblk(c, DOM_ALL, 128, grp), reg, c->P, c->E, c->st);
-    c->launches += 2;
+    for_slices(c, DOM_ALL, 128, grp, [&](const Work* w, int n) {
+      launch_les(c->pd, w, n, reg, c->P, c->E, c->st);
+      c->launches += 2;
+    });
   }
   return check_launch(c, "con2prim");
 }
@@ -468,9 +495,10 @@ int grmhd_set_seeder(grmhd_ctx* c, const grmhd_seeder* s, double delta) {
 static int iflux(grmhd_ctx* c, int reg, int grp = 0) {
   for (int d = 0; d < 3; ++d) {
     ProfScope ps(c, K_IFLUX);
-    launch_iflux(c->pd, wl(c, DOM_IFX + d, c->bs_if, grp), nblk(c, DOM_IFX + d, c->bs_if, grp), reg, d, c->st,
-                 c->bs_if);
-    c->launches += 1;
+    for_slices(c, DOM_IFX + d, c->bs_if, grp, [&](const Work* w, int n) {
+      launch_iflux(c->pd, w, n, reg, d, c->st, c->bs_if);
+      c->launches += 1;
+    });
   }
   return check_launch(c, "iflux");
 }
@@ -507,10 +535,11 @@ int grmhd_rhs_eval(grmhd_ctx* c, int reg, double* const* rhs) {
   if ((rc = iflux(c, reg))) return rc;
   {
     ProfScope ps(c, K_RHS);
-    launch_rhs(c->pd, wl(c, DOM_INT, c->bs_rhs), nblk(c, DOM_INT, c->bs_rhs), reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st,
-               c->bs_rhs);
+    for_slices(c, DOM_INT, c->bs_rhs, 0, [&](const Work* w, int n) {
+      launch_rhs(c->pd, w, n, reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st, c->bs_rhs);
+      c->launches += 1;
+    });
   }
-  c->launches += 1;
   return check_launch(c, "rhs");
 }
 
@@ -544,10 +573,11 @@ int grmhd_rhs_substep(grmhd_ctx* c, int stage, double dt) {
   if ((rc = iflux(c, reg))) return rc;
   {
     ProfScope ps(c, K_RHS);
-    launch_rhs(c->pd, wl(c, DOM_INT, c->bs_rhs), nblk(c, DOM_INT, c->bs_rhs), reg, 1, stage, dt, c->P, nullptr, c->st,
-               c->bs_rhs);
+    for_slices(c, DOM_INT, c->bs_rhs, 0, [&](const Work* w, int n) {
+      launch_rhs(c->pd, w, n, reg, 1, stage, dt, c->P, nullptr, c->st, c->bs_rhs);
+      c->launches += 1;
+    });
   }
-  c->launches += 1;
   return check_launch(c, "rhs fused");
 }
 
@@ -637,9 +667,10 @@ static int sub_advance(grmhd_ctx* c, int l, int msub, double dt) {
     if ((rc = iflux(c, reg, grp))) return rc;
     {
       ProfScope ps(c, K_RHS);
-      launch_rhs(c->pd, wl(c, DOM_INT, c->bs_rhs, grp), nblk(c, DOM_INT, c->bs_rhs, grp), reg, 1, s, dt, c->P,
-                 nullptr, c->st, c->bs_rhs);
-      c->launches += 1;
+      for_slices(c, DOM_INT, c->bs_rhs, grp, [&](const Work* w, int n) {
+        launch_rhs(c->pd, w, n, reg, 1, s, dt, c->P, nullptr, c->st, c->bs_rhs);
+        c->launches += 1;
+      });
     }
     if (parent) {
       ProfScope ps(c, K_DENSE);
@@ -752,6 +783,12 @@ int grmhd_graph_launch(grmhd_ctx* c) {
   return cuda_ok(c, cudaGraphLaunch(c->gexec, c->st), "graph launch");
 }
 
+int grmhd_set_per_patch(grmhd_ctx* c, int on) {
+  if (!c) return GRMHD_ERR_ARG;
+  c->per_patch = on != 0;
+  return GRMHD_OK;
+}
+
 int grmhd_set_block_sizes(grmhd_ctx* c, int bs_c2p, int bs_iflux, int bs_rhs) {
   if (!c) return GRMHD_ERR_ARG;
   auto ok = [](int b) { return b == 64 || b == 128 || b == 256; };
@@ -843,6 +880,16 @@ int grmhd_sync_status(grmhd_ctx* c) {
   if (h.flags & 2) return fail(c, GRMHD_ERR_NONFINITE, "non-finite state reached con2prim");
   if (h.flags & 1) return fail(c, GRMHD_ERR_C2P_FATAL, "fatal con2prim point");
   return GRMHD_OK;
+}
+
+int grmhd_dfma_probe(int blocks_per_sm, long long iters, double* sink, long long* fmas, void* stream) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1 || !sink || !fmas) return GRMHD_ERR_ARG;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    return GRMHD_ERR_CUDA;
+  *fmas = launch_dfma_probe(nsm * blocks_per_sm, iters, sink, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }
 
 int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* prim,

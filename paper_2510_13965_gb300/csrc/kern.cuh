@@ -173,6 +173,10 @@ void launch_dense_rec(const PatchDev* pd_dev, const Work* w, int nblk, int stage
 int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd_dev, const Work* w, int nblk, int reg,
                           double rho_min, int* err, cudaStream_t st);
 
+// FP64 FMA throughput probe: `blocks` blocks of 256 threads; returns the
+// thread-level FMAs one launch executes.
+long long launch_dfma_probe(int blocks, long long iters, double* sink, cudaStream_t st);
+
 // Block sizes the autotuner chooses from.
 constexpr int NBS = 3;
 constexpr int BS_CAND[NBS] = {64, 128, 256};

@@ -543,3 +543,32 @@ void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, cons
 }
 
 }  // namespace gk
+
+namespace gk {
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe: every thread runs kDfmaChains independent FMA
+// recurrences a <- a m + b, so the FP64 pipe, not the latency of one chain,
+// limits the rate.  The sum is stored only if it equals an impossible value,
+// which keeps the compiler from dropping the work without any memory traffic.
+constexpr int kDfmaChains = 8;
+__global__ void __launch_bounds__(256) k_dfma_probe(long long iters, double* __restrict__ sink) {
+  double a[kDfmaChains];
+  const double m = 0.9999999999, b = 1e-12 * (1 + threadIdx.x);
+#pragma unroll
+  for (int c = 0; c < kDfmaChains; ++c) a[c] = 1.0 + c * 1e-3 + threadIdx.x * 1e-9;
+  for (long long it = 0; it < iters; ++it)
+#pragma unroll
+    for (int c = 0; c < kDfmaChains; ++c) a[c] = fma(a[c], m, b);
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kDfmaChains; ++c) s += a[c];
+  if (s == -1.0) sink[blockIdx.x] = s;
+}
+
+long long launch_dfma_probe(int blocks, long long iters, double* sink, cudaStream_t st) {
+  k_dfma_probe<<<blocks, 256, 0, st>>>(iters, sink);
+  return (long long)blocks * 256 * kDfmaChains * iters;
+}
+
+}  // namespace gk

@@ -15,7 +15,12 @@
 // calls that may overlap on the GPU (for example on two streams of the same
 // device) race on it and must be serialised by the caller.  Calls on the same
 // stream are ordered and safe.
+//
+// Nothing is copied from host memory: the descriptor, the output pointer and
+// the work list are written into the array by a set-up kernel that receives
+// them as launch arguments, and the same kernel clears the device flags.
 #include <cstdint>
+#include <mutex>
 #include "kern.cuh"
 
 namespace gk {
@@ -32,17 +37,21 @@ constexpr size_t kFlagsOfs = kPdOfs + 256;
 constexpr size_t kRhsPtrOfs = kFlagsOfs + 256;
 constexpr size_t kStaticBytes = kRhsPtrOfs + 256;
 static_assert(sizeof(PatchDev) <= 256, "descriptor slot");
+static_assert(kWorkOfs % 16 == 0 && kPdOfs % 16 == 0 && kFlagsOfs % 16 == 0, "slot alignment");
 
 static __device__ __align__(256) unsigned char g_static_area[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_area_ptr[kMaxDevices] = {nullptr};
+std::mutex g_area_mu;
 
-// Device address of g_static_area on the current device (set up on the first
-// call made with that device current).
+// Device address of g_static_area on the current device, looked up on the
+// first call made with that device current (one lookup per device, also when
+// several host threads make their first calls at once).
 int area_on_current_device(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GRMHD_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_area_mu);
   if (!g_area_ptr[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_static_area) != cudaSuccess || !p) return GRMHD_ERR_CUDA;
@@ -52,13 +61,37 @@ int area_on_current_device(unsigned char** out) {
   return GRMHD_OK;
 }
 
+// Block counts per domain, passed by value to the set-up kernel.
+struct Blocks {
+  int ofs[NDOM + 1];
+};
+
+// Writes the descriptor, the output pointer and the work list (patch 0,
+// blocks 0 .. nb-1 of each domain, domains in order) into the static array
+// and clears the device flags.
+__global__ void k_static_setup(PatchDev pd, double* rhs, Blocks b) {
+  PatchDev* pd_dev = (PatchDev*)(g_static_area + kPdOfs);
+  Work* w = (Work*)(g_static_area + kWorkOfs);
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *pd_dev = pd;
+    *(double**)(g_static_area + kRhsPtrOfs) = rhs;
+    DevFlags* f = (DevFlags*)(g_static_area + kFlagsOfs);
+    f->flags = 0;
+    f->worst_status = 0;
+  }
+  for (int dom = 0; dom < NDOM; ++dom)
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < b.ofs[dom + 1] - b.ofs[dom];
+         q += gridDim.x * blockDim.x)
+      w[b.ofs[dom] + q] = Work{0, q};
+}
+
 }  // namespace
 }  // namespace gk
 
 using namespace gk;
 
 extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_desc* d, const grmhd_eos_table* eos,
-                                     int reg, double* rhs, void* stream) {
+                                     int reg, double* rhs, int* dev_flags, void* stream) {
   if (!p || !d || !rhs || reg < 0 || reg > 3) return GRMHD_ERR_ARG;
   if (eos_check(*p, eos) != GRMHD_OK) return GRMHD_ERR_ARG;
   if (les_on(*p)) return GRMHD_ERR_ARG;  // the LES point values need scratch memory
@@ -66,7 +99,7 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (d->n[0] < 4 || d->n[1] < 4 || d->n[2] < 4 || d->px < d->n[0] + 6 || !(d->dx > 0.0)) return GRMHD_ERR_ARG;
   if (!d->U[reg] || ((uintptr_t)d->U[reg] & 7) || !d->prim || ((uintptr_t)d->prim & 7) || !d->status ||
-      ((uintptr_t)rhs & 7))
+      ((uintptr_t)rhs & 7) || ((uintptr_t)dev_flags & 3))
     return GRMHD_ERR_ARG;
   Geo G;
   G.n0 = d->n[0];
@@ -82,6 +115,17 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   G.i144 = 1.0 / (144.0 * G.dx * G.dx);
   G.idx = 1.0 / G.dx;
   if (G.sf > kMaxPoints) return GRMHD_ERR_SIZE;
+
+  Blocks b;
+  int nw = 0;
+  for (int dom = 0; dom < NDOM; ++dom) {
+    b.ofs[dom] = nw;
+    int bs = (dom == DOM_INT) ? BS_INT : ((dom >= DOM_IFX && dom <= DOM_IFZ) ? BS_IF : BS_ALL);
+    long long nb = (dom_count(dom, G) + bs - 1) / bs;
+    if (nw + nb > kMaxWork) return GRMHD_ERR_SIZE;
+    nw += (int)nb;
+  }
+  b.ofs[NDOM] = nw;
 
   unsigned char* area = nullptr;
   int rc = area_on_current_device(&area);
@@ -100,32 +144,21 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   pd.Fh = pd.lam + 3 * G.sf;
   pd.seed = nullptr;
 
-  Work wl[kMaxWork];
-  int wofs[NDOM + 1];
-  int nw = 0;
-  for (int dom = 0; dom < NDOM; ++dom) {
-    wofs[dom] = nw;
-    int bs = (dom == DOM_INT) ? BS_INT : ((dom >= DOM_IFX && dom <= DOM_IFZ) ? BS_IF : BS_ALL);
-    long long nb = (dom_count(dom, G) + bs - 1) / bs;
-    if (nw + nb > kMaxWork) return GRMHD_ERR_SIZE;
-    for (long long b = 0; b < nb; ++b) wl[nw++] = Work{0, (int)b};
-  }
-  wofs[NDOM] = nw;
-
-  PatchDev* pd_dev = (PatchDev*)(area + kPdOfs);
-  Work* w_dev = (Work*)(area + kWorkOfs);
+  const PatchDev* pd_dev = (const PatchDev*)(area + kPdOfs);
+  const Work* w_dev = (const Work*)(area + kWorkOfs);
   DevFlags* flags_dev = (DevFlags*)(area + kFlagsOfs);
-  double** rhs_dev = (double**)(area + kRhsPtrOfs);
-  if (cudaMemcpyAsync(pd_dev, &pd, sizeof(pd), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(w_dev, wl, nw * sizeof(Work), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(rhs_dev, &rhs, sizeof(double*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(flags_dev, 0, sizeof(DevFlags), st) != cudaSuccess)
-    return GRMHD_ERR_CUDA;
+  double* const* rhs_dev = (double* const*)(area + kRhsPtrOfs);
+  k_static_setup<<<4, 256, 0, st>>>(pd, rhs, b);
+  if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
 
   Eos E = make_eos(*p, eos);
-  launch_c2p(pd_dev, w_dev + wofs[DOM_ALL], wofs[DOM_ALL + 1] - wofs[DOM_ALL], reg, *p, E, flags_dev, nullptr, st);
+  launch_c2p(pd_dev, w_dev + b.ofs[DOM_ALL], b.ofs[DOM_ALL + 1] - b.ofs[DOM_ALL], reg, *p, E, flags_dev, nullptr, st);
   for (int dd = 0; dd < 3; ++dd)
-    launch_iflux(pd_dev, w_dev + wofs[DOM_IFX + dd], wofs[DOM_IFX + dd + 1] - wofs[DOM_IFX + dd], reg, dd, st);
-  launch_rhs(pd_dev, w_dev + wofs[DOM_INT], wofs[DOM_INT + 1] - wofs[DOM_INT], reg, 0, 0, 0.0, *p, rhs_dev, st);
-  return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
+    launch_iflux(pd_dev, w_dev + b.ofs[DOM_IFX + dd], b.ofs[DOM_IFX + dd + 1] - b.ofs[DOM_IFX + dd], reg, dd, st);
+  launch_rhs(pd_dev, w_dev + b.ofs[DOM_INT], b.ofs[DOM_INT + 1] - b.ofs[DOM_INT], reg, 0, 0, 0.0, *p, rhs_dev, st);
+  if (cudaGetLastError() != cudaSuccess) return GRMHD_ERR_CUDA;
+  if (dev_flags &&
+      cudaMemcpyAsync(dev_flags, &flags_dev->flags, sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return GRMHD_ERR_CUDA;
+  return GRMHD_OK;
 }

@@ -373,10 +373,11 @@ DI void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
 DI void commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
-// Bounded wait for the mbarrier phase with the given parity; false on timeout.
-DI bool wait(uint32_t mbar, uint32_t parity) {
+// Bounded wait for the mbarrier phase with the given parity (at most `limit`
+// polls); false on timeout.
+DI bool wait(uint32_t mbar, uint32_t parity, long limit = WAIT_LIMIT) {
   uint32_t done = 0;
-  for (long it = 0; it < WAIT_LIMIT && !done; ++it)
+  for (long it = 0; it < limit && !done; ++it)
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -467,7 +468,9 @@ DI void put_h(unsigned char* sm, int r, const float* acc, const float* bias) {
 
 // The four layers of one tile whose inputs are in place; y = network outputs
 // of this thread's row.  Returns false (in every thread) when a wait timed out.
-DI bool forward(unsigned char* sm, uint32_t tmem, uint32_t& phase, float y[NO]) {
+// hold > 0 (test hook): no product is issued, so the barrier never completes
+// and each wait gives up after `hold` polls with nothing in flight.
+DI bool forward(unsigned char* sm, uint32_t tmem, uint32_t& phase, float y[NO], int hold = 0) {
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t mbar = su32(sm + MBAR_B);
   const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
@@ -478,7 +481,7 @@ DI bool forward(unsigned char* sm, uint32_t tmem, uint32_t& phase, float y[NO]) 
   for (int layer = 0; layer < 4; ++layer) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && hold == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (layer == 0) {
         mma(tmem, sdesc(su32(sm + X_B)), sdesc(su32(sm + W1_B)), IDESC_N64, 0u);
@@ -491,11 +494,12 @@ DI bool forward(unsigned char* sm, uint32_t tmem, uint32_t& phase, float y[NO]) 
       }
       commit(mbar);
     }
-    bool done = wait(mbar, phase);
+    const long limit = hold > 0 ? (long)hold : WAIT_LIMIT;
+    bool done = wait(mbar, phase, limit);
     phase ^= 1u;
     if (__syncthreads_or(!done)) {
       // Timed out: let the MMA finish (bounded) before the caller frees TMEM.
-      wait(mbar, phase ^ 1u);
+      wait(mbar, phase ^ 1u, limit);
       ok = false;
       break;
     }
@@ -545,7 +549,7 @@ DI void end(uint32_t tmem) {
 template <int MODE>
 __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restrict__ in, const float* __restrict__ w,
                                                 const float* __restrict__ norm, void* __restrict__ out,
-                                                int* __restrict__ err) {
+                                                int* __restrict__ err, int hold) {
   extern __shared__ __align__(1024) unsigned char smem[];
   tc::load(w, norm, smem);
   const uint32_t tmem = tc::begin(smem);
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
     }
     tc::put_x(smem, s, f, nm, valid);
     float y[NO];
-    if (!tc::forward(smem, tmem, phase, y)) {
+    if (!tc::forward(smem, tmem, phase, y, hold)) {
       if (s == 0) atomicOr(err, 1);
       break;
     }
@@ -610,7 +614,7 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
 // get NaN seeds.  Persistent over the work list.
 __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
                                                   int nblk, int reg, double rho_min, const float* __restrict__ wts,
-                                                  const float* __restrict__ norm, int* __restrict__ err) {
+                                                  const float* __restrict__ norm, int* __restrict__ err, int hold) {
   extern __shared__ __align__(1024) unsigned char smem[];
   tc::load(wts, norm, smem);
   const uint32_t tmem = tc::begin(smem);
@@ -665,7 +669,7 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
     float y[NO] = {0.0f, 0.0f, 0.0f};
     if (__syncthreads_or(solve)) {
       tc::put_x(smem, s, f, nm, solve);
-      if (!tc::forward(smem, tmem, phase, y)) {
+      if (!tc::forward(smem, tmem, phase, y, hold)) {
         if (s == 0) atomicOr(err, 4);
         break;
       }
@@ -693,7 +697,7 @@ __global__ void __launch_bounds__(TM) k_mlp_train(long long n, const float* __re
                                                   const unsigned long long* __restrict__ step,
                                                   const float* __restrict__ w, const float* __restrict__ norm,
                                                   float* __restrict__ gpart, double* __restrict__ lpart, float scale) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(1024) unsigned char smem[];
   u16* S = reinterpret_cast<u16*>(smem);
   float* F = reinterpret_cast<float*>(smem + (size_t)S_END_TRAIN * 2);
   load_params(w, norm, S, F);
@@ -963,6 +967,7 @@ struct grmhd_seeder {
   double* lpart = nullptr;            // [MAX_TILES]
   void* block = nullptr;              // one allocation for all of the above
   cudaStream_t cap = nullptr;         // stream used for graph capture
+  int hold = 0;                       // test hook: polls per product wait with no product issued
 };
 
 namespace {
@@ -1034,7 +1039,7 @@ int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd, const Work*
     per_dev[dev] = (sms > 0 ? sms : 1) * tc_ctas_per_sm((const void*)k_mlp_patch, dev);
   }
   int grid = nblk < per_dev[dev] ? nblk : per_dev[dev];
-  k_mlp_patch<<<grid, TM, tc::SMEM, st>>>(pd, w, nblk, reg, rho_min, s->w, s->norm, err);
+  k_mlp_patch<<<grid, TM, tc::SMEM, st>>>(pd, w, nblk, reg, rho_min, s->w, s->norm, err, s->hold);
   return last_rc();
 }
 }  // namespace gk
@@ -1137,14 +1142,15 @@ int grmhd_seeder_targets(long long n, const double* cons, const double* roots, f
 int grmhd_seeder_forward(grmhd_seeder* s, long long n, const float* f, float* t_out, void* stream) {
   if (!s || n < 0 || (n > 0 && (!f || !t_out))) return GRMHD_ERR_ARG;
   if (n == 0) return GRMHD_OK;
-  k_mlp_fwd<1><<<fwd_grid<1>(n), TM, tc::SMEM, (cudaStream_t)stream>>>(n, f, s->w, s->norm, t_out, s->err);
+  k_mlp_fwd<1><<<fwd_grid<1>(n), TM, tc::SMEM, (cudaStream_t)stream>>>(n, f, s->w, s->norm, t_out, s->err, s->hold);
   return last_rc();
 }
 
 int grmhd_seeder_infer(grmhd_seeder* s, long long n, const double* cons, double* seeds, void* stream) {
   if (!s || n < 0 || (n > 0 && (!cons || !seeds))) return GRMHD_ERR_ARG;
   if (n == 0) return GRMHD_OK;
-  k_mlp_fwd<0><<<fwd_grid<0>(n), TM, tc::SMEM, (cudaStream_t)stream>>>(n, cons, s->w, s->norm, seeds, s->err);
+  k_mlp_fwd<0><<<fwd_grid<0>(n), TM, tc::SMEM, (cudaStream_t)stream>>>(n, cons, s->w, s->norm, seeds, s->err,
+                                                                        s->hold);
   return last_rc();
 }
 
@@ -1210,6 +1216,12 @@ int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float
   // The executable graph may be destroyed while its launches are pending.
   cudaGraphExecDestroy(ge);
   return rc;
+}
+
+int grmhd_seeder_hold_products(grmhd_seeder* s, int polls) {
+  if (!s || polls < 0) return GRMHD_ERR_ARG;
+  s->hold = polls;
+  return GRMHD_OK;
 }
 
 int grmhd_seeder_status(grmhd_seeder* s) {

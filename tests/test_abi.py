@@ -41,7 +41,7 @@ def test_binding_covers_the_header():
 
 
 def test_abi_version_and_argument_checks(lib):
-    assert lib.grmhd_abi_version() == 1
+    assert lib.grmhd_abi_version() == 2
     ctx = ctypes.c_void_p(1)
     # Host-side argument validation needs no GPU: NULL params are rejected before any CUDA call.
     assert lib.grmhd_init_patches(ctypes.byref(ctx), None, 1, None, None, None) == -1
@@ -96,4 +96,5 @@ def test_les_rejected_by_the_allocation_free_entry(lib):
     import synth
     p = g.make_params({**synth.ideal_params(bc=1), "les_c": (0.0, 0.0, 0.0, 8.0)})
     d = g.PatchDesc()
-    assert lib.grmhd_rhs_eval_static(ctypes.byref(p), ctypes.byref(d), None, 0, ctypes.c_void_p(8), None) == -1
+    assert lib.grmhd_rhs_eval_static(ctypes.byref(p), ctypes.byref(d), None, 0, ctypes.c_void_p(8), None,
+                                     None) == -1

@@ -76,7 +76,7 @@ def test_degenerate_patch_shapes_match_oracle():
         assert np.array_equal(pt.status[q].cpu().numpy(), st_o), n
         prim_check(pt.prim[q].cpu().numpy(), prim_o, pt.status[q].cpu().numpy(), st_o, Uo[22:25])
         rhs_o = O.rhs_patch(Uo, prim_o, n, DX)
-        ok, bad = _rhs_ok(interior(rhs[q].cpu().numpy(), n), interior(rhs_o, n), U=interior(Uo, n), dx=DX)
+        ok, bad = _rhs_ok(interior(rhs[q].cpu().numpy(), n), interior(rhs_o, n), O, U, n, DX)
         assert ok, (n, bad)
 
 

@@ -74,7 +74,7 @@ def test_rhs_with_les_matches_oracle(case, les):
     P0 = dict(P, les_c=(0.0, 0.0, 0.0, 0.0))
     rhs_0 = oracle.Oracle(P0).rhs_patch(Uo, prim_o, n, dx)
     assert np.abs(interior(rhs_o - rhs_0, n)[28:31]).max() > 1e-6 * np.abs(interior(rhs_o, n)[28:31]).max()
-    ok, bad = _rhs_ok(interior(rhs_g.cpu().numpy(), n), interior(rhs_o, n), U=interior(Uo, n), dx=dx)
+    ok, bad = _rhs_ok(interior(rhs_g.cpu().numpy(), n), interior(rhs_o, n), O, U, n, dx)
     assert ok, bad
 
 
@@ -131,5 +131,5 @@ def test_rhs_with_les_table_eos_matches_oracle(les):
     Uo = U.copy()
     prim_o, st_o, _, _ = O.con2prim_patch(Uo, n)
     rhs_o = O.rhs_patch(Uo, prim_o, n, dx)
-    ok, bad = _rhs_ok(interior(rhs_g.cpu().numpy(), n), interior(rhs_o, n), U=interior(Uo, n), dx=dx)
+    ok, bad = _rhs_ok(interior(rhs_g.cpu().numpy(), n), interior(rhs_o, n), O, U, n, dx)
     assert ok, bad

@@ -279,6 +279,50 @@ def test_seeded_patch_con2prim_matches_oracle(table_setup):
     assert res[True][2]["iterations"] != res[False][2]["iterations"]
 
 
+def test_tensor_core_wait_timeout_is_reported_and_harmless(table_setup):
+    """The bounded waits of the tensor-core kernels: with the products held
+    back (no product issued, so nothing ever arrives at the barrier) every
+    wait gives up after 64 polls; the kernels record the timeout, free their
+    tensor memory and stop.  The seeder's status and the context's status
+    report it, a seeded con2prim still gives the oracle's plain primitives,
+    and once the hold is lifted the same seeder works again."""
+    table, P0, O0, T = table_setup
+    S = g.Seeder(seed=3)
+    params, _ = S.get_params()
+    x = np.random.default_rng(5).normal(size=(700, 8)).astype(np.float32)
+    S.hold_products(64)
+    S.forward(torch.as_tensor(x, device="cuda"))
+    with pytest.raises(g.GrmhdError):
+        S.status()
+    # Inside a context's con2prim: the timeout reaches grmhd_sync_status.
+    P = synth.table_params(table, bc=1)
+    n, dx = (16, 16, 16), 1.0
+    ID = synth.tov_id(n=n, x0=(-8.0,) * 3, dx=dx, seed=3, table=table, rho_atmo=P["rho_atmo"])
+    O = oracle.Oracle(P, table)
+    U = O.init_state(ID, n, dx)
+    pt = g.Patches(P, [dict(n=n, dx=dx, x0=(-8.0,) * 3)], table=T)
+    pt.U[0][0].copy_(torch.as_tensor(U, device="cuda"))
+    torch.cuda.synchronize()
+    pt.set_seeder(S, 3e-2)
+    pt.con2prim(0)
+    pt.synchronize()
+    assert pt.sync_status() == -4  # GRMHD_ERR_TIMEOUT
+    Uo = U.copy()
+    po, so, _, _ = O.con2prim_patch(Uo, n)
+    prim_check(pt.prim[0].cpu().numpy().reshape(NP, -1), po.reshape(NP, -1),
+               pt.status[0].cpu().numpy().reshape(-1), so.reshape(-1), Uo[22:25].reshape(3, -1))
+    # Lifted: the forward matches the oracle network again and no timeout is reported.
+    S.hold_products(0)
+    S.status()
+    y = S.forward(torch.as_tensor(x, device="cuda")).cpu().numpy().astype(np.float64)
+    assert S.status() == 0
+    y_o = oracle.mlp_forward(params, x, bf16=True)
+    assert _rel_l2(y, y_o) <= 1e-3
+    pt.con2prim(0)
+    pt.synchronize()
+    assert pt.sync_status() == 0
+
+
 def _flat_cons_numpy(n, seed):
     """Conserved states of the isolated con2prim workload built on the host
     (the oracle's inputs never come from the CUDA path): seeded primitives,
