@@ -51,11 +51,13 @@ RHS_TRAFFIC_BYTES_PER_POINT = (192.75e6 + 208.55e6) / 64 ** 3
 # The line's peak is the measured one (the library's FMA throughput probe,
 # timed before the timed region); this derived figure is reported beside it.
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
-# FP64 flops that k_rhs executes per interior point (ncu: DADD + DMUL + 2 DFMA,
-# thread-level, on the 64^3 case; profiles/substep_kernels_tov64_ncu_full.md):
-# fewer than the algorithmic count, since the kernel shares differences,
-# reciprocals and the Christoffel contraction.
-RHS_EXECUTED_FLOPS_PER_POINT = 5200.0
+# FP64 work k_rhs executes per interior point (ncu, thread-level, on the 64^3
+# case; profiles/fp64_instruction_mix_substep_kernels_tov64.md): 5264 flops
+# (DADD + DMUL + 2 DFMA), fewer than the algorithmic count since the kernel
+# shares differences, reciprocals and the Christoffel contraction, issued as
+# 3538 FP64 instructions (all of them adds, multiplies or FMAs).
+RHS_EXECUTED_FLOPS_PER_POINT = 5264.0
+RHS_FP64_INST_PER_POINT = 3538.0
 
 
 def _args():
@@ -148,6 +150,20 @@ class Clocks:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _schedule_summary(pt):
+    """The launch schedule the autotuner kept: per kernel kind, how many
+    patches use each tile shape (0 linear chunks, 1 row segments, 2 32x2xb,
+    3 16x4xb, 4 8x8xb boxes), and the persistent-pool flags."""
+    shapes, pers = pt.get_schedule()
+    out = {}
+    for k, name in enumerate(("c2p", "iflux", "rhs")):
+        hist = {}
+        for t in shapes:
+            hist[str(t[k])] = hist.get(str(t[k]), 0) + 1
+        out[name] = {"tile_shape_patches": hist, "persistent": bool(pers[k])}
+    return out
 
 
 def _dist():
@@ -331,7 +347,8 @@ def run_grmhd(args):
     if rc != 0:
         raise SystemExit("warm-up failed: status %d" % rc)
 
-    fp64_peak = g.fp64_peak_tflops()
+    fp64_peak, peak_shape = g.fp64_peak_tflops()
+    fp64_add = g.fp64_add_rate()
 
     # ---- timed region: K RK4 steps, kernels bracketed by CUDA events ----------
     clocks = Clocks(local) if rank == 0 else None
@@ -387,10 +404,17 @@ def run_grmhd(args):
     executed = RHS_EXECUTED_FLOPS_PER_POINT * zones / (avg_rhs_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "kernel": "k_rhs (CCZ4 + MHD RHS + RK epilogue)", "achieved": achieved,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak, "traffic": traffic,
-                "peak_source": "measured: FP64 FMA throughput probe (grmhd_dfma_probe), best of 5 launches",
+                "peak_source": "measured: FP64 FMA throughput probe (grmhd_dfma_probe), best launch over "
+                               "blocks/SM x chains/thread shapes (best %d x %d)" % peak_shape,
                 "peak_derived": FP64_PEAK_TFLOPS, "flops_per_point": RHS_FLOPS_PER_POINT + RK_FLOPS_PER_POINT,
                 "executed_flops_per_point": RHS_EXECUTED_FLOPS_PER_POINT, "achieved_executed": executed,
-                "frac_executed": executed / fp64_peak}
+                "frac_executed": executed / fp64_peak,
+                # FP64 instruction issue: k_rhs's FP64 instructions per second
+                # against the faster of the probes' FMA and addition rates.
+                "fp64_inst_per_point": RHS_FP64_INST_PER_POINT,
+                "fp64_probe_inst_per_s": {"fma": fp64_peak * 1e12 / 2, "add": fp64_add},
+                "frac_fp64_issue": RHS_FP64_INST_PER_POINT * zones / (avg_rhs_ms / 1e3) /
+                                   max(fp64_peak * 1e12 / 2, fp64_add)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -399,6 +423,7 @@ def run_grmhd(args):
                        "n": [edge] * 3, "dx": dx, "domain": "[-20,20]^3",
                        "step": "one RK4 step (4 fused substeps)", "parallelism": "replicas" if ws > 1 else "1 GPU",
                        "block_sizes": {"c2p": chosen[0], "iflux": chosen[1], "rhs": chosen[2]},
+                       "schedule": _schedule_summary(pt),
                        "l2": "inputs larger than L2 (616 MB per RK register)"},
             "substeps_per_s": 4 * args.steps * ws / (ms_max / 1e3),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
@@ -506,7 +531,8 @@ def _batched_measure(args, K):
            "zone_updates_per_s": {k: zones / (v / 1e3) for k, v in ms.items()},
            "ms_per_step": ms, "launches_per_step": launches,
            "speedup_batched_vs_plain_per_patch": ms["plain_per_patch_graph"] / ms["batched_graph"],
-           "autotuned_block_sizes": list(chosen), "status": rc, "setup_s": gen_s, "clocks": clk}
+           "autotuned_block_sizes": list(chosen), "schedule": _schedule_summary(batched), "status": rc,
+           "setup_s": gen_s, "clocks": clk}
     if seeded is not None:
         out["speedup_batched_nn_seeded_vs_plain_per_patch"] = ms["plain_per_patch_graph"] / seeded["ms_per_step"]
         out["nn_seeded"] = seeded
@@ -838,6 +864,7 @@ def _amr_measure(args, K, seeded=False, per_patch=False):
     rc = pt.sync_status()
     if rc != 0:
         raise SystemExit("warm-up failed: status %d" % rc)
+    chosen = pt.autotune(dt, reps=1)
     # Every variant restarts from this state (the interface fluxes cost more
     # as the atmosphere picks up motion, so the variants advance the same states).
     snap = [u[0].clone() for u in pt.U] if (seeded or per_patch) else None
@@ -876,6 +903,7 @@ def _amr_measure(args, K, seeded=False, per_patch=False):
            "unit": UNIT, "scale": args.amr_scale, "patches": len(specs), "interior_points": zones,
            "finest_dx": min(s_["dx"] for s_ in specs), "dt": dt, "subcycling": "none",
            "eos": "synthetic table 256x128x64", "l2": "inputs larger than L2", "steps": K,
+           "autotuned_block_sizes": list(chosen), "schedule": _schedule_summary(pt),
            "value": zones / (ms / 1e3), "ms_per_step": ms, "launches_per_step": launches,
            "kernel_ms_per_step": {k: v[0] for k, v in prof_k.items() if v[1]},
            "kernel_share": {k: v[0] / tot for k, v in prof_k.items() if v[1]},

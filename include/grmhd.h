@@ -323,14 +323,34 @@ int grmhd_set_per_patch(grmhd_ctx* ctx, int on);
  * kernels (each 64, 128 or 256; 128 at creation). */
 int grmhd_set_block_sizes(grmhd_ctx* ctx, int bs_c2p, int bs_iflux, int bs_rhs);
 
-/* Autotuner: runs reps fused stage-0 substeps (after one warm-up) with each
- * candidate block size on this context's own patches, times every kernel kind
- * with CUDA events and keeps the fastest size per kind.  It overwrites the
- * stage registers U[1] and U[3] and may apply con2prim corrections to U[0], so
- * call it before stepping or between steps.  chosen (3 ints, may be NULL)
- * receives the sizes kept for con2prim, interface fluxes and right-hand side.
- * Synchronises the stream. */
+/* Autotuner (no counterpart in the paper), three phases on this context's own
+ * patches, each timed with CUDA events:
+ *   1. threads per block of the con2prim, interface-flux and right-hand-side
+ *      kernels (64, 128, 256), from reps fused stage-0 substeps per candidate;
+ *   2. a tile shape per patch-size class (longest edge <= 16, 24, 32, 48, 64,
+ *      96, 128, larger) and kernel kind, each candidate shape's kernel timed
+ *      alone on the class's patches (reps launches): 0 linear chunks of the
+ *      block size, 1 row segments, 2 boxes of 32 x 2 x bs/64, 3 of
+ *      16 x 4 x bs/64, 4 of 8 x 8 x bs/64 points;
+ *   3. for con2prim and the interface fluxes, a persistent pool of blocks
+ *      (as many as are resident at once, each looping over the work items)
+ *      or one block per work item, from whole substeps.
+ * It overwrites the stage registers U[1] and U[3] and may apply con2prim
+ * corrections to U[0], so call it before stepping or between steps; it
+ * discards a captured graph (capture again afterwards).  chosen (3 ints, may
+ * be NULL) receives the block sizes kept for con2prim, interface fluxes and
+ * right-hand side; grmhd_get_schedule returns the rest.  Synchronises. */
 int grmhd_autotune(grmhd_ctx* ctx, double dt, int reps, int* chosen);
+
+/* The launch schedule: shapes[3 * p + k] is the tile shape (0..4, see
+ * grmhd_autotune) of patch p for kernel kind k (0 con2prim, 1 interface
+ * fluxes, 2 right-hand side); pers[k] (k = 0, 1; pers[2] must be 0: the
+ * right-hand-side kernel has no persistent form) selects the persistent pool.
+ * Either pointer may be NULL (unchanged).  Every schedule computes every
+ * point with the same arithmetic, so results do not depend on it.  Setting
+ * a schedule synchronises and discards a captured graph. */
+int grmhd_set_schedule(grmhd_ctx* ctx, const int* shapes, const int* pers);
+int grmhd_get_schedule(grmhd_ctx* ctx, int* shapes, int* pers);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around
  * each eager launch (not inside graph capture).  grmhd_profile(ctx, 1)
@@ -369,17 +389,82 @@ int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long 
 int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
                    double* prim, int8_t* status, int32_t* iters, void* stream);
 
+/* ---- sharding a hierarchy across ranks --------------------------------------
+ *
+ * The paper decomposes the grid into boxes owned by MPI ranks (Sec. IV A)
+ * and exchanges ghost data between them.  Here each rank (one GPU) evolves a
+ * subset of the patches of a fixed mesh-refinement hierarchy (bc = 3) and, per
+ * Runge-Kutta substep, receives once the source points its ghost fill reads
+ * from other ranks' patches.  A point a ghost task reads is resolved to its
+ * source: an interior point of some patch, or a level-0 ghost point (filled
+ * on the level-0 patch's rank first).  This needs a nested hierarchy: every
+ * prolongation stencil of a level l >= 2 inside interiors of level l-1.
+ * Restriction becomes one copy per coarse point from the finest interior
+ * point that coincides with it (the cascade of direct copies in one step),
+ * with one more exchange per step.  Results are bitwise those of one context
+ * holding every patch.
+ *
+ * Protocol of one RK step on every rank (stages s = 0.., input register
+ * reg(s) as for grmhd_rhs_substep):
+ *   for each stage: grmhd_shard_ghost0(ctx, reg); for every peer: pack the
+ *   ghost-phase send list from reg, exchange, unpack the receive list into
+ *   reg; grmhd_rhs_substep(ctx, s, dt) (fills levels 1.. and advances the
+ *   rank's own patches);
+ *   then: pack the restriction send lists from register 0, exchange, unpack
+ *   into register 0, grmhd_restrict(ctx, 0). */
+
+/* Owner rank (0..nranks-1) of every patch: Morton order of the patch centres
+ * (finest-level grid units), cut into nranks runs of about equal interior
+ * point count.  Host only; d needs geometry (n, px, level, x0, dx) only. */
+int grmhd_shard_partition(int npatch, const grmhd_patch_desc* d, int nranks, int* owner);
+
+/* Exchange plan of rank `rank` for the hierarchy d partitioned by owner.
+ * Host only.  role (npatch ints, may be NULL): 0 the rank holds no array of
+ * the patch, 1 the rank evolves it, 2 mirror (the rank holds an array that
+ * receives source points).  counts (4 nranks): for every peer q, the numbers
+ * of points of [ghost-phase send to q, ghost-phase receive from q,
+ * restriction send to q, restriction receive from q]; q = rank is a local
+ * copy.  lists (may be NULL for a size query; cap ints): for q = 0.. in
+ * order, the four lists as (patch, offset) int pairs, offset in the patch's
+ * ghosted layout; a send list on rank q and the matching receive list on
+ * rank r have the same length and order (the source of the i-th sent value
+ * lands at the i-th received point).  GRMHD_ERR_ARG when the hierarchy is
+ * not nested (message on stderr); GRMHD_ERR_SIZE when cap is too small. */
+int grmhd_shard_plan(int npatch, const grmhd_patch_desc* d, const int* owner, int nranks, int rank, int* role,
+                     long long* counts, int* lists, long long cap);
+
+/* Context of rank `rank` over the whole hierarchy d (every patch described;
+ * the arrays of patches with role 0 in the plan may be NULL and are never
+ * touched).  Evolves only the rank's own patches; ghost tasks only for them;
+ * restriction as composed copies into them.  Sub-cycling and grmhd_step are
+ * not available on it (see the protocol above). */
+int grmhd_init_shard(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d, const int* owner,
+                     int nranks, int rank, const grmhd_eos_table* eos, void* stream);
+
+/* Outer-boundary extrapolation of the level-0 patch (register reg) if this
+ * rank evolves it; nothing otherwise. */
+int grmhd_shard_ghost0(grmhd_ctx* ctx, int reg);
+
+/* Gather (pack) / scatter (unpack) of the 32 fields of register reg at n
+ * points: pts device [n][2] ints (patch, offset), buf device [32][n] doubles
+ * (field-major).  Enqueued on the context's stream. */
+int grmhd_shard_pack(grmhd_ctx* ctx, int reg, const int* pts, long long n, double* buf);
+int grmhd_shard_unpack(grmhd_ctx* ctx, int reg, const int* pts, long long n, const double* buf);
+
 /* ---- FP64 peak probe ------------------------------------------------------ */
 
 /* Measurement aid with no counterpart in the paper: one launch of
- * blocks_per_sm (1..8) blocks of 256 threads per SM, each thread running 8
- * independent FP64 fused multiply-add chains for iters iterations.  *fmas
- * receives the thread-level FMAs of the launch (2 FP64 flops each); the caller
- * times the launch on `stream` with CUDA events to measure the FP64 peak that
- * the right-hand-side kernels are compared with.  sink: a device array of at
+ * blocks_per_sm (1..8) blocks of 256 threads per SM, each thread running
+ * `chains` (4, 8 or 16) independent FP64 fused multiply-add chains for iters
+ * iterations (rounded up to a multiple of 4); chains = -4, -8 or -16 runs
+ * addition chains instead (the FP64 instruction rate of adds).  *fmas
+ * receives the thread-level FMAs (or additions) of the launch (2 FP64 flops
+ * per FMA); the caller times the
+ * launch on `stream` with CUDA events to measure the FP64 peak that the
+ * right-hand-side kernels are compared with.  sink: a device array of at
  * least blocks_per_sm * (SM count) doubles, written only in a case that does
  * not occur (it keeps the arithmetic from being optimised away). */
-int grmhd_dfma_probe(int blocks_per_sm, long long iters, double* sink, long long* fmas, void* stream);
+int grmhd_dfma_probe(int blocks_per_sm, int chains, long long iters, double* sink, long long* fmas, void* stream);
 
 /* ---- allocation-free right-hand side -------------------------------------- */
 

@@ -104,6 +104,7 @@ def lib(flops=False, omp=False):
             "oracle_adam": (i, [vp, vp, vp, vp, l, d, d, d, d, i]),
             "oracle_seeder_features": (i, [l, vp, vp]),
             "oracle_hier_ghost_fill": (i, [vp, i, vp, vp, vp]),
+            "oracle_hier_ghost_fill_from": (i, [vp, i, vp, vp, vp, i]),
             "oracle_hier_restrict": (i, [i, vp, vp, vp]),
             "oracle_hier_rk4_step": (i, [vp, vp, i, vp, vp, d, vp, vp, vp, vp, vp, vp]),
             "oracle_eos_derivs": (i, [vp, vp, d, d, d, vp]),
@@ -447,9 +448,11 @@ class Hierarchy:
     def init_state(self, q, ID):
         self.U[0][q][...] = self.O.init_state(np.ascontiguousarray(ID), self.specs[q]["n"], self.specs[q]["dx"])
 
-    def ghost_fill(self, reg=0):
-        return self.O.L.oracle_hier_ghost_fill(_ref(self.O.P), len(self.specs), _p(self.meta), _p(self.dx),
-                                              self._ptrs(self.U[reg]))
+    def ghost_fill(self, reg=0, lmin=0):
+        """Ghost fill of the hierarchy; lmin >= 1 starts at that level and
+        leaves the level-0 patch's outer ghosts untouched."""
+        return self.O.L.oracle_hier_ghost_fill_from(_ref(self.O.P), len(self.specs), _p(self.meta), _p(self.dx),
+                                                   self._ptrs(self.U[reg]), int(lmin))
 
     def restrict(self, reg=0):
         return self.O.L.oracle_hier_restrict(len(self.specs), _p(self.meta), _p(self.dx), self._ptrs(self.U[reg]))

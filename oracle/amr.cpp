@@ -52,6 +52,7 @@
 #include <vector>
 
 #include "oracle.hpp"
+#include <algorithm>
 
 namespace {
 
@@ -119,7 +120,7 @@ real prolong(const hpatch& r, const double* U, int f, const long c[3], const int
   return odd[2] ? midpoint(zline) : zline[0];
 }
 
-int ghost_fill_hier(const oracle_params* P, std::vector<hpatch>& H, double* const* U) {
+int ghost_fill_hier(const oracle_params* P, std::vector<hpatch>& H, double* const* U, int lmin) {
   int maxl = 0, nl0 = 0, p0 = -1;
   for (int p = 0; p < (int)H.size(); ++p) {
     if (H[p].level > maxl) maxl = H[p].level;
@@ -131,8 +132,8 @@ int ghost_fill_hier(const oracle_params* P, std::vector<hpatch>& H, double* cons
   if (nl0 != 1) return -1;
   oracle_params P1 = *P;
   P1.bc = 1;
-  ghost_fill(&P1, H[p0].G, U[p0], NF);
-  for (int l = 1; l <= maxl; ++l) {
+  if (lmin <= 0) ghost_fill(&P1, H[p0].G, U[p0], NF);
+  for (int l = std::max(1, lmin); l <= maxl; ++l) {
     for (int p = 0; p < (int)H.size(); ++p) {
       const hpatch& h = H[p];
       if (h.level != l) continue;
@@ -475,7 +476,15 @@ int oracle_hier_subcycle_step(const oracle_params* P, const oracle_eos_table* E,
 // ghost point covered by neither its level nor the next coarser one).
 int oracle_hier_ghost_fill(const oracle_params* P, int np, const int* meta, const double* dx, double* const* U) {
   std::vector<hpatch> H = parse(np, meta, dx);
-  return ghost_fill_hier(P, H, U);
+  return ghost_fill_hier(P, H, U, 0);
+}
+
+// The same from level lmin on: lmin >= 1 leaves the level-0 patch's outer
+// ghosts as they are.
+int oracle_hier_ghost_fill_from(const oracle_params* P, int np, const int* meta, const double* dx, double* const* U,
+                                int lmin) {
+  std::vector<hpatch> H = parse(np, meta, dx);
+  return ghost_fill_hier(P, H, U, lmin);
 }
 
 int oracle_hier_restrict(int np, const int* meta, const double* dx, double* const* U) {
@@ -511,7 +520,7 @@ int oracle_hier_rk4_step_mask(const oracle_params* P, const oracle_eos_table* E,
   const int nsub = P->rk == 1 ? 3 : 4;
   for (int s = 0; s < nsub; ++s) {
     double* const* in = s == 0 ? U0 : s == 1 ? U1 : s == 2 ? U2 : U1;
-    int rc = ghost_fill_hier(P, H, in);
+    int rc = ghost_fill_hier(P, H, in, 0);
     if (rc) return rc;
     for (int p = 0; p < np; ++p) {
       std::vector<double> k((size_t)NF * H[p].G.sf, 0.0);

@@ -93,9 +93,22 @@ _SIGS = {
     "grmhd_rhs_eval_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_set_per_patch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "grmhd_seeder_hold_products": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
-    "grmhd_dfma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p, ctypes.c_void_p,
+    "grmhd_shard_partition": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "grmhd_shard_plan": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong]),
+    "grmhd_init_shard": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "grmhd_shard_ghost0": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_shard_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
+                                        ctypes.c_void_p]),
+    "grmhd_shard_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_longlong,
+                                          ctypes.c_void_p]),
+    "grmhd_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_get_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "grmhd_seeder_hold_products": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "grmhd_dfma_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_seeder_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong]),
     "grmhd_seeder_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "grmhd_seeder_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -353,8 +366,23 @@ class Patches:
     def set_block_sizes(self, bs_c2p, bs_iflux, bs_rhs):
         _check(self.L.grmhd_set_block_sizes(self.ctx, bs_c2p, bs_iflux, bs_rhs), self.ctx, "grmhd_set_block_sizes")
 
+    def set_schedule(self, shapes=None, pers=None):
+        """Tile shape per patch and kernel kind (list of (c2p, iflux, rhs) per
+        patch, 0..4) and persistent flags (c2p, iflux, rhs = 0)."""
+        sh = None if shapes is None else (ctypes.c_int * (3 * len(self.specs)))(*[int(v) for t in shapes for v in t])
+        pe = None if pers is None else (ctypes.c_int * 3)(*[int(v) for v in pers])
+        _check(self.L.grmhd_set_schedule(self.ctx, sh, pe), self.ctx, "grmhd_set_schedule")
+
+    def get_schedule(self):
+        """(shapes per patch [(c2p, iflux, rhs)], persistent flags (c2p, iflux, rhs))."""
+        sh = (ctypes.c_int * (3 * len(self.specs)))()
+        pe = (ctypes.c_int * 3)()
+        _check(self.L.grmhd_get_schedule(self.ctx, sh, pe), self.ctx, "grmhd_get_schedule")
+        return [tuple(sh[3 * i:3 * i + 3]) for i in range(len(self.specs))], tuple(pe)
+
     def autotune(self, dt, reps=2):
-        """Pick the fastest block size per kernel kind on these patches; returns (c2p, iflux, rhs)."""
+        """Block sizes, tile shapes per patch-size class and persistent launches
+        from timed trials on these patches; returns the block sizes (c2p, iflux, rhs)."""
         self._enter()
         ch = (ctypes.c_int * 3)()
         _check(self.L.grmhd_autotune(self.ctx, float(dt), int(reps), ch), self.ctx, "grmhd_autotune")
@@ -390,28 +418,45 @@ def prim2con_flat(params, prim, B, table=None, stream=None):
     return cons
 
 
-def fp64_peak_tflops(iters=4000, blocks_per_sm=4, reps=5):
-    """Measured FP64 throughput of this GPU (TFLOP/s, 2 flops per FMA): the
-    best of `reps` launches of the library's FMA probe, each timed with CUDA
-    events on the current stream after one untimed launch."""
+def _fp64_probe(shapes, iters, reps, add):
     torch = _torch()
     L = load()
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    sink = torch.zeros(nsm * blocks_per_sm, dtype=torch.float64, device="cuda")
-    fmas = ctypes.c_longlong(0)
+    sink = torch.zeros(nsm * 8, dtype=torch.float64, device="cuda")
+    n = ctypes.c_longlong(0)
     s = torch.cuda.current_stream()
-    best = 0.0
-    for r in range(reps + 1):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        rc = L.grmhd_dfma_probe(int(blocks_per_sm), int(iters), _vp(sink), ctypes.byref(fmas),
-                                ctypes.c_void_p(s.cuda_stream))
-        e1.record(s)
-        _check(rc, None, "grmhd_dfma_probe")
-        torch.cuda.synchronize()
-        if r:
-            best = max(best, 2.0 * fmas.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
-    return best
+    best, best_shape = 0.0, None
+    for bps, ch in shapes:
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            rc = L.grmhd_dfma_probe(int(bps), -int(ch) if add else int(ch), int(iters * 8 // ch), _vp(sink),
+                                    ctypes.byref(n), ctypes.c_void_p(s.cuda_stream))
+            e1.record(s)
+            _check(rc, None, "grmhd_dfma_probe")
+            torch.cuda.synchronize()
+            rate = n.value / (e0.elapsed_time(e1) / 1e3)
+            if r and rate > best:
+                best, best_shape = rate, (bps, ch)
+    return best, best_shape
+
+
+PROBE_SHAPES = ((2, 8), (4, 8), (8, 8), (4, 16), (8, 4), (2, 16))
+
+
+def fp64_peak_tflops(iters=4000, reps=3, shapes=PROBE_SHAPES):
+    """Measured FP64 throughput of this GPU (TFLOP/s, 2 flops per FMA): the
+    library's FMA probe over a few launch shapes (blocks per SM, chains per
+    thread), each launch timed with CUDA events on the current stream after
+    one untimed launch; the best rate seen.  Returns (TFLOP/s, best shape)."""
+    rate, shape = _fp64_probe(shapes, iters, reps, False)
+    return 2.0 * rate / 1e12, shape
+
+
+def fp64_add_rate(iters=4000, reps=3, shapes=PROBE_SHAPES):
+    """Measured FP64 addition rate (thread instructions per second), the
+    same way with addition chains."""
+    return _fp64_probe(shapes, iters, reps, True)[0]
 
 
 def c2p_flat(params, cons, table=None, iters=False, stream=None, out=None):
@@ -559,3 +604,217 @@ def seeder_targets(cons, roots, stream=None):
     _check(load().grmhd_seeder_targets(roots.shape[0], _vp(cons), _vp(roots), _vp(t), _stream(torch, stream)), None,
            "grmhd_seeder_targets")
     return t
+
+
+# ---- sharding a hierarchy across ranks --------------------------------------
+
+def _geometry_descs(specs):
+    """Patch descriptors carrying geometry only (no arrays)."""
+    d = (PatchDesc * len(specs))()
+    for i, s in enumerate(specs):
+        n = tuple(int(v) for v in s["n"])
+        d[i].n[:] = list(n)
+        d[i].px = n[0] + 2 * NG
+        d[i].level = int(s.get("level", 0))
+        d[i].x0[:] = [float(v) for v in s.get("x0", (0.0, 0.0, 0.0))]
+        d[i].dx = float(s["dx"])
+    return d
+
+
+def shard_partition(specs, nranks):
+    """Owner rank of every patch (Morton order, balanced by interior points)."""
+    d = _geometry_descs(specs)
+    owner = (ctypes.c_int * len(specs))()
+    _check(load().grmhd_shard_partition(len(specs), d, int(nranks), owner), None, "grmhd_shard_partition")
+    return [int(v) for v in owner]
+
+
+SHARD_LISTS = ("gsend", "grecv", "rsend", "rrecv")
+
+
+def shard_plan(specs, owner, nranks, rank):
+    """(role per patch, lists) for one rank: lists[q][name] is an int32 array
+    (m, 2) of (patch, offset) points for peer q, name in SHARD_LISTS (ghost
+    phase send / receive, restriction send / receive)."""
+    import numpy as np
+    L = load()
+    n = len(specs)
+    d = _geometry_descs(specs)
+    own = (ctypes.c_int * n)(*owner)
+    role = (ctypes.c_int * n)()
+    counts = (ctypes.c_longlong * (4 * nranks))()
+    _check(L.grmhd_shard_plan(n, d, own, nranks, rank, role, counts, None, 0), None, "grmhd_shard_plan")
+    total = 2 * sum(counts)
+    buf = np.zeros(max(total, 1), dtype=np.int32)
+    _check(L.grmhd_shard_plan(n, d, own, nranks, rank, role, counts, ctypes.c_void_p(buf.ctypes.data), total), None,
+           "grmhd_shard_plan")
+    lists, o = [], 0
+    for q in range(nranks):
+        lq = {}
+        for k, name in enumerate(SHARD_LISTS):
+            m = counts[4 * q + k]
+            lq[name] = buf[o:o + 2 * m].reshape(m, 2).copy()
+            o += 2 * m
+        lists.append(lq)
+    return [int(v) for v in role], lists
+
+
+def exchange_buffers(send, recv, rank, group=None, tag=0):
+    """Point-to-point exchange of packed buffers: send[q] goes to rank q and
+    recv[q] is filled from rank q (torch tensors; q == rank is a local copy).
+    Works with any torch.distributed backend (NCCL for device tensors, gloo
+    for host tensors)."""
+    import torch.distributed as dist
+    ops = []
+    for q, t in recv.items():
+        if q != rank and t.numel():
+            ops.append(dist.irecv(t, src=q, group=group, tag=tag))
+    for q, t in send.items():
+        if q != rank and t.numel():
+            ops.append(dist.isend(t, dst=q, group=group, tag=tag))
+    if rank in send and send[rank].numel():
+        recv[rank].copy_(send[rank])
+    for op in ops:
+        op.wait()
+
+
+class ShardedHierarchy:
+    """This rank's part of a mesh-refinement hierarchy (bc 3) sharded across
+    ranks (one GPU each; see grmhd_init_shard): arrays for its own patches and
+    for the mirrors its ghost fill reads, and one exchange of source points per
+    substep (and one per step for the restriction) through torch.distributed.
+    Every rank must call step() with the same dt."""
+
+    def __init__(self, params, specs, rank, nranks, table=None, device="cuda", group=None, stream=None):
+        torch = _torch()
+        import numpy as np
+        self.torch, self.rank, self.nranks, self.group = torch, rank, nranks, group
+        self.L = L = load()
+        self.params = make_params(params)
+        self.rk3 = int(params.get("rk", 0)) == 1
+        self.owner = shard_partition(specs, nranks)
+        self.role, lists = shard_plan(specs, self.owner, nranks, rank)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self.device = device
+        self.specs = []
+        self.U = [None] * len(specs)
+        self.prim = [None] * len(specs)
+        self.status = [None] * len(specs)
+        descs = _geometry_descs(specs)
+        dummy_p = torch.zeros(8, dtype=torch.float64, device=device)
+        dummy_s = torch.zeros(8, dtype=torch.int8, device=device)
+        self._dummy = (dummy_p, dummy_s)
+        for i, s in enumerate(specs):
+            n = tuple(int(v) for v in s["n"])
+            shp = (n[2] + 2 * NG, n[1] + 2 * NG, n[0] + 2 * NG)
+            self.specs.append(dict(n=n, px=n[0] + 2 * NG, dx=float(s["dx"]), shape=shp))
+            if self.role[i] == 0:
+                continue
+            regs = [torch.zeros((NF,) + shp, dtype=torch.float64, device=device) for _ in range(4)]
+            self.U[i] = regs
+            for r in range(4):
+                descs[i].U[r] = regs[r].data_ptr()
+            if self.role[i] == 1:
+                self.prim[i] = torch.zeros((NP,) + shp, dtype=torch.float64, device=device)
+                self.status[i] = torch.zeros(shp, dtype=torch.int8, device=device)
+                descs[i].prim = self.prim[i].data_ptr()
+                descs[i].status = self.status[i].data_ptr()
+            else:  # a mirror is never converted or evolved
+                descs[i].prim = dummy_p.data_ptr()
+                descs[i].status = dummy_s.data_ptr()
+        self.descs = descs
+        torch.cuda.current_stream().synchronize()
+        own = (ctypes.c_int * len(specs))(*self.owner)
+        ctx = ctypes.c_void_p()
+        _check(L.grmhd_init_shard(ctypes.byref(ctx), ctypes.byref(self.params), len(specs), descs, own, nranks, rank,
+                                  table.ref if table is not None else None, ctypes.c_void_p(self.stream.cuda_stream)),
+               None, "grmhd_init_shard")
+        self.ctx = ctx
+        self._table = table
+        self.lists = [{k: torch.as_tensor(np.ascontiguousarray(v), device=device) for k, v in lq.items()}
+                      for lq in lists]
+        self.points_exchanged = {k: int(sum(lq[k].shape[0] for lq in lists)) for k in SHARD_LISTS}
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.stream.synchronize()
+                self.L.grmhd_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    def init_state(self, patch, id_tensor):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        id_tensor.record_stream(self.stream)
+        _check(self.L.grmhd_init_state(self.ctx, patch, ctypes.c_void_p(id_tensor.data_ptr())), self.ctx,
+               "grmhd_init_state")
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+
+    def ghost0(self, reg):
+        """Level-0 outer ghosts of register reg (on the level-0 patch's rank)."""
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        _check(self.L.grmhd_shard_ghost0(self.ctx, reg), self.ctx, "grmhd_shard_ghost0")
+
+    def pack(self, reg, phase):
+        """Send buffers {peer: [32, m] tensor} of register reg for phase "g"
+        (ghost sources) or "r" (restriction sources)."""
+        torch = self.torch
+        name = phase + "send"
+        send = {}
+        self.stream.wait_stream(torch.cuda.current_stream())
+        for q in range(self.nranks):
+            ps = self.lists[q][name]
+            send[q] = torch.empty((NF, ps.shape[0]), dtype=torch.float64, device=self.device)
+            if ps.shape[0]:
+                _check(self.L.grmhd_shard_pack(self.ctx, reg, ctypes.c_void_p(ps.data_ptr()), ps.shape[0],
+                                               ctypes.c_void_p(send[q].data_ptr())), self.ctx, "grmhd_shard_pack")
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return send
+
+    def recv_buffers(self, phase):
+        name = phase + "recv"
+        return {q: self.torch.empty((NF, self.lists[q][name].shape[0]), dtype=self.torch.float64, device=self.device)
+                for q in range(self.nranks)}
+
+    def unpack(self, reg, phase, recv):
+        """Scatter the received buffers into the mirrors (register reg)."""
+        torch = self.torch
+        name = phase + "recv"
+        self.stream.wait_stream(torch.cuda.current_stream())
+        for q in range(self.nranks):
+            pr = self.lists[q][name]
+            if pr.shape[0]:
+                _check(self.L.grmhd_shard_unpack(self.ctx, reg, ctypes.c_void_p(pr.data_ptr()), pr.shape[0],
+                                                 ctypes.c_void_p(recv[q].data_ptr())), self.ctx, "grmhd_shard_unpack")
+            recv[q].record_stream(self.stream)
+
+    def substep(self, stage, dt):
+        _check(self.L.grmhd_rhs_substep(self.ctx, stage, float(dt)), self.ctx, "grmhd_rhs_substep")
+
+    def restrict(self):
+        _check(self.L.grmhd_restrict(self.ctx, 0), self.ctx, "grmhd_restrict")
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+
+    def stage_registers(self):
+        return (0, 1, 2) if self.rk3 else (0, 1, 2, 1)
+
+    def step(self, dt):
+        """One RK step of this rank's patches (the exchange protocol of
+        grmhd_init_shard), exchanging through torch.distributed."""
+        for s, reg in enumerate(self.stage_registers()):
+            self.ghost0(reg)
+            recv = self.recv_buffers("g")
+            exchange_buffers(self.pack(reg, "g"), recv, self.rank, self.group, tag=1)
+            self.unpack(reg, "g", recv)
+            self.substep(s, dt)
+        recv = self.recv_buffers("r")
+        exchange_buffers(self.pack(0, "r"), recv, self.rank, self.group, tag=2)
+        self.unpack(0, "r", recv)
+        self.restrict()
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def sync_status(self):
+        return self.L.grmhd_sync_status(self.ctx)

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrmhd.so")
-SOURCES = ["api.cu", "kernels.cu", "rhs.cu", "noalloc.cu", "seeder.cu", "amr.cu", "les.cu"]
+SOURCES = ["api.cu", "kernels.cu", "rhs.cu", "noalloc.cu", "seeder.cu", "amr.cu", "les.cu", "shard.cu"]
 HEADERS = ["dev.cuh", "c2p.cuh", "kern.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH

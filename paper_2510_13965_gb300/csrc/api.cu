@@ -1,4 +1,5 @@
 // Host side of the C ABI declared in include/grmhd.h.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -25,6 +26,21 @@ struct grmhd_ctx {
   // list's start; used when per_patch launches are on.
   std::vector<std::array<std::array<std::vector<std::pair<int, int>>, NDOM>, NBS>> pslice;
   bool per_patch = false;
+  // Schedule of the con2prim (kind 0), interface-flux (1) and right-hand-side
+  // (2) launches: a tile shape per patch and kind (0 = linear chunks, see
+  // work_point) and a persistent flag per kind (kinds 0 and 1); their work
+  // lists live in twork, laid out like work (empty for the ghost-line domains).
+  std::vector<std::array<int, 3>> shape;
+  bool pers[3] = {false, false, false};
+  bool rhs_tiled = false;
+  Work* twork = nullptr;
+  std::vector<std::array<std::array<int, NDOM + 1>, NBS>> twofs;
+  std::vector<std::array<std::array<std::vector<std::pair<int, int>>, NDOM>, NBS>> tpslice;
+  std::vector<int> group_of;  // per group: -1 all patches, else the level
+  // Sharded contexts (grmhd_init_shard): per patch 0 absent, 1 local
+  // (evolved), 2 mirror (holds exchanged source points only); all 1 otherwise.
+  std::vector<int> role;
+  bool shard = false;
   double* scratch = nullptr;
   DevFlags* flags = nullptr;
   C2PStats* stats = nullptr;
@@ -129,6 +145,72 @@ static void for_slices(grmhd_ctx* c, int dom, int bs, int grp, Fn fn) {
   for (const auto& sl : c->pslice[grp][b][dom]) fn(w + sl.first, sl.second);
 }
 
+// The same over the tuned lists of the con2prim, interface-flux and
+// right-hand-side launches.
+template <class Fn>
+static void for_tslices(grmhd_ctx* c, int dom, int bs, int grp, Fn fn) {
+  const int b = bs_index(bs);
+  const Work* w = c->twork + c->twofs[grp][b][dom];
+  if (!c->per_patch) {
+    fn(w, c->twofs[grp][b][dom + 1] - c->twofs[grp][b][dom]);
+    return;
+  }
+  for (const auto& sl : c->tpslice[grp][b][dom]) fn(w + sl.first, sl.second);
+}
+
+static int kind_of(int dom) {
+  return dom == DOM_ALL ? 0 : (dom >= DOM_IFX && dom <= DOM_IFZ ? 1 : (dom == DOM_INT ? 2 : -1));
+}
+static int log2_bs(int bs) { return bs == 64 ? 6 : (bs == 256 ? 8 : 7); }
+
+// (Re)builds the tuned work lists from the schedule and uploads them; a
+// captured graph refers to the old lists, so it is discarded.
+static int build_tuned(grmhd_ctx* c) {
+  std::vector<Work> wl;
+  const int ngrp = (int)c->group_of.size();
+  c->twofs.assign(ngrp, {});
+  c->tpslice.assign(ngrp, {});
+  bool tiled = false;
+  for (int i = 0; i < c->np; ++i) tiled = tiled || c->shape[i][2] != 0;
+  for (int g = 0; g < ngrp; ++g)
+    for (int b = 0; b < NBS; ++b) {
+      const int lb = log2_bs(BS_CAND[b]);
+      for (int dom = 0; dom < NDOM; ++dom) {
+        c->twofs[g][b][dom] = (int)wl.size();
+        const int kind = kind_of(dom);
+        if (kind < 0) continue;
+        for (int i = 0; i < c->np; ++i) {
+          if (c->role[i] != 1 || (c->group_of[g] >= 0 && c->desc[i].level != c->group_of[g])) continue;
+          const int sh = c->shape[i][kind];
+          const long long nt = dom_tiles(dom, c->pd_host[i].G, lb, sh);
+          c->tpslice[g][b][dom].push_back({(int)wl.size() - c->twofs[g][b][dom], (int)nt});
+          for (long long t = 0; t < nt; ++t) wl.push_back(Work{i, (int)t | (sh << TILE_BITS)});
+        }
+      }
+      c->twofs[g][b][NDOM] = (int)wl.size();
+    }
+  int rc;
+  if ((rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync"))) return rc;
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  if (c->graph) {
+    cudaGraphDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  cudaFree(c->twork);
+  c->twork = nullptr;
+  if ((rc = cuda_ok(c, cudaMalloc(&c->twork, (wl.size() + 1) * sizeof(Work)), "cudaMalloc tuned work")))
+    return GRMHD_ERR_NOMEM;
+  if (!wl.empty() &&
+      (rc = cuda_ok(c, cudaMemcpy(c->twork, wl.data(), wl.size() * sizeof(Work), cudaMemcpyHostToDevice),
+                    "copy tuned work")))
+    return rc;
+  c->rhs_tiled = tiled;
+  return GRMHD_OK;
+}
+
 extern "C" {
 
 int grmhd_abi_version(void) { return 2; }
@@ -149,6 +231,7 @@ void grmhd_destroy(grmhd_ctx* c) {
   if (c->graph) cudaGraphDestroy(c->graph);
   cudaFree(c->pd);
   cudaFree(c->work);
+  cudaFree(c->twork);
   cudaFree(c->dense_buf);
   cudaFree(c->les_buf);
   cudaFree(c->amr_tp);
@@ -161,8 +244,27 @@ void grmhd_destroy(grmhd_ctx* c) {
   delete c;
 }
 
-int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d,
-                       const grmhd_eos_table* eos, void* stream) {
+static Geo geo_of(const grmhd_patch_desc& d) {
+  Geo G;
+  G.n0 = d.n[0];
+  G.n1 = d.n[1];
+  G.n2 = d.n[2];
+  G.px = d.px;
+  G.sy = d.px;
+  G.sz = G.sy * (G.n1 + 6);
+  G.sf = G.sz * (G.n2 + 6);
+  G.dx = d.dx;
+  G.i12 = 1.0 / (12.0 * G.dx);
+  G.i12s = 1.0 / (12.0 * G.dx * G.dx);
+  G.i144 = 1.0 / (144.0 * G.dx * G.dx);
+  G.idx = 1.0 / G.dx;
+  return G;
+}
+
+// Context creation; S: the plan of one rank of a sharded hierarchy, or null
+// (every patch local).
+static int init_impl(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d,
+                     const grmhd_eos_table* eos, void* stream, const ShardPlan* S) {
   if (!out) return GRMHD_ERR_ARG;
   *out = nullptr;
   if (!p || !d || npatch <= 0) return GRMHD_ERR_ARG;
@@ -170,9 +272,12 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   if (p->bc < 0 || p->bc > 3) return GRMHD_ERR_ARG;
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (p->rk != 0 && p->rk != 1) return GRMHD_ERR_ARG;
+  std::vector<int> role(npatch, 1);
+  if (S) role = S->role;
   for (int i = 0; i < npatch; ++i) {
     const grmhd_patch_desc& q = d[i];
     if (q.n[0] < 4 || q.n[1] < 4 || q.n[2] < 4 || q.px < q.n[0] + 6 || !(q.dx > 0.0)) return GRMHD_ERR_ARG;
+    if (role[i] == 0) continue;  // absent from this rank: its arrays are not touched
     for (int r = 0; r < 4; ++r)
       if (!q.U[r] || ((uintptr_t)q.U[r] & 7)) return GRMHD_ERR_ARG;
     if (!q.prim || ((uintptr_t)q.prim & 7) || !q.status) return GRMHD_ERR_ARG;
@@ -184,26 +289,18 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   c->np = npatch;
   c->desc.assign(d, d + npatch);
   c->pd_host.resize(npatch);
-  // scratch: Fp (30) + lam (3) + Fh (30) doubles per ghosted point
+  c->role = role;
+  c->shard = S != nullptr;
+  // scratch: Fp (30) + lam (3) + Fh (30) doubles per ghosted point of every
+  // patch this rank holds (mirrors too: the x-midpoint pre-pass of a ghost
+  // fill writes into the coarse patch's Fp)
   size_t total = 0;
   std::vector<size_t> ofs(npatch);
   for (int i = 0; i < npatch; ++i) {
-    Geo G;
-    G.n0 = d[i].n[0];
-    G.n1 = d[i].n[1];
-    G.n2 = d[i].n[2];
-    G.px = d[i].px;
-    G.sy = d[i].px;
-    G.sz = G.sy * (G.n1 + 6);
-    G.sf = G.sz * (G.n2 + 6);
-    G.dx = d[i].dx;
-    G.i12 = 1.0 / (12.0 * G.dx);
-    G.i12s = 1.0 / (12.0 * G.dx * G.dx);
-    G.i144 = 1.0 / (144.0 * G.dx * G.dx);
-    G.idx = 1.0 / G.dx;
-    c->pd_host[i].G = G;
+    c->pd_host[i] = PatchDev();
+    c->pd_host[i].G = geo_of(d[i]);
     ofs[i] = total;
-    total += (size_t)63 * G.sf;
+    if (role[i]) total += (size_t)63 * c->pd_host[i].G.sf;
   }
   int rc;
   if ((rc = cuda_ok(c, cudaMalloc(&c->scratch, total * sizeof(double)), "cudaMalloc scratch")) != GRMHD_OK) {
@@ -212,24 +309,31 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   }
   for (int i = 0; i < npatch; ++i) {
     PatchDev& q = c->pd_host[i];
+    for (int r = 0; r < REG_DENSE + NDENSE; ++r) q.U[r] = nullptr;
+    q.seed = nullptr;
+    q.les = nullptr;
+    q.prim = nullptr;
+    q.status = nullptr;
+    q.Fp = q.lam = q.Fh = nullptr;
+    if (!role[i]) continue;
     for (int r = 0; r < 4; ++r) q.U[r] = d[i].U[r];
     q.prim = d[i].prim;
     q.status = d[i].status;
     q.Fp = c->scratch + ofs[i];
     q.lam = q.Fp + 30 * q.G.sf;
     q.Fh = q.lam + 3 * q.G.sf;
-    q.seed = nullptr;
-    q.les = nullptr;
   }
   if (les_on(*p)) {
     size_t ltot = 0;
-    for (int i = 0; i < npatch; ++i) ltot += (size_t)LES_NAUX * c->pd_host[i].G.sf;
+    for (int i = 0; i < npatch; ++i)
+      if (role[i] == 1) ltot += (size_t)LES_NAUX * c->pd_host[i].G.sf;
     if ((rc = cuda_ok(c, cudaMalloc(&c->les_buf, ltot * sizeof(double)), "cudaMalloc LES values")) != GRMHD_OK) {
       grmhd_destroy(c);
       return GRMHD_ERR_NOMEM;
     }
     size_t lo = 0;
     for (int i = 0; i < npatch; ++i) {
+      if (role[i] != 1) continue;
       c->pd_host[i].les = c->les_buf + lo;
       lo += (size_t)LES_NAUX * c->pd_host[i].G.sf;
     }
@@ -248,6 +352,9 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
   }
   c->wofs.assign(ngrp, {});
   c->pslice.assign(ngrp, {});
+  c->group_of.assign(ngrp, -1);
+  for (int g = 1; g < ngrp; ++g) c->group_of[g] = g - 1;
+  c->shape.assign(npatch, {0, 0, 0});
   std::vector<Work> wl;
   for (int g = 0; g < ngrp; ++g)
     for (int b = 0; b < NBS; ++b) {
@@ -255,7 +362,7 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
       for (int dom = 0; dom < NDOM; ++dom) {
         c->wofs[g][b][dom] = (int)wl.size();
         for (int i = 0; i < npatch; ++i) {
-          if (g > 0 && d[i].level != g - 1) continue;
+          if (role[i] != 1 || (g > 0 && d[i].level != g - 1)) continue;
           long long n = dom_count(dom, c->pd_host[i].G);
           long long nb = (n + bs - 1) / bs;
           c->pslice[g][b][dom].push_back({(int)wl.size() - c->wofs[g][b][dom], (int)nb});
@@ -280,6 +387,21 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
       std::fprintf(stderr, "grmhd_init_patches: %s\n", plan.err.c_str());
       grmhd_destroy(c);
       return GRMHD_ERR_ARG;
+    }
+    if (S) {
+      // This rank's ghost tasks, stencil points and composed restriction
+      // copies (all under level 1: they are independent of one another).
+      for (int l = 1; l < plan.nlev; ++l) {
+        plan.ghost[l].assign(S->ghost.begin() + S->gofs[l], S->ghost.begin() + S->gofs[l + 1]);
+        plan.restr[l].clear();
+        plan.tpts[l] = S->tpts[l];
+        plan.xpts[l] = S->xpts[l];
+        plan.nsame[l] = 0;
+        for (const auto& t : plan.ghost[l])
+          if (!(t.odd & AMR_COARSE)) ++plan.nsame[l];
+      }
+      if (plan.nlev > 1) plan.restr[1] = S->restr;
+      plan.sub_err = "sharded hierarchy (sub-cycling is not available across ranks)";
     }
     c->amr_level0 = plan.level0;
     c->amr_nlev = plan.nlev;
@@ -343,12 +465,68 @@ int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const
       (rc = cuda_ok(c, cudaMemcpyAsync(c->pd, c->pd_host.data(), npatch * sizeof(PatchDev), cudaMemcpyHostToDevice,
                                        c->st), "copy pd")) ||
       (rc = cuda_ok(c, cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->st), "clear flags")) ||
-      (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync"))) {
+      (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync")) || (rc = build_tuned(c))) {
     grmhd_destroy(c);
     return rc;
   }
   *out = c;
   return GRMHD_OK;
+}
+
+int grmhd_init_patches(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d,
+                       const grmhd_eos_table* eos, void* stream) {
+  return init_impl(out, p, npatch, d, eos, stream, nullptr);
+}
+
+int grmhd_shard_partition(int npatch, const grmhd_patch_desc* d, int nranks, int* owner) {
+  return shard_partition(d, npatch, nranks, owner);
+}
+
+int grmhd_shard_plan(int npatch, const grmhd_patch_desc* d, const int* owner, int nranks, int rank, int* role,
+                     long long* counts, int* lists, long long cap) {
+  if (!d || !owner || npatch < 1 || nranks < 1 || rank < 0 || rank >= nranks || !counts) return GRMHD_ERR_ARG;
+  std::vector<Geo> geo(npatch);
+  for (int i = 0; i < npatch; ++i) geo[i] = geo_of(d[i]);
+  ShardPlan S;
+  if (shard_plan(d, geo, npatch, owner, nranks, rank, S) != GRMHD_OK) {
+    std::fprintf(stderr, "grmhd_shard_plan: %s\n", S.err.c_str());
+    return GRMHD_ERR_ARG;
+  }
+  if (role)
+    for (int i = 0; i < npatch; ++i) role[i] = S.role[i];
+  long long need = 0;
+  for (int q = 0; q < nranks; ++q) {
+    counts[4 * q + 0] = (long long)S.gsend[q].size();
+    counts[4 * q + 1] = (long long)S.grecv[q].size();
+    counts[4 * q + 2] = (long long)S.rsend[q].size();
+    counts[4 * q + 3] = (long long)S.rrecv[q].size();
+    need += counts[4 * q] + counts[4 * q + 1] + counts[4 * q + 2] + counts[4 * q + 3];
+  }
+  if (!lists) return GRMHD_OK;
+  if (cap < 2 * need) return GRMHD_ERR_SIZE;
+  long long o = 0;
+  for (int q = 0; q < nranks; ++q)
+    for (const auto* v : {&S.gsend[q], &S.grecv[q], &S.rsend[q], &S.rrecv[q]})
+      for (const auto& pt : *v) {
+        lists[o++] = pt.patch;
+        lists[o++] = pt.ofs;
+      }
+  return GRMHD_OK;
+}
+
+int grmhd_init_shard(grmhd_ctx** out, const grmhd_params* p, int npatch, const grmhd_patch_desc* d, const int* owner,
+                     int nranks, int rank, const grmhd_eos_table* eos, void* stream) {
+  if (!out) return GRMHD_ERR_ARG;
+  *out = nullptr;
+  if (!p || !d || !owner || npatch < 1 || p->bc != 3) return GRMHD_ERR_ARG;
+  std::vector<Geo> geo(npatch);
+  for (int i = 0; i < npatch; ++i) geo[i] = geo_of(d[i]);
+  ShardPlan S;
+  if (shard_plan(d, geo, npatch, owner, nranks, rank, S) != GRMHD_OK) {
+    std::fprintf(stderr, "grmhd_init_shard: %s\n", S.err.c_str());
+    return GRMHD_ERR_ARG;
+  }
+  return init_impl(out, p, npatch, d, eos, stream, &S);
 }
 
 static int nblk(grmhd_ctx* c, int dom, int bs = 128, int grp = 0) {
@@ -363,14 +541,16 @@ static const Work* wl(grmhd_ctx* c, int dom, int bs = 128, int grp = 0) {
 // to one patch: work items are grouped by patch in increasing order.
 static void patch_range(grmhd_ctx* c, int dom, int patch, int* first, int* cnt) {
   long long before = 0;
-  for (int i = 0; i < patch; ++i) before += (dom_count(dom, c->pd_host[i].G) + BS_ALL - 1) / BS_ALL;
+  for (int i = 0; i < patch; ++i)
+    if (c->role[i] == 1) before += (dom_count(dom, c->pd_host[i].G) + BS_ALL - 1) / BS_ALL;
   *first = (int)before;
   *cnt = (int)((dom_count(dom, c->pd_host[patch].G) + BS_ALL - 1) / BS_ALL);
 }
 
 int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
   if (!c) return GRMHD_ERR_ARG;
-  if (patch < 0 || patch >= c->np || !id) return fail(c, GRMHD_ERR_ARG, "init_state: bad patch or id");
+  if (patch < 0 || patch >= c->np || !id || c->role[patch] != 1)
+    return fail(c, GRMHD_ERR_ARG, "init_state: bad patch (or not evolved on this rank) or id");
   const PatchDev& q = c->pd_host[patch];
   {
     ProfScope ps(c, K_INIT);
@@ -397,28 +577,34 @@ int grmhd_init_state(grmhd_ctx* c, int patch, const double* id) {
   return check_launch(c, "init ghost");
 }
 
+// Ghost fill of hierarchy levels 1.. in order (bc 3).
+static int fill_levels(grmhd_ctx* c, int reg) {
+  for (int l = 1; l < c->amr_nlev; ++l) {
+    // The coarser level's x-midpoints once per row, then the fill (uses the
+    // coarser level's pointwise-flux scratch).
+    ProfScope ps(c, K_GHOST);
+    launch_amr_xmid(c->pd, c->amr_tp + c->amr_xofs[l], c->amr_xcnt[l], reg, c->st);
+    launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st, -1, true);
+    c->launches += 2;
+  }
+  return check_launch(c, "ghost hierarchy");
+}
+
 int grmhd_ghost_fill(grmhd_ctx* c, int reg) {
   if (!c) return GRMHD_ERR_ARG;
   if (reg < 0 || reg > 3) return fail(c, GRMHD_ERR_ARG, "ghost_fill: reg");
   if (c->P.bc == 3) {
-    // Level 0: outer boundary extrapolation of its single patch; then each
-    // finer level from its own interiors and the next coarser level.
-    for (int ax = 0; ax < 3; ++ax) {
+    // Level 0: outer boundary extrapolation of its single patch (on the rank
+    // that evolves it); then each finer level from its own interiors and the
+    // next coarser level.
+    for (int ax = 0; ax < 3 && c->role[c->amr_level0] == 1; ++ax) {
       int first, cnt;
       patch_range(c, DOM_GX + ax, c->amr_level0, &first, &cnt);
       ProfScope ps(c, K_GHOST);
       launch_ghost(c->pd, wl(c, DOM_GX + ax) + first, cnt, reg, ax, 1, c->st);
       c->launches += 1;
     }
-    for (int l = 1; l < c->amr_nlev; ++l) {
-      // The coarser level's x-midpoints once per row, then the fill (uses the
-      // coarser level's pointwise-flux scratch).
-      ProfScope ps(c, K_GHOST);
-      launch_amr_xmid(c->pd, c->amr_tp + c->amr_xofs[l], c->amr_xcnt[l], reg, c->st);
-      launch_amr(c->pd, c->amr + c->amr_gofs[l], c->amr_gcnt[l], reg, c->st, -1, true);
-      c->launches += 2;
-    }
-    return check_launch(c, "ghost hierarchy");
+    return fill_levels(c, reg);
   }
   if (c->P.bc == 2) {
     if (reg != 0) {
@@ -449,9 +635,9 @@ static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats, int grp = 0) {
   }
   {
     ProfScope ps(c, K_C2P);
-    for_slices(c, DOM_ALL, c->bs_c2p, grp, [&](const Work* w, int n) {
+    for_tslices(c, DOM_ALL, c->bs_c2p, grp, [&](const Work* w, int n) {
       launch_c2p(c->pd, w, n, reg, c->P, c->E, c->flags, stats ? c->stats : nullptr, c->st, c->bs_c2p,
-                 c->seeder != nullptr, c->seed_delta);
+                 c->seeder != nullptr, c->seed_delta, c->pers[0]);
       c->launches += 1;
     });
   }
@@ -475,10 +661,12 @@ int grmhd_set_seeder(grmhd_ctx* c, const grmhd_seeder* s, double delta) {
   int rc;
   if (!c->seed_buf) {
     size_t total = 0;
-    for (int i = 0; i < c->np; ++i) total += 3 * (size_t)c->pd_host[i].G.sf;
+    for (int i = 0; i < c->np; ++i)
+      if (c->role[i] == 1) total += 3 * (size_t)c->pd_host[i].G.sf;
     if ((rc = cuda_ok(c, cudaMalloc(&c->seed_buf, total * sizeof(float)), "cudaMalloc seeds"))) return GRMHD_ERR_NOMEM;
     size_t o = 0;
     for (int i = 0; i < c->np; ++i) {
+      if (c->role[i] != 1) continue;
       c->pd_host[i].seed = c->seed_buf + o;
       o += 3 * (size_t)c->pd_host[i].G.sf;
     }
@@ -495,8 +683,8 @@ int grmhd_set_seeder(grmhd_ctx* c, const grmhd_seeder* s, double delta) {
 static int iflux(grmhd_ctx* c, int reg, int grp = 0) {
   for (int d = 0; d < 3; ++d) {
     ProfScope ps(c, K_IFLUX);
-    for_slices(c, DOM_IFX + d, c->bs_if, grp, [&](const Work* w, int n) {
-      launch_iflux(c->pd, w, n, reg, d, c->st, c->bs_if);
+    for_tslices(c, DOM_IFX + d, c->bs_if, grp, [&](const Work* w, int n) {
+      launch_iflux(c->pd, w, n, reg, d, c->st, c->bs_if, c->pers[1]);
       c->launches += 1;
     });
   }
@@ -526,7 +714,7 @@ int grmhd_rhs_eval(grmhd_ctx* c, int reg, double* const* rhs) {
   if (!c) return GRMHD_ERR_ARG;
   if (reg < 0 || reg > 3 || !rhs) return fail(c, GRMHD_ERR_ARG, "rhs_eval: args");
   for (int i = 0; i < c->np; ++i)
-    if (!rhs[i]) return fail(c, GRMHD_ERR_ARG, "rhs_eval: null rhs");
+    if (c->role[i] == 1 && !rhs[i]) return fail(c, GRMHD_ERR_ARG, "rhs_eval: null rhs");
   int rc;
   if ((rc = cuda_ok(c, cudaMemcpyAsync(c->rhs_ptrs, rhs, c->np * sizeof(double*), cudaMemcpyHostToDevice, c->st),
                     "rhs ptrs")) ||
@@ -535,8 +723,8 @@ int grmhd_rhs_eval(grmhd_ctx* c, int reg, double* const* rhs) {
   if ((rc = iflux(c, reg))) return rc;
   {
     ProfScope ps(c, K_RHS);
-    for_slices(c, DOM_INT, c->bs_rhs, 0, [&](const Work* w, int n) {
-      launch_rhs(c->pd, w, n, reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st, c->bs_rhs);
+    for_tslices(c, DOM_INT, c->bs_rhs, 0, [&](const Work* w, int n) {
+      launch_rhs(c->pd, w, n, reg, 0, 0, 0.0, c->P, c->rhs_ptrs, c->st, c->bs_rhs, c->rhs_tiled);
       c->launches += 1;
     });
   }
@@ -568,13 +756,15 @@ int grmhd_rhs_substep(grmhd_ctx* c, int stage, double dt) {
   if (stage < 0 || stage > (rk3 ? 2 : 3)) return fail(c, GRMHD_ERR_ARG, "rhs_substep: stage");
   int reg = rk3 ? kStageInRk3[stage] : kStageIn[stage];
   int rc;
-  if ((rc = grmhd_ghost_fill(c, reg))) return rc;
+  // A sharded context fills levels 1.. only: level 0's ghosts come from
+  // grmhd_shard_ghost0 on its own rank, before the exchange.
+  if ((rc = c->shard ? fill_levels(c, reg) : grmhd_ghost_fill(c, reg))) return rc;
   if ((rc = c2p_and_fluxes(c, reg, false))) return rc;
   if ((rc = iflux(c, reg))) return rc;
   {
     ProfScope ps(c, K_RHS);
-    for_slices(c, DOM_INT, c->bs_rhs, 0, [&](const Work* w, int n) {
-      launch_rhs(c->pd, w, n, reg, 1, stage, dt, c->P, nullptr, c->st, c->bs_rhs);
+    for_tslices(c, DOM_INT, c->bs_rhs, 0, [&](const Work* w, int n) {
+      launch_rhs(c->pd, w, n, reg, 1, stage, dt, c->P, nullptr, c->st, c->bs_rhs, c->rhs_tiled);
       c->launches += 1;
     });
   }
@@ -667,8 +857,8 @@ static int sub_advance(grmhd_ctx* c, int l, int msub, double dt) {
     if ((rc = iflux(c, reg, grp))) return rc;
     {
       ProfScope ps(c, K_RHS);
-      for_slices(c, DOM_INT, c->bs_rhs, grp, [&](const Work* w, int n) {
-        launch_rhs(c->pd, w, n, reg, 1, s, dt, c->P, nullptr, c->st, c->bs_rhs);
+      for_tslices(c, DOM_INT, c->bs_rhs, grp, [&](const Work* w, int n) {
+        launch_rhs(c->pd, w, n, reg, 1, s, dt, c->P, nullptr, c->st, c->bs_rhs, c->rhs_tiled);
         c->launches += 1;
       });
     }
@@ -734,8 +924,35 @@ int grmhd_set_subcycling(grmhd_ctx* c, int on) {
   return GRMHD_OK;
 }
 
+int grmhd_shard_ghost0(grmhd_ctx* c, int reg) {
+  if (!c || !c->shard || reg < 0 || reg > 3) return GRMHD_ERR_ARG;
+  for (int ax = 0; ax < 3 && c->role[c->amr_level0] == 1; ++ax) {
+    int first, cnt;
+    patch_range(c, DOM_GX + ax, c->amr_level0, &first, &cnt);
+    ProfScope ps(c, K_GHOST);
+    launch_ghost(c->pd, wl(c, DOM_GX + ax) + first, cnt, reg, ax, 1, c->st);
+    c->launches += 1;
+  }
+  return check_launch(c, "level-0 ghosts");
+}
+
+int grmhd_shard_pack(grmhd_ctx* c, int reg, const int* pts, long long n, double* buf) {
+  if (!c || reg < 0 || reg > 3 || n < 0 || (n > 0 && (!pts || !buf))) return GRMHD_ERR_ARG;
+  launch_shard_pack(c->pd, reinterpret_cast<const AmrPoint*>(pts), n, reg, buf, c->st);
+  c->launches += n > 0;
+  return check_launch(c, "shard pack");
+}
+
+int grmhd_shard_unpack(grmhd_ctx* c, int reg, const int* pts, long long n, const double* buf) {
+  if (!c || reg < 0 || reg > 3 || n < 0 || (n > 0 && (!pts || !buf))) return GRMHD_ERR_ARG;
+  launch_shard_unpack(c->pd, reinterpret_cast<const AmrPoint*>(pts), n, reg, buf, c->st);
+  c->launches += n > 0;
+  return check_launch(c, "shard unpack");
+}
+
 int grmhd_step(grmhd_ctx* c, double dt) {
   if (!c) return GRMHD_ERR_ARG;
+  if (c->shard) return fail(c, GRMHD_ERR_ARG, "step: a sharded context steps through the exchange protocol");
   if (c->subcycle) return sub_advance(c, 0, 0, dt);
   const int nsub = c->P.rk == 1 ? 3 : 4;
   for (int s = 0; s < nsub; ++s) {
@@ -799,10 +1016,83 @@ int grmhd_set_block_sizes(grmhd_ctx* c, int bs_c2p, int bs_iflux, int bs_rhs) {
   return GRMHD_OK;
 }
 
+int grmhd_set_schedule(grmhd_ctx* c, const int* shapes, const int* pers) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (shapes)
+    for (int i = 0; i < 3 * c->np; ++i)
+      if (shapes[i] < 0 || shapes[i] >= NSHAPE) return fail(c, GRMHD_ERR_ARG, "set_schedule: shape 0..4");
+  if (pers && pers[2]) return fail(c, GRMHD_ERR_ARG, "set_schedule: the right-hand side has no persistent form");
+  if (shapes)
+    for (int i = 0; i < c->np; ++i)
+      for (int k = 0; k < 3; ++k) c->shape[i][k] = shapes[3 * i + k];
+  if (pers)
+    for (int k = 0; k < 2; ++k) c->pers[k] = pers[k] != 0;
+  return build_tuned(c);
+}
+
+int grmhd_get_schedule(grmhd_ctx* c, int* shapes, int* pers) {
+  if (!c) return GRMHD_ERR_ARG;
+  if (shapes)
+    for (int i = 0; i < c->np; ++i)
+      for (int k = 0; k < 3; ++k) shapes[3 * i + k] = c->shape[i][k];
+  if (pers)
+    for (int k = 0; k < 3; ++k) pers[k] = c->pers[k] ? 1 : 0;
+  return GRMHD_OK;
+}
+
+// Size class of a patch for the tile-shape search: its longest edge, in the
+// bins <= 16, 24, 32, 48, 64, 96, 128, larger.
+static int size_class(const grmhd_patch_desc& d) {
+  const int e = std::max(d.n[0], std::max(d.n[1], d.n[2]));
+  const int lim[7] = {16, 24, 32, 48, 64, 96, 128};
+  for (int k = 0; k < 7; ++k)
+    if (e <= lim[k]) return k;
+  return 7;
+}
+
+// Times `reps` launches of kernel kind `kind` (after one untimed launch) over
+// the given patches with tile shape sh, on stage-0 data (register 0 in, the
+// fused stage-0 outputs U[1], U[3] out: repeated launches change nothing).
+static double time_kind(grmhd_ctx* c, int kind, const std::vector<int>& patches, int sh, int reps, Work* tmp,
+                        size_t cap, cudaEvent_t e0, cudaEvent_t e1) {
+  const int bs = kind == 0 ? c->bs_c2p : (kind == 1 ? c->bs_if : c->bs_rhs);
+  const int lb = log2_bs(bs);
+  double total = 0.0;
+  const int ndir = kind == 1 ? 3 : 1;
+  for (int d = 0; d < ndir; ++d) {
+    const int dom = kind == 0 ? DOM_ALL : (kind == 1 ? DOM_IFX + d : DOM_INT);
+    std::vector<Work> wl;
+    for (int i : patches) {
+      const long long nt = dom_tiles(dom, c->pd_host[i].G, lb, sh);
+      for (long long t = 0; t < nt; ++t) wl.push_back(Work{i, (int)t | (sh << TILE_BITS)});
+    }
+    if (wl.empty()) continue;
+    if (wl.size() > cap) return -1.0;  // cannot happen: the buffer holds the largest trial list
+    if (cudaMemcpy(tmp, wl.data(), wl.size() * sizeof(Work), cudaMemcpyHostToDevice) != cudaSuccess) return -1.0;
+    const int n = (int)wl.size();
+    for (int r = 0; r <= reps; ++r) {
+      if (r == 1) cudaEventRecord(e0, c->st);
+      if (kind == 0)
+        launch_c2p(c->pd, tmp, n, 0, c->P, c->E, c->flags, nullptr, c->st, bs, c->seeder != nullptr, c->seed_delta);
+      else if (kind == 1)
+        launch_iflux(c->pd, tmp, n, 0, d, c->st, bs);
+      else
+        launch_rhs(c->pd, tmp, n, 0, 1, 0, 0.0, c->P, nullptr, c->st, bs, sh != 0);
+    }
+    cudaEventRecord(e1, c->st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+    total += ms;
+  }
+  return total;
+}
+
 int grmhd_autotune(grmhd_ctx* c, double dt, int reps, int* chosen) {
   if (!c) return GRMHD_ERR_ARG;
   if (reps < 1) return fail(c, GRMHD_ERR_ARG, "autotune: reps");
   bool was = c->profiling;
+  // Phase 1: block size per kernel kind, from whole substeps with the
+  // current schedule.
   double best[3] = {1e300, 1e300, 1e300};
   int pick[3] = {128, 128, 128};
   int rc = GRMHD_OK;
@@ -831,6 +1121,71 @@ int grmhd_autotune(grmhd_ctx* c, double dt, int reps, int* chosen) {
     chosen[1] = pick[1];
     chosen[2] = pick[2];
   }
+  if (rc) return rc;
+  // Phase 2: tile shape per patch-size class and kernel kind, each kind timed
+  // alone on the class's patches (con2prim, then interface fluxes, then the
+  // right-hand side, so every kernel reads current inputs).
+  if ((rc = grmhd_rhs_substep(c, 0, dt)) || (rc = cuda_ok(c, cudaStreamSynchronize(c->st), "sync"))) return rc;
+  std::vector<std::vector<int>> cls(8);
+  for (int i = 0; i < c->np; ++i)
+    if (c->role[i] == 1) cls[size_class(c->desc[i])].push_back(i);
+  // The largest trial list: one domain, one class, one shape at a time.
+  size_t maxw = 1;
+  for (int kind = 0; kind < 3; ++kind) {
+    const int lb = log2_bs(kind == 0 ? c->bs_c2p : (kind == 1 ? c->bs_if : c->bs_rhs));
+    for (const auto& pl : cls)
+      for (int dom = 0; dom < NDOM; ++dom) {
+        if (kind_of(dom) != kind) continue;
+        for (int sh = 0; sh < NSHAPE; ++sh) {
+          size_t m = 0;
+          for (int i : pl) m += (size_t)dom_tiles(dom, c->pd_host[i].G, lb, sh);
+          maxw = std::max(maxw, m);
+        }
+      }
+  }
+  Work* tmp = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if ((rc = cuda_ok(c, cudaMalloc(&tmp, maxw * sizeof(Work)), "cudaMalloc autotune list"))) return GRMHD_ERR_NOMEM;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int kind = 0; kind < 3 && rc == GRMHD_OK; ++kind)
+    for (const auto& pl : cls) {
+      if (pl.empty()) continue;
+      double tbest = 1e300;
+      int sbest = 0;
+      for (int sh = 0; sh < NSHAPE; ++sh) {
+        double t = time_kind(c, kind, pl, sh, reps, tmp, maxw, e0, e1);
+        if (t < 0.0) {
+          rc = fail(c, GRMHD_ERR_CUDA, "autotune: tile timing");
+          break;
+        }
+        if (t < tbest) {
+          tbest = t;
+          sbest = sh;
+        }
+      }
+      for (int i : pl) c->shape[i][kind] = sbest;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(tmp);
+  if (rc || (rc = build_tuned(c))) return rc;
+  // Phase 3: persistent pool or one block per item, for con2prim and the
+  // interface fluxes, from whole substeps with the chosen shapes.
+  for (int kind = 0; kind < 2 && rc == GRMHD_OK; ++kind) {
+    double t[2] = {0.0, 0.0};
+    for (int p = 0; p < 2 && rc == GRMHD_OK; ++p) {
+      c->pers[kind] = p != 0;
+      if ((rc = grmhd_rhs_substep(c, 0, dt)) || (rc = grmhd_profile(c, 1))) break;
+      for (int r = 0; r < reps && rc == GRMHD_OK; ++r) rc = grmhd_rhs_substep(c, 0, dt);
+      double ms[NKIND];
+      long long cnt[NKIND];
+      if (rc || (rc = grmhd_profile_read(c, ms, cnt, NKIND))) break;
+      t[p] = ms[kind == 0 ? K_C2P : K_IFLUX];
+    }
+    c->pers[kind] = t[1] < t[0];
+  }
+  grmhd_profile(c, was ? 1 : 0);
   return rc;
 }
 
@@ -882,13 +1237,18 @@ int grmhd_sync_status(grmhd_ctx* c) {
   return GRMHD_OK;
 }
 
-int grmhd_dfma_probe(int blocks_per_sm, long long iters, double* sink, long long* fmas, void* stream) {
-  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1 || !sink || !fmas) return GRMHD_ERR_ARG;
+int grmhd_dfma_probe(int blocks_per_sm, int chains, long long iters, double* sink, long long* fmas, void* stream) {
+  // chains < 0: addition chains of |chains| (the FP64 add rate)
+  const bool add = chains < 0;
+  if (add) chains = -chains;
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || (chains != 4 && chains != 8 && chains != 16) || iters < 1 || !sink ||
+      !fmas)
+    return GRMHD_ERR_ARG;
   int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
     return GRMHD_ERR_CUDA;
-  *fmas = launch_dfma_probe(nsm * blocks_per_sm, iters, sink, (cudaStream_t)stream);
+  *fmas = launch_dfma_probe(nsm * blocks_per_sm, chains, iters, sink, (cudaStream_t)stream, add);
   return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_CUDA;
 }
 

@@ -80,6 +80,89 @@ DI void dom_decode(int dom, const Geo& G, long long q, int& i, int& j, int& k) {
   k = (int)(q / ey) + oz;
 }
 
+// ---- tile-shaped work items -------------------------------------------------
+// A work item's `block` field holds a tile index in bits 0-23 and a tile shape
+// in bits 24-30.  Shape 0: the domain's points in linear chunks of the block
+// size (x fastest, wrapping across rows).  Shape s >= 1: boxes of
+// 2^lx x 2^ly x 2^lz points, lx + ly + lz = log2(block size), tiles numbered x
+// fastest over the domain; points of a box outside the domain are idle.
+constexpr int NSHAPE = 5;
+constexpr int TILE_BITS = 24;
+constexpr int TILE_MASK = (1 << TILE_BITS) - 1;
+
+// log2 extents of shape s (1..4) for a block of 2^b threads (b = 6, 7, 8):
+// 1: a row segment 2^b x 1 x 1; 2: 32 x 2 x 2^(b-6); 3: 16 x 4 x 2^(b-6);
+// 4: 8 x 8 x 2^(b-6).
+inline __host__ __device__ void shape_log2(int b, int s, int& lx, int& ly, int& lz) {
+  switch (s) {
+    case 1: lx = b; ly = 0; lz = 0; break;
+    case 2: lx = 5; ly = 1; lz = b - 6; break;
+    case 3: lx = 4; ly = 2; lz = b - 6; break;
+    default: lx = 3; ly = 3; lz = b - 6; break;
+  }
+}
+
+// Extents and origin of a domain's point box (not for the ghost-line domains).
+inline __host__ __device__ void dom_box(int dom, const Geo& G, int ex[3], int o[3]) {
+  ex[0] = G.n0; ex[1] = G.n1; ex[2] = G.n2;
+  o[0] = o[1] = o[2] = 0;
+  if (dom == DOM_ALL) {
+    for (int a = 0; a < 3; ++a) ex[a] += 6, o[a] = -3;
+  } else if (dom >= DOM_IFX && dom <= DOM_IFZ) {
+    ex[dom - DOM_IFX] += 1;
+    o[dom - DOM_IFX] = -1;
+  }
+}
+
+// Number of work items of a domain in shape s for blocks of 2^b threads.
+inline long long dom_tiles(int dom, const Geo& G, int b, int s) {
+  if (s == 0) return (dom_count(dom, G) + (1 << b) - 1) >> b;
+  int ex[3], o[3], l[3];
+  dom_box(dom, G, ex, o);
+  shape_log2(b, s, l[0], l[1], l[2]);
+  long long n = 1;
+  for (int a = 0; a < 3; ++a) n *= (ex[a] + (1 << l[a]) - 1) >> l[a];
+  return n;
+}
+
+// Point (i, j, k) of thread tid of a work item; false when the thread is idle.
+DI bool work_point(int dom, const Geo& G, int blk, int tid, int bs_log2, int& i, int& j, int& k) {
+  const int s = blk >> TILE_BITS, t = blk & TILE_MASK;
+  if (s == 0) {
+    long long q = ((long long)t << bs_log2) + tid;
+    if (q >= dom_count(dom, G)) return false;
+    dom_decode(dom, G, q, i, j, k);
+    return true;
+  }
+  int ex[3], o[3], l0, l1, l2;
+  dom_box(dom, G, ex, o);
+  shape_log2(bs_log2, s, l0, l1, l2);
+  const int ntx = (ex[0] + (1 << l0) - 1) >> l0, nty = (ex[1] + (1 << l1) - 1) >> l1;
+  const int bx = t % ntx, r = t / ntx, by = r % nty, bz = r / nty;
+  const int x = (bx << l0) + (tid & ((1 << l0) - 1));
+  const int y = (by << l1) + ((tid >> l0) & ((1 << l1) - 1));
+  const int z = (bz << l2) + (tid >> (l0 + l1));
+  if (x >= ex[0] || y >= ex[1] || z >= ex[2]) return false;
+  i = x + o[0];
+  j = y + o[1];
+  k = z + o[2];
+  return true;
+}
+
+// Grid of a launch over nitems work items: one block per item, or (pers) a
+// persistent pool of at most as many blocks as are resident on the GPU at
+// once, each looping over the items with stride gridDim.x.
+template <class K>
+inline int grid_for(K kernel, int bs, int nitems, bool pers) {
+  if (!pers) return nitems;
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, bs, 0);
+  long long g = (long long)(nsm > 0 ? nsm : 1) * (per > 0 ? per : 1);
+  return (int)(g < nitems ? g : nitems);
+}
+
 struct C2PStats {
   unsigned long long points, iters, corrected, failed;
 };
@@ -102,11 +185,17 @@ void launch_ghost(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int 
                   int f0 = 0, int f1 = NF);
 // bs: threads per block of the launch (64, 128 or 256); the work list must
 // have been built for the same block size.
+// Work lists of the con2prim, interface-flux and right-hand-side launches may
+// hold tile-shaped items (see work_point); pers: persistent launch (grid_for).
 void launch_c2p(const PatchDev* pd_dev, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs = 128, bool seeded = false, double delta = 0.0);
-void launch_iflux(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs = 128);
+                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs = 128, bool seeded = false, double delta = 0.0,
+                bool pers = false);
+void launch_iflux(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs = 128,
+                  bool pers = false);
+// tiled: the work list may hold tile-shaped items (shape >= 1); otherwise
+// all items are linear chunks (shape 0).
 void launch_rhs(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int mode, int stage, double dt,
-                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs = 128);
+                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs = 128, bool tiled = false);
 void launch_ghost_copy(const PatchDev* pd_dev, const Work* w, int nblk, int reg, cudaStream_t st);
 void launch_rk(const PatchDev* pd_dev, const Work* w, int nblk, int stage, double dt, double* const* rhs_dev,
                cudaStream_t st, int rk = 0);
@@ -168,14 +257,40 @@ void launch_amr_time(const PatchDev* pd_dev, const AmrPoint* pts, long long n, c
 // at the interior points of the work list (block size 128).
 void launch_dense_rec(const PatchDev* pd_dev, const Work* w, int nblk, int stage, int rk, cudaStream_t st);
 
+// ---- sharding across ranks (shard.cu) ----------------------------------------
+// Owner rank of every patch: Morton order of the patch centres cut into
+// nranks runs of about equal interior point count.
+int shard_partition(const grmhd_patch_desc* d, int np, int nranks, int* owner);
+// Sharding plan of one rank; see the file comment.
+struct ShardPlan {
+  std::vector<int> role;                          // per patch: 0 absent, 1 local, 2 mirror
+  std::vector<std::vector<AmrPoint>> gsend, grecv;  // per peer: ghost-phase sources / their mirror points
+  std::vector<std::vector<AmrPoint>> rsend, rrecv;  // per peer: restriction sources / their mirror points
+  std::vector<AmrTask> ghost;                     // the rank's ghost tasks, levels 1.., in level order
+  std::vector<long long> gofs;                    // per level: first ghost task (size nlev + 1)
+  std::vector<AmrTask> restr;                     // composed restriction copies into local patches
+  std::vector<std::vector<AmrPoint>> tpts, xpts;  // per level: coarse stencil points, x-midpoint rows
+  int level0 = -1, nlev = 0;
+  std::string err;
+};
+// The plan of rank `rank` (GRMHD_ERR_ARG with S.err when the hierarchy is not
+// nested as the single exchange per substep needs).
+int shard_plan(const grmhd_patch_desc* d, const std::vector<Geo>& geo, int np, const int* owner, int nranks, int rank,
+               ShardPlan& S);
+// Gather / scatter of register reg at n listed points into / from a [32][n] buffer.
+void launch_shard_pack(const PatchDev* pd, const AmrPoint* pts, long long n, int reg, double* buf, cudaStream_t st);
+void launch_shard_unpack(const PatchDev* pd, const AmrPoint* pts, long long n, int reg, const double* buf,
+                         cudaStream_t st);
+
 // Learned seeder over patch points (seeder.cu): seeds of every point of the
 // work list (blocks of 128 points) of register reg into PatchDev::seed.
 int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd_dev, const Work* w, int nblk, int reg,
                           double rho_min, int* err, cudaStream_t st);
 
-// FP64 FMA throughput probe: `blocks` blocks of 256 threads; returns the
-// thread-level FMAs one launch executes.
-long long launch_dfma_probe(int blocks, long long iters, double* sink, cudaStream_t st);
+// FP64 throughput probe: `blocks` blocks of 256 threads, each thread running
+// `chains` (4, 8 or 16) independent FMA (or, add, addition) chains; returns
+// the thread-level instructions one launch executes.
+long long launch_dfma_probe(int blocks, int chains, long long iters, double* sink, cudaStream_t st, bool add);
 
 // Block sizes the autotuner chooses from.
 constexpr int NBS = 3;

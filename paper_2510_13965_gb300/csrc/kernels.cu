@@ -204,19 +204,17 @@ void launch_ghost(const PatchDev* pd, const Work* w, int nblk, int reg, int axis
 // con2prim at every point, then the point-wise flux vectors F^d (10 fields)
 // and max |lambda^{+-}_fast| along d for the directions whose interface
 // stencils use this point.
-template <bool STATS, int BS, bool SEEDED>
-__global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
-                                                 grmhd_params P, Eos E, DevFlags* flags, C2PStats* stats,
-                                                 double delta) {
-  Work wk = w[blockIdx.x];
+// con2prim and point-wise fluxes of one work item (see k_c2p); adds the
+// item's iteration, correction, failure and point counts to acc.
+template <bool SEEDED, int LB>
+DI void c2p_item(const PatchDev* __restrict__ pd, const Work wk, int reg, const grmhd_params& P, const Eos& E,
+                 DevFlags* flags, double delta, unsigned long long acc[4]) {
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
-  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
-  bool active = q < dom_count(DOM_ALL, G);
+  int i, j, k;
+  const bool active = work_point(DOM_ALL, G, wk.block, threadIdx.x, LB, i, j, k);
   int st_code = 0, iters = 0;
   if (active) {
-    int i, j, k;
-    dom_decode(DOM_ALL, G, q, i, j, k);
     const long long o = at(G, i, j, k), sf = G.sf;
     double* U = PD.U[reg];
     double gt[6], gtu[6], gdd[6], guu[6];
@@ -317,8 +315,29 @@ __global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, con
       }
     }
   }
+  acc[0] += iters;
+  acc[1] += st_code > 0;
+  acc[2] += st_code < 0;
+  acc[3] += active;
+}
+
+// PERS: a persistent pool of blocks loops over the work items with stride
+// gridDim.x; otherwise one block per item (the loop costs registers, so it
+// exists only in the persistent instantiations).
+template <bool STATS, int BS, bool SEEDED, bool PERS>
+__global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int nitems,
+                                                 int reg, grmhd_params P, Eos E, DevFlags* flags, C2PStats* stats,
+                                                 double delta) {
+  constexpr int LB = BS == 64 ? 6 : (BS == 128 ? 7 : 8);
+  unsigned long long acc[4] = {0, 0, 0, 0};
+  if constexpr (PERS) {
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x)
+      c2p_item<SEEDED, LB>(pd, w[item], reg, P, E, flags, delta, acc);
+  } else {
+    c2p_item<SEEDED, LB>(pd, w[blockIdx.x], reg, P, E, flags, delta, acc);
+  }
   if (STATS) {
-    unsigned long long it = iters, cor = st_code > 0, bad = st_code < 0, pts = active;
+    unsigned long long it = acc[0], cor = acc[1], bad = acc[2], pts = acc[3];
     for (int off = 16; off > 0; off >>= 1) {
       it += __shfl_down_sync(0xffffffffu, it, off);
       cor += __shfl_down_sync(0xffffffffu, cor, off);
@@ -334,43 +353,54 @@ __global__ void __launch_bounds__(BS) k_c2p(const PatchDev* __restrict__ pd, con
   }
 }
 
-template <int BS>
+template <int BS, bool PERS>
 static void launch_c2p_bs(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
                           DevFlags* flags, C2PStats* stats, cudaStream_t st, bool seeded, double delta) {
   if (seeded) {
-    if (stats)
-      k_c2p<true, BS, true><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, delta);
-    else
-      k_c2p<false, BS, true><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, delta);
+    if (stats) {
+      auto k = k_c2p<true, BS, true, PERS>;
+      k<<<grid_for(k, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg, P, E, flags, stats, delta);
+    } else {
+      auto k = k_c2p<false, BS, true, PERS>;
+      k<<<grid_for(k, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg, P, E, flags, stats, delta);
+    }
   } else if (stats) {
-    k_c2p<true, BS, false><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, 0.0);
+    auto k = k_c2p<true, BS, false, PERS>;
+    k<<<grid_for(k, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg, P, E, flags, stats, 0.0);
   } else {
-    k_c2p<false, BS, false><<<nblk, BS, 0, st>>>(pd, w, reg, P, E, flags, stats, 0.0);
+    auto k = k_c2p<false, BS, false, PERS>;
+    k<<<grid_for(k, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg, P, E, flags, stats, 0.0);
   }
 }
 
 void launch_c2p(const PatchDev* pd, const Work* w, int nblk, int reg, const grmhd_params& P, const Eos& E,
-                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs, bool seeded, double delta) {
+                DevFlags* flags, C2PStats* stats, cudaStream_t st, int bs, bool seeded, double delta, bool pers) {
   if (nblk <= 0) return;
-  if (bs == 64) launch_c2p_bs<64>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
-  else if (bs == 256) launch_c2p_bs<256>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
-  else launch_c2p_bs<128>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  if (pers) {
+    if (bs == 64) launch_c2p_bs<64, true>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+    else if (bs == 256) launch_c2p_bs<256, true>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+    else launch_c2p_bs<128, true>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  } else if (bs == 64) {
+    launch_c2p_bs<64, false>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  } else if (bs == 256) {
+    launch_c2p_bs<256, false>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  } else {
+    launch_c2p_bs<128, false>(pd, w, nblk, reg, P, E, flags, stats, st, seeded, delta);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Interface fluxes along direction D: lambda = max over points i-2 .. i+3,
 // g^{+-} = F +- lambda U, F^L = MP5(g^+_{i-2..i+2}), F^R = MP5(g^-_{i+3..i-1}),
 // Fhat = (F^L + F^R) / 2 (MP5 commutes with the positive factor 1/2).
-template <int D, int BS>
-__global__ void __launch_bounds__(BS) k_iflux(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg) {
-  Work wk = w[blockIdx.x];
+// Interface fluxes of one work item along direction D (see k_iflux).
+template <int D, int LB>
+DI void iflux_item(const PatchDev* __restrict__ pd, const Work wk, int reg) {
+  constexpr int dom = D == 0 ? DOM_IFX : (D == 1 ? DOM_IFY : DOM_IFZ);
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
-  constexpr int dom = D == 0 ? DOM_IFX : (D == 1 ? DOM_IFY : DOM_IFZ);
-  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
-  if (q >= dom_count(dom, G)) return;
   int i, j, k;
-  dom_decode(dom, G, q, i, j, k);
+  if (!work_point(dom, G, wk.block, threadIdx.x, LB, i, j, k)) return;
   const long long o = at(G, i, j, k), sf = G.sf;
   const long long s = D == 0 ? 1 : (D == 1 ? G.sy : G.sz);
   const double* lam = PD.lam + (long long)D * sf + o;
@@ -395,18 +425,38 @@ __global__ void __launch_bounds__(BS) k_iflux(const PatchDev* __restrict__ pd, c
   }
 }
 
-template <int BS>
-static void launch_iflux_bs(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st) {
-  if (dir == 0) k_iflux<0, BS><<<nblk, BS, 0, st>>>(pd, w, reg);
-  if (dir == 1) k_iflux<1, BS><<<nblk, BS, 0, st>>>(pd, w, reg);
-  if (dir == 2) k_iflux<2, BS><<<nblk, BS, 0, st>>>(pd, w, reg);
+// PERS: a persistent pool of blocks loops over the work items (see k_c2p).
+template <int D, int BS, bool PERS>
+__global__ void __launch_bounds__(BS) k_iflux(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int nitems,
+                                                   int reg) {
+  constexpr int LB = BS == 64 ? 6 : (BS == 128 ? 7 : 8);
+  if constexpr (PERS) {
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) iflux_item<D, LB>(pd, w[item], reg);
+  } else {
+    iflux_item<D, LB>(pd, w[blockIdx.x], reg);
+  }
 }
 
-void launch_iflux(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs) {
+template <int BS, bool PERS>
+static void launch_iflux_bs(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st) {
+  if (dir == 0) k_iflux<0, BS, PERS><<<grid_for(k_iflux<0, BS, PERS>, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg);
+  if (dir == 1) k_iflux<1, BS, PERS><<<grid_for(k_iflux<1, BS, PERS>, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg);
+  if (dir == 2) k_iflux<2, BS, PERS><<<grid_for(k_iflux<2, BS, PERS>, BS, nblk, PERS), BS, 0, st>>>(pd, w, nblk, reg);
+}
+
+void launch_iflux(const PatchDev* pd, const Work* w, int nblk, int reg, int dir, cudaStream_t st, int bs, bool pers) {
   if (nblk <= 0) return;
-  if (bs == 64) launch_iflux_bs<64>(pd, w, nblk, reg, dir, st);
-  else if (bs == 256) launch_iflux_bs<256>(pd, w, nblk, reg, dir, st);
-  else launch_iflux_bs<128>(pd, w, nblk, reg, dir, st);
+  if (pers) {
+    if (bs == 64) launch_iflux_bs<64, true>(pd, w, nblk, reg, dir, st);
+    else if (bs == 256) launch_iflux_bs<256, true>(pd, w, nblk, reg, dir, st);
+    else launch_iflux_bs<128, true>(pd, w, nblk, reg, dir, st);
+  } else if (bs == 64) {
+    launch_iflux_bs<64, false>(pd, w, nblk, reg, dir, st);
+  } else if (bs == 256) {
+    launch_iflux_bs<256, false>(pd, w, nblk, reg, dir, st);
+  } else {
+    launch_iflux_bs<128, false>(pd, w, nblk, reg, dir, st);
+  }
 }
 
 // Frozen ghosts (bc 2): the ghost zones of every register hold the ghost values
@@ -547,28 +597,50 @@ void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, cons
 namespace gk {
 
 // ---------------------------------------------------------------------------
-// FP64 FMA throughput probe: every thread runs kDfmaChains independent FMA
-// recurrences a <- a m + b, so the FP64 pipe, not the latency of one chain,
-// limits the rate.  The sum is stored only if it equals an impossible value,
-// which keeps the compiler from dropping the work without any memory traffic.
-constexpr int kDfmaChains = 8;
+// FP64 FMA throughput probe: every thread runs CH independent FMA
+// recurrences a <- a m + b (m, b per chain, in registers), unrolled four
+// times, so the FP64 pipe, not the latency of one chain or the loop
+// arithmetic, limits the rate.  The sum is stored only if it equals an
+// impossible value, which keeps the compiler from dropping the work without
+// any memory traffic.
+// ADD: the chains are additions a <- a + b instead (the FP64 add rate).
+template <int CH, bool ADD>
 __global__ void __launch_bounds__(256) k_dfma_probe(long long iters, double* __restrict__ sink) {
-  double a[kDfmaChains];
-  const double m = 0.9999999999, b = 1e-12 * (1 + threadIdx.x);
+  double a[CH], m[CH], b[CH];
 #pragma unroll
-  for (int c = 0; c < kDfmaChains; ++c) a[c] = 1.0 + c * 1e-3 + threadIdx.x * 1e-9;
-  for (long long it = 0; it < iters; ++it)
+  for (int c = 0; c < CH; ++c) {
+    a[c] = 1.0 + c * 1e-3 + threadIdx.x * 1e-9;
+    m[c] = 0.9999999999 - c * 1e-13;
+    b[c] = 1e-12 * (1 + threadIdx.x + c);
+  }
+  for (long long it = 0; it < iters; it += 4)
 #pragma unroll
-    for (int c = 0; c < kDfmaChains; ++c) a[c] = fma(a[c], m, b);
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < CH; ++c) a[c] = ADD ? a[c] + b[c] : fma(a[c], m[c], b[c]);
   double s = 0.0;
 #pragma unroll
-  for (int c = 0; c < kDfmaChains; ++c) s += a[c];
+  for (int c = 0; c < CH; ++c) s += a[c];
   if (s == -1.0) sink[blockIdx.x] = s;
 }
 
-long long launch_dfma_probe(int blocks, long long iters, double* sink, cudaStream_t st) {
-  k_dfma_probe<<<blocks, 256, 0, st>>>(iters, sink);
-  return (long long)blocks * 256 * kDfmaChains * iters;
+long long launch_dfma_probe(int blocks, int chains, long long iters, double* sink, cudaStream_t st, bool add) {
+  iters = (iters + 3) / 4 * 4;
+  if (add) {
+    if (chains == 16)
+      k_dfma_probe<16, true><<<blocks, 256, 0, st>>>(iters, sink);
+    else if (chains == 4)
+      k_dfma_probe<4, true><<<blocks, 256, 0, st>>>(iters, sink);
+    else
+      k_dfma_probe<8, true><<<blocks, 256, 0, st>>>(iters, sink);
+  } else if (chains == 16) {
+    k_dfma_probe<16, false><<<blocks, 256, 0, st>>>(iters, sink);
+  } else if (chains == 4) {
+    k_dfma_probe<4, false><<<blocks, 256, 0, st>>>(iters, sink);
+  } else {
+    k_dfma_probe<8, false><<<blocks, 256, 0, st>>>(iters, sink);
+  }
+  return (long long)blocks * 256 * (chains == 16 ? 16 : (chains == 4 ? 4 : 8)) * iters;
 }
 
 }  // namespace gk

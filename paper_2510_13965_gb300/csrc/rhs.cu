@@ -12,16 +12,27 @@ namespace gk {
 
 constexpr double PI = 3.14159265358979323846;
 
-template <int MODE, int BS>  // MODE 0: write L(U) to rhs[patch]; 1: fused RK4 stage combination
+// One block per work item.  TILED: the items may be tile-shaped (see
+// work_point); otherwise every item is a linear chunk of the interior, whose
+// decode needs fewer registers (the tile decode adds ~0.1 KB to the spill
+// frame at 255 registers).  A loop over items (a persistent pool of blocks)
+// is not offered: it raised the spill frame from 0.9 to 1.3 KB.
+template <int MODE, int BS, bool TILED>  // MODE 0: write L(U) to rhs[patch]; 1: fused RK stage combination
 __global__ void __launch_bounds__(BS) k_rhs(const PatchDev* __restrict__ pd, const Work* __restrict__ w, int reg,
                                                  int stage, double dt, grmhd_params P, double* const* rhs_out) {
+  constexpr int LB = BS == 64 ? 6 : (BS == 128 ? 7 : 8);
+  {
   Work wk = w[blockIdx.x];
   const PatchDev& PD = pd[wk.patch];
   const Geo G = PD.G;
-  long long q = (long long)wk.block * blockDim.x + threadIdx.x;
-  if (q >= dom_count(DOM_INT, G)) return;
   int pi, pj, pk;
-  dom_decode(DOM_INT, G, q, pi, pj, pk);
+  if constexpr (TILED) {
+    if (!work_point(DOM_INT, G, wk.block, threadIdx.x, LB, pi, pj, pk)) return;
+  } else {
+    const long long q = (long long)wk.block * blockDim.x + threadIdx.x;
+    if (q >= dom_count(DOM_INT, G)) return;
+    dom_decode(DOM_INT, G, q, pi, pj, pk);
+  }
   const long long o = at(G, pi, pj, pk), sf = G.sf;
   const long long st[3] = {1, G.sy, G.sz};
   const double* U = PD.U[reg] + o;
@@ -447,23 +458,32 @@ __global__ void __launch_bounds__(BS) k_rhs(const PatchDev* __restrict__ pd, con
     }
   }
 #undef FP
+  }
 }
 
-template <int BS>
+template <int BS, bool TILED>
 static void launch_rhs_bs(const PatchDev* pd, const Work* w, int nblk, int reg, int mode, int stage, double dt,
                           const grmhd_params& P, double* const* rhs_dev, cudaStream_t st) {
   if (mode == 0)
-    k_rhs<0, BS><<<nblk, BS, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
+    k_rhs<0, BS, TILED><<<nblk, BS, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
   else
-    k_rhs<1, BS><<<nblk, BS, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
+    k_rhs<1, BS, TILED><<<nblk, BS, 0, st>>>(pd, w, reg, stage, dt, P, rhs_dev);
 }
 
 void launch_rhs(const PatchDev* pd, const Work* w, int nblk, int reg, int mode, int stage, double dt,
-                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs) {
+                const grmhd_params& P, double* const* rhs_dev, cudaStream_t st, int bs, bool tiled) {
   if (nblk <= 0) return;
-  if (bs == 64) launch_rhs_bs<64>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
-  else if (bs == 256) launch_rhs_bs<256>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
-  else launch_rhs_bs<128>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  if (tiled) {
+    if (bs == 64) launch_rhs_bs<64, true>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+    else if (bs == 256) launch_rhs_bs<256, true>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+    else launch_rhs_bs<128, true>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  } else if (bs == 64) {
+    launch_rhs_bs<64, false>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  } else if (bs == 256) {
+    launch_rhs_bs<256, false>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  } else {
+    launch_rhs_bs<128, false>(pd, w, nblk, reg, mode, stage, dt, P, rhs_dev, st);
+  }
 }
 
 }  // namespace gk

@@ -166,6 +166,51 @@ def test_per_patch_launches_equal_batched_launches_bitwise():
             assert torch.equal(a.prim[q], b.prim[q]), (seeded, q)
 
 
+@pytest.mark.parametrize("layout", ["hierarchy", "uneven"])
+def test_every_schedule_gives_the_same_result_bitwise(layout):
+    """Tile shapes per patch and kernel kind, persistent pools of blocks, and
+    the autotuner's own choice compute every point with the same arithmetic:
+    two RK4 steps agree bit for bit with the default schedule (linear chunks,
+    one block per work item).  Layouts: the five-patch hierarchy (ragged
+    tiles at every patch edge) and 12 uneven frozen-ghost patches of the
+    batched configuration's edge set."""
+    if layout == "hierarchy":
+        specs, ids = _tov_hierarchy()
+        P = synth.ideal_params(bc=3)
+    else:
+        specs = synth.batched_specs(npatch=12, seed=5)
+        _, norm = synth.config0_id(n=(32, 32, 32), seed=0, return_norm=True)
+        ids = [synth.batched_id(s_, seed=0, norm=norm) for s_ in specs]
+        P = synth.ideal_params(bc=2)
+    rng = np.random.default_rng(9)
+    dt = 0.25 * min(s_["dx"] for s_ in specs)
+    runs = []
+    for variant in ("default", "random", "tuned"):
+        pt = g.Patches(P, specs)
+        for q, ID in enumerate(ids):
+            pt.init_state(q, torch.as_tensor(ID, device="cuda"))
+        pt.synchronize()
+        if variant == "random":
+            shapes = [tuple(int(v) for v in rng.integers(0, 5, 3)) for _ in specs]
+            pt.set_schedule(shapes, (1, 1, 0))
+            assert pt.get_schedule() == (shapes, (1, 1, 0))
+        elif variant == "tuned":
+            U0 = [u[0].clone() for u in pt.U]
+            pt.autotune(dt, reps=1)
+            for u, u0 in zip(pt.U, U0):
+                u[0].copy_(u0)
+        pt.step(dt)
+        pt.capture_graph(1, dt)
+        pt.graph_launch()
+        pt.synchronize()
+        assert pt.sync_status() == 0
+        runs.append(pt)
+    for pt in runs[1:]:
+        for q in range(len(specs)):
+            assert torch.equal(runs[0].U[q][0], pt.U[q][0]), q
+            assert torch.equal(runs[0].prim[q], pt.prim[q]), q
+
+
 def test_uncovered_fine_ghosts_are_rejected():
     specs = synth.small_hierarchy()
     specs[1] = synth.hierarchy.spec((12, 12, 12), 1, (1, 12, 12), 1.0, (-12.0,) * 3)
