@@ -125,6 +125,15 @@ DI double mm4(double a, double b, double c, double d) {
   if (ineg(a) && ineg(b) && ineg(c) && ineg(d)) return imax(imax(a, b), imax(c, d));
   return 0.0;
 }
+// Order of x against y as the sign of the rounded difference x - y (which
+// has the sign of the exact one, and is zero exactly when x == y, +0 == -0),
+// taken on the integer pipe: -1, 0 or +1.
+DI int iorder(double x, double y) {
+  const long long kx = __double_as_longlong(x), ky = __double_as_longlong(y);
+  if (kx == ky || ((kx | ky) << 1) == 0) return 0;
+  return okey(x) > okey(y) ? 1 : -1;
+}
+
 // Interface value between c and d from a..e (= F_{i-2} .. F_{i+2}).
 // The 5th-order value is formed from differences to c,
 //   f = c + (2 (a - c) - 13 (b - c) + 27 (d - c) - 3 (e - c)) / 60,
@@ -135,12 +144,12 @@ DI double mp5(double a, double b, double c, double d, double e) {
   double dp = d - c, dm = c - b;
   double t = fma(-3.0, e - c, fma(27.0, dp, fma(2.0, a - c, 13.0 * dm)));
   double f = fma(t, 1.0 / 60.0, c);
-  double s1 = f - c;
-  if ((__double_as_longlong(s1) << 1) == 0) return f;
+  // (f - c)(f - f_MP) < 0 as a test of the two differences' signs, taken by
+  // integer comparisons (no FP64 subtraction, product or compare).
+  const int s1 = iorder(f, c);
+  if (s1 == 0) return f;
   double fmp = c + mm2(dp, al * dm);
-  // (f - c)(f - f_MP) < 0 as a sign test (no product, no FP64 compare).
-  double s2 = f - fmp;
-  if ((ipos(s1) && ineg(s2)) || (ineg(s1) && ipos(s2))) return f;
+  if (s1 * iorder(f, fmp) < 0) return f;
   double d_m = dm - (b - a), d_0 = dp - dm, d_p = (e - d) - dp;
   double m4p = mm4(fma(4.0, d_0, -d_p), fma(4.0, d_p, -d_0), d_0, d_p);
   double m4m = mm4(fma(4.0, d_0, -d_m), fma(4.0, d_m, -d_0), d_0, d_m);

@@ -392,7 +392,9 @@ void launch_c2p(const PatchDev* pd, const Work* w, int nblk, int reg, const grmh
 // ---------------------------------------------------------------------------
 // Interface fluxes along direction D: lambda = max over points i-2 .. i+3,
 // g^{+-} = F +- lambda U, F^L = MP5(g^+_{i-2..i+2}), F^R = MP5(g^-_{i+3..i-1}),
-// Fhat = (F^L + F^R) / 2 (MP5 commutes with the positive factor 1/2).
+// stored as 2 Fhat = F^L + F^R (MP5 commutes with the positive factor 1/2;
+// the right-hand side folds the 1/2 into 1/dx, a power-of-two scaling that
+// changes no rounding).
 // Interface fluxes of one work item along direction D (see k_iflux).
 template <int D, int LB>
 DI void iflux_item(const PatchDev* __restrict__ pd, const Work wk, int reg) {
@@ -421,7 +423,7 @@ DI void iflux_item(const PatchDev* __restrict__ pd, const Work wk, int reg) {
     }
     double FL = mp5(gp[0], gp[1], gp[2], gp[3], gp[4]);
     double FR = mp5(gm[5], gm[4], gm[3], gm[2], gm[1]);
-    Fh[f * sf] = 0.5 * (FL + FR);
+    Fh[f * sf] = FL + FR;
   }
 }
 

@@ -643,10 +643,16 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
       for (int m = 0; m < 6; ++m) gt[m] = U[(GT + m) * sf + o];
       double chi = U[CHI * sf + o];
       double det = det3(gt);
-      double ichi = 1.0 / chi;
-      double isg = 1.0 / (sqrt(det) * ichi * sqrt(ichi));
-      double D = U[DD * sf + o] * isg;
-      if (D >= rho_min && isfinite(D)) {
+      // D = Dbar / sqrt(gamma) >= rho_min, with sqrt(gamma) = sqrt(det gt)
+      // chi^(-3/2), tested as Dbar^2 chi^3 >= rho_min^2 det gt (all factors
+      // positive): no square root or division for the atmosphere points,
+      // which are most points.  A decision rounded the other way at the
+      // threshold only changes whether the point gets a seed.
+      const double Db = U[DD * sf + o];
+      if (Db > 0.0 && Db * Db * (chi * chi * chi) >= (rho_min * rho_min) * det && isfinite(Db)) {
+        double ichi = 1.0 / chi;
+        double isg = 1.0 / (sqrt(det) * ichi * sqrt(ichi));
+        double D = Db * isg;
         double gtu[6];
         inv3(gt, 1.0 / det, gtu);
         double Sd[3], Bu[3];
