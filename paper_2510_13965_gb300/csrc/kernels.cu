@@ -406,9 +406,10 @@ DI void iflux_item(const PatchDev* __restrict__ pd, const Work wk, int reg) {
   const long long o = at(G, i, j, k), sf = G.sf;
   const long long s = D == 0 ? 1 : (D == 1 ? G.sy : G.sz);
   const double* lam = PD.lam + (long long)D * sf + o;
+  // The maximum on the integer pipe (imax: the order of the doubles' keys).
   double L = ld(lam - 2 * s);
 #pragma unroll
-  for (int m = -1; m <= 3; ++m) L = fmax(L, ld(lam + m * s));
+  for (int m = -1; m <= 3; ++m) L = imax(L, ld(lam + m * s));
   const double* Fp = PD.Fp + (long long)D * 10 * sf + o;
   const double* Uc = PD.U[reg] + (long long)DD * sf + o;
   double* Fh = PD.Fh + (long long)D * 10 * sf + o;

@@ -2,13 +2,11 @@
 // con2prim.
 //
 // Network 8 -> 64 -> 64 -> 64 -> 3 (ReLU).  One CTA of 128 threads (4 warps)
-// owns a tile of 128 samples.  Weights are converted to BF16 in shared memory;
-// activations stay in shared memory as BF16.  Every product is
-// mma.sync.m16n8k16 (BF16 operands, FP32 accumulate):
-//   forward        H_l = relu(H_{l-1} W_l + b_l)      warp w: sample rows 32w..32w+31
-//   backward       dZ_l = [H_l > 0] (dZ_{l+1} W_{l+1}^T)    same rows
-//   weight grads   dW_l = H_{l-1}^T dZ_l             warp w: 16 rows of dW_l, K = 128 samples
-// The tile's partial gradient goes to its own slot of a partial-gradient
+// owns a tile of 128 samples.  Every product of inference and training is a
+// tcgen05.mma with M = 128 samples: BF16 operands in shared memory, FP32
+// accumulator in tensor memory, read back with tcgen05.ld (namespace tc:
+// inference; namespace tt: forward, backward and weight gradients).  A
+// training tile's partial gradient goes to its own slot of a partial-gradient
 // array; the Adam kernel sums the slots in a fixed order, so training is
 // deterministic.
 #include <cuda_bf16.h>
@@ -27,237 +25,14 @@ static_assert(NPAR == GRMHD_SEEDER_NPARAMS, "parameter count");
 constexpr int NNORM = 2 * NI + 2 * NO;
 static_assert(NNORM == GRMHD_SEEDER_NNORM, "normalisation count");
 constexpr int TM = 128;    // samples per CTA
-constexpr int LDH = 72;    // row stride (BF16 elements) of 64-wide tiles: conflict-free fragment loads
-constexpr int LDX = 24;    // row stride of 16-wide tiles
 constexpr int MAX_BATCH = 65536;
 constexpr int MAX_TILES = MAX_BATCH / TM;
 
 typedef unsigned short u16;
 
-// Shared-memory layout (BF16 tiles as raw 16-bit words).
-constexpr int S_W1 = 0;                      // [16][LDH]   rows 8..15 zero
-constexpr int S_W2 = S_W1 + 16 * LDH;        // [64][LDH]
-constexpr int S_W3 = S_W2 + 64 * LDH;        // [64][LDH]
-constexpr int S_W4 = S_W3 + 64 * LDH;        // [64][LDX]   cols 3.. zero
-constexpr int S_X = S_W4 + 64 * LDX;         // [128][LDX]  cols 8.. zero
-constexpr int S_H1 = S_X + TM * LDX;         // [128][LDH]
-constexpr int S_H2 = S_H1 + TM * LDH;
-constexpr int S_H3 = S_H2 + TM * LDH;        // training only (inference ping-pongs H1 / H2)
-constexpr int S_DZ = S_H3 + TM * LDH;        // training only
-constexpr int S_DY = S_DZ + TM * LDH;        // [128][LDX]  training only
-constexpr int S_END_INFER = S_H3;
-constexpr int S_END_TRAIN = S_DY + TM * LDX;
-// FP32 area after the BF16 words: biases (3 x 64 + 4), normalisation (22),
-// outputs Y[128][4], per-warp bias-gradient partials [4][64 * 3 + 4], loss partials [4].
-constexpr int F_B = 0;
-constexpr int F_NORM = F_B + 3 * NH + 4;
-constexpr int F_Y = F_NORM + NNORM + 2;
-constexpr int F_GB = F_Y + TM * 4;
-constexpr int F_LOSS = F_GB + 4 * (3 * NH + 4);
-constexpr int F_END = F_LOSS + 4 * 2;  // doubles stored as float pairs
-constexpr size_t smem_bytes(bool train) {
-  return (size_t)(train ? S_END_TRAIN : S_END_INFER) * 2 + (size_t)F_END * 4;
-}
-
 DI u16 bf(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
-DI bool pos(u16 h) { return h != 0 && !(h & 0x8000u); }
 DI uint32_t pk(u16 lo, u16 hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 DI uint32_t pkf(float lo, float hi) { return pk(bf(lo), bf(hi)); }
-
-// A fragment of a 16x16 tile whose element (r, c) is p[r * sr + c * sc].
-DI void frag_a(const u16* p, int sr, int sc, int lane, uint32_t a[4]) {
-  int g = lane >> 2, t2 = (lane & 3) * 2;
-  a[0] = pk(p[g * sr + t2 * sc], p[g * sr + (t2 + 1) * sc]);
-  a[1] = pk(p[(g + 8) * sr + t2 * sc], p[(g + 8) * sr + (t2 + 1) * sc]);
-  a[2] = pk(p[g * sr + (t2 + 8) * sc], p[g * sr + (t2 + 9) * sc]);
-  a[3] = pk(p[(g + 8) * sr + (t2 + 8) * sc], p[(g + 8) * sr + (t2 + 9) * sc]);
-}
-// B fragment of a 16x8 (k x n) tile whose element (k, n) is p[k * sr + n * sc].
-DI void frag_b(const u16* p, int sr, int sc, int lane, uint32_t b[2]) {
-  int g = lane >> 2, t2 = (lane & 3) * 2;
-  b[0] = pk(p[t2 * sr + g * sc], p[(t2 + 1) * sr + g * sc]);
-  b[1] = pk(p[(t2 + 8) * sr + g * sc], p[(t2 + 9) * sr + g * sc]);
-}
-DI void mma(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-DI void st2(u16* p, float lo, float hi) { *reinterpret_cast<uint32_t*>(p) = pkf(lo, hi); }
-
-// Hidden layer on the warp's 32 rows: out = bf16(relu(in W + b)), W [K][64] at w (stride LDH).
-template <int KS>
-DI void fwd_hidden(const u16* in, int ldin, const u16* w, const float* b, u16* out, int row0, int lane) {
-  int g = lane >> 2, t2 = (lane & 3) * 2;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      acc[nt][0] = acc[nt][2] = b[nt * 8 + t2];
-      acc[nt][1] = acc[nt][3] = b[nt * 8 + t2 + 1];
-    }
-    const u16* a0 = in + (row0 + mt * 16) * ldin;
-#pragma unroll
-    for (int ks = 0; ks < KS; ++ks) {
-      uint32_t a[4];
-      frag_a(a0 + ks * 16, ldin, 1, lane, a);
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        uint32_t bb[2];
-        frag_b(w + ks * 16 * LDH + nt * 8, LDH, 1, lane, bb);
-        mma(acc[nt], a, bb);
-      }
-    }
-    u16* o = out + (row0 + mt * 16) * LDH;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      st2(o + g * LDH + nt * 8 + t2, fmaxf(acc[nt][0], 0.f), fmaxf(acc[nt][1], 0.f));
-      st2(o + (g + 8) * LDH + nt * 8 + t2, fmaxf(acc[nt][2], 0.f), fmaxf(acc[nt][3], 0.f));
-    }
-  }
-}
-
-// Output layer on the warp's 32 rows: Y[s][j] = in[s] . W4[:, j] + b4[j], j < 3.
-DI void fwd_out(const u16* in, const u16* w4, const float* b4, float* Y, int row0, int lane) {
-  int g = lane >> 2, t2 = (lane & 3) * 2;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    float acc[4];
-    acc[0] = acc[2] = t2 < NO ? b4[t2] : 0.f;
-    acc[1] = acc[3] = t2 + 1 < NO ? b4[t2 + 1] : 0.f;
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      uint32_t a[4], bb[2];
-      frag_a(in + (row0 + mt * 16) * LDH + ks * 16, LDH, 1, lane, a);
-      frag_b(w4 + ks * 16 * LDX, LDX, 1, lane, bb);
-      mma(acc, a, bb);
-    }
-    int r = row0 + mt * 16 + g;
-    if (t2 < 4) {
-      Y[r * 4 + t2] = acc[0];
-      Y[r * 4 + t2 + 1] = acc[1];
-      Y[(r + 8) * 4 + t2] = acc[2];
-      Y[(r + 8) * 4 + t2 + 1] = acc[3];
-    }
-  }
-}
-
-// Activation gradient on the warp's 32 rows:
-//   dz[s][k] = [h[s][k] > 0] sum_j d[s][j] W[k][j]
-// d: [128][K] at (din, ldd); W stored as w[k * ldw + j] (k < 64, j < K);
-// the bf16(dz) goes to out (stride LDH), the FP32 column sums of dz to gb[64].
-template <int KS>
-DI void bwd_act(const u16* din, int ldd, const u16* w, int ldw, const u16* h, u16* out, float* gb, int row0,
-                int lane) {
-  int g = lane >> 2, t2 = (lane & 3) * 2;
-  float cs[8][2];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) cs[nt][0] = cs[nt][1] = 0.f;
-#pragma unroll
-  for (int mt = 0; mt < 2; ++mt) {
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < KS; ++ks) {
-      uint32_t a[4];
-      frag_a(din + (row0 + mt * 16) * ldd + ks * 16, ldd, 1, lane, a);
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        uint32_t bb[2];
-        frag_b(w + nt * 8 * ldw + ks * 16, 1, ldw, lane, bb);  // (k = j, n = unit) -> w[unit][j]
-        mma(acc[nt], a, bb);
-      }
-    }
-    int r0 = row0 + mt * 16 + g, r1 = r0 + 8;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      int c = nt * 8 + t2;
-      float v0 = pos(h[r0 * LDH + c]) ? acc[nt][0] : 0.f;
-      float v1 = pos(h[r0 * LDH + c + 1]) ? acc[nt][1] : 0.f;
-      float v2 = pos(h[r1 * LDH + c]) ? acc[nt][2] : 0.f;
-      float v3 = pos(h[r1 * LDH + c + 1]) ? acc[nt][3] : 0.f;
-      st2(out + r0 * LDH + c, v0, v1);
-      st2(out + r1 * LDH + c, v2, v3);
-      cs[nt][0] += v0 + v2;
-      cs[nt][1] += v1 + v3;
-    }
-  }
-  // Column sums over the warp's rows: reduce over the 8 row groups.
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      float v = cs[nt][e];
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (g == 0) gb[nt * 8 + t2 + e] = v;
-    }
-}
-
-// Weight gradient rows k0..k0+15 of dW = A^T D over the 128 samples:
-// A: [128][*] at (a, lda) (columns k), D: [128][*] at (d, ldd) (columns j).
-// Writes dW[k][j] = out[k * nj + j] for k < kmax, j < nj, columns nt0..nt0+NT-1 (n8 tiles).
-template <int NT>
-DI void bwd_weight(const u16* a, int lda, const u16* d, int ldd, float* out, int nj, int k0, int kmax, int nt0,
-                   int lane) {
-  int g = lane >> 2, t2 = (lane & 3) * 2;
-  float acc[NT][4];
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-#pragma unroll
-  for (int ks = 0; ks < TM / 16; ++ks) {
-    uint32_t af[4];
-    frag_a(a + ks * 16 * lda + k0, 1, lda, lane, af);  // (r = k, c = sample)
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      uint32_t bb[2];
-      frag_b(d + ks * 16 * ldd + (nt0 + nt) * 8, ldd, 1, lane, bb);
-      mma(acc[nt], af, bb);
-    }
-  }
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) {
-    int j = (nt0 + nt) * 8 + t2;
-    int k = k0 + g;
-    if (k < kmax) {
-      if (j < nj) out[k * nj + j] = acc[nt][0];
-      if (j + 1 < nj) out[k * nj + j + 1] = acc[nt][1];
-    }
-    if (k + 8 < kmax) {
-      if (j < nj) out[(k + 8) * nj + j] = acc[nt][2];
-      if (j + 1 < nj) out[(k + 8) * nj + j + 1] = acc[nt][3];
-    }
-  }
-}
-
-// Loads the weights (BF16) and biases / normalisation (FP32) into shared memory.
-DI void load_params(const float* __restrict__ w, const float* __restrict__ norm, u16* S, float* F) {
-  for (int q = threadIdx.x; q < 16 * LDH; q += blockDim.x) {
-    int k = q / LDH, j = q % LDH;
-    S[S_W1 + q] = (k < NI && j < NH) ? bf(w[OW1 + k * NH + j]) : 0;
-  }
-  for (int q = threadIdx.x; q < 64 * LDH; q += blockDim.x) {
-    int k = q / LDH, j = q % LDH;
-    S[S_W2 + q] = j < NH ? bf(w[OW2 + k * NH + j]) : 0;
-    S[S_W3 + q] = j < NH ? bf(w[OW3 + k * NH + j]) : 0;
-  }
-  for (int q = threadIdx.x; q < 64 * LDX; q += blockDim.x) {
-    int k = q / LDX, j = q % LDX;
-    S[S_W4 + q] = j < NO ? bf(w[OW4 + k * NO + j]) : 0;
-  }
-  for (int q = threadIdx.x; q < NH; q += blockDim.x) {
-    F[F_B + q] = w[OB1 + q];
-    F[F_B + NH + q] = w[OB2 + q];
-    F[F_B + 2 * NH + q] = w[OB3 + q];
-  }
-  if (threadIdx.x < 4) F[F_B + 3 * NH + threadIdx.x] = threadIdx.x < NO ? w[OB4 + threadIdx.x] : 0.f;
-  if (threadIdx.x < NNORM) F[F_NORM + threadIdx.x] = norm[threadIdx.x];
-}
 
 // Features of one conserved state from its undensitized D, DYe, tau and the
 // invariants S2 = S_i S^i, B2 = B_i B^i, SB = S_i B^i (Kastaun's scalars: the
@@ -295,6 +70,76 @@ DI void features(const double* c, float f[NI]) {
               c[3] * c[6] + c[4] * c[7] + c[5] * c[8], f, &sr, &Q);
 }
 
+// ---- FP32 feature path of the inference kernels ------------------------------
+// At inference the features are rounded to BF16 (relative 2^-9) and the seeds
+// are polished by the FP64 root finder, so FP32 carries enough of them: the
+// inference kernels read the FP64 state, narrow it to FP32 on the integer
+// pipe and form features and seeds in FP32, leaving the narrow FP64 pipe to
+// the con2prim and flux kernels.  (1 + q)^2 - r^2 loses about 2 W^2 ulps to
+// cancellation, below the BF16 rounding for W < 100.
+
+// FP64 -> FP32 with the mantissa truncated (relative error below 2^-23);
+// magnitudes below FP32's normal range give a signed zero, above it a signed
+// infinity; NaN stays NaN.
+DI float narrow(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sgn = hi & 0x80000000u, mh = hi & 0xfffffu, ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex - 1023 + 127;
+  if (e >= 255) return __uint_as_float(sgn | 0x7f800000u | ((ex == 0x7ffu && (mh | lo)) ? 0x400000u : 0u));
+  if (e <= 0) return __uint_as_float(sgn);
+  return __uint_as_float(sgn | ((unsigned)e << 23) | (mh << 3) | (lo >> 29));
+}
+// FP32 -> FP64, exact for normal numbers, zeros, infinities and NaN (FP32
+// subnormals give a signed zero).
+DI double widen(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned sgn = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned hi;
+  if (e == 0xffu) hi = sgn | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  else if (e == 0u) hi = sgn;
+  else hi = sgn | ((e + (1023u - 127u)) << 20) | (m >> 3);
+  const unsigned lo = e == 0u ? 0u : (m & 7u) << 29;
+  return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+
+DI float det3f(const float g[6]) {
+  return g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) + g[2] * (g[1] * g[4] - g[3] * g[2]);
+}
+DI void inv3f(const float g[6], float idet, float u[6]) {
+  u[0] = (g[3] * g[5] - g[4] * g[4]) * idet;
+  u[1] = (g[2] * g[4] - g[1] * g[5]) * idet;
+  u[2] = (g[1] * g[4] - g[2] * g[3]) * idet;
+  u[3] = (g[0] * g[5] - g[2] * g[2]) * idet;
+  u[4] = (g[1] * g[2] - g[0] * g[4]) * idet;
+  u[5] = (g[0] * g[3] - g[1] * g[1]) * idet;
+}
+DI void lower3f(const float g[6], const float v[3], float o[3]) {
+  o[0] = g[0] * v[0] + g[1] * v[1] + g[2] * v[2];
+  o[1] = g[1] * v[0] + g[3] * v[1] + g[4] * v[2];
+  o[2] = g[2] * v[0] + g[4] * v[1] + g[5] * v[2];
+}
+
+// The features of features_sc in FP32 (the same formulas); sr = sqrt(1 + r^2)
+// and Q = max(1 + q, 1e-30) for the seed map.
+DI void features_f32(float D, float DYe, float tau, float S2, float B2, float SB, float f[NI], float* sr, float* Qo) {
+  const float iD = 1.0f / D;
+  const float q = tau * iD, s = sqrtf(S2), r = s * iD, b2 = B2 * iD;
+  const float Q = fmaxf(1.0f + q, 1e-30f);
+  const float X = fmaxf((1.0f + q - r) * (1.0f + q + r), 1e-30f);
+  const float den = s * sqrtf(B2);
+  f[0] = log10f(D);
+  f[1] = DYe * iD;
+  f[2] = logf(Q);
+  f[3] = logf(X);
+  f[4] = r / Q;
+  f[5] = log10f(fmaxf(b2, 1e-30f));
+  f[6] = den > 0.f ? SB / den : 0.f;
+  f[7] = b2 / Q;
+  *sr = sqrtf(fmaf(r, r, 1.f));
+  *Qo = Q;
+}
+
 // (sqrt(1 + r^2), max(1 + q, 1e-30)) of a flat-metric state: the scalings of
 // the mu_+ and mu targets.
 DI void target_scales(const double* c, double* sr, double* Q) {
@@ -302,26 +147,6 @@ DI void target_scales(const double* c, double* sr, double* Q) {
   double r = sqrt(c[3] * c[3] + c[4] * c[4] + c[5] * c[5]) / D;
   *sr = sqrt(1.0 + r * r);
   *Q = fmax(1.0 + c[2] / D, 1e-30);
-}
-
-// Writes the standardized, BF16-rounded input row of sample row s.
-DI void put_x(u16* X, int s, const float f[NI], const float* norm, bool valid) {
-#pragma unroll
-  for (int k = 0; k < NI; ++k) X[s * LDX + k] = valid ? bf((f[k] - norm[k]) / norm[NI + k]) : 0;
-#pragma unroll
-  for (int k = NI; k < 16; ++k) X[s * LDX + k] = 0;
-}
-
-// Forward through the three hidden layers and the output (warp-local rows).
-DI void forward_tile(u16* S, float* F, u16* h3_out, int row0, int lane) {
-  fwd_hidden<1>(S + S_X, LDX, S + S_W1, F + F_B, S + S_H1, row0, lane);
-  __syncwarp();
-  fwd_hidden<4>(S + S_H1, LDH, S + S_W2, F + F_B + NH, S + S_H2, row0, lane);
-  __syncwarp();
-  fwd_hidden<4>(S + S_H2, LDH, S + S_W3, F + F_B + 2 * NH, h3_out, row0, lane);
-  __syncwarp();
-  fwd_out(h3_out, S + S_W4, F + F_B + 3 * NH, F + F_Y, row0, lane);
-  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -544,6 +369,398 @@ DI void end(uint32_t tmem) {
 }
 }  // namespace tc
 
+// ---------------------------------------------------------------------------
+// Training on the tcgen05 tensor cores.  One CTA of 128 threads owns a tile
+// of 128 samples; every product is a tcgen05.mma with M = 128, BF16 operands
+// in shared memory (K-major no-swizzle core layout, as for inference) and an
+// FP32 accumulator in tensor memory:
+//   forward         H_l = relu(H_{l-1} W_l + b_l)        A = H_{l-1} [128 x K], B = W_l^T [N x K]
+//   backward data   dZ_l = [H_l > 0] (dZ_{l+1} W_{l+1}^T)  A = dZ_{l+1}, B = W_{l+1} [in x out]
+//   weight grads    two stacked products over K = 128 samples:
+//     [dZ3^T; dZ2^T] [H2^T; H1^T]^T  -> dW3^T and dW2^T on its diagonal blocks,
+//     [dZ1^T; dY^T]  [X^T; H3^T]^T    -> dW1^T and dW4^T on its diagonal blocks,
+//   so no operand is padded to M = 128 with zeros beyond dY's 3 rows.
+// The epilogues write each activation and gradient twice: as the next
+// product's A operand (row = sample) and transposed (row = unit) for the
+// weight-gradient products; the ReLU masks are kept as bits.  Bias gradients
+// are exact FP32 column sums of the unrounded dz (warp reduce-scatter, then
+// a fixed-order sum over the warps), as in the oracle.
+namespace tt {
+using tc::core_off;
+using tc::sdesc;
+using tc::su32;
+constexpr uint32_t COLS = 256;
+constexpr int WF1 = 0;              // B fwd 1: 64 out x 16 in (inputs 8..15 zero)
+constexpr int WF2 = WF1 + 2048;     // B fwd 2: 64 x 64
+constexpr int WF3 = WF2 + 8192;     // B fwd 3
+constexpr int WF4 = WF3 + 8192;     // B fwd 4: 16 out (3 used) x 64 in
+constexpr int WB2 = WF4 + 2048;     // B bwd 2: 64 in x 64 out
+constexpr int WB3 = WB2 + 8192;     // B bwd 3
+constexpr int WB4 = WB3 + 8192;     // B bwd 4: 64 in x 16 out (3 used)
+constexpr int XA = WB4 + 2048;      // A fwd 1: 128 x 16
+constexpr int HA = XA + 4096;       // A fwd 2 / 4: 128 x 64 (H1, then H3)
+constexpr int HB = HA + 16384;      // A fwd 3: H2
+constexpr int DYA = HB + 16384;     // A bwd 4: 128 x 16 (3 used)
+constexpr int DZA = DYA + 4096;     // A bwd 3 / 2: 128 x 64 (dZ3, then dZ2)
+constexpr int A1 = DZA + 16384;     // 128 x K 128: rows 0-63 dZ3^T, 64-127 dZ2^T
+constexpr int B1 = A1 + 32768;      // 128 x K 128: rows 0-63 H2^T, 64-127 H1^T
+constexpr int A2 = B1 + 32768;      // 128 x K 128: rows 0-63 dZ1^T, 64-66 dY^T, rest 0
+constexpr int B2 = A2 + 32768;      // 80 x K 128: rows 0-7 X^T, 8-15 0, 16-79 H3^T
+constexpr int MASK = B2 + 20480;    // ReLU masks: uint64 [3][128]
+constexpr int FL = MASK + 3 * 128 * 8;
+// floats at FL: biases b1 b2 b3 (3 x 64) + b4 (4); normalisation (22 + 2);
+// bias-gradient partials [4 warps][196]; loss partials (4 doubles).
+constexpr int TF_B = 0, TF_NORM = 3 * NH + 4, TF_GB = TF_NORM + NNORM + 2, TF_LOSS = TF_GB + 4 * (3 * NH + 4);
+constexpr int NFL = TF_LOSS + 8;
+constexpr int MBAR = FL + NFL * 4;
+constexpr int TADDR = MBAR + 8;
+constexpr int SMEM = TADDR + 8;
+static_assert(MBAR % 8 == 0, "mbarrier alignment");
+static_assert(SMEM <= 227 * 1024, "shared memory");
+constexpr uint32_t idesc_n(int n) { return tc::IDESC_BASE | ((uint32_t)(n >> 3) << 17); }
+
+DI void st16(unsigned char* sm, int off, float v) { *reinterpret_cast<u16*>(sm + off) = bf(v); }
+// Row r of a 128-row K-major operand, K = 0..63, as BF16, 16 bytes at a time.
+DI void put_row64(unsigned char* sm, int base, int r, const float* v) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    *reinterpret_cast<uint4*>(sm + base + core_off(r, 8 * c, 128)) =
+        make_uint4(pkf(v[8 * c], v[8 * c + 1]), pkf(v[8 * c + 2], v[8 * c + 3]), pkf(v[8 * c + 4], v[8 * c + 5]),
+                   pkf(v[8 * c + 6], v[8 * c + 7]));
+}
+// Element (row0 + k, s) of a K-major operand of `rows` rows (row0 a multiple
+// of 8, s the K index) sits at col_base(base, s, rows, row0) + col_off(k):
+// core_off split into its part fixed by the thread and its part fixed by k.
+DI int col_base(int base, int s, int rows, int row0) {
+  return base + (s >> 4) * (rows * 32) + row0 * 32 + ((s >> 3) & 1) * 128 + (s & 7) * 2;
+}
+DI int col_off(int k) { return (k >> 3) * 256 + (k & 7) * 16; }
+
+// Issues ksteps MMAs of K = 16 (A rows 128, B rows brows) into TMEM column col.
+DI void issue(unsigned char* sm, uint32_t tmem, int col, int a, int b, int brows, int ksteps, uint32_t idesc) {
+  for (int ks = 0; ks < ksteps; ++ks)
+    tc::mma(tmem + (uint32_t)col, sdesc(su32(sm + a + ks * 128 * 32)), sdesc(su32(sm + b + ks * brows * 32)), idesc,
+            ks > 0 ? 1u : 0u);
+}
+
+// Makes the threads' shared-memory writes visible to the tensor cores.
+DI void pre_issue() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+}
+
+// Commits the issued products, waits for them (bounded) and makes TMEM
+// readable; false in every thread on timeout (after a second bounded wait).
+DI bool finish(unsigned char* sm, uint32_t& phase) {
+  const uint32_t mbar = su32(sm + MBAR);
+  if (threadIdx.x == 0) tc::commit(mbar);
+  bool done = tc::wait(mbar, phase);
+  phase ^= 1u;
+  if (__syncthreads_or(!done)) {
+    tc::wait(mbar, phase ^ 1u);
+    return false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return true;
+}
+
+// Warp reduce-scatter of v[64] (column values of the warp's 32 rows): lane l
+// returns the sums over the warp of columns 2l and 2l + 1, in a fixed order.
+DI void reduce_scatter64(const float v[64], float out[2], int lane) {
+  float a[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const bool hi = lane & 16;
+    float keep = hi ? v[32 + i] : v[i], send = hi ? v[i] : v[32 + i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const bool hi = lane & 8;
+    float keep = hi ? a[16 + i] : a[i], send = hi ? a[i] : a[16 + i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 4;
+    float keep = hi ? a[8 + i] : a[i], send = hi ? a[i] : a[8 + i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 2;
+    float keep = hi ? a[4 + i] : a[i], send = hi ? a[i] : a[4 + i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 1;
+    float keep = hi ? a[2 + i] : a[i], send = hi ? a[i] : a[2 + i];
+    out[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
+}
+
+}  // namespace tt
+
+// Forward and backward over one tile of the batch [off, off + nb) on the
+// tcgen05 tensor cores; writes the tile's partial gradient (gpart[tile][NPAR])
+// and sum of squared errors (lpart[tile]).  off = (step[0] mod nbatch) * nb
+// when step is given, else 0.  A tensor-core wait that runs out sets bit 2 of
+// *err and the tile's outputs are left unwritten.
+__global__ void __launch_bounds__(TM) k_mlp_train_tc(long long n, const float* __restrict__ X,
+                                                     const float* __restrict__ T, int nb, long long nbatch,
+                                                     const unsigned long long* __restrict__ step,
+                                                     const float* __restrict__ w, const float* __restrict__ norm,
+                                                     float* __restrict__ gpart, double* __restrict__ lpart, float scale,
+                                                     int* __restrict__ err) {
+  using namespace tt;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sm = smem;
+  const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
+  float* F = reinterpret_cast<float*>(sm + FL);
+  uint64_t* mask = reinterpret_cast<uint64_t*>(sm + MASK);
+  // Weights in both orientations.  Every parameter is read once, coalesced
+  // (consecutive threads read consecutive floats), with all of a thread's
+  // loads in flight together; the padding of WF1, WF4, WB4 and the stacked
+  // A2 / B2 operands is zeroed first.
+  for (int q = s; q < 2048 / 16; q += TM) {
+    reinterpret_cast<uint4*>(sm + WF1)[q] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(sm + WF4)[q] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4*>(sm + WB4)[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int q = s; q < (32768 + 20480) / 16; q += TM)  // A2 and B2 (contiguous)
+    reinterpret_cast<uint4*>(sm + A2)[q] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  {
+    static_assert(NH * NH % TM == 0 && NI * NH % TM == 0 && NH * NO <= 2 * TM, "weight split over the threads");
+    float v2[NH * NH / TM], v3[NH * NH / TM], v1[NI * NH / TM], v4[2];
+#pragma unroll
+    for (int t = 0; t < NH * NH / TM; ++t) {
+      v2[t] = __ldg(w + OW2 + s + TM * t);
+      v3[t] = __ldg(w + OW3 + s + TM * t);
+    }
+#pragma unroll
+    for (int t = 0; t < NI * NH / TM; ++t) v1[t] = __ldg(w + OW1 + s + TM * t);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) v4[t] = s + TM * t < NH * NO ? __ldg(w + OW4 + s + TM * t) : 0.f;
+#pragma unroll
+    for (int t = 0; t < NH * NH / TM; ++t) {
+      const int e = s + TM * t, in = e >> 6, out = e & 63;  // W[in][out]
+      st16(sm, WF2 + core_off(out, in, 64), v2[t]);
+      st16(sm, WB2 + core_off(in, out, 64), v2[t]);
+      st16(sm, WF3 + core_off(out, in, 64), v3[t]);
+      st16(sm, WB3 + core_off(in, out, 64), v3[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < NI * NH / TM; ++t) {
+      const int e = s + TM * t;
+      st16(sm, WF1 + core_off(e & 63, e >> 6, 64), v1[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int e = s + TM * t, in = e / NO, out = e - in * NO;
+      if (e < NH * NO) {
+        st16(sm, WF4 + core_off(out, in, 16), v4[t]);
+        st16(sm, WB4 + core_off(in, out, 64), v4[t]);
+      }
+    }
+  }
+  for (int q = s; q < NH; q += TM) {
+    F[TF_B + q] = w[OB1 + q];
+    F[TF_B + NH + q] = w[OB2 + q];
+    F[TF_B + 2 * NH + q] = w[OB3 + q];
+  }
+  if (s < 4) F[TF_B + 3 * NH + s] = s < NO ? w[OB4 + s] : 0.f;
+  if (s < NNORM) F[TF_NORM + s] = norm[s];
+  if (s == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(sm + MBAR)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(sm + TADDR)), "r"(COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + TADDR);
+  const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
+  uint32_t phase = 0;
+  bool ok = true;
+
+  // Input row s: standardized features into X (A operand) and X^T (B2 rows 0-7).
+  long long off = step ? (long long)(step[0] % (unsigned long long)nbatch) * nb : 0;
+  long long i = (long long)blockIdx.x * TM + s;
+  const bool valid = i < nb && off + i < n;
+  const long long q = off + i;
+  const float* nm = F + TF_NORM;
+  float xr[NI];
+  static_assert(NI == 8, "two float4 per sample");
+  if (valid && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    const float4 p0 = reinterpret_cast<const float4*>(X + q * NI)[0], p1 = reinterpret_cast<const float4*>(X + q * NI)[1];
+    xr[0] = p0.x, xr[1] = p0.y, xr[2] = p0.z, xr[3] = p0.w, xr[4] = p1.x, xr[5] = p1.y, xr[6] = p1.z, xr[7] = p1.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < NI; ++k) xr[k] = valid ? X[q * NI + k] : 0.f;
+  }
+  {
+    float x[NI];
+#pragma unroll
+    for (int k = 0; k < NI; ++k) x[k] = valid ? (xr[k] - nm[k]) / nm[NI + k] : 0.f;
+    *reinterpret_cast<uint4*>(sm + XA + core_off(s, 0, 128)) =
+        make_uint4(pkf(x[0], x[1]), pkf(x[2], x[3]), pkf(x[4], x[5]), pkf(x[6], x[7]));
+    *reinterpret_cast<uint4*>(sm + XA + core_off(s, 8, 128)) = make_uint4(0u, 0u, 0u, 0u);
+    const int tb = col_base(B2, s, 80, 0);
+#pragma unroll
+    for (int k = 0; k < NI; ++k) st16(sm, tb + col_off(k), x[k]);
+  }
+  float v[64];
+  // ---- forward: three hidden layers ----
+#pragma unroll 1
+  for (int l = 0; l < 3 && ok; ++l) {
+    pre_issue();
+    if (s == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue(sm, tmem, 0, l == 0 ? XA : (l == 1 ? HA : HB), l == 0 ? WF1 : (l == 1 ? WF2 : WF3), 64, l == 0 ? 1 : 4,
+            idesc_n(64));
+    }
+    if (!(ok = finish(sm, phase))) break;
+    tc::ld64(ta, v);
+    uint64_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 64; ++k) {
+      v[k] = fmaxf(v[k] + F[TF_B + l * NH + k], 0.f);
+      m |= (uint64_t)(v[k] > 0.f) << k;
+    }
+    put_row64(sm, l == 1 ? HB : HA, s, v);
+    // transposed copies: H1 -> B1 rows 64-127, H2 -> B1 rows 0-63, H3 -> B2 rows 16-79
+    const int tb = l == 0 ? col_base(B1, s, 128, 64) : (l == 1 ? col_base(B1, s, 128, 0) : col_base(B2, s, 80, 16));
+#pragma unroll
+    for (int k = 0; k < 64; ++k) st16(sm, tb + col_off(k), v[k]);
+    mask[l * 128 + s] = m;
+  }
+  // ---- output layer and error ----
+  double se = 0.0;
+  if (ok) {
+    pre_issue();
+    if (s == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue(sm, tmem, 0, HA, WF4, 16, 4, idesc_n(16));
+    }
+    ok = finish(sm, phase);
+  }
+  if (ok) {
+    float y[16];
+    tc::ld16(ta, y);
+    const float* tn = nm + 2 * NI;
+    float dy[NO];
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      float e = 0.f;
+      if (valid) e = y[j] + F[TF_B + 3 * NH + j] - (T[q * NO + j] - tn[j]) / tn[NO + j];
+      se += (double)e * (double)e;
+      dy[j] = scale * e;
+    }
+    static_assert(NO == 3, "dy packing");
+    *reinterpret_cast<uint4*>(sm + DYA + core_off(s, 0, 128)) =
+        make_uint4(pkf(dy[0], dy[1]), pkf(dy[2], 0.f), 0u, 0u);
+    *reinterpret_cast<uint4*>(sm + DYA + core_off(s, 8, 128)) = make_uint4(0u, 0u, 0u, 0u);
+    const int tb = col_base(A2, s, 128, 64);
+#pragma unroll
+    for (int j = 0; j < NO; ++j) st16(sm, tb + col_off(j), dy[j]);
+    float* gbw = F + TF_GB + warp * (3 * NH + 4);
+#pragma unroll
+    for (int j = 0; j < NO; ++j) {
+      float t = dy[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) gbw[3 * NH + j] = t;
+    }
+  }
+  // ---- backward data: dZ3, dZ2, dZ1 ----
+#pragma unroll 1
+  for (int l = 2; l >= 0 && ok; --l) {  // dZ of hidden layer l + 1
+    const int c = 2 - l;
+    pre_issue();
+    if (s == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue(sm, tmem, 0, c == 0 ? DYA : DZA, c == 0 ? WB4 : (c == 1 ? WB3 : WB2), 64, c == 0 ? 1 : 4, idesc_n(64));
+    }
+    if (!(ok = finish(sm, phase))) break;
+    tc::ld64(ta, v);
+    const uint64_t m = mask[l * 128 + s];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) v[k] = (m >> k) & 1 ? v[k] : 0.f;
+    // dZ3 / dZ2: A operand of the next product; all three transposed into the
+    // stacked operands (dZ3 -> A1 rows 0-63, dZ2 -> A1 rows 64-127, dZ1 -> A2 rows 0-63).
+    if (l > 0) put_row64(sm, DZA, s, v);
+    const int tb = l == 2 ? col_base(A1, s, 128, 0) : (l == 1 ? col_base(A1, s, 128, 64) : col_base(A2, s, 128, 0));
+#pragma unroll
+    for (int k = 0; k < 64; ++k) st16(sm, tb + col_off(k), v[k]);
+    float sum2[2];
+    tt::reduce_scatter64(v, sum2, lane);
+    float* gbw = F + TF_GB + warp * (3 * NH + 4) + l * NH;
+    gbw[2 * lane] = sum2[0];
+    gbw[2 * lane + 1] = sum2[1];
+  }
+  // ---- weight gradients: the two stacked products ----
+  if (ok) {
+    pre_issue();
+    if (s == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue(sm, tmem, 128, A1, B1, 128, 8, idesc_n(128));
+      issue(sm, tmem, 0, A2, B2, 80, 8, idesc_n(80));
+    }
+    ok = finish(sm, phase);
+  }
+  float* gp = gpart + (size_t)blockIdx.x * NPAR;
+  if (ok) {
+    const int m = warp * 32 + lane;  // row of both products
+    if (warp < 2) {
+      tc::ld64(ta + 128, v);  // dW3^T row m: columns = H2 units (in)
+#pragma unroll
+      for (int k = 0; k < 64; ++k) gp[OW3 + k * NH + m] = v[k];
+      float d1[16];
+      tc::ld16(ta, d1);  // dW1^T row m: columns 0-7 = input features
+#pragma unroll
+      for (int k = 0; k < NI; ++k) gp[OW1 + k * NH + m] = d1[k];
+    } else {
+      tc::ld64(ta + 192, v);  // dW2^T row m - 64
+#pragma unroll
+      for (int k = 0; k < 64; ++k) gp[OW2 + k * NH + (m - 64)] = v[k];
+      tc::ld64(ta + 16, v);  // dW4^T rows 64-66: columns 16-79 = H3 units
+      if (m < 64 + NO)
+#pragma unroll
+        for (int k = 0; k < 64; ++k) gp[OW4 + k * NO + (m - 64)] = v[k];
+    }
+  }
+  // ---- bias gradients and loss: fixed-order sums of the warp partials ----
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+  double* lw = reinterpret_cast<double*>(F + TF_LOSS);
+  if (lane == 0) lw[warp] = se;
+  __syncthreads();
+  if (ok) {
+    for (int c = s; c < 3 * NH + NO; c += TM) {
+      float t = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 4; ++ww) t += F[TF_GB + ww * (3 * NH + 4) + c];
+      int dst = c < NH ? OB1 + c : c < 2 * NH ? OB2 + (c - NH) : c < 3 * NH ? OB3 + (c - 2 * NH) : OB4 + (c - 3 * NH);
+      gp[dst] = t;
+    }
+    if (s == 0) lpart[blockIdx.x] = ((lw[0] + lw[1]) + lw[2]) + lw[3];
+  } else if (s == 0) {
+    atomicOr(err, 4);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
+  }
+}
+
 // MODE 0: inference from conserved states to seeds (double [n][3]).
 // MODE 1: forward from raw features to targets (float [n][3]).
 template <int MODE>
@@ -563,13 +780,15 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
     long long q = tile * TM + s;
     bool valid = q < n;
     float f[NI];
+    float sr = 1.f, Q = 1.f;
     if (valid) {
       if (MODE == 0) {
-        double c[9];
+        float c[9];
         const double* cp = static_cast<const double*>(in) + q * 10;
 #pragma unroll
-        for (int m = 0; m < 9; ++m) c[m] = cp[m];
-        features(c, f);
+        for (int m = 0; m < 9; ++m) c[m] = narrow(cp[m]);
+        features_f32(c[0], c[1], c[2], c[3] * c[3] + c[4] * c[4] + c[5] * c[5],
+                     c[6] * c[6] + c[7] * c[7] + c[8] * c[8], c[3] * c[6] + c[4] * c[7] + c[5] * c[8], f, &sr, &Q);
       } else {
         const float* fp = static_cast<const float*>(in) + q * NI;
 #pragma unroll
@@ -588,14 +807,10 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
     float t2 = fmaf(y[2], tn[NO + 2], tn[2]);
     if (MODE == 0) {
       // Seeds need no more than FP32 accuracy: the FP64 root finder polishes them.
-      const double* cp = static_cast<const double*>(in) + q * 10;
-      float D = (float)cp[0];
-      float r = sqrtf((float)(cp[3] * cp[3] + cp[4] * cp[4] + cp[5] * cp[5])) / D;
-      float Q = fmaxf(1.f + (float)(cp[2] / cp[0]), 1e-30f);
       double* o = static_cast<double*>(out) + q * 3;
-      o[0] = (double)(expf(t0) / sqrtf(1.f + r * r));
-      o[1] = (double)(expf(t1) / Q);
-      o[2] = (double)expf(t2);
+      o[0] = widen(expf(t0) / sr);
+      o[1] = widen(expf(t1) / Q);
+      o[2] = widen(expf(t2));
     } else {
       float* o = static_cast<float*>(out) + q * 3;
       o[0] = t0;
@@ -622,6 +837,7 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
   const float* nm = F + 3 * NH + 4;
   const float* tn = nm + 2 * NI;
   const int s = threadIdx.x;
+  const float rho_min_f = narrow(rho_min);
   uint32_t phase = 0;
   for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
     const Work wk = w[b];
@@ -632,41 +848,40 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
     bool solve = false;
     long long o = 0;
     float f[NI];
-    double sr = 1.0, Q = 1.0;
+    float sr = 1.f, Q = 1.f;
     if (valid) {
       int i, j, k;
       dom_decode(DOM_ALL, G, q, i, j, k);
       o = at(G, i, j, k);
       const long long sf = G.sf;
       const double* U = PD.U[reg];
-      double gt[6];
-      for (int m = 0; m < 6; ++m) gt[m] = U[(GT + m) * sf + o];
-      double chi = U[CHI * sf + o];
-      double det = det3(gt);
-      // D = Dbar / sqrt(gamma) >= rho_min, with sqrt(gamma) = sqrt(det gt)
-      // chi^(-3/2), tested as Dbar^2 chi^3 >= rho_min^2 det gt (all factors
-      // positive): no square root or division for the atmosphere points,
-      // which are most points.  A decision rounded the other way at the
-      // threshold only changes whether the point gets a seed.
-      const double Db = U[DD * sf + o];
-      if (Db > 0.0 && Db * Db * (chi * chi * chi) >= (rho_min * rho_min) * det && isfinite(Db)) {
-        double ichi = 1.0 / chi;
-        double isg = 1.0 / (sqrt(det) * ichi * sqrt(ichi));
-        double D = Db * isg;
-        double gtu[6];
-        inv3(gt, 1.0 / det, gtu);
-        double Sd[3], Bu[3];
+      float gt[6];
+      for (int m = 0; m < 6; ++m) gt[m] = narrow(U[(GT + m) * sf + o]);
+      const float chi = narrow(U[CHI * sf + o]);
+      const float det = det3f(gt);
+      // D = Dbar / sqrt(gamma) with sqrt(gamma) = sqrt(det gt) chi^(-3/2);
+      // atmosphere points (D < rho_min, most points), which con2prim resets
+      // without solving, get no seed.  A decision rounded the other way at
+      // the threshold only changes whether the point gets a seed.
+      const float ichi = 1.0f / chi;
+      const float isg = 1.0f / (sqrtf(det) * ichi * sqrtf(ichi));
+      const float Db = narrow(U[DD * sf + o]), D = Db * isg;
+      if (D >= rho_min_f && isfinite(D)) {
+        float gtu[6];
+        inv3f(gt, 1.0f / det, gtu);
+        float Sd[3], Bu[3];
         for (int a = 0; a < 3; ++a) {
-          Sd[a] = U[(DD + 3 + a) * sf + o] * isg;
-          Bu[a] = U[(DD + 6 + a) * sf + o] * isg;
+          Sd[a] = narrow(U[(DD + 3 + a) * sf + o]) * isg;
+          Bu[a] = narrow(U[(DD + 6 + a) * sf + o]) * isg;
         }
-        double Su[3], Bd[3];
-        lower3(gtu, Sd, Su);  // gt^ij S_j; times chi below
-        lower3(gt, Bu, Bd);   // gt_ij B^j; times 1/chi below
-        double S2 = chi * (Sd[0] * Su[0] + Sd[1] * Su[1] + Sd[2] * Su[2]);
-        double B2 = ichi * (Bu[0] * Bd[0] + Bu[1] * Bd[1] + Bu[2] * Bd[2]);
-        double SB = Sd[0] * Bu[0] + Sd[1] * Bu[1] + Sd[2] * Bu[2];
-        features_sc(D, U[(DD + 1) * sf + o] * isg, U[(DD + 2) * sf + o] * isg, S2, B2, SB, f, &sr, &Q);
+        float Su[3], Bd[3];
+        lower3f(gtu, Sd, Su);  // gt^ij S_j; times chi below
+        lower3f(gt, Bu, Bd);   // gt_ij B^j; times 1/chi below
+        const float S2 = chi * (Sd[0] * Su[0] + Sd[1] * Su[1] + Sd[2] * Su[2]);
+        const float B2 = ichi * (Bu[0] * Bd[0] + Bu[1] * Bd[1] + Bu[2] * Bd[2]);
+        const float SB = Sd[0] * Bu[0] + Sd[1] * Bu[1] + Sd[2] * Bu[2];
+        features_f32(D, narrow(U[(DD + 1) * sf + o]) * isg, narrow(U[(DD + 2) * sf + o]) * isg, S2, B2, SB,
+                     f, &sr, &Q);
         solve = true;
       }
     }
@@ -684,8 +899,8 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
       float* sd = PD.seed + o;
       const long long sf = G.sf;
       if (solve) {
-        sd[0] = expf(fmaf(y[0], tn[NO + 0], tn[0])) / (float)sr;
-        sd[sf] = expf(fmaf(y[1], tn[NO + 1], tn[1])) / (float)Q;
+        sd[0] = expf(fmaf(y[0], tn[NO + 0], tn[0])) / sr;
+        sd[sf] = expf(fmaf(y[1], tn[NO + 1], tn[1])) / Q;
         sd[2 * sf] = expf(fmaf(y[2], tn[NO + 2], tn[2]));
       } else {
         sd[0] = sd[sf] = sd[2 * sf] = __int_as_float(0x7fc00000);
@@ -693,88 +908,6 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
     }
   }
   tc::end(tmem);
-}
-
-// Forward and backward over one tile of the batch [off, off + nb); writes the
-// tile's partial gradient (gpart[tile][NPAR]) and sum of squared errors (lpart[tile]).
-// off = (step[0] mod nbatch) * nb when step is given, else 0.
-__global__ void __launch_bounds__(TM) k_mlp_train(long long n, const float* __restrict__ X,
-                                                  const float* __restrict__ T, int nb, long long nbatch,
-                                                  const unsigned long long* __restrict__ step,
-                                                  const float* __restrict__ w, const float* __restrict__ norm,
-                                                  float* __restrict__ gpart, double* __restrict__ lpart, float scale) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  u16* S = reinterpret_cast<u16*>(smem);
-  float* F = reinterpret_cast<float*>(smem + (size_t)S_END_TRAIN * 2);
-  load_params(w, norm, S, F);
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, row0 = warp * 32, s = threadIdx.x;
-  long long off = step ? (long long)(step[0] % (unsigned long long)nbatch) * nb : 0;
-  long long i = (long long)blockIdx.x * TM + s;  // index within the batch
-  bool valid = i < nb && off + i < n;
-  long long q = off + i;
-  float f[NI];
-  if (valid)
-#pragma unroll
-    for (int k = 0; k < NI; ++k) f[k] = X[q * NI + k];
-  put_x(S + S_X, s, f, F + F_NORM, valid);
-  __syncwarp();
-  forward_tile(S, F, S + S_H3, row0, lane);
-  // Output error: dy = scale (y - t_std); loss partial; bf16(dy) into DY.
-  const float* nm = F + F_NORM + 2 * NI;
-  float dy[NO];
-  double se = 0.0;
-#pragma unroll
-  for (int j = 0; j < NO; ++j) {
-    float e = 0.f;
-    if (valid) {
-      float tj = (T[q * NO + j] - nm[j]) / nm[NO + j];
-      e = F[F_Y + s * 4 + j] - tj;
-    }
-    se += (double)e * (double)e;
-    dy[j] = scale * e;
-  }
-  u16* DY = S + S_DY;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) DY[s * LDX + j] = j < NO ? bf(dy[j]) : 0;
-  // b4 gradient and loss: warp sums, then fixed-order sums over the warps.
-  float* gbw = F + F_GB + warp * (3 * NH + 4);
-#pragma unroll
-  for (int j = 0; j < NO; ++j) {
-    float v = dy[j];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) gbw[3 * NH + j] = v;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
-  double* lw = reinterpret_cast<double*>(F + F_LOSS);
-  if (lane == 0) lw[warp] = se;
-  __syncthreads();
-  float* gp = gpart + (size_t)blockIdx.x * NPAR;
-  // dW4 (warp: rows 16w..16w+15) and dZ3 (warp rows) -> DZ.
-  bwd_weight<1>(S + S_H3, LDH, DY, LDX, gp + OW4, NO, warp * 16, NH, 0, lane);
-  bwd_act<1>(DY, LDX, S + S_W4, LDX, S + S_H3, S + S_DZ, gbw + 2 * NH, row0, lane);
-  __syncthreads();
-  // dW3 = H2^T dZ3; dZ2 -> H3 buffer (H3 no longer needed).
-  bwd_weight<8>(S + S_H2, LDH, S + S_DZ, LDH, gp + OW3, NH, warp * 16, NH, 0, lane);
-  bwd_act<4>(S + S_DZ, LDH, S + S_W3, LDH, S + S_H2, S + S_H3, gbw + NH, row0, lane);
-  __syncthreads();
-  // dW2 = H1^T dZ2; dZ1 -> DZ buffer.
-  bwd_weight<8>(S + S_H1, LDH, S + S_H3, LDH, gp + OW2, NH, warp * 16, NH, 0, lane);
-  bwd_act<4>(S + S_H3, LDH, S + S_W2, LDH, S + S_H1, S + S_DZ, gbw, row0, lane);
-  __syncthreads();
-  // dW1 = X^T dZ1 (rows k < 8; warp: column tiles 2w, 2w+1).
-  bwd_weight<2>(S + S_X, LDX, S + S_DZ, LDH, gp + OW1, NH, 0, NI, warp * 2, lane);
-  // Bias gradients and loss: fixed-order sums of the warp partials.
-  for (int c = threadIdx.x; c < 3 * NH + NO; c += blockDim.x) {
-    float v = 0.f;
-#pragma unroll
-    for (int ww = 0; ww < 4; ++ww) v += F[F_GB + ww * (3 * NH + 4) + c];
-    int dst = c < NH ? OB1 + c : c < 2 * NH ? OB2 + (c - NH) : c < 3 * NH ? OB3 + (c - 2 * NH) : OB4 + (c - 3 * NH);
-    gp[dst] = v;
-  }
-  if (threadIdx.x == 0) lpart[blockIdx.x] = ((lw[0] + lw[1]) + lw[2]) + lw[3];
 }
 
 // Sums nparts partial gradients (fixed order) into grad and the loss partials into loss.
@@ -983,8 +1116,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 bool attr_set = false;
 int set_smem_attrs() {
   if (attr_set) return GRMHD_OK;
-  if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(true)) !=
-          cudaSuccess ||
+  if (cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tt::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_patch, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
@@ -1165,8 +1297,8 @@ int grmhd_seeder_grad(grmhd_seeder* s, long long n, const float* f, const float*
   if (!s || n < 1 || n > MAX_BATCH || !f || !t || !grad) return GRMHD_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   int tiles = (int)grid_of(n, TM);
-  k_mlp_train<<<tiles, TM, smem_bytes(true), st>>>(n, f, t, (int)n, 1, nullptr, s->w, s->norm, s->gpart, s->lpart,
-                                                   (float)(2.0 / (3.0 * (double)n)));
+  k_mlp_train_tc<<<tiles, TM, tt::SMEM, st>>>(n, f, t, (int)n, 1, nullptr, s->w, s->norm, s->gpart, s->lpart,
+                                              (float)(2.0 / (3.0 * (double)n)), s->err);
   k_reduce_grad<<<grid_of(NPAR, 256), 256, 0, st>>>(s->gpart, tiles, s->lpart, grad, loss, 1.0 / (3.0 * (double)n));
   return last_rc();
 }
@@ -1205,8 +1337,8 @@ int grmhd_seeder_train(grmhd_seeder* s, long long n, const float* f, const float
   const float scale = (float)(2.0 / (3.0 * (double)bsz));
   const double lscale = 1.0 / (3.0 * (double)bsz * (double)nbatch);
   for (long long b = 0; b < nbatch; ++b) {
-    k_mlp_train<<<tiles, TM, smem_bytes(true), s->cap>>>(n, f, t, bsz, nbatch, s->ctr, s->w, s->norm, s->gpart,
-                                                         s->lpart, scale);
+    k_mlp_train_tc<<<tiles, TM, tt::SMEM, s->cap>>>(n, f, t, bsz, nbatch, s->ctr, s->w, s->norm, s->gpart,
+                                                    s->lpart, scale, s->err);
     k_adam<<<grid_of(NPAR, 256), 256, 0, s->cap>>>(s->w, s->m, s->v, s->gpart, tiles, s->ctr, 0, total, nbatch,
                                                     cfg->lr, cfg->lr_final, cfg->beta1, cfg->beta2, cfg->eps, s->lpart,
                                                     loss_hist, lscale);

@@ -211,6 +211,51 @@ def test_every_schedule_gives_the_same_result_bitwise(layout):
             assert torch.equal(runs[0].prim[q], pt.prim[q]), q
 
 
+def test_scaled_star_hierarchy_steps_match_oracle():
+    """Config 4 at scale 0.25 (the magnetised star with the synthetic table on
+    5 levels, 13 patches, 0.49 M interior points): 20 synchronous RK4 steps on
+    the GPU through a CUDA graph against the oracle's OpenMP build (bitwise the
+    serial oracle) from the identical state, and the oracle's twin from a
+    1e-14-perturbed start, the problem's rounding sensitivity (reading A26).
+    Per field over all patches (a field spans the hierarchy, reading A44):
+    max |gpu - oracle| / max |oracle| within max(1e-9, 10 x the twin's drift)."""
+    table = synth.make_table()
+    P = synth.table_params(table, bc=3)
+    specs = synth.amr_tov_layout(scale=0.25)
+    prof = synth.tov_profile()
+    O = oracle.Oracle(P, table, threads=0)
+    H, Ht = oracle.Hierarchy(O, specs), oracle.Hierarchy(O, specs)
+    for q, s in enumerate(specs):
+        H.init_state(q, synth.tov_id(n=s["n"], x0=s["x0"], dx=s["dx"], seed=4000 + q, table=table,
+                                     rho_atmo=P["rho_atmo"], profile=prof))
+    assert H.restrict(0) == 0
+    rng = np.random.default_rng(7)
+    for q in range(len(specs)):
+        Ht.U[0][q][...] = H.U[0][q] * (1.0 + 1e-14 * rng.uniform(-1.0, 1.0, H.U[0][q].shape))
+    pt = g.Patches(P, specs, table=g.Table(table))
+    _upload_all(pt, H, reg=0)
+    dt = 0.25 * min(s["dx"] for s in specs)
+    pt.capture_graph(1, dt)
+    for _ in range(20):
+        pt.graph_launch()
+        assert H.rk4_step(dt) >= 0
+        assert Ht.rk4_step(dt) >= 0
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    d_gpu, d_twin, scale = np.zeros(NF), np.zeros(NF), np.zeros(NF)
+    for q, s in enumerate(specs):
+        want = interior(H.U[0][q], s["n"]).reshape(NF, -1)
+        got = interior(pt.U[q][0].cpu().numpy(), s["n"]).reshape(NF, -1)
+        twin = interior(Ht.U[0][q], s["n"]).reshape(NF, -1)
+        scale = np.maximum(scale, np.abs(want).max(axis=1))
+        d_gpu = np.maximum(d_gpu, np.abs(got - want).max(axis=1))
+        d_twin = np.maximum(d_twin, np.abs(twin - want).max(axis=1))
+    e_gpu, e_twin = d_gpu / np.maximum(scale, 1e-300), d_twin / np.maximum(scale, 1e-300)
+    print("scaled star hierarchy, 20 steps: max over fields GPU %.3g, twin %.3g" % (e_gpu.max(), e_twin.max()))
+    bad = {f: (e_gpu[f], e_twin[f]) for f in range(NF) if not e_gpu[f] <= max(1e-9, 10.0 * e_twin[f])}
+    assert not bad, bad
+
+
 def test_uncovered_fine_ghosts_are_rejected():
     specs = synth.small_hierarchy()
     specs[1] = synth.hierarchy.spec((12, 12, 12), 1, (1, 12, 12), 1.0, (-12.0,) * 3)
