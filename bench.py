@@ -42,10 +42,10 @@ WORKLOAD = "tov_magnetised_128^3_rk4_step"
 RHS_FLOPS_PER_POINT = 6724.0
 RK_FLOPS_PER_POINT = (128.0 * 3 + 64.0) / 4.0
 # DRAM bytes (read + write) per interior point of one k_rhs launch, from the
-# ncu capture in profiles/launch_list_tov128.md (64^3 case, k_rhs<1, 128>,
-# 192.75 + 208.55 MB over 262,144 points), scaled to a launch by its points;
+# ncu capture in profiles/launch_list_tov128.md (64^3 case, k_rhs<1, 128, 0>,
+# 204.49 + 303.53 MB over 262,144 points), scaled to a launch by its points;
 # set to None whenever k_rhs changes until it is captured again.
-RHS_TRAFFIC_BYTES_PER_POINT = (192.75e6 + 208.55e6) / 64 ** 3
+RHS_TRAFFIC_BYTES_PER_POINT = (204.493824e6 + 303.534592e6) / 64 ** 3
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 4 FP64 flops per
 # clock per SM x 2070 MHz (nominal GB300 FP64 1.25 TFLOP/s = 152 x 2.07 GHz x 3.97).
 # The line's peak is the measured one (the library's FMA throughput probe,
@@ -381,17 +381,25 @@ def run_grmhd(args):
     host_out = torch.empty_like(host_in).pin_memory()
     nbytes = host_in.numel() * host_in.element_size()
     torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.e2e_steps)]
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    for k in range(args.e2e_steps):
         with torch.cuda.stream(s):
+            ev[k][0].record(s)
             pt.U[0][0].copy_(host_in, non_blocking=True)
+            ev[k][1].record(s)
         pt.step(dt)
         with torch.cuda.stream(s):
+            ev[k][2].record(s)
             host_out.copy_(pt.U[0][0], non_blocking=True)
+            ev[k][3].record(s)
         s.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_s = _max_over_ranks(ws, e2e_s)
-    e2e = {"value": ws * zones / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    h2d_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.e2e_steps
+    d2h_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.e2e_steps
+    e2e = {"value": ws * zones / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "ms_per_step": 1e3 * e2e_s, "h2d_ms": h2d_ms, "d2h_ms": d2h_ms}
 
     if rank != 0:
         return 0

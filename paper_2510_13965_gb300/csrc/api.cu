@@ -54,6 +54,10 @@ struct grmhd_ctx {
   const grmhd_seeder* seeder = nullptr;
   double seed_delta = 0.0;
   float* seed_buf = nullptr;
+  // points to seed (the seeder's first pass): (patch, point offset) and the count
+  int2* seed_list = nullptr;
+  int* seed_count = nullptr;
+  long long seed_cap = 0;
   int amr_level0 = -1, amr_nlev = 0;
   std::vector<long long> amr_gofs, amr_gcnt, amr_rofs, amr_rcnt, amr_gsame;
   // per level: coarse points its prolongation stencils read (sub-cycling)
@@ -241,6 +245,7 @@ void grmhd_destroy(grmhd_ctx* c) {
   cudaFree(c->rhs_ptrs);
   cudaFree(c->amr);
   cudaFree(c->seed_buf);
+  cudaFree(c->seed_list);
   delete c;
 }
 
@@ -627,9 +632,10 @@ static int c2p_and_fluxes(grmhd_ctx* c, int reg, bool stats, int grp = 0) {
     ProfScope ps(c, K_SEED);
     int rc = GRMHD_OK;
     for_slices(c, DOM_ALL, 128, grp, [&](const Work* w, int n) {
-      int r = launch_seeder_patches(c->seeder, c->pd, w, n, reg, c->P.rho_min, &c->flags->flags, c->st);
+      int r = launch_seeder_patches(c->seeder, c->pd, w, n, reg, c->P.rho_min, c->seed_list, c->seed_count,
+                                    c->seed_cap, &c->flags->flags, c->st);
       if (r && !rc) rc = r;
-      c->launches += 1;
+      c->launches += 2;
     });
     if (rc) return fail(c, rc, "seeder launch");
   }
@@ -663,7 +669,21 @@ int grmhd_set_seeder(grmhd_ctx* c, const grmhd_seeder* s, double delta) {
     size_t total = 0;
     for (int i = 0; i < c->np; ++i)
       if (c->role[i] == 1) total += 3 * (size_t)c->pd_host[i].G.sf;
-    if ((rc = cuda_ok(c, cudaMalloc(&c->seed_buf, total * sizeof(float)), "cudaMalloc seeds"))) return GRMHD_ERR_NOMEM;
+    // The list holds every local point (point offsets fit an int: a patch's
+    // field has fewer than 2^31 points) and, after it, the count.
+    const long long cap = (long long)(total / 3);
+    for (int i = 0; i < c->np; ++i)
+      if (c->role[i] == 1 && c->pd_host[i].G.sf >= (1LL << 31))
+        return fail(c, GRMHD_ERR_ARG, "set_seeder: a patch has 2^31 or more points");
+    if ((rc = cuda_ok(c, cudaMalloc(&c->seed_list, (size_t)cap * sizeof(int2) + 16), "cudaMalloc seed list")))
+      return GRMHD_ERR_NOMEM;
+    if ((rc = cuda_ok(c, cudaMalloc(&c->seed_buf, total * sizeof(float)), "cudaMalloc seeds"))) {
+      cudaFree(c->seed_list);
+      c->seed_list = nullptr;
+      return GRMHD_ERR_NOMEM;
+    }
+    c->seed_cap = cap;
+    c->seed_count = reinterpret_cast<int*>(c->seed_list + cap);
     size_t o = 0;
     for (int i = 0; i < c->np; ++i) {
       if (c->role[i] != 1) continue;

@@ -283,9 +283,11 @@ void launch_shard_unpack(const PatchDev* pd, const AmrPoint* pts, long long n, i
                          cudaStream_t st);
 
 // Learned seeder over patch points (seeder.cu): seeds of every point of the
-// work list (blocks of 128 points) of register reg into PatchDev::seed.
+// work list (blocks of 128 points) of register reg into PatchDev::seed, in
+// two passes: the atmosphere test lists the points to solve (list of
+// capacity cap, its length in *count), then the network runs on the list.
 int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd_dev, const Work* w, int nblk, int reg,
-                          double rho_min, int* err, cudaStream_t st);
+                          double rho_min, int2* list, int* count, long long cap, int* err, cudaStream_t st);
 
 // FP64 throughput probe: `blocks` blocks of 256 threads, each thread running
 // `chains` (4, 8 or 16) independent FMA (or, add, addition) chains; returns

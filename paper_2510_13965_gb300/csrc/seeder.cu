@@ -821,15 +821,93 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
   tc::end(tmem);
 }
 
-// Seeds for the points of patch work items (blocks of 128 points, DOM_ALL):
-// features from the conserved variables of register reg and the metric
-// (gamma_ij = gt_ij / chi, gamma^ij = chi gt^ij, sqrt(gamma) = sqrt(det gt)
-// chi^(-3/2)), network, seeds (float) into PatchDev::seed.  Atmosphere points
-// (D < rho_min, which con2prim resets without solving) and non-finite states
-// get NaN seeds.  Persistent over the work list.
-__global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
-                                                  int nblk, int reg, double rho_min, const float* __restrict__ wts,
-                                                  const float* __restrict__ norm, int* __restrict__ err, int hold) {
+// ---- seeds for the points of patches ---------------------------------------
+// Features of patch point o from the conserved variables of register reg and
+// the metric (gamma_ij = gt_ij / chi, gamma^ij = chi gt^ij, sqrt(gamma) =
+// sqrt(det gt) chi^(-3/2)), in FP32.  False for atmosphere points (D <
+// rho_min, which con2prim resets without solving) and non-finite states: a
+// decision rounded the other way at the threshold only changes whether the
+// point gets a seed.  With feats false only the atmosphere test runs.
+template <bool FEATS>
+DI bool patch_point(const PatchDev& PD, long long o, int reg, float rho_min, float f[NI], float* sr, float* Q) {
+  const long long sf = PD.G.sf;
+  const double* U = PD.U[reg];
+  float gt[6];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) gt[m] = narrow(U[(GT + m) * sf + o]);
+  const float chi = narrow(U[CHI * sf + o]);
+  const float det = det3f(gt);
+  const float ichi = 1.0f / chi;
+  const float isg = 1.0f / (sqrtf(det) * ichi * sqrtf(ichi));
+  const float D = narrow(U[DD * sf + o]) * isg;
+  if (!(D >= rho_min && isfinite(D))) return false;
+  if (!FEATS) return true;
+  float gtu[6];
+  inv3f(gt, 1.0f / det, gtu);
+  float Sd[3], Bu[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Sd[a] = narrow(U[(DD + 3 + a) * sf + o]) * isg;
+    Bu[a] = narrow(U[(DD + 6 + a) * sf + o]) * isg;
+  }
+  float Su[3], Bd[3];
+  lower3f(gtu, Sd, Su);  // gt^ij S_j; times chi below
+  lower3f(gt, Bu, Bd);   // gt_ij B^j; times 1/chi below
+  const float S2 = chi * (Sd[0] * Su[0] + Sd[1] * Su[1] + Sd[2] * Su[2]);
+  const float B2 = ichi * (Bu[0] * Bd[0] + Bu[1] * Bd[1] + Bu[2] * Bd[2]);
+  const float SB = Sd[0] * Bu[0] + Sd[1] * Bu[1] + Sd[2] * Bu[2];
+  features_f32(D, narrow(U[(DD + 1) * sf + o]) * isg, narrow(U[(DD + 2) * sf + o]) * isg, S2, B2, SB, f, sr, Q);
+  return true;
+}
+
+DI void nan_seed(const PatchDev& PD, long long o) {
+  float* sd = PD.seed + o;
+  sd[0] = sd[PD.G.sf] = sd[2 * PD.G.sf] = __int_as_float(0x7fc00000);
+}
+
+// Pass 1 over the points of patch work items (blocks of 128 points, DOM_ALL):
+// the atmosphere test; points to solve are appended to `list` (patch, point
+// offset; warp-aggregated, in no particular order), the others get NaN seeds
+// (which con2prim ignores).  Most points of a star's hierarchy are
+// atmosphere, so the network then runs on full tiles of fluid points only.
+__global__ void __launch_bounds__(TM) k_seed_scan(const PatchDev* __restrict__ pd, const Work* __restrict__ w,
+                                                  int reg, double rho_min, int2* __restrict__ list,
+                                                  int* __restrict__ count, long long cap) {
+  const Work wk = w[blockIdx.x];
+  const PatchDev& PD = pd[wk.patch];
+  const long long q = (long long)wk.block * TM + threadIdx.x;
+  bool solve = false;
+  long long o = 0;
+  if (q < dom_count(DOM_ALL, PD.G)) {
+    int i, j, k;
+    dom_decode(DOM_ALL, PD.G, q, i, j, k);
+    o = at(PD.G, i, j, k);
+    solve = patch_point<false>(PD, o, reg, narrow(rho_min), nullptr, nullptr, nullptr);
+    if (!solve) nan_seed(PD, o);
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, solve);
+  if (!m) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (solve) {
+    const long long e = (long long)base + __popc(m & ((1u << lane) - 1u));
+    if (e < cap) list[e] = make_int2(wk.patch, (int)o);
+    else nan_seed(PD, o);  // cannot happen: the list holds every point
+  }
+}
+
+// Pass 2: seeds of the listed points (count written by pass 1), tiles of 128
+// list entries on the tcgen05 tensor cores; seeds (float) into
+// PatchDev::seed.  Persistent; CTAs without a tile return before any set-up.
+__global__ void __launch_bounds__(TM) k_mlp_list(const PatchDev* __restrict__ pd, const int2* __restrict__ list,
+                                                 const int* __restrict__ count, long long cap, int reg,
+                                                 double rho_min, const float* __restrict__ wts,
+                                                 const float* __restrict__ norm, int* __restrict__ err, int hold) {
+  const int nl = (int)((long long)*count < cap ? (long long)*count : cap);
+  const int ntiles = (nl + TM - 1) / TM;
+  if ((int)blockIdx.x >= ntiles) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   tc::load(wts, norm, smem);
   const uint32_t tmem = tc::begin(smem);
@@ -839,71 +917,32 @@ __global__ void __launch_bounds__(TM) k_mlp_patch(const PatchDev* __restrict__ p
   const int s = threadIdx.x;
   const float rho_min_f = narrow(rho_min);
   uint32_t phase = 0;
-  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const Work wk = w[b];
-    const PatchDev& PD = pd[wk.patch];
-    const Geo G = PD.G;
-    long long q = (long long)wk.block * TM + s;
-    bool valid = q < dom_count(DOM_ALL, G);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int e = tile * TM + s;
+    int2 it = make_int2(0, 0);
     bool solve = false;
-    long long o = 0;
     float f[NI];
     float sr = 1.f, Q = 1.f;
-    if (valid) {
-      int i, j, k;
-      dom_decode(DOM_ALL, G, q, i, j, k);
-      o = at(G, i, j, k);
-      const long long sf = G.sf;
-      const double* U = PD.U[reg];
-      float gt[6];
-      for (int m = 0; m < 6; ++m) gt[m] = narrow(U[(GT + m) * sf + o]);
-      const float chi = narrow(U[CHI * sf + o]);
-      const float det = det3f(gt);
-      // D = Dbar / sqrt(gamma) with sqrt(gamma) = sqrt(det gt) chi^(-3/2);
-      // atmosphere points (D < rho_min, most points), which con2prim resets
-      // without solving, get no seed.  A decision rounded the other way at
-      // the threshold only changes whether the point gets a seed.
-      const float ichi = 1.0f / chi;
-      const float isg = 1.0f / (sqrtf(det) * ichi * sqrtf(ichi));
-      const float Db = narrow(U[DD * sf + o]), D = Db * isg;
-      if (D >= rho_min_f && isfinite(D)) {
-        float gtu[6];
-        inv3f(gt, 1.0f / det, gtu);
-        float Sd[3], Bu[3];
-        for (int a = 0; a < 3; ++a) {
-          Sd[a] = narrow(U[(DD + 3 + a) * sf + o]) * isg;
-          Bu[a] = narrow(U[(DD + 6 + a) * sf + o]) * isg;
-        }
-        float Su[3], Bd[3];
-        lower3f(gtu, Sd, Su);  // gt^ij S_j; times chi below
-        lower3f(gt, Bu, Bd);   // gt_ij B^j; times 1/chi below
-        const float S2 = chi * (Sd[0] * Su[0] + Sd[1] * Su[1] + Sd[2] * Su[2]);
-        const float B2 = ichi * (Bu[0] * Bd[0] + Bu[1] * Bd[1] + Bu[2] * Bd[2]);
-        const float SB = Sd[0] * Bu[0] + Sd[1] * Bu[1] + Sd[2] * Bu[2];
-        features_f32(D, narrow(U[(DD + 1) * sf + o]) * isg, narrow(U[(DD + 2) * sf + o]) * isg, S2, B2, SB,
-                     f, &sr, &Q);
-        solve = true;
-      }
+    if (e < nl) {
+      it = list[e];
+      solve = patch_point<true>(pd[it.x], it.y, reg, rho_min_f, f, &sr, &Q);
     }
-    // A tile without a point to solve (atmosphere, padding) skips the network;
-    // the branch is uniform across the CTA, so the mbarrier phase stays in step.
-    float y[NO] = {0.0f, 0.0f, 0.0f};
-    if (__syncthreads_or(solve)) {
-      tc::put_x(smem, s, f, nm, solve);
-      if (!tc::forward(smem, tmem, phase, y, hold)) {
-        if (s == 0) atomicOr(err, 4);
-        break;
-      }
+    tc::put_x(smem, s, f, nm, solve);
+    float y[NO];
+    if (!tc::forward(smem, tmem, phase, y, hold)) {
+      if (s == 0) atomicOr(err, 4);
+      break;
     }
-    if (valid) {
-      float* sd = PD.seed + o;
-      const long long sf = G.sf;
+    if (e < nl) {
+      const PatchDev& PD = pd[it.x];
       if (solve) {
+        float* sd = PD.seed + it.y;
+        const long long sf = PD.G.sf;
         sd[0] = expf(fmaf(y[0], tn[NO + 0], tn[0])) / sr;
         sd[sf] = expf(fmaf(y[1], tn[NO + 1], tn[1])) / Q;
         sd[2 * sf] = expf(fmaf(y[2], tn[NO + 2], tn[2]));
       } else {
-        sd[0] = sd[sf] = sd[2 * sf] = __int_as_float(0x7fc00000);
+        nan_seed(PD, it.y);
       }
     }
   }
@@ -1119,7 +1158,7 @@ int set_smem_attrs() {
   if (cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tt::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_fwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess ||
       cudaFuncSetAttribute(k_mlp_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess ||
-      cudaFuncSetAttribute(k_mlp_patch, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
+      cudaFuncSetAttribute(k_mlp_list, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM) != cudaSuccess)
     return GRMHD_ERR_CUDA;
   attr_set = true;
   return GRMHD_OK;
@@ -1128,8 +1167,8 @@ int set_smem_attrs() {
 unsigned grid_of(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 // Resident CTAs per SM of a tensor-core inference kernel, from its registers
-// and shared memory, at most 4 (each CTA holds 64 of the SM's 512 TMEM
-// columns; 4 leaves room for other work).
+// and shared memory, at most 5 (each CTA holds 64 of the SM's 512 TMEM
+// columns; 5 leaves 192 for other work).
 int tc_ctas_per_sm(const void* fn, int dev) {
   cudaFuncAttributes fa;
   int smem_sm = 0;
@@ -1139,7 +1178,7 @@ int tc_ctas_per_sm(const void* fn, int dev) {
   int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * TM) : 4;
   int by_smem = smem_sm / (tc::SMEM + 1024);
   int n = by_regs < by_smem ? by_regs : by_smem;
-  return n < 1 ? 1 : (n > 4 ? 4 : n);
+  return n < 1 ? 1 : (n > 5 ? 5 : n);
 }
 
 // Persistent grid of the forward kernels: resident CTAs per SM x SMs, at most
@@ -1165,8 +1204,9 @@ int last_rc() { return cudaGetLastError() == cudaSuccess ? GRMHD_OK : GRMHD_ERR_
 
 namespace gk {
 int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd, const Work* w, int nblk, int reg, double rho_min,
-                          int* err, cudaStream_t st) {
+                          int2* list, int* count, long long cap, int* err, cudaStream_t st) {
   if (!s || nblk <= 0) return nblk <= 0 ? GRMHD_OK : GRMHD_ERR_ARG;
+  if (!list || !count || cap < 1) return GRMHD_ERR_ARG;
   static int per_dev[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1174,10 +1214,15 @@ int launch_seeder_patches(const grmhd_seeder* s, const PatchDev* pd, const Work*
   if (!per_dev[dev]) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    per_dev[dev] = (sms > 0 ? sms : 1) * tc_ctas_per_sm((const void*)k_mlp_patch, dev);
+    per_dev[dev] = (sms > 0 ? sms : 1) * tc_ctas_per_sm((const void*)k_mlp_list, dev);
   }
-  int grid = nblk < per_dev[dev] ? nblk : per_dev[dev];
-  k_mlp_patch<<<grid, TM, tc::SMEM, st>>>(pd, w, nblk, reg, rho_min, s->w, s->norm, err, s->hold);
+  if (cudaMemsetAsync(count, 0, sizeof(int), st) != cudaSuccess) return GRMHD_ERR_CUDA;
+  k_seed_scan<<<nblk, TM, 0, st>>>(pd, w, reg, rho_min, list, count, cap);
+  // The grid covers every listed point however many pass 1 finds (at most
+  // one tile per block and round).
+  const long long tiles = ((long long)nblk * TM + TM - 1) / TM;
+  const int grid = (int)(tiles < per_dev[dev] ? tiles : per_dev[dev]);
+  k_mlp_list<<<grid, TM, tc::SMEM, st>>>(pd, list, count, cap, reg, rho_min, s->w, s->norm, err, s->hold);
   return last_rc();
 }
 }  // namespace gk
