@@ -164,6 +164,7 @@ int oracle_c2p_flat(const oracle_params* P, const oracle_eos_table* E, long n, c
                     int8_t* status, int* iters) {
   const double gt[6] = {1, 0, 0, 1, 0, 1};
   int worst = 0;
+  ORACLE_PAR_FOR_STATES
   for (long q = 0; q < n; ++q) {
     double co[10];
     int it = 0;
@@ -189,6 +190,7 @@ int oracle_c2p_flat_ext(const oracle_params* P, const oracle_eos_table* E, long 
                         int8_t* status, int* iters, const double* seeds, double delta, double* roots, int8_t* seeded) {
   const double gt[6] = {1, 0, 0, 1, 0, 1};
   int worst = 0;
+  ORACLE_PAR_FOR_STATES
   for (long q = 0; q < n; ++q) {
     double co[10];
     int it = 0, sd = 0;

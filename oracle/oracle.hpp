@@ -124,9 +124,11 @@ static const int NG = 3;
 #ifdef _OPENMP
 #define ORACLE_PAR_FOR _Pragma("omp parallel for collapse(2) schedule(static)")
 #define ORACLE_PAR_FOR_C2P _Pragma("omp parallel for collapse(2) schedule(static) reduction(min : worst) reduction(+ : its)")
+#define ORACLE_PAR_FOR_STATES _Pragma("omp parallel for schedule(static) reduction(min : worst)")
 #else
 #define ORACLE_PAR_FOR
 #define ORACLE_PAR_FOR_C2P
+#define ORACLE_PAR_FOR_STATES
 #endif
 
 // ---- patch-level steps (patch.cpp) ------------------------------------------

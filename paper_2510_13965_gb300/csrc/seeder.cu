@@ -827,8 +827,7 @@ __global__ void __launch_bounds__(TM) k_mlp_fwd(long long n, const void* __restr
 // sqrt(det gt) chi^(-3/2)), in FP32.  False for atmosphere points (D <
 // rho_min, which con2prim resets without solving) and non-finite states: a
 // decision rounded the other way at the threshold only changes whether the
-// point gets a seed.  With feats false only the atmosphere test runs.
-template <bool FEATS>
+// point gets a seed.
 DI bool patch_point(const PatchDev& PD, long long o, int reg, float rho_min, float f[NI], float* sr, float* Q) {
   const long long sf = PD.G.sf;
   const double* U = PD.U[reg];
@@ -841,7 +840,6 @@ DI bool patch_point(const PatchDev& PD, long long o, int reg, float rho_min, flo
   const float isg = 1.0f / (sqrtf(det) * ichi * sqrtf(ichi));
   const float D = narrow(U[DD * sf + o]) * isg;
   if (!(D >= rho_min && isfinite(D))) return false;
-  if (!FEATS) return true;
   float gtu[6];
   inv3f(gt, 1.0f / det, gtu);
   float Sd[3], Bu[3];
@@ -882,7 +880,13 @@ __global__ void __launch_bounds__(TM) k_seed_scan(const PatchDev* __restrict__ p
     int i, j, k;
     dom_decode(DOM_ALL, PD.G, q, i, j, k);
     o = at(PD.G, i, j, k);
-    solve = patch_point<false>(PD, o, reg, narrow(rho_min), nullptr, nullptr, nullptr);
+    // D = Dbar chi^(3/2) / sqrt(det gt), with det gt = 1 (the conformal
+    // metric's determinant, 1 up to truncation error): two loads per point
+    // instead of eight.  The second pass tests again with the determinant.
+    const double* U = PD.U[reg];
+    const float chi = narrow(U[CHI * PD.G.sf + o]);
+    const float D = narrow(U[DD * PD.G.sf + o]) * chi * sqrtf(chi);
+    solve = D >= narrow(rho_min) && isfinite(D);
     if (!solve) nan_seed(PD, o);
   }
   const unsigned m = __ballot_sync(0xffffffffu, solve);
@@ -925,7 +929,7 @@ __global__ void __launch_bounds__(TM) k_mlp_list(const PatchDev* __restrict__ pd
     float sr = 1.f, Q = 1.f;
     if (e < nl) {
       it = list[e];
-      solve = patch_point<true>(pd[it.x], it.y, reg, rho_min_f, f, &sr, &Q);
+      solve = patch_point(pd[it.x], it.y, reg, rho_min_f, f, &sr, &Q);
     }
     tc::put_x(smem, s, f, nm, solve);
     float y[NO];

@@ -345,16 +345,16 @@ def _flat_cons_numpy(n, seed):
     return cons
 
 
-def test_full_size_con2prim_sampled():
+def test_full_size_con2prim_all_states():
     """The isolated con2prim workload at full size: 2^24 states, the
     256 x 128 x 64 table, plain and NN-seeded (the bench's recipe: 2^20 GPU-made
-    training pairs, delta = 0.03) in single launches; 4096 seeded-random states
-    redone by the oracle: statuses bit-exact, primitives within the con2prim
-    bounds."""
+    training pairs, delta = 0.03) in single launches, every state redone by the
+    oracle (its OpenMP build on all host cores, bitwise the serial oracle):
+    statuses bit-exact, primitives within the con2prim bounds."""
     table = synth.make_table()
     P = synth.table_params(table)
     T = g.Table(table)
-    O = oracle.Oracle(P, table)
+    O = oracle.Oracle(P, table, threads=0)
     n = 1 << 24
     cons = _flat_cons_numpy(n, seed=3)
     cg = torch.as_tensor(cons, device="cuda")
@@ -371,7 +371,6 @@ def test_full_size_con2prim_sampled():
     S.train(g.seeder_features(ctr)[keep].contiguous(), g.seeder_targets(ctr, roots)[keep].contiguous(),
             batch=4096, epochs=40, lr=3e-3, lr_final=3e-5)
     ps, ss, _, _, _ = (a.cpu().numpy() for a in g.c2p_flat_seeded(P, cg, S.infer(cg), 0.03, table=T))
-    idx = np.sort(np.random.default_rng(5).choice(n, 4096, replace=False))
-    po, so, _ = O.c2p_flat(cons[idx])
+    po, so, _ = O.c2p_flat(cons)
     for p_, s_ in ((pg, sg), (ps, ss)):
-        prim_check(p_[idx].T, po.T, s_[idx], so, cons[idx, :3].T)
+        prim_check(p_.T, po.T, s_, so, cons[:, :3].T)

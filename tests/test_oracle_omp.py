@@ -37,3 +37,31 @@ def test_openmp_oracle_is_bitwise_the_serial_oracle():
         par = _run(Opar, P, n, dx, ID, steps)
         for a, b in zip(serial, par):
             assert np.array_equal(a, b)
+
+
+def test_openmp_oracle_flat_con2prim_is_bitwise_the_serial_oracle():
+    """The flat-metric con2prim over independent states (the isolated
+    con2prim workload's 256 x 128 x 64 table, plain and with seeds)."""
+    table = synth.make_table()
+    P = synth.table_params(table)
+    s = synth.c2p_states(3000, seed=7)
+    rho, ye, v, B = s["rho"], s["ye"], s["v"], s["B"]
+    p, eps, _ = synth.eos_table.model(rho, s["T"], ye)
+    v2 = np.einsum("ij,ij->i", v, v)
+    W2 = 1.0 / (1.0 - v2)
+    h = rho * (1.0 + eps) + p
+    B2 = np.einsum("ij,ij->i", B, B)
+    vB = np.einsum("ij,ij->i", v, B)
+    cons = np.zeros((3000, 10))
+    cons[:, 0] = rho * np.sqrt(W2)
+    cons[:, 1] = cons[:, 0] * ye
+    cons[:, 2] = h * W2 - p + B2 - 0.5 * (B2 / W2 + vB * vB) - cons[:, 0]
+    cons[:, 3:6] = (h * W2 + B2)[:, None] * v - vB[:, None] * B
+    cons[:, 6:9] = B
+    Os, Op = oracle.Oracle(P, table), oracle.Oracle(P, table, threads=4)
+    for a, b in zip(Os.c2p_flat(cons), Op.c2p_flat(cons)):
+        assert np.array_equal(a, b)
+    _, _, _, roots, _ = Os.c2p_flat_ext(cons)
+    seeds = roots * (1.0 + 0.01 * np.random.default_rng(2).uniform(-1.0, 1.0, roots.shape))
+    for a, b in zip(Os.c2p_flat_ext(cons, seeds, 0.03), Op.c2p_flat_ext(cons, seeds, 0.03)):
+        assert np.array_equal(a, b)
