@@ -312,6 +312,10 @@ static int init_impl(grmhd_ctx** out, const grmhd_params* p, int npatch, const g
     grmhd_destroy(c);
     return GRMHD_ERR_NOMEM;
   }
+  if ((rc = eos_set_atmo(c->P, c->E, c->st)) != GRMHD_OK) {
+    grmhd_destroy(c);
+    return rc;
+  }
   for (int i = 0; i < npatch; ++i) {
     PatchDev& q = c->pd_host[i];
     for (int r = 0; r < REG_DENSE + NDENSE; ++r) q.U[r] = nullptr;

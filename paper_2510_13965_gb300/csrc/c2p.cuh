@@ -14,6 +14,10 @@
 
 namespace gk {
 
+struct EosOut {
+  double p, eps, T, cs2;
+};
+
 struct Eos {
   int kind;
   double gam, K, eps_max;
@@ -26,10 +30,10 @@ struct Eos {
   const double* p;
   const double* e;
   const double* c;
-};
-
-struct EosOut {
-  double p, eps, T, cs2;
+  // The atmosphere's state eos_T(rho_atmo, T_atmo, ye_atmo), evaluated once
+  // on the device when atmo_set (a context's EOS); else per atmosphere point.
+  int atmo_set;
+  EosOut atmo;
 };
 
 DI void tab_loc(const Eos& E, double x, double x0, double idx, int n, int* i, double* w) {
@@ -633,7 +637,7 @@ DI void c2p_point(const grmhd_params& P, const Eos& E, const double cb[9], const
     }
   }
   if (status & 1) {
-    EosOut eo = eos_T(E, P.rho_atmo, P.T_atmo, P.ye_atmo);
+    const EosOut eo = E.atmo_set ? E.atmo : eos_T(E, P.rho_atmo, P.T_atmo, P.ye_atmo);
     rho = P.rho_atmo;
     eps = eo.eps;
     p = eo.p;

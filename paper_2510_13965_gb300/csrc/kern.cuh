@@ -174,6 +174,8 @@ struct DevFlags {
 };
 
 Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T);
+// Evaluates the atmosphere's EOS state once on the device into E (synchronous).
+int eos_set_atmo(const grmhd_params& P, Eos& E, cudaStream_t st);
 // GRMHD_OK when the EOS kind and its parameters (table pointers and sizes,
 // hybrid pieces) are usable, else GRMHD_ERR_ARG.
 int eos_check(const grmhd_params& P, const grmhd_eos_table* T);

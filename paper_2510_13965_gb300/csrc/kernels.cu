@@ -20,6 +20,8 @@ Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T) {
   E.nr = E.nt = E.ny = 0;
   E.lr0 = E.idlr = E.lt0 = E.dlt = E.idlt = E.ye0 = E.idye = 0.0;
   E.p = E.e = E.c = nullptr;
+  E.atmo_set = 0;
+  E.atmo = EosOut{0.0, 0.0, 0.0, 0.0};
   E.npoly = 0;
   for (int i = 0; i < 4; ++i) E.hK[i] = E.ha[i] = E.hg[i] = 0.0;
   for (int i = 0; i < 3; ++i) E.hr[i] = 0.0;
@@ -54,6 +56,28 @@ Eos make_eos(const grmhd_params& P, const grmhd_eos_table* T) {
     E.c = T->cs2;
   }
   return E;
+}
+
+// The atmosphere's EOS state, evaluated once by the same device code that
+// con2prim would run at every atmosphere point (so the stored values are
+// those it would compute).
+__global__ void k_atmo_state(grmhd_params P, Eos E, EosOut* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = eos_T(E, P.rho_atmo, P.T_atmo, P.ye_atmo);
+}
+
+int eos_set_atmo(const grmhd_params& P, Eos& E, cudaStream_t st) {
+  EosOut* d = nullptr;
+  EosOut h;
+  if (cudaMalloc(&d, sizeof(EosOut)) != cudaSuccess) return GRMHD_ERR_NOMEM;
+  k_atmo_state<<<1, 32, 0, st>>>(P, E, d);
+  const bool ok = cudaGetLastError() == cudaSuccess &&
+                  cudaMemcpyAsync(&h, d, sizeof(EosOut), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                  cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(d);
+  if (!ok) return GRMHD_ERR_CUDA;
+  E.atmo = h;
+  E.atmo_set = 1;
+  return GRMHD_OK;
 }
 
 int eos_check(const grmhd_params& P, const grmhd_eos_table* T) {
