@@ -5,8 +5,8 @@ Only the tests, the smoke check and the benchmark's CPU-baseline leg use it;
 the product (the CUDA library and its binding) never imports this package.
 Arrays are numpy float64, C-contiguous, field-major (nf, n2+6, n1+6, px).
 
-Parity unpinned: the R^chi Z-term factor, kappa_2 and the damping, gauge and
-cleaning constants (see oracle.hpp); no closed form in the paper fixes them.
+Parity unpinned: kappa_2 and the damping, gauge and cleaning constants (see
+oracle.hpp): parameter values that no closed form in the paper fixes.
 """
 import ctypes
 import os

@@ -9,13 +9,12 @@
 // -ffp-contract=off.  It shares no code with the CUDA path; only the tests,
 // the smoke check and the benchmark's CPU-baseline leg may load it.
 //
-// Parity unpinned: the factor of the Z-term in the conformal Ricci part R^chi
-// (taken literally from Sec. II A), kappa_2 (named in the K and Theta
-// equations, never defined; 0 here) and the damping, gauge and cleaning
-// constants (kappa_z, kappa_c, eta, c_b, kappa_b; the paper bounds some and
-// fixes none).  No closed form in the paper fixes these terms or values, so
-// no pin can show that the reading taken is the paper's.  Every other
-// function is pinned by the tests.
+// Parity unpinned: kappa_2 (named in the K and Theta equations, never
+// defined; 0 here) and the damping, gauge and cleaning constants (kappa_z,
+// kappa_c, eta, c_b, kappa_b; the paper bounds some and fixes none): values,
+// not formulas, that no closed form in the paper fixes.  Every function is
+// pinned by the tests, the Z-term of the conformal Ricci part R^chi (taken
+// literally from Sec. II A) by the covariant Z4 identity it must reproduce.
 #pragma once
 #include <cstdint>
 #include "real.hpp"

@@ -10,7 +10,9 @@ Ricci split, D_i D_j alpha, the trace-free projection, the Lie-derivative and
 advection terms, and the A-products.  A static Kerr-Schild black hole pins the
 Gammahat equation (all of its terms act), a conformally flat metric pins
 R = -8 psi^-5 lap(psi), and flat space with constant gauge gives exact zeros.
-Errors must fall at 4th order with the grid spacing.
+With Gammahat^i moved off Gt^i (Z^i != 0), the Ricci split must give the Z4
+term R_ij + D_i Z_j + D_j Z_i of the physical metric, which pins the Z-term
+of R^chi_ij.  Errors must fall at 4th order with the grid spacing.
 """
 import numpy as np
 import sympy as sp
@@ -145,6 +147,47 @@ def test_ricci_tensor_matches_textbook():
         assert np.all(Z == 0.0)
         errs.append(np.concatenate([np.abs(R6 - _adm.six(Ac.Ric)[:, 0]), [abs(Rtr - Ac.R[0])],
                                     np.abs(Gt - Ac.Gt[:, 0])]))
+    errs = np.array(errs)
+    assert np.all(errs[0] / errs[1] > 11.0), errs
+    assert errs[1].max() < 1e-6
+
+
+def test_ricci_with_z_matches_covariant_z4_identity():
+    # With Z^i != 0 (Gammahat^i = Gt^i + V^i, so Z^i = chi V^i / 2) the
+    # combination Rhat_ij + R^chi_ij, built with Gammahat^i, is the Z4 Ricci
+    # term R_ij + D_i Z_j + D_j Z_i of the physical metric (Z_i = gamma_ij Z^j):
+    # this pins the Z-term of R^chi_ij against the covariant identity the
+    # conformal decomposition must reproduce.  The reference side uses exact
+    # derivatives; the oracle's 4th-order differences must converge to it.
+    V = [0.05 * sp.sin(x + 2 * y), 0.04 * sp.cos(y - z), 0.06 * sp.sin(z + 0.5 * x)]
+    Vf = [_adm.Field(e) for e in V]
+    center = (0.3, -0.2, 0.1)
+    n = 8
+    errs = []
+    for dx in (0.1, 0.05):
+        O, U, prim, rc, Ac, P = _patch(_generic, center, dx, n=n)
+        x0 = [c - (n // 2) * dx for c in center]
+        zz, yy, xx = synth.grid_coords((n, n, n), x0, dx)
+        shp = synth.patch_shape((n, n, n))
+        X3 = [np.broadcast_to(a, shp) for a in (xx, yy, zz)]
+        for a in range(3):
+            U[15 + a] += Vf[a].eval(*X3)[0]
+        R6, Rtr, Gt, Z = O.geom_point(U, prim, (n, n, n), dx, n // 2, n // 2, n // 2)
+        # Exact reference at the centre.
+        g, dg, gu, Gam = Ac.g[..., 0], Ac.dg[..., 0], Ac.gu[..., 0], Ac.Gam[..., 0]
+        chi = np.linalg.det(g) ** (-1.0 / 3.0)
+        dchi = -(1.0 / 3.0) * chi * np.einsum("ij,kij->k", gu, dg)
+        Vc = np.array([f.eval(*[np.array(v) for v in center])[0] for f in Vf])
+        dV = np.array([f.eval(*[np.array(v) for v in center])[1] for f in Vf]).T  # dV[i, k] = d_i V^k
+        Zu = 0.5 * chi * Vc
+        dZu = 0.5 * np.outer(dchi, Vc) + 0.5 * chi * dV  # d_i Z^k
+        Zl = g @ Zu
+        dZl = np.einsum("ijk,k->ij", dg, Zu) + np.einsum("jk,ik->ij", g, dZu)  # d_i Z_j
+        DZ = dZl - np.einsum("kij,k->ij", Gam, Zl)  # D_i Z_j
+        want = Ac.Ric[..., 0] + DZ + DZ.T
+        assert np.allclose(Z, Zu, rtol=0, atol=1e-10 + 1e-3 * dx ** 2)
+        errs.append(np.concatenate([np.abs(R6 - _adm.six(want)),
+                                    [abs(Rtr - np.einsum("ij,ij->", gu, want))]]))
     errs = np.array(errs)
     assert np.all(errs[0] / errs[1] > 11.0), errs
     assert errs[1].max() < 1e-6
