@@ -262,7 +262,7 @@ static Geo geo_of(const grmhd_patch_desc& d) {
   G.i12 = 1.0 / (12.0 * G.dx);
   G.i12s = 1.0 / (12.0 * G.dx * G.dx);
   G.i144 = 1.0 / (144.0 * G.dx * G.dx);
-  G.idx = 1.0 / G.dx;
+  G.ihdx = 0.5 / G.dx;
   return G;
 }
 

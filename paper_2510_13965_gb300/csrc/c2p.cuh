@@ -298,7 +298,9 @@ DI void prim2con(const double gdd[6], double rho, double eps, double p, const do
   double Bv = B[0] * vd[0] + B[1] * vd[1] + B[2] * vd[2];
   double iW2 = 1.0 - v2;
   double W = rsqrt(iW2);
-  double W2 = 1.0 / iW2;
+  // 1 / iW2, with the quotient at rest (v = 0: atmosphere points) taken
+  // without the division sequence (1 / 1 is exactly 1).
+  double W2 = iW2 == 1.0 ? 1.0 : 1.0 / iW2;
   double h = fma(rho, 1.0 + eps, p);
   double D = rho * W;
   double hW2 = h * W2;
@@ -439,6 +441,7 @@ struct C2POut {
   int iters;       // evaluations of f_a and of the master function
   int seeded;      // bit 0: seed usable; bit 1: master bracket from the seed; bit 2: mu_+ not solved
   double mu_plus, mu, W_root;  // roots and W at mu (0 unless the root finds converged; mu_+ 0 if not solved)
+  double isg;                  // 1 / sqrt(gamma), for the caller's flux epilogue
 };
 
 // con2prim at one point (appendix "Conversion from conserved to primitive
@@ -452,13 +455,14 @@ DI void c2p_point(const grmhd_params& P, const Eos& E, const double cb[9], const
   o.iters = 0;
   o.seeded = 0;
   o.mu_plus = o.mu = o.W_root = 0.0;
+  const double isg = 1.0 / sg;
+  o.isg = isg;
   bool finite = isfinite(sg) && sg > 0.0;
   for (int n = 0; n < 9; ++n) finite = finite && isfinite(cb[n]);
   if (!finite) {
     o.status = -5;
     return;
   }
-  double isg = 1.0 / sg;
   double D = cb[0] * isg;
   double B[3] = {cb[6] * isg, cb[7] * isg, cb[8] * isg};
   int status = 0;

@@ -35,7 +35,7 @@ struct Geo {
   int n0, n1, n2, px;
   long long sy, sz, sf;  // strides (x stride 1)
   double dx;
-  double i12, i12s, i144, idx;  // 1/(12 dx), 1/(12 dx^2), 1/(144 dx^2), 1/dx
+  double i12, i12s, i144, ihdx;  // 1/(12 dx), 1/(12 dx^2), 1/(144 dx^2), 1/(2 dx)
 };
 
 DI long long at(const Geo& G, int i, int j, int k) {

@@ -280,7 +280,7 @@ DI void c2p_item(const PatchDev* __restrict__ pd, const Work wk, int reg, const 
     if (need[0] || need[1] || need[2]) {
       const double* pr = r.prim;
       double v[3] = {pr[VX], pr[VY], pr[VZ]};
-      double isg = 1.0 / sg;
+      const double isg = r.isg;  // 1 / sg, formed once by c2p_point
       double B[3] = {cb[6] * isg, cb[7] * isg, cb[8] * isg};
       double Sl[3] = {cb[3] * isg, cb[4] * isg, cb[5] * isg};
       double vd[3], Bd[3];
@@ -290,7 +290,9 @@ DI void c2p_item(const PatchDev* __restrict__ pd, const Work wk, int reg, const 
       double B2 = B[0] * Bd[0] + B[1] * Bd[1] + B[2] * Bd[2];
       double Bv = B[0] * vd[0] + B[1] * vd[1] + B[2] * vd[2];
       double W = pr[WW];
-      double iW2 = 1.0 / (W * W);
+      // At rest (W = 1, v = 0: atmosphere points) the quotients 1 / W^2 and
+      // al / den are exact without their division sequences.
+      double iW2 = W == 1.0 ? 1.0 : 1.0 / (W * W);
       double piso = pr[PRS] + 0.5 * fma(iW2, B2, Bv * Bv);
       double Sij[6];
 #pragma unroll
@@ -305,11 +307,11 @@ DI void c2p_item(const PatchDev* __restrict__ pd, const Work wk, int reg, const 
       double phib = U[PHI * sf + o];
       double b2 = fma(B2, iW2, Bv * Bv);
       double h = fma(pr[RHO], 1.0 + pr[EPS], pr[PRS]);
-      double ca2 = b2 / (h + b2);
+      double ca2 = b2 == 0.0 ? 0.0 : b2 / (h + b2);  // no field (the atmosphere outside a star): exactly 0
       double cs2 = pr[CS2];
       double a2 = cs2 + ca2 - cs2 * ca2;
       double den = fma(-v2, a2, 1.0);
-      double pre = al / den;
+      double pre = den == 1.0 ? al : al / den;
       double a2w = a2 * (1.0 - v2);
       double oma2 = 1.0 - a2;
       const double cb2 = P.c_b * P.c_b;

@@ -113,7 +113,7 @@ extern "C" int grmhd_rhs_eval_static(const grmhd_params* p, const grmhd_patch_de
   G.i12 = 1.0 / (12.0 * G.dx);
   G.i12s = 1.0 / (12.0 * G.dx * G.dx);
   G.i144 = 1.0 / (144.0 * G.dx * G.dx);
-  G.idx = 1.0 / G.dx;
+  G.ihdx = 0.5 / G.dx;
   if (G.sf > kMaxPoints) return GRMHD_ERR_SIZE;
 
   Blocks b;

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(BS) k_rhs(const PatchDev* __restrict__ pd, con
 
   // ---- MHD: flux divergence and sources -------------------------------------------
   {
-    const double idx = 0.5 * G.idx;  // the interface arrays hold 2 Fhat
+    const double idx = G.ihdx;  // 1/(2 dx): the interface arrays hold 2 Fhat
 #pragma unroll
     for (int n = 0; n < 10; ++n) r[NST + n] = 0.0;
 #pragma unroll
