@@ -9,12 +9,13 @@
 // -ffp-contract=off.  It shares no code with the CUDA path; only the tests,
 // the smoke check and the benchmark's CPU-baseline leg may load it.
 //
-// Parity unpinned: kappa_2 (named in the K and Theta equations, never
-// defined; 0 here) and the damping, gauge and cleaning constants (kappa_z,
-// kappa_c, eta, c_b, kappa_b; the paper bounds some and fixes none): values,
-// not formulas, that no closed form in the paper fixes.  Every function is
-// pinned by the tests, the Z-term of the conformal Ricci part R^chi (taken
-// literally from Sec. II A) by the covariant Z4 identity it must reproduce.
+// Parity unpinned: the value of kappa_2 (named in the K and Theta equations,
+// never defined; 0 here) and of the damping, gauge and cleaning constants
+// (kappa_z, kappa_c, eta, c_b, kappa_b; the paper bounds some and fixes
+// none): values, not formulas, that no closed form in the paper fixes.  Every
+// function is pinned by the tests: the Z-term of the conformal Ricci part
+// R^chi (taken literally from Sec. II A) and every Theta, Z and kappa_2 term
+// of the spacetime equations by the covariant Z4 system they must reproduce.
 #pragma once
 #include <cstdint>
 #include "real.hpp"

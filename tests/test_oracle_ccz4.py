@@ -12,9 +12,13 @@ Gammahat equation (all of its terms act), a conformally flat metric pins
 R = -8 psi^-5 lap(psi), and flat space with constant gauge gives exact zeros.
 With Gammahat^i moved off Gt^i (Z^i != 0), the Ricci split must give the Z4
 term R_ij + D_i Z_j + D_j Z_i of the physical metric, which pins the Z-term
-of R^chi_ij.  Errors must fall at 4th order with the grid spacing.
+of R^chi_ij; with Theta != 0 as well, every spacetime right-hand side must be
+the covariant Z4 system with its kappa_z damping written in the CCZ4
+variables (kappa_2 = 0 and 0.3), which pins every Theta and Z term.
+Errors must fall at 4th order with the grid spacing.
 """
 import numpy as np
+import pytest
 import sympy as sp
 
 import oracle
@@ -190,6 +194,115 @@ def test_ricci_with_z_matches_covariant_z4_identity():
                                     [abs(Rtr - np.einsum("ij,ij->", gu, want))]]))
     errs = np.array(errs)
     assert np.all(errs[0] / errs[1] > 11.0), errs
+    assert errs[1].max() < 1e-6
+
+
+def _z4_fields(center, dx, n, V, Th, params=None):
+    """The generic vacuum data with Theta != 0 (Khat = K - 2 Theta) and
+    Gammahat^i = Gt^i + V^i (Z^i = chi V^i / 2): the oracle's right-hand side
+    at the centre, and the reference quantities there."""
+    O, U, prim, _, Ac, P = _patch(_generic, center, dx, n=n, params=params)
+    x0 = [c - (n // 2) * dx for c in center]
+    zz, yy, xx = synth.grid_coords((n, n, n), x0, dx)
+    shp = synth.patch_shape((n, n, n))
+    X3 = [np.broadcast_to(a, shp) for a in (xx, yy, zz)]
+    th = Th.eval(*X3)[0]
+    U[14] = th
+    U[13] -= 2.0 * th
+    for a in range(3):
+        U[15 + a] += V[a].eval(*X3)[0]
+    rhs = O.rhs_patch(U, prim, (n, n, n), dx)
+    c = n // 2 + 3
+    return rhs[:, c, c, c], Ac, P
+
+
+def _z4_expected(Ac, P, center, V, Th):
+    """The covariant Z4 system (vacuum, damping kappa_z (n_a Z_b + n_b Z_a -
+    g_ab n^c Z_c)) in 3+1 form, mapped to the CCZ4 variables: d_t of
+    gt_ij, At_ij, chi, Khat = K - 2 Theta, Theta, alpha, beta^i."""
+    pt = [np.array(v) for v in center]
+    g, dg, gu, Gam = Ac.g[..., 0], Ac.dg[..., 0], Ac.gu[..., 0], Ac.Gam[..., 0]
+    K, trK, al, dal, be = Ac.K[..., 0], Ac.trK[0], Ac.al[0], Ac.dal[:, 0], Ac.be[:, 0]
+    chi = np.linalg.det(g) ** (-1.0 / 3.0)
+    dchi = -(1.0 / 3.0) * chi * np.einsum("ij,kij->k", gu, dg)
+    Vc = np.array([f.eval(*pt)[0] for f in V])
+    dV = np.array([f.eval(*pt)[1] for f in V]).T  # dV[i, k] = d_i V^k
+    th, dth = Th.eval(*pt)[0], Th.eval(*pt)[1]
+    Zu = 0.5 * chi * Vc
+    dZu = 0.5 * np.outer(dchi, Vc) + 0.5 * chi * dV
+    Zl = g @ Zu
+    dZl = np.einsum("ijk,k->ij", dg, Zu) + np.einsum("jk,ik->ij", g, dZu)
+    DZ = dZl - np.einsum("kij,k->ij", Gam, Zl)  # D_i Z_j
+    divZ = np.einsum("ij,ij->", gu, DZ)
+    k1, k2 = P["kappa_z"], P["kappa_2"]
+    KK = np.einsum("ik,jl,kl,ij->", gu, gu, K, K)
+    R = Ac.R[0]
+    # (d_t - L_beta) K_ij = ADM + alpha [2 D_(i Z_j) - 2 Theta K_ij - k1 (1 + k2) Theta gamma_ij]
+    dtK = Ac.dt_K[..., 0] + al * (DZ + DZ.T - 2.0 * th * K - k1 * (1.0 + k2) * th * g)
+    dtTh = be @ dth + 0.5 * al * (R + 2.0 * divZ + (trK - 2.0 * th) * trK - KK - 2.0 * (Zu @ dal) / al
+                                  - 2.0 * k1 * (2.0 + k2) * th)
+    dtg = Ac.dt_g[..., 0]
+    dt_trK = np.einsum("ij,ij->", gu, dtK) - np.einsum("ik,jl,kl,ij->", gu, gu, K, dtg)
+    dt_chi = -(chi / 3.0) * np.einsum("ij,ij->", gu, dtg)
+    gt = chi * g
+    dt_gt = dt_chi * g + chi * dtg
+    dt_At = dt_chi * K + chi * dtK - (dt_gt * trK + gt * dt_trK) / 3.0
+    e = np.full(NF, np.nan)
+    e[0:6] = _adm.six(dt_gt)
+    e[6:12] = _adm.six(dt_At)
+    e[12] = dt_chi
+    e[13] = dt_trK - 2.0 * dtTh
+    e[14] = dtTh
+    # Gammahat^i = Gt^i + 2 gt^ij Z_j: d_t Gt^i from the spatial derivatives of
+    # d_t gt_jk, and (d_t - L_beta) Z_i = alpha [D_j (K^j_i - delta^j_i K)
+    # + d_i Theta - 2 K_i^j Z_j - Theta d_i alpha / alpha - kappa_z Z_i].
+    dK, ddg, dbe, ddbe = Ac.dK[..., 0], Ac.ddg[..., 0], Ac.dbe[..., 0], Ac.ddbe[..., 0]
+    d_dtg = (-2.0 * (np.einsum("l,jk->ljk", dal, K) + al * dK) + np.einsum("lm,mjk->ljk", dbe, dg)
+             + np.einsum("m,lmjk->ljk", be, ddg) + np.einsum("lmk,jm->ljk", dg, dbe)
+             + np.einsum("mk,ljm->ljk", g, ddbe) + np.einsum("ljm,km->ljk", dg, dbe)
+             + np.einsum("jm,lkm->ljk", g, ddbe))
+    dgu = -np.einsum("ac,lcd,db->lab", gu, dg, gu)
+    d_dtchi = -(1.0 / 3.0) * (dchi * np.einsum("ab,ab->", gu, dtg) + chi * np.einsum("lab,ab->l", dgu, dtg)
+                              + chi * np.einsum("ab,lab->l", gu, d_dtg))
+    dgt = np.einsum("l,jk->ljk", dchi, g) + chi * dg
+    d_dtgt = (np.einsum("l,jk->ljk", d_dtchi, g) + dt_chi * dg + np.einsum("l,jk->ljk", dchi, dtg)
+              + chi * d_dtg)
+    gtu = gu / chi
+    dtgtu = -gtu @ dt_gt @ gtu
+    dtGt = (np.einsum("ij,kl,ljk->i", dtgtu, gtu, dgt) + np.einsum("ij,kl,ljk->i", gtu, dtgtu, dgt)
+            + np.einsum("ij,kl,ljk->i", gtu, gtu, d_dtgt))
+    DK = dK - np.einsum("mjk,mi->jki", Gam, K) - np.einsum("mji,km->jki", Gam, K)  # D_j K_ki
+    divK = np.einsum("jk,jki->i", gu, DK)
+    dtrK = np.einsum("iab,ab->i", dgu, K) + np.einsum("ab,iab->i", gu, dK)
+    KZ = K @ gu @ Zl
+    dtZl = (np.einsum("j,ji->i", be, dZl) + np.einsum("j,ij->i", Zl, dbe)
+            + al * (divK - dtrK + dth - 2.0 * KZ - th * dal / al - k1 * Zl))
+    e[15:18] = dtGt + 2.0 * dtgtu @ Zl + 2.0 * gtu @ dtZl
+    Khat = trK - 2.0 * th
+    e[18] = be @ dal - 2.0 * al * Khat
+    Gh = Ac.Gt[:, 0] + Vc
+    e[19:22] = Ac.dbe[:, :, 0].T @ be + 0.75 * Gh - P["eta"] * be
+    return e
+
+
+@pytest.mark.parametrize("kappa_2", [0.0, 0.3])
+def test_theta_and_z_terms_match_covariant_z4_system(kappa_2):
+    # Theta != 0 and Z^i != 0: the oracle's CCZ4 right-hand sides of all 22
+    # spacetime fields must be the covariant Z4 system with its kappa_z
+    # damping (Sec. II A) written in the CCZ4 variables, Gammahat^i included.
+    # This pins every Theta and Z term of the equations.
+    V = [_adm.Field(e) for e in (0.05 * sp.sin(x + 2 * y), 0.04 * sp.cos(y - z), 0.06 * sp.sin(z + 0.5 * x))]
+    Th = _adm.Field(0.01 + 0.02 * sp.sin(x - y + 0.5 * z))
+    center = (0.3, -0.2, 0.1)
+    fields = list(range(0, 22))
+    errs = []
+    for dx in (0.05, 0.025):  # Khat's error is pre-asymptotic at 0.1 (ratio 9.8 to 0.05)
+        rc, Ac, P = _z4_fields(center, dx, 8, V, Th, params=synth.ideal_params(bc=1, kappa_2=kappa_2))
+        e = _z4_expected(Ac, P, center, V, Th)
+        errs.append(np.abs(rc[fields] - e[fields]))
+    errs = np.array(errs)
+    ratio = errs[0] / np.maximum(errs[1], 1e-300)
+    assert np.all((ratio > 11.0) | (errs[1] < 1e-11)), (ratio, errs)
     assert errs[1].max() < 1e-6
 
 
