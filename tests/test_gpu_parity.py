@@ -91,6 +91,37 @@ def test_init_con2prim_rhs_parity(case):
     assert ok, bad
 
 
+@pytest.mark.parametrize("case", ["fourier_periodic_32", "tov_40"])
+def test_rhs_parity_with_theta_and_z(case):
+    """Constraint-violating states: Theta != 0 and Gammahat^i off Gt^i
+    (Z^i != 0), so every Theta and Z term of the spacetime equations (pinned
+    in the oracle against the covariant Z4 system) acts; con2prim and the
+    right-hand side from the identical state against the oracle."""
+    P, n, dx, ID = CASES[case]()
+    pt, O, U = _setup(P, n, dx, ID)
+    pt.synchronize()
+    # smooth fields with one to two wavelengths across the patch
+    k, j, i = np.meshgrid(*(np.arange(m) / m for m in U.shape[1:]), indexing="ij")
+    th = 0.01 * np.sin(2 * np.pi * (i + 2 * j - k)) + 0.005
+    U = U.copy()
+    U[14] += th
+    U[13] -= 2.0 * th
+    U[15] += 0.03 * np.cos(2 * np.pi * (i - j))
+    U[16] += 0.02 * np.sin(2 * np.pi * (j + k))
+    U[17] += 0.04 * np.cos(2 * np.pi * (k + 2 * i))
+    _upload(pt, U)
+    pt.con2prim(0)
+    rhs_g = pt.rhs_eval(0)[0]
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    Uo = U.copy()
+    prim_o, st_o, _, _ = O.con2prim_patch(Uo, n)
+    assert np.array_equal(pt.status[0].cpu().numpy(), st_o)
+    rhs_o = O.rhs_patch(Uo, prim_o, n, dx)
+    ok, bad = _rhs_ok(_interior(rhs_g.cpu().numpy(), n), _interior(rhs_o, n), O, U, n, dx)
+    assert ok, bad
+
+
 def test_flat_space_constant_gauge_exact_zero_on_gpu():
     P = synth.ideal_params(bc=0, eta=0.0)
     n = (8, 8, 8)
