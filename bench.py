@@ -259,25 +259,33 @@ def cpu_baseline_c2p(n=1 << 19):
 
 def cpu_baseline_amr(scale=0.25):
     """One RK4 step of the hierarchy workload at a reduced scale on the oracle
-    (serial; every level at the finest time step, restriction at the end)."""
+    (every level at the finest time step, restriction at the end): its OpenMP
+    build on all host cores (the value), the serial build on one core beside it."""
     import oracle
     import synth
     table = synth.make_table()
     P = synth.table_params(table, bc=3)
     specs = synth.amr_tov_layout(scale=scale)
     prof = synth.tov_profile()
-    H = oracle.Hierarchy(oracle.Oracle(P, table), specs)
-    for q, s_ in enumerate(specs):
-        H.init_state(q, synth.tov_id(n=s_["n"], x0=s_["x0"], dx=s_["dx"], seed=4000 + q, table=table,
-                                     rho_atmo=P["rho_atmo"], profile=prof))
-    H.restrict(0)
+    ids = [synth.tov_id(n=s_["n"], x0=s_["x0"], dx=s_["dx"], seed=4000 + q, table=table,
+                        rho_atmo=P["rho_atmo"], profile=prof) for q, s_ in enumerate(specs)]
     zones = int(sum(np.prod(s_["n"]) for s_ in specs))
-    t0 = time.perf_counter()
-    H.rk4_step(0.25 * min(s_["dx"] for s_ in specs))
-    el = time.perf_counter() - t0
-    return {"value": zones / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "one RK4 step of the %d-patch hierarchy at scale %g (%d interior points), serial C++ "
-                      "oracle, %.1f s" % (len(specs), scale, zones, el)}
+    res = {}
+    for threads in (0, None):
+        O = oracle.Oracle(P, table, threads=threads)
+        H = oracle.Hierarchy(O, specs)
+        for q, ID in enumerate(ids):
+            H.init_state(q, ID)
+        H.restrict(0)
+        t0 = time.perf_counter()
+        H.rk4_step(0.25 * min(s_["dx"] for s_ in specs))
+        el = time.perf_counter() - t0
+        res[threads] = (zones / el, el, getattr(O, "threads", 1))
+    v, el, cores = res[0]
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "one RK4 step of the %d-patch hierarchy at scale %g (%d interior points), the C++ "
+                      "oracle's OpenMP build on %d host threads, %.1f s" % (len(specs), scale, zones, cores, el),
+            "serial_1_core": {"value": res[None][0], "seconds": res[None][1]}}
 
 
 def run_reference(args):
