@@ -374,3 +374,42 @@ def test_full_size_con2prim_all_states():
     po, so, _ = O.c2p_flat(cons)
     for p_, s_ in ((pg, sg), (ps, ss)):
         prim_check(p_.T, po.T, s_, so, cons[:, :3].T)
+
+
+@pytest.mark.parametrize("x0", [(30.0, 30.0, 30.0), (6.0, -8.0, -8.0)], ids=["all_atmosphere", "star_edge"])
+def test_seeded_patch_with_few_or_no_points_to_solve(table_setup, x0):
+    """Patch seeding lists the points to solve and runs the network on them:
+    a patch of atmosphere only (an empty list: every network block returns
+    before its set-up) and one at the star's edge (a partial tile).  Statuses
+    equal the oracle's and the primitives are within the con2prim bounds; the
+    atmosphere points, which take no seed, are bitwise the plain results."""
+    table, P0, O0, T = table_setup
+    P = synth.table_params(table, bc=1)
+    n, dx = (16, 16, 16), 1.0
+    ID = synth.tov_id(n=n, x0=x0, dx=dx, seed=5, table=table, rho_atmo=P["rho_atmo"])
+    O = oracle.Oracle(P, table)
+    U = O.init_state(ID, n, dx)
+    S = g.Seeder(seed=4)
+    res = {}
+    for seeded in (False, True):
+        pt = g.Patches(P, [dict(n=n, dx=dx, x0=x0)], table=T)
+        pt.U[0][0].copy_(torch.as_tensor(U, device="cuda"))
+        torch.cuda.synchronize()
+        if seeded:
+            pt.set_seeder(S, 3e-2)
+        pt.con2prim(0)
+        pt.synchronize()
+        assert pt.sync_status() == 0
+        res[seeded] = (pt.prim[0].cpu().numpy(), pt.status[0].cpu().numpy())
+    Uo = U.copy()
+    po, so, _, _ = O.con2prim_patch(Uo, n)
+    for seeded in (False, True):
+        pg, sg = res[seeded]
+        prim_check(pg.reshape(NP, -1), po.reshape(NP, -1), sg.reshape(-1), so.reshape(-1),
+                   Uo[22:25].reshape(3, -1))
+    atmo = so == 1
+    assert np.array_equal(res[True][0][:, atmo], res[False][0][:, atmo])
+    if x0[0] > 20.0:
+        assert np.all(atmo)
+    else:
+        assert 0 < np.count_nonzero(~atmo) < atmo.size
