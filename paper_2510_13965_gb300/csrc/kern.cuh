@@ -201,6 +201,14 @@ void launch_rhs(const PatchDev* pd_dev, const Work* w, int nblk, int reg, int mo
 void launch_ghost_copy(const PatchDev* pd_dev, const Work* w, int nblk, int reg, cudaStream_t st);
 void launch_rk(const PatchDev* pd_dev, const Work* w, int nblk, int stage, double dt, double* const* rhs_dev,
                cudaStream_t st, int rk = 0);
+// Flat-state con2prim processing order grouped by the binary exponent of
+// B^2 / D (a counting sort on the device into stream-ordered memory), or null
+// below ORDER_MIN_STATES states (or when the memory is not available: the
+// states are then solved in the given order).  Free with c2p_flat_order_free
+// on the same stream after the solve's launch.
+constexpr long long ORDER_MIN_STATES = 1 << 16;
+int32_t* c2p_flat_order(long long n, const double* cons, cudaStream_t st);
+void c2p_flat_order_free(int32_t* order, cudaStream_t st);
 void launch_c2p_flat(const grmhd_params& P, const Eos& E, long long n, const double* cons, double* prim,
                      int8_t* status, int32_t* iters, cudaStream_t st);
 void launch_prim2con_flat(const grmhd_params& P, const Eos& E, long long n, const double* prim, const double* B,

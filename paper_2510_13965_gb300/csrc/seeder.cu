@@ -1100,9 +1100,11 @@ __global__ void __launch_bounds__(128) k_c2p_flat_seeded(grmhd_params P, Eos E, 
                                                           const double* __restrict__ seeds, double delta,
                                                           double* __restrict__ prim, int8_t* __restrict__ status,
                                                           int32_t* __restrict__ iters, double* __restrict__ roots,
-                                                          int8_t* __restrict__ seeded) {
+                                                          int8_t* __restrict__ seeded,
+                                                          const int32_t* __restrict__ order) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= n) return;
+  if (order) q = order[q];  // thread i solves state order[i]
   const double g[6] = {1.0, 0.0, 0.0, 1.0, 0.0, 1.0};
   double cb[9];
   for (int m = 0; m < 9; ++m) cb[m] = ld(cons + q * 10 + m);
@@ -1436,8 +1438,11 @@ int grmhd_c2p_flat_seeded(const grmhd_params* p, const grmhd_eos_table* eos, lon
   if (p->max_iter < 1 || !(p->h0 > 0.0)) return GRMHD_ERR_ARG;
   if (seeds && !(delta > 0.0 && delta < 1.0)) return GRMHD_ERR_ARG;
   if (n == 0) return GRMHD_OK;
-  k_c2p_flat_seeded<<<grid_of(n, 128), 128, 0, (cudaStream_t)stream>>>(*p, make_eos(*p, eos), n, cons, seeds, delta,
-                                                                       prim, status, iters, roots, seeded);
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* order = c2p_flat_order(n, cons, st);
+  k_c2p_flat_seeded<<<grid_of(n, 128), 128, 0, st>>>(*p, make_eos(*p, eos), n, cons, seeds, delta, prim, status,
+                                                      iters, roots, seeded, order);
+  c2p_flat_order_free(order, st);
   return last_rc();
 }
 

@@ -413,3 +413,30 @@ def test_seeded_patch_with_few_or_no_points_to_solve(table_setup, x0):
         assert np.all(atmo)
     else:
         assert 0 < np.count_nonzero(~atmo) < atmo.size
+
+
+def test_flat_con2prim_order_changes_no_result(table_setup):
+    """From 2^16 states on, the flat con2prim solves the states grouped by the
+    binary exponent of B^2 / D (a counting sort on the device) so that warps
+    hold states of similar evaluation counts.  Every state's arithmetic is
+    unchanged: 2^17 states in one call (grouped) equal the same states in
+    four calls of 2^15 (given order) bit for bit, plain and seeded."""
+    table, P0, O0, T = table_setup
+    P = synth.table_params(table)
+    n = 1 << 17
+    cons = torch.as_tensor(_flat_cons_numpy(n, seed=11), device="cuda")
+    parts = [cons[k * (n // 4):(k + 1) * (n // 4)].contiguous() for k in range(4)]
+    whole = g.c2p_flat(P, cons, table=T, iters=True)
+    split = [g.c2p_flat(P, c, table=T, iters=True) for c in parts]
+    for a, b in zip(whole, (torch.cat([s[i] for s in split]) for i in range(3))):
+        assert torch.equal(a, b)
+    # Seeded: perturbed roots of the plain solve as seeds.
+    _, _, _, roots, _ = g.c2p_flat_seeded(P, cons, None, table=T)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    seeds = roots * (1.0 + 0.02 * (torch.rand(roots.shape, device="cuda", generator=gen, dtype=torch.float64) - 0.5))
+    whole = g.c2p_flat_seeded(P, cons, seeds, 0.03, table=T)
+    split = [g.c2p_flat_seeded(P, parts[k], seeds[k * (n // 4):(k + 1) * (n // 4)].contiguous(), 0.03, table=T)
+             for k in range(4)]
+    for i in range(5):
+        assert torch.equal(whole[i], torch.cat([s[i] for s in split])), i
+    assert torch.count_nonzero(whole[4]) > 0  # seed brackets were used
