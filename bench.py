@@ -43,9 +43,9 @@ RHS_FLOPS_PER_POINT = 6724.0
 RK_FLOPS_PER_POINT = (128.0 * 3 + 64.0) / 4.0
 # DRAM bytes (read + write) per interior point of one k_rhs launch, from the
 # ncu capture in profiles/launch_list_tov128.md (64^3 case, k_rhs<1, 128, 0>,
-# 204.49 + 303.53 MB over 262,144 points), scaled to a launch by its points;
+# 192.53 + 208.27 MB over 262,144 points), scaled to a launch by its points;
 # set to None whenever k_rhs changes until it is captured again.
-RHS_TRAFFIC_BYTES_PER_POINT = (204.493824e6 + 303.534592e6) / 64 ** 3
+RHS_TRAFFIC_BYTES_PER_POINT = (192.530176e6 + 208.266752e6) / 64 ** 3
 # FP64 peak derived from the unit counts and clocks: 152 SMs x 4 FP64 flops per
 # clock per SM x 2070 MHz (nominal GB300 FP64 1.25 TFLOP/s = 152 x 2.07 GHz x 3.97).
 # The line's peak is the measured one (the library's FMA throughput probe,
