@@ -122,6 +122,26 @@ def test_rhs_parity_with_theta_and_z(case):
     assert ok, bad
 
 
+@pytest.mark.parametrize("edge", [32, 128])
+def test_periodic_conserved_rhs_telescopes(edge):
+    """D and DYe are conserved: their right-hand sides are differences of the
+    interface fluxes, which each neighbour shares, so over a periodic box
+    they sum to zero but for the rounding of the differences (a property at
+    any size; 128^3 is the headline workload's size)."""
+    P = synth.ideal_params(bc=0)
+    n, dx = (edge,) * 3, 1.0 / edge
+    pt = g.Patches(P, [dict(n=n, dx=dx)])
+    pt.init_state(0, torch.as_tensor(synth.config0_id(n=n, seed=2), device="cuda"))
+    pt.con2prim(0)
+    r = pt.rhs_eval(0)[0]
+    pt.synchronize()
+    assert pt.sync_status() == 0
+    for f in (22, 23):
+        v = r[f][3:3 + edge, 3:3 + edge, 3:3 + edge].double()
+        total, scale = float(v.sum()), float(v.abs().sum())
+        assert scale > 0.0 and abs(total) <= 1e-12 * scale, (f, total, scale)
+
+
 def test_flat_space_constant_gauge_exact_zero_on_gpu():
     P = synth.ideal_params(bc=0, eta=0.0)
     n = (8, 8, 8)
