@@ -211,14 +211,18 @@ def test_every_schedule_gives_the_same_result_bitwise(layout):
             assert torch.equal(runs[0].prim[q], pt.prim[q]), q
 
 
-def test_scaled_star_hierarchy_steps_match_oracle():
+@pytest.mark.parametrize("seeded", [False, True], ids=["plain", "nn_seeded"])
+def test_scaled_star_hierarchy_steps_match_oracle(seeded):
     """Config 4 at scale 0.25 (the magnetised star with the synthetic table on
     5 levels, 13 patches, 0.49 M interior points): 20 synchronous RK4 steps on
     the GPU through a CUDA graph against the oracle's OpenMP build (bitwise the
     serial oracle) from the identical state, and the oracle's twin from a
     1e-14-perturbed start, the problem's rounding sensitivity (reading A26).
     Per field over all patches (a field spans the hierarchy, reading A44):
-    max |gpu - oracle| / max |oracle| within max(1e-9, 10 x the twin's drift)."""
+    max |gpu - oracle| / max |oracle| within max(1e-9, 10 x the twin's drift).
+    The NN-seeded variant runs the patch seeding (atmosphere scan, network on
+    the listed points) and the seeded con2prim in every substep of the graph
+    against the oracle's plain con2prim."""
     table = synth.make_table()
     P = synth.table_params(table, bc=3)
     specs = synth.amr_tov_layout(scale=0.25)
@@ -232,8 +236,22 @@ def test_scaled_star_hierarchy_steps_match_oracle():
     rng = np.random.default_rng(7)
     for q in range(len(specs)):
         Ht.U[0][q][...] = H.U[0][q] * (1.0 + 1e-14 * rng.uniform(-1.0, 1.0, H.U[0][q].shape))
-    pt = g.Patches(P, specs, table=g.Table(table))
+    T = g.Table(table)
+    pt = g.Patches(P, specs, table=T)
     _upload_all(pt, H, reg=0)
+    if seeded:
+        st_ = synth.c2p_states(1 << 16, seed=13)
+        prim = np.zeros((1 << 16, 10))
+        prim[:, 0], prim[:, 7], prim[:, 8] = st_["rho"], st_["ye"], st_["T"]
+        prim[:, 3:6] = st_["v"]
+        cons = g.prim2con_flat(P, torch.as_tensor(prim, device="cuda"), torch.as_tensor(st_["B"], device="cuda"),
+                               table=T)
+        _, s0, _, roots, _ = g.c2p_flat_seeded(P, cons, None, table=T)
+        keep = s0 >= 0
+        S = g.Seeder(seed=2)
+        S.train(g.seeder_features(cons)[keep].contiguous(), g.seeder_targets(cons, roots)[keep].contiguous(),
+                batch=1024, epochs=8, lr=3e-3, lr_final=3e-5)
+        pt.set_seeder(S, 3e-2)
     dt = 0.25 * min(s["dx"] for s in specs)
     pt.capture_graph(1, dt)
     for _ in range(20):
@@ -251,7 +269,8 @@ def test_scaled_star_hierarchy_steps_match_oracle():
         d_gpu = np.maximum(d_gpu, np.abs(got - want).max(axis=1))
         d_twin = np.maximum(d_twin, np.abs(twin - want).max(axis=1))
     e_gpu, e_twin = d_gpu / np.maximum(scale, 1e-300), d_twin / np.maximum(scale, 1e-300)
-    print("scaled star hierarchy, 20 steps: max over fields GPU %.3g, twin %.3g" % (e_gpu.max(), e_twin.max()))
+    print("scaled star hierarchy (%s), 20 steps: max over fields GPU %.3g, twin %.3g"
+          % ("seeded" if seeded else "plain", e_gpu.max(), e_twin.max()))
     bad = {f: (e_gpu[f], e_twin[f]) for f in range(NF) if not e_gpu[f] <= max(1e-9, 10.0 * e_twin[f])}
     assert not bad, bad
 
