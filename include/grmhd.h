@@ -385,7 +385,12 @@ int grmhd_prim2con_flat(const grmhd_params* p, const grmhd_eos_table* eos, long 
 
 /* con2prim of n states with a flat metric (the isolated recovery workload).
  * cons: device [n][10]; prim: device [n][10]; status: device [n];
- * iters: device [n] or NULL. */
+ * iters: device [n] or NULL.  From 2^16 states on, the states are solved in
+ * an order grouped by the binary exponent of B^2 / D (warps then hold states
+ * of similar root-finder cost); the order is a counting sort on the device
+ * into n + 128 ints of stream-ordered scratch (cudaMallocAsync on `stream`,
+ * freed after the solve's launch; if it cannot be had, the given order is
+ * used).  Every state's result is independent of the order, bit for bit. */
 int grmhd_c2p_flat(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
                    double* prim, int8_t* status, int32_t* iters, void* stream);
 
@@ -652,7 +657,8 @@ int grmhd_set_seeder(grmhd_ctx* ctx, const grmhd_seeder* s, double delta);
  * receives (mu_+, mu, W at mu), zeros where a root find failed and mu_+ = 0
  * when it was not solved; seeded (device int8 [n] or NULL): bit 0 the mu_+
  * seed bracket was used, bit 1 the mu seed bracket, bit 2 mu_+ was not solved.
- * The third seed (W) is not used. */
+ * The third seed (W) is not used.  The processing order and its scratch are
+ * those of grmhd_c2p_flat. */
 int grmhd_c2p_flat_seeded(const grmhd_params* p, const grmhd_eos_table* eos, long long n, const double* cons,
                           const double* seeds, double delta, double* prim, int8_t* status, int32_t* iters,
                           double* roots, int8_t* seeded, void* stream);
