@@ -95,7 +95,8 @@ def test_init_con2prim_rhs_parity(case):
 def test_rhs_parity_with_theta_and_z(case):
     """Constraint-violating states: Theta != 0 and Gammahat^i off Gt^i
     (Z^i != 0), so every Theta and Z term of the spacetime equations (pinned
-    in the oracle against the covariant Z4 system) acts; con2prim and the
+    in the oracle against the covariant Z4 system) acts, and det gt != 1,
+    tr At != 0, so the kappa_c damping terms act too; con2prim and the
     right-hand side from the identical state against the oracle."""
     P, n, dx, ID = CASES[case]()
     pt, O, U = _setup(P, n, dx, ID)
@@ -109,6 +110,8 @@ def test_rhs_parity_with_theta_and_z(case):
     U[15] += 0.03 * np.cos(2 * np.pi * (i - j))
     U[16] += 0.02 * np.sin(2 * np.pi * (j + k))
     U[17] += 0.04 * np.cos(2 * np.pi * (k + 2 * i))
+    U[0:6] *= 1.01
+    U[6:12] += 0.005 * U[0:6]
     _upload(pt, U)
     pt.con2prim(0)
     rhs_g = pt.rhs_eval(0)[0]

@@ -306,6 +306,38 @@ def test_theta_and_z_terms_match_covariant_z4_system(kappa_2):
     assert errs[1].max() < 1e-6
 
 
+def test_kappa_c_damps_the_algebraic_constraints():
+    # The kappa_c terms (Sec. II A) exist to damp the algebraic constraints
+    # det gt = 1 and tr At = 0 at the rate alpha kappa_c: with gt_ij scaled by
+    # s (det gt = s^3 everywhere, so d_k ln det gt = 0) the trace of d_t gt_ij
+    # is d_t ln det gt = -alpha kappa_c ln det gt (the Lie-derivative and At
+    # terms have zero trace), and with At_ij shifted by a gt_ij the kappa_c
+    # part of d_t tr At is -alpha kappa_c tr At.  Differences converge at 4th
+    # order (Kreiss-Oliger and finite differences).
+    s_, a_ = 1.02, 0.01
+    center = (0.3, -0.2, 0.1)
+    errs = []
+    for dx in (0.05, 0.025):
+        P = synth.ideal_params(bc=1, kappa_c=0.05)
+        O, U, prim, _, Ac, _ = _patch(_generic, center, dx, params=P)
+        U[0:6] *= s_
+        U[6:12] += a_ * U[0:6]
+        rc = O.rhs_patch(U, prim, (8, 8, 8), dx)[:, 7, 7, 7]
+        P0 = dict(P, kappa_c=0.0)
+        r0 = oracle.Oracle(P0).rhs_patch(U, prim, (8, 8, 8), dx)[:, 7, 7, 7]
+        gt = _adm.sym_full(U[0:6, 7, 7, 7])
+        gtu = np.linalg.inv(gt)
+        al = U[18, 7, 7, 7]
+        lndet = np.log(np.linalg.det(gt))
+        trA = np.einsum("ij,ij->", gtu, _adm.sym_full(U[6:12, 7, 7, 7]))
+        tr_dg = np.einsum("ij,ij->", gtu, _adm.sym_full(rc[0:6]))
+        dA_kc = np.einsum("ij,ij->", gtu, _adm.sym_full(rc[6:12] - r0[6:12]))
+        errs.append([abs(tr_dg + al * P["kappa_c"] * lndet), abs(dA_kc + al * P["kappa_c"] * trA)])
+    errs = np.array(errs)
+    assert errs[1, 0] < 1e-7 and (errs[1, 0] < 1e-12 or errs[0, 0] / errs[1, 0] > 11.0), errs
+    assert errs[1, 1] < 1e-14, errs
+
+
 def test_conformally_flat_ricci_scalar():
     # gamma_ij = psi^4 delta_ij: R = -8 psi^-5 lap(psi).
     psi = 1 + 0.3 * sp.exp(-((x - 0.1) ** 2 + y ** 2 + (z + 0.2) ** 2))
