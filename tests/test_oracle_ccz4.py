@@ -14,7 +14,10 @@ With Gammahat^i moved off Gt^i (Z^i != 0), the Ricci split must give the Z4
 term R_ij + D_i Z_j + D_j Z_i of the physical metric, which pins the Z-term
 of R^chi_ij; with Theta != 0 as well, every spacetime right-hand side must be
 the covariant Z4 system with its kappa_z damping written in the CCZ4
-variables (kappa_2 = 0 and 0.3), which pins every Theta and Z term.
+variables (kappa_2 = 0 and 0.3), which pins every Theta and Z term; with a
+moving magnetised fluid, its stress-energy source (E, S_i, S_ij projected
+from the four-dimensional tensor) pins every matter coupling; the kappa_c
+terms are pinned by the damping of the algebraic constraints.
 Errors must fall at 4th order with the grid spacing.
 """
 import numpy as np
@@ -197,7 +200,7 @@ def test_ricci_with_z_matches_covariant_z4_identity():
     assert errs[1].max() < 1e-6
 
 
-def _z4_fields(center, dx, n, V, Th, params=None):
+def _z4_fields(center, dx, n, V, Th, params=None, matter=False):
     """The generic vacuum data with Theta != 0 (Khat = K - 2 Theta) and
     Gammahat^i = Gt^i + V^i (Z^i = chi V^i / 2): the oracle's right-hand side
     at the centre, and the reference quantities there."""
@@ -206,6 +209,17 @@ def _z4_fields(center, dx, n, V, Th, params=None):
     zz, yy, xx = synth.grid_coords((n, n, n), x0, dx)
     shp = synth.patch_shape((n, n, n))
     X3 = [np.broadcast_to(a, shp) for a in (xx, yy, zz)]
+    if matter:
+        # Re-initialise with the fluid in the initial data, then solve con2prim.
+        A = _generic(*X3)
+        ID = A.id_array()
+        fe = lambda e: _adm.Field(sp.sympify(e)).eval(*X3)[0]
+        ID[16], ID[17], ID[24] = fe(_MATTER["rho"]), fe(_MATTER["eps"]), fe(_MATTER["ye"])
+        for a in range(3):
+            ID[18 + a] = fe(_MATTER["v"][a])
+            ID[21 + a] = fe(_MATTER["B"][a])
+        U = O.init_state(np.ascontiguousarray(ID), (n, n, n), dx)
+        prim, _, _, _ = O.con2prim_patch(U, (n, n, n))
     th = Th.eval(*X3)[0]
     U[14] = th
     U[13] -= 2.0 * th
@@ -216,7 +230,7 @@ def _z4_fields(center, dx, n, V, Th, params=None):
     return rhs[:, c, c, c], Ac, P
 
 
-def _z4_expected(Ac, P, center, V, Th):
+def _z4_expected(Ac, P, center, V, Th, matter=None):
     """The covariant Z4 system (vacuum, damping kappa_z (n_a Z_b + n_b Z_a -
     g_ab n^c Z_c)) in 3+1 form, mapped to the CCZ4 variables: d_t of
     gt_ij, At_ij, chi, Khat = K - 2 Theta, Theta, alpha, beta^i."""
@@ -241,6 +255,10 @@ def _z4_expected(Ac, P, center, V, Th):
     dtK = Ac.dt_K[..., 0] + al * (DZ + DZ.T - 2.0 * th * K - k1 * (1.0 + k2) * th * g)
     dtTh = be @ dth + 0.5 * al * (R + 2.0 * divZ + (trK - 2.0 * th) * trK - KK - 2.0 * (Zu @ dal) / al
                                   - 2.0 * k1 * (2.0 + k2) * th)
+    Em, Sm, Smm = (0.0, np.zeros(3), np.zeros((3, 3))) if matter is None else matter
+    Str = np.einsum("ij,ij->", gu, Smm)
+    dtK = dtK - 8.0 * np.pi * al * (Smm - 0.5 * (Str - Em) * g)
+    dtTh = dtTh - 8.0 * np.pi * al * Em
     dtg = Ac.dt_g[..., 0]
     dt_trK = np.einsum("ij,ij->", gu, dtK) - np.einsum("ik,jl,kl,ij->", gu, gu, K, dtg)
     dt_chi = -(chi / 3.0) * np.einsum("ij,ij->", gu, dtg)
@@ -276,7 +294,7 @@ def _z4_expected(Ac, P, center, V, Th):
     dtrK = np.einsum("iab,ab->i", dgu, K) + np.einsum("ab,iab->i", gu, dK)
     KZ = K @ gu @ Zl
     dtZl = (np.einsum("j,ji->i", be, dZl) + np.einsum("j,ij->i", Zl, dbe)
-            + al * (divK - dtrK + dth - 2.0 * KZ - th * dal / al - k1 * Zl))
+            + al * (divK - dtrK + dth - 2.0 * KZ - th * dal / al - k1 * Zl) - 8.0 * np.pi * al * Sm)
     e[15:18] = dtGt + 2.0 * dtgtu @ Zl + 2.0 * gtu @ dtZl
     Khat = trK - 2.0 * th
     e[18] = be @ dal - 2.0 * al * Khat
@@ -299,6 +317,67 @@ def test_theta_and_z_terms_match_covariant_z4_system(kappa_2):
     for dx in (0.05, 0.025):  # Khat's error is pre-asymptotic at 0.1 (ratio 9.8 to 0.05)
         rc, Ac, P = _z4_fields(center, dx, 8, V, Th, params=synth.ideal_params(bc=1, kappa_2=kappa_2))
         e = _z4_expected(Ac, P, center, V, Th)
+        errs.append(np.abs(rc[fields] - e[fields]))
+    errs = np.array(errs)
+    ratio = errs[0] / np.maximum(errs[1], 1e-300)
+    assert np.all((ratio > 11.0) | (errs[1] < 1e-11)), (ratio, errs)
+    assert errs[1].max() < 1e-6
+
+
+# Matter fields (ideal gas, Gamma = 2 in the synthetic parameters): rho, eps,
+# v^i (Eulerian, contravariant), B^i (Eulerian, not densitized), Ye.
+_MATTER = dict(rho=1e-3 * (1 + 0.2 * sp.sin(x + y)), eps=0.05 * (1 + 0.1 * sp.cos(y - z)),
+               v=[0.1 * sp.sin(z), 0.08 * sp.cos(x), -0.06 * sp.sin(x + y)],
+               B=[0.004 * sp.cos(y), 0.003 * sp.sin(z - x), 0.005], ye=sp.Float(0.1))
+
+
+def _eulerian_projections(Ac, P, pt):
+    """E, S_i, S_ij of the ideal-MHD stress-energy tensor built in four
+    dimensions (u^mu, b^mu, T^{mu nu} = (rho h + b^2) u u + (p + b^2/2) g - b b)
+    and projected on the Eulerian observer: the textbook definitions, not the
+    3+1 formulas the oracle evaluates."""
+    ev = lambda e: float(_adm.Field(sp.sympify(e)).eval(*[np.array(v) for v in pt])[0])
+    rho, eps = ev(_MATTER["rho"]), ev(_MATTER["eps"])
+    v = np.array([ev(e) for e in _MATTER["v"]])
+    B = np.array([ev(e) for e in _MATTER["B"]])
+    g, al, be = Ac.g[..., 0], Ac.al[0], Ac.be[:, 0]
+    p = (P["gamma_th"] - 1.0) * rho * eps
+    g4 = np.zeros((4, 4))
+    bl = g @ be
+    g4[0, 0] = -al * al + be @ bl
+    g4[0, 1:] = g4[1:, 0] = bl
+    g4[1:, 1:] = g
+    W = 1.0 / np.sqrt(1.0 - v @ g @ v)
+    u = np.concatenate([[W / al], W * (v - be / al)])
+    b0 = W * (B @ g @ v) / al
+    b = np.concatenate([[b0], (B + al * b0 * u[1:]) / W])
+    b2 = b @ g4 @ b
+    T = (rho * (1 + eps) + p + b2) * np.outer(u, u) + (p + 0.5 * b2) * np.linalg.inv(g4) - np.outer(b, b)
+    n_lo = np.array([-al, 0.0, 0.0, 0.0])
+    n_up = np.concatenate([[1.0 / al], -be / al])
+    Tlo = g4 @ T @ g4
+    E = n_lo @ T @ n_lo
+    S_i = -(Tlo @ n_up)[1:]
+    S_ij = Tlo[1:, 1:]
+    return E, S_i, S_ij
+
+
+def test_matter_terms_match_covariant_z4_system_with_sources():
+    # A moving, magnetised ideal-gas fluid on the generic metric, with Theta
+    # and Z nonzero: the spacetime right-hand sides must be the covariant Z4
+    # system with the stress-energy source 8 pi (T_mu nu - T g_mu nu / 2),
+    # i.e. -8 pi alpha [S_ij - (S - E) gamma_ij / 2] in d_t K_ij, -8 pi alpha E
+    # in d_t Theta and -8 pi alpha S_i in d_t Z_i, with E, S_i, S_ij projected
+    # from the four-dimensional stress-energy tensor.  This pins every matter
+    # coupling of the CCZ4 equations (At_ij, Khat, Theta, Gammahat).
+    V = [_adm.Field(e) for e in (0.05 * sp.sin(x + 2 * y), 0.04 * sp.cos(y - z), 0.06 * sp.sin(z + 0.5 * x))]
+    Th = _adm.Field(0.01 + 0.02 * sp.sin(x - y + 0.5 * z))
+    center = (0.3, -0.2, 0.1)
+    fields = list(range(0, 22))
+    errs = []
+    for dx in (0.05, 0.025):
+        rc, Ac, P = _z4_fields(center, dx, 8, V, Th, matter=True)
+        e = _z4_expected(Ac, P, center, V, Th, matter=_eulerian_projections(Ac, P, center))
         errs.append(np.abs(rc[fields] - e[fields]))
     errs = np.array(errs)
     ratio = errs[0] / np.maximum(errs[1], 1e-300)
