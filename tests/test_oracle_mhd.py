@@ -87,6 +87,62 @@ def test_flux_matches_covariant_stress_energy_flat_space():
             assert abs(F[9] - P["c_b"] ** 2 * B[d]) < 1e-18
 
 
+def test_flux_matches_covariant_stress_energy_curved():
+    # Lapse, shift and a non-diagonal 3-metric: the conservative fluxes along
+    # d are sqrt(-g) times the d-components of the four-dimensional currents,
+    # with sqrt(-g) = alpha sqrt(gamma): rho u^d for D, T^d_i for S_i,
+    # alpha T^{0 d} - rho u^d for tau, and -*F^{d i} = b^i u^d - b^d u^i
+    # (the dual Faraday tensor) for B^i, all built here from u^mu and b^mu.
+    rng = np.random.default_rng(7)
+    P = synth.ideal_params()
+    O = oracle.Oracle(P)
+    six = lambda M: np.array([M[0, 0], M[0, 1], M[0, 2], M[1, 1], M[1, 2], M[2, 2]])
+    for _ in range(20):
+        A = rng.uniform(-0.15, 0.15, (3, 3))
+        g = np.eye(3) + 0.5 * (A + A.T)
+        al = rng.uniform(0.6, 1.2)
+        be = rng.uniform(-0.2, 0.2, 3)
+        rho, eps, ye = 10 ** rng.uniform(-4, -2), rng.uniform(0.05, 1.0), 0.1
+        v = rng.uniform(-0.3, 0.3, 3)
+        B = rng.uniform(-0.05, 0.05, 3)
+        sg = np.sqrt(np.linalg.det(g))
+        chi = np.linalg.det(g) ** (-1.0 / 3.0)
+        p = (P["gamma_th"] - 1.0) * rho * eps
+        W = 1.0 / np.sqrt(1.0 - v @ g @ v)
+        pr = np.zeros(NP)
+        pr[0], pr[1], pr[2], pr[3:6], pr[6], pr[7] = rho, eps, p, v, W, ye
+        pr[9] = P["gamma_th"] * p / (rho * (1 + eps) + p)
+        U = np.zeros(NF)
+        U[0:6] = six(chi * g)
+        U[12] = chi
+        U[18] = al
+        U[19:22] = be
+        U[22:31] = np.asarray(oracle.prim2con_point(pr, B, six(g))) * sg
+        # Four-dimensional quantities.
+        g4 = np.zeros((4, 4))
+        bl = g @ be
+        g4[0, 0] = -al * al + be @ bl
+        g4[0, 1:] = g4[1:, 0] = bl
+        g4[1:, 1:] = g
+        u = np.concatenate([[W / al], W * (v - be / al)])
+        b0 = W * (B @ g @ v) / al
+        b = np.concatenate([[b0], (B + al * b0 * u[1:]) / W])
+        b2 = b @ g4 @ b
+        T = (rho * (1 + eps) + p + b2) * np.outer(u, u) + (p + 0.5 * b2) * np.linalg.inv(g4) - np.outer(b, b)
+        Tmix = T @ g4  # T^mu_nu
+        sqg = al * sg
+        for d in range(3):
+            F, lam = O.flux_point(U, pr, d)
+            k = d + 1
+            scale = sqg * abs(T[0, 0])
+            assert abs(F[0] - sqg * rho * u[k]) < 1e-13 * sqg * rho * W
+            assert abs(F[1] - sqg * rho * ye * u[k]) < 1e-13 * sqg * rho * W
+            assert abs(F[2] - sqg * (al * T[0, k] - rho * u[k])) < 1e-12 * scale
+            assert np.allclose(F[3:6], sqg * Tmix[k, 1:], rtol=1e-11, atol=1e-13 * scale)
+            induction = sqg * (b[1:] * u[k] - b[k] * u[1:])
+            assert np.allclose(F[6:9], induction, rtol=1e-11, atol=1e-14 * np.abs(B).max())
+
+
 def _uniform_patch(O, n, v, B, rho=1e-3, eps=0.1, dx=0.1):
     shp = synth.patch_shape(n)
     ID = np.zeros((26,) + shp)
