@@ -385,6 +385,81 @@ def test_matter_terms_match_covariant_z4_system_with_sources():
     assert errs[1].max() < 1e-6
 
 
+def _spacetime_fluid_at(pt):
+    """g_mu nu, sqrt(gamma), alpha, beta, rho, Ye, u^mu and T^{mu nu} of the
+    generic metric and the _MATTER fluid at a point (exact field values)."""
+    Ac = _adm_at(_generic, pt)
+    P = synth.ideal_params()
+    ev = lambda e: float(_adm.Field(sp.sympify(e)).eval(*[np.array(v) for v in pt])[0])
+    rho, eps, ye = ev(_MATTER["rho"]), ev(_MATTER["eps"]), ev(_MATTER["ye"])
+    v = np.array([ev(e) for e in _MATTER["v"]])
+    B = np.array([ev(e) for e in _MATTER["B"]])
+    g, al, be = Ac.g[..., 0], Ac.al[0], Ac.be[:, 0]
+    p = (P["gamma_th"] - 1.0) * rho * eps
+    g4 = np.zeros((4, 4))
+    g4[0, 0] = -al * al + be @ g @ be
+    g4[0, 1:] = g4[1:, 0] = g @ be
+    g4[1:, 1:] = g
+    W = 1.0 / np.sqrt(1.0 - v @ g @ v)
+    u = np.concatenate([[W / al], W * (v - be / al)])
+    b0 = W * (B @ g @ v) / al
+    b = np.concatenate([[b0], (B + al * b0 * u[1:]) / W])
+    b2 = b @ g4 @ b
+    T = (rho * (1 + eps) + p + b2) * np.outer(u, u) + (p + 0.5 * b2) * np.linalg.inv(g4) - np.outer(b, b)
+    return dict(g4=g4, sg=np.sqrt(np.linalg.det(g)), al=al, be=be, rho=rho, ye=ye, u=u, T=T, K=Ac.K[..., 0])
+
+
+def _d(fun, pt, k, h=2e-3):
+    """d/dx^k of fun at pt: 8th-order central differences of the exact fields."""
+    c = [4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0]
+    acc = 0.0
+    for m, cm in enumerate(c, start=1):
+        e = np.zeros(3)
+        e[k] = m * h
+        acc = acc + cm * (np.asarray(fun(tuple(np.add(pt, e)))) - np.asarray(fun(tuple(np.subtract(pt, e)))))
+    return acc / h
+
+
+def test_mhd_sources_match_covariant_conservation_laws():
+    # A moving, magnetised fluid on the generic metric (lapse, shift, a
+    # non-diagonal 3-metric, K_ij): the right-hand sides of Dbar, taubar and
+    # Sbar_i must be the covariant conservation laws nabla_mu (rho u^mu) = 0
+    # and nabla_mu T^mu_nu = 0 in conservative form: -d_k F^k plus, for
+    # Sbar_i, (1/2) sqrt(-g) T^{mu nu} d_i g_mu nu, and for taubar
+    # alpha sqrt(gamma) [T^00 (beta^i beta^j K_ij - beta^i d_i alpha)
+    # + T^0i (2 beta^j K_ij - d_i alpha) + T^ij K_ij], with the fluxes of the
+    # four-dimensional currents and their derivatives taken from the exact
+    # fields.  The oracle's conservative finite differences must converge to
+    # them (Sec. II B and III C).
+    center = (0.3, -0.2, 0.1)
+    zero = [_adm.Field(sp.Integer(0))] * 3
+    F = lambda q: _spacetime_fluid_at(q)
+    def fluxes(q):
+        f = F(q)
+        sqg = f["al"] * f["sg"]
+        Tm = f["T"] @ f["g4"]  # T^mu_nu
+        return np.array([[sqg * f["rho"] * f["u"][k + 1]] + [sqg * (f["al"] * f["T"][0, k + 1] - f["rho"] * f["u"][k + 1])]
+                         + list(sqg * Tm[k + 1, 1:]) for k in range(3)])  # [k][D, tau, S_1..3]
+    divF = sum(_d(lambda q: fluxes(q)[k], center, k) for k in range(3))
+    f0 = F(center)
+    sqg = f0["al"] * f0["sg"]
+    dg4 = [_d(lambda q: F(q)["g4"], center, i) for i in range(3)]
+    dal = np.array([_d(lambda q: F(q)["al"], center, i) for i in range(3)])
+    src_S = np.array([0.5 * sqg * np.sum(f0["T"] * dg4[i]) for i in range(3)])
+    T, K, be = f0["T"], f0["K"], f0["be"]
+    src_tau = sqg * (T[0, 0] * (be @ K @ be - be @ dal) + T[0, 1:] @ (2.0 * K @ be - dal) + np.sum(T[1:, 1:] * K))
+    want = np.concatenate([[-divF[0]], [-divF[1] + src_tau], -divF[2:] + src_S])
+    errs = []
+    for dx in (0.05, 0.025):
+        rc, Ac, P = _z4_fields(center, dx, 8, zero, _adm.Field(sp.Integer(0)), matter=True)
+        got = np.concatenate([[rc[22]], [rc[24]], rc[25:28]])
+        errs.append(np.abs(got - want))
+    errs = np.array(errs)
+    ratio = errs[0] / np.maximum(errs[1], 1e-300)
+    assert np.all(ratio > 11.0), (ratio, errs, want)
+    assert errs[1].max() < 1e-3 * np.abs(want).max(), (errs, want)
+
+
 def test_kappa_c_damps_the_algebraic_constraints():
     # The kappa_c terms (Sec. II A) exist to damp the algebraic constraints
     # det gt = 1 and tr At = 0 at the rate alpha kappa_c: with gt_ij scaled by
