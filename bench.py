@@ -58,6 +58,13 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 # 3538 FP64 instructions (all of them adds, multiplies or FMAs).
 RHS_EXECUTED_FLOPS_PER_POINT = 5264.0
 RHS_FP64_INST_PER_POINT = 3538.0
+# The other substep kernels' FP64 instructions from the same capture: k_iflux
+# 386 per interior point = 380 per interface (65 x 64^2 interfaces per
+# launch), k_c2p 529 per interior point = 404 per ghosted point (70^3 points
+# per launch), scaled to other sizes by interfaces and ghosted points (the
+# same star on the same domain).
+IFLUX_FP64_INST_PER_IFACE = 386.0 * 64 ** 3 / (65 * 64 ** 2)
+C2P_FP64_INST_PER_POINT = 529.0 * 64 ** 3 / 70 ** 3
 
 
 def _args():
@@ -448,6 +455,17 @@ def run_grmhd(args):
                 "fp64_probe_inst_per_s": {"fma": fp64_peak * 1e12 / 2, "add": fp64_add},
                 "frac_fp64_issue": RHS_FP64_INST_PER_POINT * zones / (avg_rhs_ms / 1e3) /
                                    max(fp64_peak * 1e12 / 2, fp64_add)}
+    # The other substep kernels against the same FP64 instruction rate.
+    probe_rate = max(fp64_peak * 1e12 / 2, fp64_add)
+    other = {}
+    for kind, name, per, units in (("iflux", "k_iflux", IFLUX_FP64_INST_PER_IFACE, (edge + 1) * edge * edge),
+                                   ("c2p", "k_c2p", C2P_FP64_INST_PER_POINT, (edge + 6) ** 3)):
+        kms, kn = prof.get(kind, (0.0, 0))
+        if kn:
+            rate = per * units / (kms / kn / 1e3)
+            other[name] = {"ms_per_launch": kms / kn, "launches": kn, "fp64_inst_per_unit": per,
+                           "units_per_launch": units, "fp64_inst_per_s": rate, "frac_fp64_issue": rate / probe_rate}
+    roofline["other_kernels"] = other
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
